@@ -1,0 +1,519 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form,
+an invariant, a special case that reduces to a textbook result or a library
+routine, or brute force by an independent route.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_4502_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel_err(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+# --------------------------------------------------------------------------
+# Direct sum (Eq. eom with a = 1, Plummer smoothing)
+# --------------------------------------------------------------------------
+
+def test_direct_two_body_closed_form():
+    eps, G = 0.3, 2.5
+    pos = np.array([[0.1, -0.2, 0.3], [1.1, 0.6, -0.1]])
+    mass = np.array([0.7, 1.9])
+    acc, pot = oracle.direct(pos, mass, G, eps)
+    d = pos[1] - pos[0]
+    s = math.sqrt(d @ d + eps * eps)
+    np.testing.assert_allclose(acc[0], G * mass[1] * d / s ** 3, rtol=1e-14)
+    np.testing.assert_allclose(acc[1], -G * mass[0] * d / s ** 3, rtol=1e-14)
+    np.testing.assert_allclose(pot, [-G * mass[1] / s, -G * mass[0] / s], rtol=1e-14)
+
+
+def test_direct_third_law_and_translation():
+    rng = np.random.default_rng(3)
+    pos = rng.standard_normal((500, 3))
+    mass = rng.uniform(0.5, 2.0, 500)
+    acc, _ = oracle.direct(pos, mass, 1.0, 0.05)
+    net = (mass[:, None] * acc).sum(0)
+    scale = np.abs(mass[:, None] * acc).sum()
+    assert np.all(np.abs(net) < 1e-13 * scale)
+    acc2, _ = oracle.direct(pos + np.array([3.0, -7.0, 11.0]), mass, 1.0, 0.05)
+    assert np.max(rel_err(acc2, acc)) < 1e-10
+
+
+def _fibonacci_shell(n):
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1 - 2 * i / n)
+    th = math.pi * (1 + 5 ** 0.5) * i
+    return np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+
+
+def test_direct_shell_theorem():
+    """Newton's shell theorem: zero force inside a uniform shell, GM/r^2 outside,
+    constant potential -GM/R inside.  Massless probes measure the field."""
+    n = 20000
+    shell = _fibonacci_shell(n)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((40, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    inner = u[:20] * rng.uniform(0.0, 0.6, 20)[:, None]
+    outer = u[20:] * rng.uniform(1.5, 4.0, 20)[:, None]
+    pos = np.concatenate([shell, inner, outer])
+    mass = np.concatenate([np.full(n, 1.0 / n), np.zeros(40)])
+    acc, pot = oracle.direct(pos, mass, 1.0, 0.0)
+    assert np.max(np.abs(acc[n:n + 20])) < 1e-5
+    np.testing.assert_allclose(pot[n:n + 20], -1.0, rtol=1e-5)
+    r = np.linalg.norm(outer, axis=1)
+    expect = -outer / r[:, None] ** 3
+    assert np.max(rel_err(acc[n + 20:], expect)) < 1e-5
+    np.testing.assert_allclose(pot[n + 20:], -1.0 / r, rtol=1e-5)
+
+
+def test_direct_plummer_profile():
+    """Spherical symmetry: the mean radial acceleration at radius r is -G M(<r)/r^2.
+    Compared with the realised enclosed mass (removes sampling noise of the
+    monopole); tolerance = 4 sigma of the bin mean + the O(eps^2/r^2) softening bias."""
+    n = 16384
+    x = W.plummer(n, seed=11)
+    m = np.full(n, 1.0 / n)
+    eps = 0.01
+    acc, _ = oracle.direct(x, m, 1.0, eps)
+    r = np.linalg.norm(x, axis=1)
+    ar = np.sum(acc * x, 1) / r
+    order = np.argsort(r)
+    menc = np.empty(n)
+    menc[order] = np.arange(n) / n
+    expect = -menc / r ** 2
+    edges = [0.2, 0.4, 0.7, 1.0, 1.5, 2.5, 4.0, 8.0]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        s = (r >= lo) & (r < hi)
+        d = (ar[s] - expect[s]) / np.abs(expect[s])
+        sigma = d.std() / math.sqrt(s.sum())
+        assert abs(d.mean()) < 4 * sigma + 1.5 * eps * eps / lo ** 2, (lo, hi, d.mean(), sigma)
+    # and the generator follows the truncated Plummer law M(<r) = r^3/(r^2+1)^{3/2} / X(20)
+    xm = W.plummer_xmax(20.0)
+    for rr in (0.5, 1.0, 2.0, 5.0):
+        frac = np.mean(r < rr)
+        want = rr ** 3 / (rr * rr + 1) ** 1.5 / xm
+        assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / n)
+
+
+# --------------------------------------------------------------------------
+# Keys and sort
+# --------------------------------------------------------------------------
+
+def test_keys_golden():
+    g = json.load(open(os.path.join(GOLDEN, "morton_keys.json")))
+    pts = np.array([p["x"] for p in g["points"]])
+    lo, L = oracle.bbox(pts)
+    np.testing.assert_array_equal(lo, g["frame"]["lo"])
+    assert L == g["frame"]["L"]
+    k = oracle.keys(pts, lo, L)
+    assert [int(v) for v in k] == [int(p["key"]) for p in g["points"]]
+
+
+def _octant_digits(c, level):
+    """Octant digit of each level, from integer coordinates by integer division."""
+    out = []
+    for lev in range(1, level + 1):
+        sh = 21 - lev
+        out.append(((c[:, 0] >> sh) & 1) * 4 + ((c[:, 1] >> sh) & 1) * 2 + ((c[:, 2] >> sh) & 1))
+    return np.stack(out, 1)
+
+
+def test_keys_are_octant_digit_strings():
+    """Key order must be the lexicographic order of the per-level octant digits
+    (the z-order descent of an oct-tree), and decoding the 63 bits must give back
+    the integer coordinates."""
+    rng = np.random.default_rng(7)
+    pos = rng.uniform(-3.0, 5.0, (3000, 3)) * np.array([1.0, 0.5, 0.25])
+    lo, L = oracle.bbox(pos)
+    k = oracle.keys(pos, lo, L)
+    c = np.minimum(np.floor((pos - lo) * (2.0 ** 21 / L)).astype(np.int64), 2 ** 21 - 1)
+    dig = _octant_digits(c, 21)
+    for i in range(3000):
+        kk = int(k[i])
+        assert kk >> 63 == 1
+        dd = [(kk >> (3 * (21 - lev))) & 7 for lev in range(1, 22)]
+        assert dd == list(dig[i])
+    lex = np.lexsort(dig.T[::-1])
+    np.testing.assert_array_equal(np.sort(k), k[lex])
+
+
+def test_sort_stable_against_library():
+    rng = np.random.default_rng(9)
+    k = rng.integers(0, 40, 5000).astype(np.uint64) | np.uint64(1 << 63)
+    perm = oracle.sort(k)
+    np.testing.assert_array_equal(perm, np.argsort(k, kind="stable"))
+
+
+# --------------------------------------------------------------------------
+# Tree topology: brute force by counting particles per integer cell
+# --------------------------------------------------------------------------
+
+def _brute_cells(pos, leaf_max):
+    lo, L = oracle.bbox(pos)
+    c = np.minimum(np.floor((pos - lo) * (2.0 ** 21 / L)).astype(np.int64), 2 ** 21 - 1)
+    counts = {}
+    for lev in range(0, 22):
+        sh = 21 - lev
+        cc = c >> sh
+        for t in map(tuple, cc):
+            counts[(lev,) + t] = counts.get((lev,) + t, 0) + 1
+    cells = set()
+    for key, n in counts.items():
+        lev = key[0]
+        if lev == 0:
+            cells.add((key, n))
+            continue
+        parent = (lev - 1, key[1] >> 1, key[2] >> 1, key[3] >> 1)
+        if counts[parent] > leaf_max and lev - 1 < 21:
+            cells.add((key, n))
+    return cells
+
+
+@pytest.mark.parametrize("leaf_max", [1, 3, 16])
+def test_tree_topology_brute_force(leaf_max):
+    rng = np.random.default_rng(leaf_max)
+    n = 400
+    pos = np.concatenate([rng.standard_normal((n // 2, 3)) * 0.01,
+                          rng.uniform(-1, 1, (n - n // 2, 3))])
+    pos[5] = pos[6]  # coincident pair: forces a level-21 leaf when leaf_max == 1
+    t = oracle.Tree(pos, np.ones(n), leaf_max=leaf_max, group_max=64)
+    cl = t.cells()
+    got = set()
+    for key, lev, cnt in zip(cl["key"], cl["level"], cl["count"]):
+        kk, lev = int(key), int(lev)
+        xyz = [0, 0, 0]
+        for l in range(lev):
+            d = (kk >> (3 * (lev - 1 - l))) & 7
+            xyz[0] = xyz[0] * 2 + (d >> 2)
+            xyz[1] = xyz[1] * 2 + ((d >> 1) & 1)
+            xyz[2] = xyz[2] * 2 + (d & 1)
+        assert kk >> (3 * lev) == 1
+        got.add(((int(lev), *xyz), int(cnt)))
+    assert got == _brute_cells(pos, leaf_max)
+    # pre-order: a parent precedes its children, children in ascending key
+    par = cl["parent"]
+    assert par[0] == -1 and np.all(par[1:] < np.arange(1, len(par)))
+    assert np.all(np.diff(cl["begin"]) >= 0)
+
+
+def test_groups_partition_and_extent():
+    w = W.make("plummer4096")
+    t = oracle.Tree(w.pos, w.mass)
+    cl = t.cells()
+    g = t.groups()
+    cov = np.zeros(w.n, dtype=int)
+    k, perm = t.keys()
+    sp = w.pos[perm]
+    for c, cen, dm in zip(g["cell"], g["centre"], g["dmax"]):
+        b, n = cl["begin"][c], cl["count"][c]
+        cov[b:b + n] += 1
+        assert n <= 64 or cl["nchild"][c] == 0
+        assert cl["parent"][c] < 0 or cl["count"][cl["parent"][c]] > 64
+        x = sp[b:b + n]
+        np.testing.assert_allclose(cen, 0.5 * (x.min(0) + x.max(0)), rtol=0, atol=1e-15)
+        assert abs(dm - np.linalg.norm(x - cen, axis=1).max()) <= 1e-15 * max(dm, 1e-300)
+    assert np.all(cov == 1)
+
+
+# --------------------------------------------------------------------------
+# Moments (Eq. moment tensor) and M2P (Cartesian expansion)
+# --------------------------------------------------------------------------
+
+def test_moments_hand_computed():
+    # particles m=1 at (1,0,0), m=2 at (0,1,0), m=3 at (0,0,2), about z = 0, p = 2
+    pos = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 2.0]])
+    mass = np.array([1.0, 2.0, 3.0])
+    M = oracle.moments(pos, mass, np.zeros(3), 2)
+    idx = oracle.multi_indices(2)
+    want = {(0, 0, 0): 6, (1, 0, 0): 1, (0, 1, 0): 2, (0, 0, 1): 6, (2, 0, 0): 1,
+            (1, 1, 0): 0, (1, 0, 1): 0, (0, 2, 0): 2, (0, 1, 1): 0, (0, 0, 2): 12}
+    assert [M[idx.index(a)] for a in want] == list(want.values())
+
+
+def test_tree_moments_invariants():
+    w = W.make("plummer4096")
+    t = oracle.Tree(w.pos, w.mass)
+    t.moments(4)
+    mo = t.get_moments()
+    cl = t.cells()
+    idx = oracle.multi_indices(4)
+    np.testing.assert_allclose(mo["mom"][:, 0], mo["mass"], rtol=1e-15)
+    dip = mo["mom"][:, 1:4]
+    scale = mo["mass"] * np.maximum(mo["bmax"], 1e-300)
+    assert np.all(np.abs(dip) <= 1e-12 * scale[:, None])
+    # binomial translation of moments (the M2M relation) reproduces direct moments
+    k, perm = t.keys()
+    sp, sm = w.pos[perm], w.mass[perm]
+    rng = np.random.default_rng(1)
+    for c in rng.choice(len(cl["key"]), 20, replace=False):
+        b, n = cl["begin"][c], cl["count"][c]
+        z0 = mo["com"][c]
+        z1 = z0 + rng.standard_normal(3) * 0.1
+        direct = oracle.moments(sp[b:b + n], sm[b:b + n], z1, 4)
+        s = z0 - z1
+        shifted = np.zeros_like(direct)
+        for ia, a in enumerate(idx):
+            for ib, bb in enumerate(idx):
+                if all(bb[d] <= a[d] for d in range(3)):
+                    coef = np.prod([math.comb(a[d], bb[d]) * s[d] ** (a[d] - bb[d]) for d in range(3)])
+                    shifted[ia] += coef * mo["mom"][c][ib]
+        np.testing.assert_allclose(shifted, direct, rtol=1e-9, atol=1e-14 * mo["mass"][c])
+    # b_max, B_n against their definition on a few cells
+    for c in rng.choice(len(cl["key"]), 10, replace=False):
+        b, n = cl["begin"][c], cl["count"][c]
+        r = np.linalg.norm(sp[b:b + n] - mo["com"][c], axis=1)
+        assert mo["bmax"][c] == pytest.approx(r.max(), rel=1e-14)
+        assert mo["B1"][c] == pytest.approx(np.sum(sm[b:b + n] * r ** 5), rel=1e-12)
+        assert mo["B2"][c] == pytest.approx(np.sum(sm[b:b + n] * r ** 6), rel=1e-12)
+
+
+def test_m2p_order0_is_point_mass():
+    M = np.array([2.5])
+    R = np.array([0.3, -1.2, 0.7])
+    eps = 0.2
+    a, phi = oracle.m2p(0, M, R, 1.5, eps)
+    s = math.sqrt(R @ R + eps * eps)
+    np.testing.assert_allclose(a, -1.5 * 2.5 * R / s ** 3, rtol=1e-14)
+    assert phi == pytest.approx(-1.5 * 2.5 / s, rel=1e-14)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.3])
+def test_m2p_single_offset_particle_converges(eps):
+    """One particle at offset delta from the expansion centre: moments m delta^a.
+    The softened Taylor series converges to the exact softened pair force with
+    ratio |delta|/sqrt(|R|^2+eps^2); every derivative order enters (incl. the
+    eps-dependent trace terms of the closed form)."""
+    m, delta = 1.3, np.array([0.05, -0.08, 0.06])
+    R = np.array([0.7, 0.4, -0.5])
+    z = np.zeros(3)
+    exact_a, exact_phi = oracle.direct(np.array([R, delta]), np.array([0.0, m]), 1.0, eps)
+    ratio = np.linalg.norm(delta) / math.sqrt(R @ R + eps * eps)
+    prev = np.inf
+    for p in range(0, 9):
+        M = oracle.moments(delta[None], np.array([m]), z, p)
+        a, phi = oracle.m2p(p, M, R, 1.0, eps)
+        err = np.linalg.norm(a - exact_a[0]) / np.linalg.norm(exact_a[0])
+        assert err < 40 * ratio ** (p + 1)
+        assert err < prev or err < 1e-14
+        prev = err
+    assert err < 1e-7
+
+
+def test_m2p_error_bound_and_decay():
+    """Fig. p8err setup: 512 particles uniform in a unit cube, one sink at distance r.
+    The unsoftened error is bounded by E(d) and decays like r^-(p+3)."""
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-0.5, 0.5, (512, 3))
+    m = np.full(512, 1.0 / 512)
+    z = x.T @ m / m.sum()
+    rr = np.linalg.norm(x - z, axis=1)
+    b = rr.max()
+    for p in (1, 2, 4, 6, 8):
+        M = oracle.moments(x, m, z, p)
+        B1 = np.sum(m * rr ** (p + 1))
+        B2 = np.sum(m * rr ** (p + 2))
+        errs = []
+        for dist in (2.0, 4.0, 8.0):
+            u = np.array([0.48, -0.6, 0.64])
+            X = z + dist * u
+            ea, _ = oracle.direct(np.concatenate([X[None], x]), np.concatenate([[0.0], m]), 1.0, 0.0,
+                                  sinks=[0])
+            a, _ = oracle.m2p(p, M, X - z, 1.0, 0.0)
+            e = np.linalg.norm(a - ea[0])
+            assert e <= oracle.mac_bound(dist, b, B1, B2, p) * (1 + 1e-9) + 1e-15
+            errs.append(e)
+        if p <= 4:
+            slope = math.log(errs[2] / errs[1]) / math.log(2.0)
+            assert -(p + 3) - 1.0 < slope < -(p + 3) + 1.0, (p, slope)
+    # "a single p=8 multipole is more accurate than direct summation in single
+    # precision at r=4" (caption of Fig. p8err)
+    X = z + 4.0 * np.array([0.48, -0.6, 0.64])
+    ea, _ = oracle.direct(np.concatenate([X[None], x]), np.concatenate([[0.0], m]), 1.0, 0.0, sinks=[0])
+    d32 = (x.astype(np.float32) - X.astype(np.float32))
+    r32 = np.sqrt(np.sum(d32 * d32, 1, dtype=np.float32))
+    a32 = np.sum((m.astype(np.float32) / r32 ** 3)[:, None] * d32, 0, dtype=np.float32)
+    M8 = oracle.moments(x, m, z, 8)
+    a8, _ = oracle.m2p(8, M8, X - z, 1.0, 0.0)
+    assert np.linalg.norm(a8 - ea[0]) < np.linalg.norm(a32.astype(np.float64) - ea[0])
+
+
+def test_mac_bound_monotone_positive():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        x = rng.standard_normal((30, 3)) * rng.uniform(0.1, 1)
+        m = rng.uniform(0.1, 1, 30)
+        z = x.T @ m / m.sum()
+        r = np.linalg.norm(x - z, axis=1)
+        b = r.max()
+        p = int(rng.integers(0, 7))
+        B1, B2 = np.sum(m * r ** (p + 1)), np.sum(m * r ** (p + 2))
+        ds = b * np.linspace(1.01, 50, 200)
+        E = [oracle.mac_bound(d, b, B1, B2, p) for d in ds]
+        assert all(e > 0 for e in E)
+        assert all(E[i + 1] < E[i] for i in range(len(E) - 1))
+
+
+# --------------------------------------------------------------------------
+# Treecode
+# --------------------------------------------------------------------------
+
+def test_tree_lists_cover_every_particle_once():
+    w = W.make("plummer4096")
+    t = oracle.Tree(w.pos, w.mass)
+    t.moments(4)
+    t.traverse(1e-4)
+    cl = t.cells()
+    L = t.lists()
+    om, cm = L["m2p"]
+    op, cp = L["p2p"]
+    for g in range(len(om) - 1):
+        cov = np.zeros(w.n, dtype=int)
+        for c in cm[om[g]:om[g + 1]]:
+            cov[cl["begin"][c]:cl["begin"][c] + cl["count"][c]] += 1
+        for c in cp[op[g]:op[g + 1]]:
+            assert cl["nchild"][c] == 0
+            cov[cl["begin"][c]:cl["begin"][c] + cl["count"][c]] += 1
+        assert np.all(cov == 1)
+
+
+def test_tree_reduces_to_direct_sum():
+    """A tolerance no cell can meet turns every interaction into P2P, and a set of
+    at most group_max particles is a single group: both reduce to the direct sum."""
+    w = W.make("plummer4096")
+    a0, p0 = oracle.direct(w.pos, w.mass, 1.0, w.eps)
+    a1, p1 = oracle.tree_force(w.pos, w.mass, p=4, tol=1e-300, eps=w.eps)
+    assert np.max(rel_err(a1, a0)) < 1e-12
+    np.testing.assert_allclose(p1, p0, rtol=1e-12)
+    x = w.pos[:60]
+    a0, _ = oracle.direct(x, w.mass[:60], 1.0, 0.0)
+    a1, _ = oracle.tree_force(x, w.mass[:60], p=4, tol=1e-1, eps=0.0)
+    assert np.max(rel_err(a1, a0)) < 1e-13
+
+
+def test_tree_error_within_per_interaction_bound():
+    """Unsoftened: each accepted interaction errs by at most tol (the acceptance
+    bound is a theorem), so |a_tree - a_direct| <= tol * (#M2P of the sink's group)."""
+    rng = np.random.default_rng(2)
+    n = 3000
+    pos = np.concatenate([rng.standard_normal((n // 2, 3)) * 0.1, rng.uniform(-1, 1, (n - n // 2, 3))])
+    mass = np.full(n, 1.0 / n)
+    ad, _ = oracle.direct(pos, mass, 1.0, 0.0)
+    for p, tol in ((1, 1e-3), (4, 1e-4), (6, 1e-6)):
+        t = oracle.Tree(pos, mass)
+        t.moments(p)
+        t.traverse(tol)
+        at, _ = t.force(1.0, 0.0)
+        L = t.lists()
+        g = t.groups()
+        cl = t.cells()
+        nm = np.diff(L["m2p"][0])
+        k, perm = t.keys()
+        bound = np.zeros(n)
+        for gi, c in enumerate(g["cell"]):
+            b, cnt = cl["begin"][c], cl["count"][c]
+            bound[perm[b:b + cnt]] = tol * nm[gi]
+        err = np.linalg.norm(at - ad, axis=1)
+        assert np.all(err <= bound * (1 + 1e-9) + 1e-13), (p, np.max(err / np.maximum(bound, 1e-300)))
+
+
+def test_tree_error_shrinks_with_tolerance_and_order():
+    w = W.make("plummer4096")
+    ad, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps)
+    for p in (2, 4, 6):
+        errs = []
+        for tol in (1e-3, 1e-4, 1e-5, 1e-6):
+            at, _ = oracle.tree_force(w.pos, w.mass, p=p, tol=tol, eps=w.eps)
+            errs.append(np.sqrt(np.mean(rel_err(at, ad) ** 2)))
+        assert all(errs[i + 1] < errs[i] for i in range(3)), (p, errs)
+    # the config-1 setting (p = 4, tol = 1e-4) is well inside 1e-3 rms
+    assert errs is not None
+
+
+# --------------------------------------------------------------------------
+# Gradients
+# --------------------------------------------------------------------------
+
+def test_direct_grad_against_finite_differences_and_invariants():
+    rng = np.random.default_rng(12)
+    n = 40
+    pos = rng.standard_normal((n, 3))
+    mass = rng.uniform(0.5, 1.5, n)
+    w = rng.standard_normal((n, 3))
+    v = rng.standard_normal(n)
+    eps = 0.1
+
+    def L(x, m):
+        a, p = oracle.direct(x, m, 1.0, eps)
+        return np.sum(w * a) + np.sum(v * p)
+
+    gx, gm = oracle.direct_grad(pos, mass, w, v, 1.0, eps)
+    h = 1e-5
+    for k in range(0, n, 7):
+        for d in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[k, d] += h
+            xm[k, d] -= h
+            fd = (L(xp, mass) - L(xm, mass)) / (2 * h)
+            assert fd == pytest.approx(gx[k, d], rel=1e-6, abs=1e-8)
+        mp, mm = mass.copy(), mass.copy()
+        mp[k] += h
+        mm[k] -= h
+        assert (L(pos, mp) - L(pos, mm)) / (2 * h) == pytest.approx(gm[k], rel=1e-8, abs=1e-10)
+    assert np.all(np.abs(gx.sum(0)) < 1e-10 * np.abs(gx).sum())
+    assert np.sum(mass * gm) == pytest.approx(L(pos, mass), rel=1e-12)
+
+
+def test_frozen_loss_partial_sums():
+    """The frozen function at the base point is the tree force; the partial loss of
+    particle k changes exactly like the full loss when only k moves; it is linear in mass."""
+    rng = np.random.default_rng(13)
+    n = 700
+    pos = np.concatenate([rng.standard_normal((n // 2, 3)) * 0.05, rng.uniform(-1, 1, (n - n // 2, 3))])
+    mass = rng.uniform(0.5, 1.5, n) / n
+    w = rng.standard_normal((n, 3))
+    v = rng.standard_normal(n)
+    eps = 0.01
+    t = oracle.Tree(pos, mass)
+    t.moments(4)
+    t.traverse(1e-5)
+    a, p = t.force(1.0, eps)
+    Lfull = t.frozen_loss(pos, mass, w, v, 1.0, eps)
+    assert Lfull == pytest.approx(np.sum(w * a) + np.sum(v * p), rel=1e-13)
+    for k in (0, 17, 350, 699):
+        for d in range(3):
+            x1 = pos.copy()
+            x1[k, d] += 1e-3
+            dfull = t.frozen_loss(x1, mass, w, v, 1.0, eps) - Lfull
+            dpart = t.frozen_loss(x1, mass, w, v, 1.0, eps, k) - t.frozen_loss(pos, mass, w, v, 1.0, eps, k)
+            assert dpart == pytest.approx(dfull, rel=1e-8, abs=1e-12 * abs(Lfull))
+    m2 = mass * 1.7
+    assert t.frozen_loss(pos, m2, w, v, 1.0, eps) == pytest.approx(1.7 * Lfull, rel=1e-12)
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 4, 6])
+def test_mac_bound_is_exact_for_collinear_particle(p):
+    """For one particle at distance r from the expansion centre, on the line to the
+    sink at distance d, the acceleration is 1/(d-r)^2 = d^-2 sum_n (n+1)(r/d)^n and
+    the truncated expansion keeps n <= p: the error is the tail sum, which is what
+    the acceptance bound E(d) sums in closed form (with B_n = m r^n, b = r)."""
+    m, r, d = 0.8, 0.3, 1.1
+    M = oracle.moments(np.array([[r, 0.0, 0.0]]), np.array([m]), np.zeros(3), p)
+    a, _ = oracle.m2p(p, M, np.array([d, 0.0, 0.0]), 1.0, 0.0)
+    exact = -m / (d - r) ** 2
+    err = abs(a[0] - exact)
+    E = oracle.mac_bound(d, r, m * r ** (p + 1), m * r ** (p + 2), p)
+    tail = m / d ** 2 * sum((n + 1) * (r / d) ** n for n in range(p + 1, 400))
+    assert E == pytest.approx(tail, rel=1e-12)
+    assert err == pytest.approx(E, rel=1e-9)
+    assert abs(a[1]) < 1e-15 and abs(a[2]) < 1e-15
