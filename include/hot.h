@@ -1,0 +1,191 @@
+/*
+ * hot.h -- C ABI of the GB300 (sm_103a) hashed oct-tree gravity library.
+ *
+ * The library evaluates the gravitational acceleration and potential of N
+ * particles with the treecode of Warren, "2HOT" (SC'13, arXiv:1310.4502):
+ *
+ *   a_i   =  G sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2}
+ *   phi_i = -G sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^{1/2}
+ *
+ * (Eq. "eom" with the expansion factor a = 1, Plummer smoothing of Sec.
+ * "Force Smoothing"), approximated by Cartesian multipole expansions of order p
+ * (Sec. "Multipole Error Bounds", Taylor expansion of the Green's function and
+ * moment tensor definition) accepted under an absolute acceleration error bound.
+ *
+ * Call order, all on the stream given to hot_create:
+ *   hot_build_tree      keys, radix sort, hashed oct-tree, sink groups
+ *   hot_compute_moments P2M / M2M moments and acceptance-test aggregates
+ *   hot_traverse        per-sink-group interaction lists under the tolerance
+ *   hot_evaluate_forces M2P + P2P interactions -> acc, pot (original order)
+ *   hot_adjoint         dL/dx, dL/dm through the frozen lists (optional)
+ * A later call of an earlier stage invalidates the later stages.
+ *
+ * Pointers: "device" pointers are CUDA device (or managed) memory of the
+ * context's device; "host" pointers are ordinary CPU memory.  Arrays are dense
+ * and row-major; [N][3] means x0 y0 z0 x1 y1 z1 ...  The library never keeps
+ * a caller pointer after a call returns; it owns its tree, moments and lists
+ * until the next hot_build_tree or hot_destroy.
+ *
+ * Errors: every int-returning call returns HOT_OK (0) or a negative HOT_E*
+ * code; hot_strerror gives its text.  No call traps the device or aborts the
+ * process.  Device-side problems (non-finite input, list scratch overflow,
+ * hash-table probe limit, an expired wait) are reported through a status word
+ * that the host reads at the synchronisation points named below.
+ *
+ * Synchronisation: hot_build_tree and hot_traverse synchronise the stream once
+ * (they need sizes on the host to allocate); the other calls are asynchronous
+ * on the stream unless stated.
+ */
+#ifndef HOT_H
+#define HOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HOT_OK = 0,
+    HOT_EINVAL = -1,     /* bad argument (N < 1, p outside [0,6], tol <= 0, eps < 0, ...) */
+    HOT_ESTATE = -2,     /* call out of order (e.g. forces before traverse) */
+    HOT_ENOMEM = -3,     /* device allocation failed */
+    HOT_EOVERFLOW = -4,  /* a capacity limit was still exceeded after the internal retry */
+    HOT_ECUDA = -5,      /* a CUDA runtime call failed */
+    HOT_EINPUT = -6,     /* non-finite position or mass, or a non-positive total mass */
+    HOT_ETIMEOUT = -7    /* a bounded device-side wait gave up */
+};
+
+enum { HOT_FP32_MIXED = 0, HOT_FP64 = 1 };
+
+typedef struct hot_ctx hot_ctx;
+
+typedef struct {
+    int p;          /* expansion order, 0..6 (potential terms |a| <= p)           */
+    double tol;     /* absolute acceleration error bound per accepted cell, > 0  */
+    double eps;     /* Plummer softening length, >= 0                             */
+    double G;       /* gravitational constant                                     */
+    int leaf_max;   /* a cell with more particles is refined (levels < 21), >= 1  */
+    int group_max;  /* sink groups: topmost cells with <= group_max particles     */
+    int precision;  /* HOT_FP32_MIXED or HOT_FP64 interaction arithmetic          */
+} hot_params;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  *out receives the context.  Host-side only; the
+ * first call on a device also loads the kernels. */
+int hot_create(hot_ctx **out, const hot_params *prm, void *cuda_stream);
+
+/* Replace the parameters (validated as in hot_create).  Changing p, tol, eps,
+ * G or precision keeps the tree; changing leaf_max or group_max requires a new
+ * hot_build_tree. */
+int hot_set_params(hot_ctx *ctx, const hot_params *prm);
+
+/* Morton keys, stable radix sort and hashed oct-tree of N particles
+ * (Sec. "Domain Decomposition": space-filling-curve keys turned into a sort;
+ * Sec. "Tree Construction and Traversal": cells addressed by key).
+ *   pos  device, [N][3] float64, not modified
+ *   mass device, [N] float64, not modified
+ * Key frame: lo = per-axis minimum, L = largest extent; integer coordinates
+ * floor((x - lo) * 2^21 / L) clamped to 2^21 - 1; key = 2^63 | 63 interleaved
+ * bits (x highest in each triplet).  Cells are key prefixes; a cell with more
+ * than leaf_max particles below level 21 is refined into its non-empty
+ * octants.  Cells are stored in depth-first pre-order (children in ascending
+ * octant) and inserted into an open-addressed hash table keyed by the cell key
+ * (leading placeholder bit: the root key is 1).  Sink groups are the topmost
+ * cells that are leaves or hold at most group_max particles.
+ * Synchronises the stream once.  Returns HOT_EINPUT for non-finite input. */
+int hot_build_tree(hot_ctx *ctx, const double *pos, const double *mass, int64_t N);
+
+/* Moments of every cell about its centre of mass (Eq. "moment tensor":
+ * M_a = sum m (x - z)^a, |a| <= p): P2M at the leaves, exact binomial
+ * translation (M2M) upwards, in float64; plus the acceptance-test aggregates
+ * b_max = max |x - z|, B_{p+1}, B_{p+2} (B_n = sum m |x - z|^n), and the
+ * interaction coefficient records.  p in [0, 6]; asynchronous. */
+int hot_compute_moments(hot_ctx *ctx, int p);
+
+/* Group-wise traversal (Sec. "Improving instruction-level parallelism": m
+ * source cells x n sink particles) under the absolute-error acceptance test
+ * (Sec. "Multipole Error Bounds", geometry of Fig. "mac"):
+ *   d = |z_c - g| - Delta_max   (g: centre of the group's bounding box,
+ *                                Delta_max: largest distance of a sink from g)
+ *   accept cell c for group g  iff  d > b_max and
+ *   E(d) = G/d^2 (1 - b_max/d)^-2 [(p+2) B_{p+1}/d^{p+1} - (p+1) B_{p+2}/d^{p+2}] <= tol.
+ * Rejected leaves go to the particle-particle list, rejected inner cells are
+ * opened.  tol > 0.  Synchronises the stream once (list sizes). */
+int hot_traverse(hot_ctx *ctx, double tol);
+
+/* Interactions on the lists: M2P (expansion of the softened kernel) and
+ * softened P2P; sums are kept per sink in float32 with compensated (Kahan)
+ * accumulation in the mixed mode, float64 otherwise.
+ *   acc device, [N][3] float64, written in the caller's original order
+ *   pot device, [N] float64 or NULL                                      */
+int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
+
+/* Adjoint of L = sum_i g_acc_i . a_i + sum_i g_pot_i phi_i through the frozen
+ * lists and frozen expansion centres (moments stay functions of positions and
+ * masses).  g_acc device [N][3]; g_pot device [N] or NULL; outputs g_pos
+ * device [N][3], g_mass device [N], original order.  Requires a preceding
+ * hot_traverse on the same tree. */
+int hot_adjoint(hot_ctx *ctx, const double *g_acc, const double *g_pot, double *g_pos,
+                double *g_mass);
+
+/* Device time in ms of the last call of each stage, measured with CUDA events
+ * on the context stream: ms[0] keys+sort, ms[1] tree build, ms[2] moments,
+ * ms[3] traversal, ms[4] interactions, ms[5] adjoint.  Synchronises. */
+int hot_stage_times(hot_ctx *ctx, float ms[6]);
+
+/* Sizes after the latest stages: out[0] N, [1] cells, [2] sink groups, [3]
+ * leaves, [4] deepest level, [5] M2P list entries, [6] P2P list entries
+ * (leaves), [7] P2P particle pairs, [8] M2P interactions (entries x sinks). */
+int hot_sizes(hot_ctx *ctx, int64_t out[9]);
+
+/* Copy an internal array to host memory (for tests).  bytes must equal the
+ * array size: see HOT_DBG_* for element type and length.  Synchronises. */
+enum {
+    HOT_DBG_FRAME = 0,        /* float64[4]: lo_x lo_y lo_z L                */
+    HOT_DBG_SORTED_KEYS = 1,  /* uint64[N]: keys in sorted order             */
+    HOT_DBG_PERM = 2,         /* int32[N]: original index of sorted slot     */
+    HOT_DBG_CELL_KEY = 3,     /* uint64[ncell]                               */
+    HOT_DBG_CELL_LEVEL = 4,   /* int32[ncell]                                */
+    HOT_DBG_CELL_BEGIN = 5,   /* int32[ncell]: first sorted slot             */
+    HOT_DBG_CELL_COUNT = 6,   /* int32[ncell]                                */
+    HOT_DBG_CELL_PARENT = 7,  /* int32[ncell] (-1 for the root)              */
+    HOT_DBG_CELL_NCHILD = 8,  /* int32[ncell]                                */
+    HOT_DBG_GROUP_CELL = 9,   /* int32[ngroup]                               */
+    HOT_DBG_GROUP_CENTRE = 10, /* float64[ngroup][3]                         */
+    HOT_DBG_GROUP_DMAX = 11,  /* float64[ngroup]                             */
+    HOT_DBG_CELL_MASS = 12,   /* float64[ncell]                              */
+    HOT_DBG_CELL_COM = 13,    /* float64[ncell][3]                           */
+    HOT_DBG_MOMENTS = 14,     /* float64[ncell][ncomp(p)], a by degree, then
+                                 a_x descending, then a_y descending         */
+    HOT_DBG_CELL_BMAX = 15,   /* float64[ncell]                              */
+    HOT_DBG_CELL_B1 = 16,     /* float64[ncell]: B_{p+1}                     */
+    HOT_DBG_CELL_B2 = 17,     /* float64[ncell]: B_{p+2}                     */
+    HOT_DBG_M2P_OFFSETS = 18, /* int64[ngroup + 1]                           */
+    HOT_DBG_M2P_CELLS = 19,   /* int32[n_m2p]                                */
+    HOT_DBG_P2P_OFFSETS = 20, /* int64[ngroup + 1]                           */
+    HOT_DBG_P2P_CELLS = 21    /* int32[n_p2p]                                */
+};
+int hot_debug_get(hot_ctx *ctx, int what, void *host_dst, size_t bytes);
+
+/* Hash-table lookup of n cell keys (host arrays): idx[i] = cell index of
+ * keys[i] or -1 when no such cell exists.  Synchronises. */
+int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
+
+/* Fused-multiply-add throughput microbenchmark (for roofline denominators):
+ * runs a register-resident FMA loop on every SM and writes the achieved
+ * FLOP/s (FMA = 2) to *flops.  dbl: 0 = float32, 1 = float64.  Synchronises. */
+int hot_fma_peak(hot_ctx *ctx, int dbl, double *flops);
+
+/* Text of a HOT_* code (static storage). */
+const char *hot_strerror(int code);
+
+/* Free the context and everything it owns (synchronises its stream). */
+void hot_destroy(hot_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOT_H */

@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Generate the straight-line multipole routines of the CUDA library.
+
+The paper produces its high-order interaction routines by metaprogramming
+(computer-algebra output translated into C, Sec. "Multipole Error Bounds"); this
+script plays that role for the GPU path.  It writes ``generated.cuh`` with, for
+every order p = 0..6:
+
+* ``m2p_eval<P>(rec, rx, ry, rz, phi, ax, ay, az)`` -- one cell-to-particle
+  interaction of the Cartesian expansion of the softened kernel
+  F(R) = (|R|^2 + eps^2)^{-1/2}, written in a traced form:
+      Phi(R) = sum_a (-1)^|a| / a!  d^a F(R) M_a
+             = rho * sum_{k} w^k sum_{|b| <= p-2k} C_{b,k} y^b,
+  with u = |R|^2 + eps^2, rho = u^{-1/2}, w = 1/u, y = R w, and per-cell
+  coefficients
+      C_{b,k} = (-1)^k (2m-1)!! / (2^k b!) * sum_{|l|=k} M_{b+2l} / l!,  m = |b|+k.
+  The gradient follows from d rho/dR = -rho y, dw/dR = -2 w y,
+  dy_e/dR_d = w delta_ed - 2 y_e y_d:
+      dPhi/dR_d = rho [ w sum_k w^k dS_k/dy_d - y_d sum_{k,n} w^k (1+2k+2n) S_{k,n} ],
+  S_{k,n} being the degree-n part of S_k.  The potential is -G Phi and the
+  acceleration +G grad Phi.
+* ``m2p_record<P>(M, inv_s, G, eps, rec)`` -- raw moments (FP64) to the record
+  read by ``m2p_eval``: every coefficient is scaled by a power of two
+  s = 1/inv_s (exact), so that R' = R/s and the coefficients stay O(1) in
+  single precision; G/s is folded in.  Layout: [inv_s, eps^2/s^2, 0, 0,
+  C_{b,k} ..., gradient coefficients b_d C_{b,k} ...].
+* the moment-translation (M2M) pair tables and multi-index tables.
+
+The flop count of each ``m2p_eval<P>`` (FMA = 2, the rsqrt as 1) is emitted as
+``M2P_FLOPS[P]``; that is the convention used for the interaction roofline.
+
+Run: python gen_kernels.py  (rewrites generated.cuh next to this file).
+"""
+import math
+import os
+import sys
+
+PMAX = 6
+
+
+def midx(p):
+    out = []
+    for n in range(p + 1):
+        for i in range(n, -1, -1):
+            for j in range(n - i, -1, -1):
+                out.append((i, j, n - i - j))
+    return out
+
+
+def ncomp(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def dfact(n):
+    r = 1
+    while n > 1:
+        r *= n
+        n -= 2
+    return r
+
+
+def fact3(a):
+    return math.factorial(a[0]) * math.factorial(a[1]) * math.factorial(a[2])
+
+
+def add(a, b):
+    return (a[0] + b[0], a[1] + b[1], a[2] + b[2])
+
+
+def mname(a):
+    return f"y{a[0]}{a[1]}{a[2]}"
+
+
+def s_terms(p):
+    """(k, n, beta) triples of the traced coefficients, in record order."""
+    out = []
+    for k in range(p // 2 + 1):
+        for n in range(p - 2 * k + 1):
+            for b in midx(n)[ncomp(n - 1) if n > 0 else 0:]:
+                out.append((k, n, b))
+    return out
+
+
+def g_terms(p):
+    """(k, d, beta) with beta_d >= 1: coefficient beta_d C_{beta,k} of dS_k/dy_d."""
+    out = []
+    for k in range(p // 2 + 1):
+        for n in range(1, p - 2 * k + 1):
+            for b in midx(n)[ncomp(n - 1):]:
+                for d in range(3):
+                    if b[d] >= 1:
+                        out.append((k, d, b))
+    return out
+
+
+def gen_eval(p):
+    S = s_terms(p)
+    Gt = g_terms(p)
+    ns, ng = len(S), len(Gt)
+    sidx = {(k, b): 4 + i for i, (k, n, b) in enumerate(S)}
+    gidx = {(k, d, b): 4 + ns + i for i, (k, d, b) in enumerate(Gt)}
+    L = []
+    fl = 0
+    L.append(f"template <typename T> __device__ __forceinline__ void m2p_eval_{p}("
+             "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {")
+    L.append("  const T is = c[0];")
+    L.append("  rx *= is; ry *= is; rz *= is;")
+    fl += 3
+    L.append("  const T u = rx * rx + ry * ry + rz * rz + c[1];")
+    fl += 6
+    L.append("  const T rho = hot_rsqrt(u);")
+    fl += 1
+    L.append("  const T w = rho * rho;")
+    fl += 1
+    L.append(f"  const T {mname((1,0,0))} = rx * w, {mname((0,1,0))} = ry * w, {mname((0,0,1))} = rz * w;")
+    fl += 3
+    L.append(f"  const T {mname((0,0,0))} = T(1);")
+    # accumulators: S_{k,n}, G_{k,d}
+    have_s = set()
+    have_g = set()
+    for n in range(0, p + 1):
+        if n >= 2:
+            for a in midx(n)[ncomp(n - 1):]:
+                d = 0 if a[0] > 0 else (1 if a[1] > 0 else 2)
+                prev = list(a)
+                prev[d] -= 1
+                unit = [mname((1,0,0)), mname((0,1,0)), mname((0,0,1))][d]
+                L.append(f"  const T {mname(a)} = {mname(tuple(prev))} * {unit};")
+                fl += 1
+        # S terms of degree n
+        for k in range(p // 2 + 1):
+            if n + 2 * k > p:
+                continue
+            acc = f"s{k}_{n}"
+            for b in midx(n)[ncomp(n - 1) if n > 0 else 0:]:
+                ci = sidx[(k, b)]
+                if acc not in have_s:
+                    if n == 0:
+                        L.append(f"  T {acc} = c[{ci}];")
+                    else:
+                        L.append(f"  T {acc} = c[{ci}] * {mname(b)};")
+                        fl += 1
+                    have_s.add(acc)
+                else:
+                    L.append(f"  {acc} += c[{ci}] * {mname(b)};")
+                    fl += 2
+        # gradient terms whose monomial y^{b-e_d} has degree n
+        for k in range(p // 2 + 1):
+            if n + 1 + 2 * k > p:
+                continue
+            for b in midx(n + 1)[ncomp(n):]:
+                for d in range(3):
+                    if b[d] < 1:
+                        continue
+                    mono = list(b)
+                    mono[d] -= 1
+                    mono = tuple(mono)
+                    gi = gidx[(k, d, b)]
+                    acc = f"g{k}_{d}"
+                    if acc not in have_g:
+                        if n == 0:
+                            L.append(f"  T {acc} = c[{gi}];")
+                        else:
+                            L.append(f"  T {acc} = c[{gi}] * {mname(mono)};")
+                            fl += 1
+                        have_g.add(acc)
+                    else:
+                        L.append(f"  {acc} += c[{gi}] * {mname(mono)};")
+                        fl += 2
+    # combine: S = sum_k w^k S_k ; Tr = sum_{k,n} w^k (1+2k+2n) S_{k,n} ; Gd = sum_k w^k g_{k,d}
+    K = p // 2
+    for k in range(K + 1):
+        terms = [f"s{k}_{n}" for n in range(p - 2 * k + 1)]
+        L.append(f"  const T S{k} = " + " + ".join(terms) + ";")
+        fl += len(terms) - 1
+        tt = [f"T({1 + 2 * k + 2 * n}) * s{k}_{n}" if (1 + 2 * k + 2 * n) != 1 else f"s{k}_{n}"
+              for n in range(p - 2 * k + 1)]
+        L.append(f"  const T Q{k} = " + " + ".join(tt) + ";")
+        fl += 2 * (len(tt) - 1) + (0 if len(tt) == 1 else 0)
+    # Horner in w
+    def horner(names):
+        expr = names[-1]
+        for nm in reversed(names[:-1]):
+            expr = f"({nm} + w * {expr})"
+        return expr
+    L.append(f"  const T S = {horner([f'S{k}' for k in range(K + 1)])};")
+    L.append(f"  const T Q = {horner([f'Q{k}' for k in range(K + 1)])};")
+    fl += 4 * K
+    for d in range(3):
+        ks = [k for k in range(K + 1) if (k, d) in {(kk, dd) for (kk, dd, _) in Gt}]
+        if ks:
+            names = [f"g{k}_{d}" if k in ks else "T(0)" for k in range(max(ks) + 1)]
+            L.append(f"  const T G{d} = {horner(names)};")
+            fl += 2 * (len(names) - 1)
+        else:
+            L.append(f"  const T G{d} = T(0);")
+    L.append("  phi -= rho * S;")
+    fl += 2
+    L.append("  const T rs = rho * is;")
+    fl += 1
+    for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
+        L.append(f"  {an} += rs * (w * G{d} - {yn} * Q);")
+        fl += 5
+    L.append("}")
+    return "\n".join(L), ns, ng, fl
+
+
+def gen_record(p):
+    """Raw moments -> scaled traced coefficients (FP64 arithmetic)."""
+    S = s_terms(p)
+    Gt = g_terms(p)
+    ns = len(S)
+    idx = {a: i for i, a in enumerate(midx(p))}
+    L = []
+    L.append(f"template <typename T> __device__ __forceinline__ void m2p_record_{p}("
+             "const double* __restrict__ M, double inv_s, double G, double eps, T* __restrict__ rec) {")
+    L.append(f"  double ip[{p + 2 + p}];")
+    L.append("  ip[0] = 1.0;")
+    L.append(f"  for (int q = 1; q < {2 * p + 2}; ++q) ip[q] = ip[q - 1] * inv_s;")
+    L.append("  rec[0] = T(inv_s); rec[1] = T((eps * inv_s) * (eps * inv_s)); rec[2] = T(0); rec[3] = T(0);")
+    L.append(f"  double C[{ns}];")
+    for i, (k, n, b) in enumerate(S):
+        m = n + k
+        const = (-1) ** k * dfact(2 * m - 1) / (2 ** k * fact3(b))
+        # sum over |l| = k of M_{b+2l} / l!
+        terms = []
+        for l in midx(k)[ncomp(k - 1) if k > 0 else 0:]:
+            a = add(b, (2 * l[0], 2 * l[1], 2 * l[2]))
+            terms.append(f"M[{idx[a]}] * {1.0 / fact3(l)!r}")
+        L.append(f"  C[{i}] = G * ip[{1 + 2 * k + n}] * {const!r} * (" + " + ".join(terms) + ");")
+        L.append(f"  rec[{4 + i}] = T(C[{i}]);")
+    sidx = {(k, b): i for i, (k, n, b) in enumerate(S)}
+    for j, (k, d, b) in enumerate(Gt):
+        L.append(f"  rec[{4 + ns + j}] = T({b[d]}.0 * C[{sidx[(k, b)]}]);")
+    L.append("}")
+    return "\n".join(L)
+
+
+def m2m_pairs(p):
+    """Pairs (alpha, beta <= alpha): M_alpha(z') += C(alpha,beta) M_beta(z) (z - z')^{alpha-beta}."""
+    ia = midx(p)
+    idx = {a: i for i, a in enumerate(ia)}
+    start, bidx, gidx, coef = [], [], [], []
+    for a in ia:
+        start.append(len(bidx))
+        for b in ia:
+            if all(b[d] <= a[d] for d in range(3)):
+                g = (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+                bidx.append(idx[b])
+                gidx.append(idx[g])
+                coef.append(math.comb(a[0], b[0]) * math.comb(a[1], b[1]) * math.comb(a[2], b[2]))
+    start.append(len(bidx))
+    return start, bidx, gidx, coef
+
+
+def main(out_path):
+    parts = []
+    parts.append("// Generated by gen_kernels.py -- do not edit by hand.\n#pragma once\n")
+    parts.append(f"#define HOT_PMAX {PMAX}")
+    parts.append(f"#define HOT_NCOMP_MAX {ncomp(PMAX)}")
+    recl, nsl, ngl, fll = [], [], [], []
+    evals, records = [], []
+    for p in range(PMAX + 1):
+        code, ns, ng, fl = gen_eval(p)
+        evals.append(code)
+        records.append(gen_record(p))
+        rl = 4 + ns + ng
+        rl = (rl + 3) // 4 * 4
+        recl.append(rl)
+        nsl.append(ns)
+        ngl.append(ng)
+        fll.append(fl)
+    parts.append("static constexpr int HOT_REC_LEN[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, recl))))
+    parts.append("static constexpr int M2P_FLOPS[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, fll))))
+    parts.append("static constexpr int HOT_NCOMP[%d] = {%s};" % (PMAX + 1, ", ".join(str(ncomp(p)) for p in range(PMAX + 1))))
+    # multi-index table (order PMAX covers every lower order as a prefix)
+    ia = midx(PMAX)
+    parts.append("__device__ __constant__ unsigned char hot_midx[%d][3] = {%s};" % (
+        len(ia), ", ".join("{%d,%d,%d}" % a for a in ia)))
+    # translation pairs of order PMAX; components are ordered so that every lower
+    # order is a prefix (alpha with |alpha| <= p come first and only reference such beta)
+    st, bi, gi, co = m2m_pairs(PMAX)
+    parts.append(f"static constexpr int M2M_NPAIR = {len(bi)};")
+    parts.append(f"__device__ const unsigned short m2m_start[{len(st)}] = {{{', '.join(map(str, st))}}};")
+    parts.append(f"__device__ const unsigned char m2m_beta[{len(bi)}] = {{{', '.join(map(str, bi))}}};")
+    parts.append(f"__device__ const unsigned char m2m_gamma[{len(gi)}] = {{{', '.join(map(str, gi))}}};")
+    parts.append(f"__device__ const double m2m_coef[{len(co)}] = {{{', '.join(repr(float(c)) for c in co)}}};")
+    parts.extend(evals)
+    parts.extend(records)
+    ev = ["template <int P, typename T> __device__ __forceinline__ void m2p_eval("
+          "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {"]
+    rc = ["template <int P, typename T> __device__ __forceinline__ void m2p_record("
+          "const double* __restrict__ M, double inv_s, double G, double eps, T* __restrict__ rec) {"]
+    for p in range(PMAX + 1):
+        kw = "if" if p == 0 else "else if"
+        ev.append(f"  {kw} constexpr (P == {p}) m2p_eval_{p}<T>(c, rx, ry, rz, phi, ax, ay, az);")
+        rc.append(f"  {kw} constexpr (P == {p}) m2p_record_{p}<T>(M, inv_s, G, eps, rec);")
+    ev.append("}")
+    rc.append("}")
+    parts.append("\n".join(ev))
+    parts.append("\n".join(rc))
+    src = "\n".join(parts) + "\n"
+    with open(out_path, "w") as f:
+        f.write(src)
+    return recl, fll
+
+
+if __name__ == "__main__":
+    here = os.path.dirname(os.path.abspath(__file__))
+    out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(here, "generated.cuh")
+    recl, fll = main(out)
+    print("record lengths", recl)
+    print("flops per M2P", fll)

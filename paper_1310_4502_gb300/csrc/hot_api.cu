@@ -1,0 +1,287 @@
+// hot_api.cu -- the C ABI declared in include/hot.h: context lifetime, argument checks,
+// stage ordering, status word, debug copies, hash lookups and the FMA microbenchmark.
+#include <new>
+
+#include "hot_common.cuh"
+#include "generated.cuh"
+
+int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx);
+
+namespace {
+
+int status_code(unsigned bits)
+{
+    if (bits & HOT_ST_INPUT) return HOT_EINPUT;
+    if (bits & HOT_ST_TIMEOUT) return HOT_ETIMEOUT;
+    if (bits & (HOT_ST_FRONTIER | HOT_ST_HASH)) return HOT_EOVERFLOW;
+    if (bits & HOT_ST_INTERNAL) return HOT_ECUDA;
+    return HOT_OK;
+}
+
+int check_params(const hot_params *p)
+{
+    if (!p) return HOT_EINVAL;
+    if (p->p < 0 || p->p > HOT_PMAX) return HOT_EINVAL;
+    if (!(p->tol > 0.0) || !(p->eps >= 0.0) || !(p->G == p->G)) return HOT_EINVAL;
+    if (p->leaf_max < 1 || p->group_max < 1 || p->leaf_max > 4096 || p->group_max > (1 << 20)) return HOT_EINVAL;
+    if (p->precision != HOT_FP32_MIXED && p->precision != HOT_FP64) return HOT_EINVAL;
+    return HOT_OK;
+}
+
+// Register-resident FMA chains: 8 independent accumulators per thread.
+template <class T>
+__global__ void k_fma(T *out, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == (T)-12345.0) out[0] = s;  // keeps the chains alive
+}
+
+}  // namespace
+
+int hot_sync_status(hot_ctx *c)
+{
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
+    unsigned bits = 0;
+    if (cudaMemcpy(&bits, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return HOT_ECUDA;
+    if (bits) cudaMemset(c->d_status, 0, sizeof(unsigned));
+    return status_code(bits);
+}
+
+extern "C" {
+
+int hot_create(hot_ctx **out, const hot_params *prm, void *cuda_stream)
+{
+    if (!out) return HOT_EINVAL;
+    *out = nullptr;
+    int e = check_params(prm);
+    if (e) return e;
+    hot_ctx *c = new (std::nothrow) hot_ctx();
+    if (!c) return HOT_ENOMEM;
+    c->prm = *prm;
+    c->st = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+        delete c;
+        return HOT_ECUDA;
+    }
+    if (cudaMalloc((void **)&c->d_status, sizeof(unsigned)) != cudaSuccess) {
+        delete c;
+        return HOT_ENOMEM;
+    }
+    cudaMemset(c->d_status, 0, sizeof(unsigned));
+    c->h_status = nullptr;
+    for (int k = 0; k < ST_TIMING_EVENTS; ++k) cudaEventCreate(&c->ev[k]);
+    *out = c;
+    return HOT_OK;
+}
+
+int hot_set_params(hot_ctx *c, const hot_params *prm)
+{
+    if (!c) return HOT_EINVAL;
+    int e = check_params(prm);
+    if (e) return e;
+    bool rebuild = prm->leaf_max != c->prm.leaf_max || prm->group_max != c->prm.group_max;
+    bool remoment = prm->p != c->prm.p || prm->eps != c->prm.eps || prm->G != c->prm.G ||
+                    prm->precision != c->prm.precision;
+    c->prm = *prm;
+    if (rebuild) c->stage = 0;
+    else if (remoment && c->stage > 1) c->stage = 1;
+    else if (c->stage > 2) c->stage = 2;
+    return HOT_OK;
+}
+
+int hot_build_tree(hot_ctx *c, const double *pos, const double *mass, int64_t N)
+{
+    if (!c || !pos || !mass || N < 1 || N > (int64_t)INT32_MAX / 2) return HOT_EINVAL;
+    c->stage = 0;
+    return hot_impl_build(c, pos, mass, N);
+}
+
+int hot_compute_moments(hot_ctx *c, int p)
+{
+    if (!c || p < 0 || p > HOT_PMAX) return HOT_EINVAL;
+    if (c->stage < 1) return HOT_ESTATE;
+    c->prm.p = p;
+    c->stage = 1;
+    return hot_impl_moments(c, p);
+}
+
+int hot_traverse(hot_ctx *c, double tol)
+{
+    if (!c || !(tol > 0.0)) return HOT_EINVAL;
+    if (c->stage < 2) return HOT_ESTATE;
+    c->stage = 2;
+    c->prm.tol = tol;
+    return hot_impl_traverse(c, tol);
+}
+
+int hot_evaluate_forces(hot_ctx *c, double *acc, double *pot)
+{
+    if (!c || !acc) return HOT_EINVAL;
+    if (c->stage < 3) return HOT_ESTATE;
+    return hot_impl_forces(c, acc, pot);
+}
+
+int hot_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
+{
+    if (!c || !g_acc || !g_pos || !g_mass) return HOT_EINVAL;
+    if (c->stage < 3) return HOT_ESTATE;
+    return hot_impl_adjoint(c, g_acc, g_pot, g_pos, g_mass);
+}
+
+int hot_stage_times(hot_ctx *c, float ms[6])
+{
+    if (!c || !ms) return HOT_EINVAL;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
+    for (int k = 0; k < 6; ++k) {
+        ms[k] = 0.f;
+        if (c->ev_used[k]) cudaEventElapsedTime(&ms[k], c->ev[2 * k], c->ev[2 * k + 1]);
+    }
+    return HOT_OK;
+}
+
+int hot_sizes(hot_ctx *c, int64_t out[9])
+{
+    if (!c || !out) return HOT_EINVAL;
+    out[0] = c->N;
+    out[1] = c->ncell;
+    out[2] = c->ngroup;
+    out[3] = c->nleaf;
+    out[4] = c->maxlevel;
+    out[5] = c->n_m2p;
+    out[6] = c->n_p2p;
+    out[7] = c->n_pairs;
+    out[8] = c->n_m2p_int;
+    return HOT_OK;
+}
+
+int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
+{
+    if (!c || !dst) return HOT_EINVAL;
+    const void *src = nullptr;
+    size_t need = 0;
+    const int64_t N = c->N, nc = c->ncell, ng = c->ngroup;
+    const int ncomp = c->p_mom >= 0 ? HOT_NCOMP[c->p_mom] : 0;
+    int min_stage = 1;
+    switch (what) {
+        case HOT_DBG_FRAME: src = c->frame.p; need = 4 * sizeof(double); break;
+        case HOT_DBG_SORTED_KEYS: src = c->key.p; need = N * sizeof(uint64_t); break;
+        case HOT_DBG_PERM: src = c->idx.p; need = N * sizeof(int32_t); break;
+        case HOT_DBG_CELL_KEY: src = c->ckey.p; need = nc * sizeof(uint64_t); break;
+        case HOT_DBG_CELL_LEVEL: src = c->clevel.p; need = nc * sizeof(int32_t); break;
+        case HOT_DBG_CELL_BEGIN: src = c->cbegin.p; need = nc * sizeof(int32_t); break;
+        case HOT_DBG_CELL_COUNT: src = c->ccount.p; need = nc * sizeof(int32_t); break;
+        case HOT_DBG_CELL_PARENT: src = c->cparent.p; need = nc * sizeof(int32_t); break;
+        case HOT_DBG_CELL_NCHILD: src = c->cnchild.p; need = nc * sizeof(int32_t); break;
+        case HOT_DBG_GROUP_CELL: src = c->gcell.p; need = ng * sizeof(int32_t); break;
+        case HOT_DBG_GROUP_CENTRE: src = c->gcen.p; need = 3 * ng * sizeof(double); break;
+        case HOT_DBG_GROUP_DMAX: src = c->gdmax.p; need = ng * sizeof(double); break;
+        case HOT_DBG_CELL_MASS: src = c->cmass.p; need = nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_CELL_COM: src = c->ccom.p; need = 3 * nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_MOMENTS: src = c->cmom.p; need = (size_t)ncomp * nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_CELL_BMAX: src = c->cbmax.p; need = nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_CELL_B1: src = c->cB1.p; need = nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_CELL_B2: src = c->cB2.p; need = nc * sizeof(double); min_stage = 2; break;
+        case HOT_DBG_M2P_OFFSETS: src = c->off_m2p.p; need = (ng + 1) * sizeof(int64_t); min_stage = 3; break;
+        case HOT_DBG_M2P_CELLS: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
+        case HOT_DBG_P2P_OFFSETS: src = c->off_p2p.p; need = (ng + 1) * sizeof(int64_t); min_stage = 3; break;
+        case HOT_DBG_P2P_CELLS: src = c->l_p2p.p; need = c->n_p2p * sizeof(int32_t); min_stage = 3; break;
+        default: return HOT_EINVAL;
+    }
+    if (c->stage < min_stage) return HOT_ESTATE;
+    if (bytes != need) return HOT_EINVAL;
+    if (need == 0) return HOT_OK;
+    if (cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, c->st) != cudaSuccess) return HOT_ECUDA;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
+    return HOT_OK;
+}
+
+int hot_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
+{
+    if (!c || (n > 0 && (!keys || !idx)) || n < 0) return HOT_EINVAL;
+    if (c->stage < 1) return HOT_ESTATE;
+    if (n == 0) return HOT_OK;
+    return hot_impl_lookup(c, keys, n, idx);
+}
+
+int hot_fma_peak(hot_ctx *c, int dbl, double *flops)
+{
+    if (!c || !flops) return HOT_EINVAL;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, 64) != cudaSuccess) return HOT_ENOMEM;
+    const int threads = 256, blocks = c->nsm * 8;
+    const int iters = dbl ? 4096 : 65536;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a, c->st);
+        if (dbl)
+            k_fma<double><<<blocks, threads, 0, c->st>>>((double *)buf, iters, 0.999999, 1e-7);
+        else
+            k_fma<float><<<blocks, threads, 0, c->st>>>((float *)buf, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(b, c->st);
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            cudaFree(buf);
+            return HOT_ECUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    *flops = 2.0 * 8.0 * (double)iters * threads * blocks / (best * 1e-3);
+    return HOT_OK;
+}
+
+const char *hot_strerror(int code)
+{
+    switch (code) {
+        case HOT_OK: return "ok";
+        case HOT_EINVAL: return "invalid argument";
+        case HOT_ESTATE: return "call out of order";
+        case HOT_ENOMEM: return "device allocation failed";
+        case HOT_EOVERFLOW: return "capacity exceeded";
+        case HOT_ECUDA: return "CUDA runtime error";
+        case HOT_EINPUT: return "non-finite or non-positive input";
+        case HOT_ETIMEOUT: return "bounded device wait expired";
+        default: return "unknown error";
+    }
+}
+
+void hot_destroy(hot_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    cudaStream_t s = c->st;
+    c->part.release(s); c->frame.release(s); c->key.release(s); c->key2.release(s); c->idx.release(s);
+    c->idx2.release(s); c->hist.release(s); c->histoff.release(s); c->scan_tmp.release(s); c->spos.release(s);
+    c->smass.release(s); c->lcp.release(s); c->leaflev.release(s); c->ncell_i.release(s); c->cell_off.release(s);
+    c->ckey.release(s); c->clevel.release(s); c->cbegin.release(s); c->ccount.release(s); c->cparent.release(s);
+    c->cend.release(s); c->child8.release(s); c->cnchild.release(s); c->level_cells.release(s);
+    c->hkey.release(s); c->hval.release(s); c->gflag.release(s); c->goff.release(s); c->gcell.release(s);
+    c->gcen.release(s); c->gdmax.release(s); c->sizes.release(s); c->cmass.release(s); c->ccom.release(s);
+    c->cmom.release(s); c->cbmax.release(s); c->cB1.release(s); c->cB2.release(s); c->item_off.release(s);
+    c->item_cell.release(s); c->item_part.release(s); c->rec32.release(s); c->rec64.release(s); c->prel.release(s);
+    c->cnt_m2p.release(s); c->cnt_p2p.release(s); c->off_m2p.release(s); c->off_p2p.release(s);
+    c->l_m2p.release(s); c->l_p2p.release(s); c->trav_scratch.release(s); c->pairs_per_group.release(s);
+    cudaStreamSynchronize(s);
+    if (c->d_status) cudaFree(c->d_status);
+    for (int k = 0; k < ST_TIMING_EVENTS; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,651 @@
+// hot_build.cu -- bounding cube, Morton keys, LSD radix sort, gather, hashed oct-tree
+// and sink groups (Warren 2013: Sec. "Domain Decomposition" -- space-filling-curve keys
+// turn the decomposition into a sort; Sec. "Tree Construction and Traversal" -- cells
+// are key prefixes addressed through a hash table).
+//
+// Tree construction is fully parallel over the sorted keys.  With lcp(a, b) the
+// number of leading equal octal digits of two keys:
+//   * the level-l cell holding particle i has more than leaf_max particles iff some
+//     window t in [i - leaf_max, i] has lcp(key_t, key_{t+leaf_max}) >= l, so the
+//     level of i's leaf is min(21, 1 + max_t lcp(key_t, key_{t+leaf_max}));
+//   * particle i is the first particle of a level-l cell iff lcp(key_{i-1}, key_i) < l,
+//     and that cell exists iff its parent was refined, i.e. iff l <= leaf level(i).
+// So particle i "owns" the cells of levels lcp(key_{i-1}, key_i)+1 .. leaf level(i);
+// a scan of those counts numbers every cell, and the numbering is the depth-first
+// pre-order of the tree (children in ascending octant), which also makes every
+// subtree a contiguous index range.
+#include "hot_common.cuh"
+
+namespace {
+
+constexpr int BT = 256;
+
+// ---------------------------------------------------------------------------
+// Bounding cube
+// ---------------------------------------------------------------------------
+__global__ void k_bbox_part(const double *__restrict__ pos, const double *__restrict__ mass,
+                            int64_t N, double *__restrict__ part, unsigned *status)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double m = mass[i];
+        bad |= !(isfinite(m) && m > 0.0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * i + d];
+            bad |= !isfinite(x);
+            lo[d] = fmin(lo[d], x);
+            hi[d] = fmax(hi[d], x);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane_id() == 0) hot_flag(status, HOT_ST_INPUT);
+    __shared__ double sh[BT / 32][6];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = warp_min(lo[d]);
+        hi[d] = warp_max(hi[d]);
+    }
+    if (lane_id() == 0)
+        for (int d = 0; d < 3; ++d) {
+            sh[threadIdx.x >> 5][d] = lo[d];
+            sh[threadIdx.x >> 5][3 + d] = hi[d];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int d = threadIdx.x;
+        double v = sh[0][d];
+        for (int w = 1; w < BT / 32; ++w) v = d < 3 ? fmin(v, sh[w][d]) : fmax(v, sh[w][d]);
+        part[6 * blockIdx.x + d] = v;
+    }
+}
+
+// frame = lo[3], L, 2^21/L
+__global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ frame)
+{
+    if (threadIdx.x != 0) return;
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = part[d];
+        hi[d] = part[3 + d];
+    }
+    for (int b = 1; b < nb; ++b)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fmin(lo[d], part[6 * b + d]);
+            hi[d] = fmax(hi[d], part[6 * b + 3 + d]);
+        }
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double e = __dsub_rn(hi[d], lo[d]);
+        if (e > ext) ext = e;
+    }
+    double L = ext > 0.0 ? ext : 1.0;
+    for (int d = 0; d < 3; ++d) frame[d] = lo[d];
+    frame[3] = L;
+    frame[4] = __ddiv_rn(2097152.0, L);
+}
+
+// ---------------------------------------------------------------------------
+// Keys: magic-number bit spreading of 21-bit integer coordinates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
+{
+    double t = __dmul_rn(__dsub_rn(x, lo), s);  // one subtract, one multiply, no contraction
+    double f = floor(t);
+    uint64_t c = (f <= 0.0) ? 0ull : (uint64_t)f;
+    return c > 2097151ull ? 2097151ull : c;
+}
+
+__global__ void k_keys(const double *__restrict__ pos, int64_t N, const double *__restrict__ frame,
+                       uint64_t *__restrict__ key, uint32_t *__restrict__ idx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = frame[4];
+    uint64_t cx = icoord(pos[3 * i + 0], frame[0], s);
+    uint64_t cy = icoord(pos[3 * i + 1], frame[1], s);
+    uint64_t cz = icoord(pos[3 * i + 2], frame[2], s);
+    key[i] = (1ull << 63) | (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
+    idx[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (key, index), 8-bit digits.  Stable: inside a tile the rank
+// of a key is (warp, round, lane) order, i.e. input order.
+// ---------------------------------------------------------------------------
+constexpr int RS_W = 8;          // warps per block
+constexpr int RS_R = 16;         // rounds of 32 keys per warp
+constexpr int RS_TILE = RS_W * RS_R * 32;
+
+__global__ void __launch_bounds__(RS_W * 32) k_rs_hist(const uint64_t *__restrict__ key, int64_t N,
+                                                       int shift, uint32_t *__restrict__ hist,
+                                                       int64_t ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int k = threadIdx.x; k < RS_TILE; k += blockDim.x) {
+        int64_t i = base + k;
+        if (i < N) atomicAdd(&h[(unsigned)(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_W * 32) k_rs_scatter(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t N, int shift, const uint32_t *__restrict__ histoff,
+    int64_t ntiles)
+{
+    __shared__ uint32_t wcnt[RS_W][256];
+    __shared__ uint32_t goff[256];
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    for (int k = lane; k < 256; k += 32) wcnt[w][k] = 0;
+    goff[threadIdx.x] = histoff[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (RS_R * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t kk[RS_R];
+    uint32_t vv[RS_R];
+    uint32_t rk[RS_R];
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        int64_t i = base + r * 32 + lane;
+        bool valid = i < N;
+        uint64_t k = valid ? kin[i] : 0ull;
+        uint32_t v = valid ? vin[i] : 0u;
+        unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & lt);
+        uint32_t b = valid ? wcnt[w][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][d] = b + __popc(peers);
+        __syncwarp();
+        kk[r] = k;
+        vv[r] = v;
+        rk[r] = b + rank;
+    }
+    __syncthreads();
+    {
+        unsigned d = threadIdx.x;
+        uint32_t run = 0;
+        for (int ww = 0; ww < RS_W; ++ww) {
+            uint32_t c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < N) {
+            unsigned d = (unsigned)(kk[r] >> shift) & 255u;
+            uint32_t p = goff[d] + wcnt[w][d] + rk[r];
+            kout[p] = kk[r];
+            vout[p] = vv[r];
+        }
+    }
+}
+
+__global__ void k_gather(const double *__restrict__ pos, const double *__restrict__ mass,
+                         const uint32_t *__restrict__ idx, int64_t N, double *__restrict__ spos,
+                         double *__restrict__ smass)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    uint32_t i = idx[s];
+    spos[3 * s + 0] = pos[3 * (int64_t)i + 0];
+    spos[3 * s + 1] = pos[3 * (int64_t)i + 1];
+    spos[3 * s + 2] = pos[3 * (int64_t)i + 2];
+    smass[s] = mass[i];
+}
+
+// ---------------------------------------------------------------------------
+// Tree
+// ---------------------------------------------------------------------------
+// lcp[i] = lcp(key_{i-1}, key_i) (255 for i = 0); win[t] = lcp(key_t, key_{t+leaf_max}).
+__global__ void k_lcp(const uint64_t *__restrict__ key, int64_t N, int leaf_max,
+                      uint8_t *__restrict__ lcp, uint8_t *__restrict__ win)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint64_t k = key[i];
+    lcp[i] = i == 0 ? 255 : (uint8_t)key_lcp_levels(key[i - 1], k);
+    win[i] = (i + leaf_max < N) ? (uint8_t)key_lcp_levels(k, key[i + leaf_max]) : 0;
+}
+
+__global__ void k_leaflevel(const uint8_t *__restrict__ lcp, const uint8_t *__restrict__ win,
+                            int64_t N, int leaf_max, uint8_t *__restrict__ leaflev,
+                            uint32_t *__restrict__ ncell_i, int64_t *__restrict__ maxlev)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ll = 0;
+    if (i < N) {
+        int64_t t0 = i - leaf_max > 0 ? i - leaf_max : 0;
+        int64_t t1 = i < N - 1 - leaf_max ? i : N - 1 - leaf_max;
+        int dmax = -1;
+        for (int64_t t = t0; t <= t1; ++t) dmax = max(dmax, (int)win[t]);
+        ll = min(HOT_MAXLEVEL, dmax + 1);
+        leaflev[i] = (uint8_t)ll;
+        int d = (i == 0) ? -1 : (int)lcp[i];
+        ncell_i[i] = ll > d ? (uint32_t)(ll - d) : 0u;
+    }
+    int m = warp_max(ll);
+    if (lane_id() == 0 && m > 0) atomicMax((unsigned long long *)maxlev, (unsigned long long)m);
+}
+
+// First j in (i, N] whose key differs from key_i in the first `lev` digits.
+__device__ int64_t run_end(const uint64_t *__restrict__ key, int64_t N, int64_t i, int lev)
+{
+    const uint64_t ki = key[i];
+    int64_t lo = i, step = 1, hi;
+    // gallop
+    for (;;) {
+        int64_t j = i + step;
+        if (j >= N) {
+            hi = N;
+            break;
+        }
+        if (key_lcp_levels(ki, key[j]) < lev) {
+            hi = j;
+            break;
+        }
+        lo = j;
+        step <<= 1;
+    }
+    // invariant: key[lo] shares the prefix, hi is the first known non-sharer (or N)
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (key_lcp_levels(ki, key[mid]) >= lev)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return hi;
+}
+
+// First t in [0, i] whose key shares the first `lev` digits with key_i.
+__device__ int64_t run_start(const uint64_t *__restrict__ key, int64_t i, int lev)
+{
+    const uint64_t ki = key[i];
+    int64_t hi = i, step = 1, lo;
+    for (;;) {
+        int64_t j = i - step;
+        if (j < 0) {
+            lo = -1;
+            break;
+        }
+        if (key_lcp_levels(ki, key[j]) < lev) {
+            lo = j;
+            break;
+        }
+        hi = j;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (key_lcp_levels(ki, key[mid]) >= lev)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return hi;
+}
+
+__global__ void k_cells(const uint64_t *__restrict__ key, int64_t N, const uint8_t *__restrict__ lcp,
+                        const uint8_t *__restrict__ leaflev, const uint32_t *__restrict__ off,
+                        int64_t ncell, uint64_t *__restrict__ ckey, int32_t *__restrict__ clevel,
+                        int32_t *__restrict__ cbegin, int32_t *__restrict__ ccount,
+                        int32_t *__restrict__ cparent, int32_t *__restrict__ cend,
+                        unsigned *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int d = (i == 0) ? -1 : (int)lcp[i];
+    int ll = leaflev[i];
+    if (ll <= d) return;
+    const uint64_t ki = key[i];
+    int64_t c0 = off[i];
+    for (int lev = d + 1; lev <= ll; ++lev) {
+        int64_t c = c0 + (lev - d - 1);
+        if (c >= ncell) {
+            hot_flag(status, HOT_ST_INTERNAL);
+            return;
+        }
+        ckey[c] = ki >> (3 * (HOT_MAXLEVEL - lev));
+        clevel[c] = lev;
+        cbegin[c] = (int32_t)i;
+        int64_t e = run_end(key, N, i, lev);
+        ccount[c] = (int32_t)(e - i);
+        cend[c] = (int32_t)(e < N ? (int64_t)off[e] : ncell);
+        if (lev == 0) {
+            cparent[c] = -1;
+        } else if (lev > d + 1) {
+            cparent[c] = (int32_t)(c - 1);
+        } else {
+            // parent: the level-(lev-1) cell holding i, owned by the first particle t of that run
+            int64_t t = run_start(key, i, lev - 1);
+            int dt = (t == 0) ? -1 : (int)lcp[t];
+            cparent[c] = (int32_t)((int64_t)off[t] + (lev - 1 - dt - 1));
+        }
+    }
+}
+
+__global__ void k_link(const uint64_t *__restrict__ ckey, const int32_t *__restrict__ cparent,
+                       const int32_t *__restrict__ clevel, int64_t ncell, int32_t *__restrict__ child8,
+                       int32_t *__restrict__ cnchild, int32_t *__restrict__ lvlcnt)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    atomicAdd(&lvlcnt[clevel[c]], 1);
+    int32_t p = cparent[c];
+    if (p < 0) return;
+    child8[8 * (int64_t)p + (int)(ckey[c] & 7u)] = (int32_t)c;
+    atomicAdd(&cnchild[p], 1);
+}
+
+// level offsets (exclusive scan of 22 counts) on one thread, then scatter.
+__global__ void k_level_off(int32_t *lvlcnt, int64_t *levoff, int64_t *sizes)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t run = 0;
+    for (int l = 0; l <= HOT_MAXLEVEL; ++l) {
+        levoff[l] = run;
+        run += lvlcnt[l];
+        lvlcnt[l] = 0;  // reused as cursor
+    }
+    levoff[HOT_MAXLEVEL + 1] = run;
+    (void)sizes;
+}
+
+__global__ void k_level_scatter(const int32_t *__restrict__ clevel, int64_t ncell,
+                                const int64_t *__restrict__ levoff, int32_t *cursor,
+                                int32_t *__restrict__ level_cells)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int l = clevel[c];
+    int32_t k = atomicAdd(&cursor[l], 1);
+    level_cells[levoff[l] + k] = (int32_t)c;
+}
+
+__device__ __forceinline__ uint64_t hash64(uint64_t k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__global__ void k_hash_insert(const uint64_t *__restrict__ ckey, int64_t ncell, uint64_t *hkey,
+                              int32_t *hval, uint64_t mask, unsigned *status)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    uint64_t k = ckey[c];
+    uint64_t h = hash64(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long prev =
+            atomicCAS((unsigned long long *)&hkey[h], 0ull, (unsigned long long)k);
+        if (prev == 0ull || prev == k) {
+            hval[h] = (int32_t)c;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    hot_flag(status, HOT_ST_HASH);
+}
+
+__global__ void k_hash_lookup(const uint64_t *__restrict__ q, int64_t n, const uint64_t *__restrict__ hkey,
+                              const int32_t *__restrict__ hval, uint64_t mask, int32_t *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = q[i];
+    int32_t r = -1;
+    if (k != 0ull) {
+        uint64_t h = hash64(k) & mask;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+            uint64_t s = hkey[h];
+            if (s == k) {
+                r = hval[h];
+                break;
+            }
+            if (s == 0ull) break;
+            h = (h + 1) & mask;
+        }
+    }
+    out[i] = r;
+}
+
+// Sink groups: topmost cells that are leaves or hold <= group_max particles.
+__global__ void k_group_flag(const int32_t *__restrict__ ccount, const int32_t *__restrict__ cparent,
+                             const int32_t *__restrict__ cnchild, int64_t ncell, int group_max,
+                             uint32_t *__restrict__ flag, int64_t *__restrict__ nleaf)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool leaf = false;
+    if (c < ncell) {
+        leaf = cnchild[c] == 0;
+        bool small = leaf || ccount[c] <= group_max;
+        int32_t p = cparent[c];
+        bool top = p < 0 || ccount[p] > group_max;
+        flag[c] = (small && top) ? 1u : 0u;
+    }
+    unsigned b = __ballot_sync(0xffffffffu, leaf);
+    if (lane_id() == 0 && b) atomicAdd((unsigned long long *)nleaf, (unsigned long long)__popc(b));
+}
+
+__global__ void k_group_write(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ goff,
+                              int64_t ncell, int32_t *__restrict__ gcell)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    if (flag[c]) gcell[goff[c]] = (int32_t)c;
+}
+
+// Group centre = centre of the sinks' bounding box; Delta_max = max |x - g|, evaluated
+// with explicit roundings ((dx*dx + dy*dy) + dz*dz, no contraction, IEEE sqrt).
+__global__ void k_group_geom(const int32_t *__restrict__ gcell, const uint32_t *__restrict__ ngroup_p,
+                             const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
+                             const double *__restrict__ spos, double *__restrict__ gcen,
+                             double *__restrict__ gdmax)
+{
+    int64_t ngroup = *ngroup_p;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned lane = lane_id();
+    for (int64_t g = warp; g < ngroup; g += nw) {
+        int32_t c = gcell[g];
+        int64_t b = cbegin[c], n = ccount[c];
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t s = b + lane; s < b + n; s += 32)
+            for (int d = 0; d < 3; ++d) {
+                double x = spos[3 * s + d];
+                lo[d] = fmin(lo[d], x);
+                hi[d] = fmax(hi[d], x);
+            }
+        double cen[3];
+        for (int d = 0; d < 3; ++d) cen[d] = __dmul_rn(__dadd_rn(warp_min(lo[d]), warp_max(hi[d])), 0.5);
+        double r2m = 0.0;
+        for (int64_t s = b + lane; s < b + n; s += 32) {
+            double dx = __dsub_rn(spos[3 * s + 0], cen[0]);
+            double dy = __dsub_rn(spos[3 * s + 1], cen[1]);
+            double dz = __dsub_rn(spos[3 * s + 2], cen[2]);
+            double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            r2m = fmax(r2m, r2);
+        }
+        r2m = warp_max(r2m);
+        if (lane == 0) {
+            for (int d = 0; d < 3; ++d) gcen[3 * g + d] = cen[d];
+            gdmax[g] = __dsqrt_rn(r2m);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
+{
+    cudaStream_t s = c->st;
+    const int leaf_max = c->prm.leaf_max;
+    c->N = N;
+    c->stage = 0;
+    hot_tic(c, 0);
+    // bbox + keys
+    int nbb = c->nsm * 4;
+    HOT_CK(c->part.ensure(6 * (size_t)nbb, s));
+    HOT_CK(c->frame.ensure(8, s));
+    HOT_CK(c->key.ensure(N, s));
+    HOT_CK(c->key2.ensure(N, s));
+    HOT_CK(c->idx.ensure(N, s));
+    HOT_CK(c->idx2.ensure(N, s));
+    k_bbox_part<<<nbb, BT, 0, s>>>(pos, mass, N, c->part.p, c->d_status);
+    k_bbox_final<<<1, 32, 0, s>>>(c->part.p, nbb, c->frame.p);
+    k_keys<<<hot_blocks(N, BT), BT, 0, s>>>(pos, N, c->frame.p, c->key.p, c->idx.p);
+    // radix sort, 8 passes of 8 bits
+    int64_t ntiles = (N + RS_TILE - 1) / RS_TILE;
+    HOT_CK(c->hist.ensure(256 * (size_t)ntiles + 1, s));
+    HOT_CK(c->histoff.ensure(256 * (size_t)ntiles + 1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(N + 256 * ntiles + 64), s));
+    uint64_t *ka = c->key.p, *kb = c->key2.p;
+    uint32_t *va = c->idx.p, *vb = c->idx2.p;
+    for (int pass = 0; pass < 8; ++pass) {
+        int shift = 8 * pass;
+        k_rs_hist<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, N, shift, c->hist.p, ntiles);
+        int r = hot_scan_u32_to_u32(c->hist.p, c->histoff.p, 256 * ntiles, c->scan_tmp.p, s);
+        if (r) return r;
+        k_rs_scatter<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, va, kb, vb, N, shift, c->histoff.p, ntiles);
+        uint64_t *tk = ka;
+        ka = kb;
+        kb = tk;
+        uint32_t *tv = va;
+        va = vb;
+        vb = tv;
+    }
+    // 8 passes: sorted data is back in key/idx
+    HOT_CK(c->spos.ensure(3 * (size_t)N, s));
+    HOT_CK(c->smass.ensure(N, s));
+    k_gather<<<hot_blocks(N, BT), BT, 0, s>>>(pos, mass, c->idx.p, N, c->spos.p, c->smass.p);
+    hot_toc(c, 0);
+
+    hot_tic(c, 1);
+    HOT_CK(c->lcp.ensure(N, s));
+    HOT_CK(c->leaflev.ensure(N, s));
+    HOT_CK(c->ncell_i.ensure(N + 1, s));
+    HOT_CK(c->cell_off.ensure(N + 1, s));
+    HOT_CK(c->sizes.ensure(64, s));
+    HOT_CK(cudaMemsetAsync(c->sizes.p, 0, 64 * sizeof(int64_t), s));
+    uint8_t *win = (uint8_t *)c->key2.p;  // scratch: key2 is free after the sort
+    k_lcp<<<hot_blocks(N, BT), BT, 0, s>>>(c->key.p, N, leaf_max, c->lcp.p, win);
+    k_leaflevel<<<hot_blocks(N, BT), BT, 0, s>>>(c->lcp.p, win, N, leaf_max, c->leaflev.p, c->ncell_i.p,
+                                                   c->sizes.p + 0);
+    int r = hot_scan_u32_to_u32(c->ncell_i.p, c->cell_off.p, N, c->scan_tmp.p, s);
+    if (r) return r;
+    // sizes[1] = ncell (cell_off[N])
+    HOT_CK(cudaMemcpyAsync(c->sizes.p + 1, c->cell_off.p + N, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    int64_t hs[2] = {0, 0};
+    HOT_CK(cudaMemcpyAsync(hs, c->sizes.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HOT_CK(cudaStreamSynchronize(s));
+    {
+        int e = hot_sync_status(c);
+        if (e) return e;
+    }
+    c->maxlevel = hs[0];
+    int64_t ncell = (int64_t)(uint32_t)hs[1];
+    c->ncell = ncell;
+    HOT_CK(c->ckey.ensure(ncell, s));
+    HOT_CK(c->clevel.ensure(ncell, s));
+    HOT_CK(c->cbegin.ensure(ncell, s));
+    HOT_CK(c->ccount.ensure(ncell, s));
+    HOT_CK(c->cparent.ensure(ncell, s));
+    HOT_CK(c->cend.ensure(ncell, s));
+    HOT_CK(c->child8.ensure(8 * (size_t)ncell, s));
+    HOT_CK(c->cnchild.ensure(ncell, s));
+    HOT_CK(c->level_cells.ensure(ncell, s));
+    HOT_CK(c->gflag.ensure(ncell + 1, s));
+    HOT_CK(c->goff.ensure(ncell + 1, s));
+    HOT_CK(c->gcell.ensure(ncell, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ncell + N + 256 * ntiles + 64), s));
+    k_cells<<<hot_blocks(N, BT), BT, 0, s>>>(c->key.p, N, c->lcp.p, c->leaflev.p, c->cell_off.p, ncell,
+                                              c->ckey.p, c->clevel.p, c->cbegin.p, c->ccount.p, c->cparent.p,
+                                              c->cend.p, c->d_status);
+    HOT_CK(cudaMemsetAsync(c->child8.p, 0xff, 8 * sizeof(int32_t) * (size_t)ncell, s));
+    HOT_CK(cudaMemsetAsync(c->cnchild.p, 0, sizeof(int32_t) * (size_t)ncell, s));
+    int32_t *lvlcnt = (int32_t *)(c->sizes.p + 8);     // 24 int32 in sizes[8..20)
+    int64_t *levoff = c->sizes.p + 24;                 // 23 int64 in sizes[24..47)
+    k_link<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ckey.p, c->cparent.p, c->clevel.p, ncell, c->child8.p,
+                                                 c->cnchild.p, lvlcnt);
+    k_level_off<<<1, 32, 0, s>>>(lvlcnt, levoff, c->sizes.p);
+    k_level_scatter<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->clevel.p, ncell, levoff, lvlcnt, c->level_cells.p);
+    // hash table, load <= 1/2
+    uint64_t hcap = 1024;
+    while (hcap < 2 * (uint64_t)ncell) hcap <<= 1;
+    c->hcap = hcap;
+    HOT_CK(c->hkey.ensure(hcap, s));
+    HOT_CK(c->hval.ensure(hcap, s));
+    HOT_CK(cudaMemsetAsync(c->hkey.p, 0, sizeof(uint64_t) * hcap, s));
+    k_hash_insert<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ckey.p, ncell, c->hkey.p, c->hval.p, hcap - 1,
+                                                        c->d_status);
+    // groups
+    k_group_flag<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ccount.p, c->cparent.p, c->cnchild.p, ncell,
+                                                       c->prm.group_max, c->gflag.p, c->sizes.p + 2);
+    r = hot_scan_u32_to_u32(c->gflag.p, c->goff.p, ncell, c->scan_tmp.p, s);
+    if (r) return r;
+    k_group_write<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->gflag.p, c->goff.p, ncell, c->gcell.p);
+    HOT_CK(c->gcen.ensure(3 * (size_t)ncell, s));
+    HOT_CK(c->gdmax.ensure(ncell, s));
+    k_group_geom<<<c->nsm * 8, 256, 0, s>>>(c->gcell.p, c->goff.p + ncell, c->cbegin.p, c->ccount.p,
+                                             c->spos.p, c->gcen.p, c->gdmax.p);
+    HOT_CK(cudaMemcpyAsync(c->sizes.p + 3, c->goff.p + ncell, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    hot_toc(c, 1);
+    int64_t hs2[48];
+    HOT_CK(cudaMemcpyAsync(hs2, c->sizes.p, 48 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HOT_CK(cudaStreamSynchronize(s));
+    {
+        int e = hot_sync_status(c);
+        if (e) return e;
+    }
+    c->nleaf = hs2[2];
+    c->ngroup = (int64_t)(uint32_t)hs2[3];
+    c->level_off.assign(HOT_MAXLEVEL + 2, 0);
+    for (int l = 0; l <= HOT_MAXLEVEL + 1; ++l) c->level_off[l] = hs2[24 + l];
+    c->stage = 1;
+    return HOT_OK;
+}
+
+int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
+{
+    cudaStream_t s = c->st;
+    uint64_t *dk = nullptr;
+    int32_t *di = nullptr;
+    HOT_CK(cudaMallocAsync((void **)&dk, sizeof(uint64_t) * (n > 0 ? n : 1), s));
+    HOT_CK(cudaMallocAsync((void **)&di, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    HOT_CK(cudaMemcpyAsync(dk, keys, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    k_hash_lookup<<<hot_blocks(n, BT), BT, 0, s>>>(dk, n, c->hkey.p, c->hval.p, c->hcap - 1, di);
+    HOT_CK(cudaMemcpyAsync(idx, di, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(dk, s);
+    cudaFreeAsync(di, s);
+    HOT_CK(cudaStreamSynchronize(s));
+    return HOT_OK;
+}

@@ -1,0 +1,227 @@
+// hot_common.cuh -- context, device buffers, status word and shared device helpers
+// of the hashed oct-tree library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "hot.h"
+
+// ---------------------------------------------------------------------------
+// Status word bits (device side).  Kernels atomicOr a bit and skip the access
+// that would have gone wrong; the host turns bits into HOT_E* codes.
+// ---------------------------------------------------------------------------
+#define HOT_ST_INPUT 1u      // non-finite position/mass
+#define HOT_ST_FRONTIER 2u   // traversal frontier scratch too small
+#define HOT_ST_HASH 4u       // hash probe limit reached
+#define HOT_ST_TIMEOUT 8u    // a bounded wait gave up
+#define HOT_ST_INTERNAL 16u  // a consistency check failed (index out of range)
+
+#define HOT_MAXLEVEL 21
+
+// ---------------------------------------------------------------------------
+// Grow-only device buffer, stream-ordered allocation.
+// ---------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t n, cudaStream_t s)
+    {
+        if (n <= cap && p) return cudaSuccess;
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        cap = 0;
+        size_t want = n + n / 8 + 64;
+        cudaError_t e = cudaMallocAsync((void **)&p, want * sizeof(T), s);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release(cudaStream_t s)
+    {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+enum { ST_TIMING_EVENTS = 14 };
+
+struct hot_ctx {
+    hot_params prm;
+    cudaStream_t st = nullptr;
+    int dev = 0, nsm = 0;
+    int stage = 0;  // 0 created, 1 tree, 2 moments, 3 lists
+    int64_t N = 0;
+
+    // keys and sort
+    DBuf<double> part;     // bbox partials
+    DBuf<double> frame;    // lo[3], L, scale
+    DBuf<uint64_t> key, key2;
+    DBuf<uint32_t> idx, idx2;
+    DBuf<uint32_t> hist, histoff;
+    DBuf<uint64_t> scan_tmp;
+    DBuf<double> spos, smass;  // sorted copies [N][3], [N]
+
+    // tree
+    DBuf<uint8_t> lcp, leaflev;
+    DBuf<uint32_t> ncell_i, cell_off;
+    int64_t ncell = 0, nleaf = 0, maxlevel = 0, ngroup = 0;
+    DBuf<uint64_t> ckey;
+    DBuf<int32_t> clevel, cbegin, ccount, cparent, cend, child8, cnchild;
+    DBuf<int32_t> level_cells;
+    std::vector<int64_t> level_off;  // host, HOT_MAXLEVEL + 2 entries
+    DBuf<uint64_t> hkey;
+    DBuf<int32_t> hval;
+    uint64_t hcap = 0;
+    DBuf<uint32_t> gflag, goff;
+    DBuf<int32_t> gcell;
+    DBuf<double> gcen, gdmax;
+    DBuf<int64_t> sizes;  // device scratch for counts read back at sync points
+
+    // moments
+    int p_mom = -1;
+    int reclen = 0;
+    DBuf<double> cmass, ccom, cmom, cbmax, cB1, cB2;
+    DBuf<uint32_t> item_off;
+    DBuf<int32_t> item_cell;
+    DBuf<double> item_part;
+    DBuf<float> rec32;
+    DBuf<double> rec64;
+    DBuf<float4> prel;
+
+    // lists
+    double tol_lists = 0;
+    int64_t n_m2p = 0, n_p2p = 0, n_pairs = 0, n_m2p_int = 0;
+    DBuf<uint32_t> cnt_m2p, cnt_p2p;
+    DBuf<int64_t> off_m2p, off_p2p;
+    DBuf<int32_t> l_m2p, l_p2p;
+    DBuf<int32_t> trav_scratch;
+    int trav_cap = 2048;
+    DBuf<int64_t> pairs_per_group;
+
+    // status
+    unsigned *d_status = nullptr;
+    unsigned *h_status = nullptr;
+
+    // timing: pairs of events per stage
+    cudaEvent_t ev[ST_TIMING_EVENTS] = {};
+    float stage_ms[6] = {0, 0, 0, 0, 0, 0};
+    bool ev_used[7] = {false, false, false, false, false, false, false};
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+#define HOT_CK(call)                                  \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            return (e_ == cudaErrorMemoryAllocation) \
+                       ? HOT_ENOMEM                   \
+                       : HOT_ECUDA;                   \
+        }                                             \
+    } while (0)
+
+static inline int hot_blocks(int64_t n, int threads, int cap = 1 << 30)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// Stage timing: start/stop a CUDA-event pair on the context stream.
+static inline void hot_tic(hot_ctx *c, int stage) { cudaEventRecord(c->ev[2 * stage], c->st); }
+static inline void hot_toc(hot_ctx *c, int stage)
+{
+    cudaEventRecord(c->ev[2 * stage + 1], c->st);
+    c->ev_used[stage] = true;
+}
+
+// Read the status word (synchronises) and clear it.
+int hot_sync_status(hot_ctx *c);
+
+// Exclusive scan of n values (In) into out[0..n] (Out); out[n] = total.
+// Device-wide, deterministic.  tmp must hold hot_scan_tmp_elems(n) uint64.
+size_t hot_scan_tmp_elems(int64_t n);
+int hot_scan_u32_to_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *tmp,
+                        cudaStream_t s);
+int hot_scan_u32_to_i64(const uint32_t *in, int64_t *out, int64_t n, uint64_t *tmp,
+                        cudaStream_t s);
+
+// Stages implemented in separate translation units.
+int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N);
+int hot_impl_moments(hot_ctx *c, int p);
+int hot_impl_traverse(hot_ctx *c, double tol);
+int hot_impl_forces(hot_ctx *c, double *acc, double *pot);
+int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos,
+                     double *g_mass);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ float hot_rsqrt(float u) { return rsqrtf(u); }
+__device__ __forceinline__ double hot_rsqrt(double u) { return rsqrt(u); }
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// Inclusive warp scan.
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    unsigned l = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (l >= (unsigned)o) v += u;
+    }
+    return v;
+}
+
+// Number of leading equal octal digits (levels) of two particle keys (0..21).
+__device__ __forceinline__ int key_lcp_levels(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return HOT_MAXLEVEL;
+    return (__clzll((long long)x) - 1) / 3;
+}
+
+__device__ __forceinline__ void hot_flag(unsigned *status, unsigned bit) { atomicOr(status, bit); }
+
+#endif  // __CUDACC__

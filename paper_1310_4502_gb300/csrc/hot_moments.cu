@@ -1,0 +1,378 @@
+// hot_moments.cu -- cell moments (Eq. "moment tensor": M_a(z) = sum m (x - z)^a about the
+// centre of mass z), built as P2M at the leaves and exact binomial translation (M2M,
+// "expand M(y0 + Delta) in powers of Delta and recollect") level by level upwards, all in
+// float64; the acceptance-test aggregates b_max = max |x - z| and B_n = sum m |x - z|^n
+// (n = p+1, p+2) taken from the particles; and the per-cell interaction records.
+#include "hot_common.cuh"
+#include "generated.cuh"
+
+namespace {
+
+constexpr int MW = 4;  // warps per block
+constexpr int CHUNK = 2048;  // particles per aggregate work item
+
+// ---------------------------------------------------------------------------
+// P2M at leaves: one warp per leaf.  Also b_max, B_{p+1}, B_{p+2} of the leaf and
+// the leaf-relative single-precision particle copy used by the P2P interactions.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
+    const int32_t *__restrict__ cnchild, int64_t ncell, const double *__restrict__ spos,
+    const double *__restrict__ smass, double *__restrict__ cmass, double *__restrict__ ccom,
+    double *__restrict__ cmom, double *__restrict__ cbmax, double *__restrict__ cB1,
+    double *__restrict__ cB2, float4 *__restrict__ prel)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    __shared__ double pw[MW][32][3][P + 1];
+    __shared__ double pm[MW][32];
+    __shared__ unsigned char mi[NC][3];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        mi[k][0] = hot_midx[k][0];
+        mi[k][1] = hot_midx[k][1];
+        mi[k][2] = hot_midx[k][2];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * MW;
+    for (int64_t c = (int64_t)blockIdx.x * MW + w; c < ncell; c += nw) {
+        if (cnchild[c] != 0) continue;
+        const int64_t b = cbegin[c], n = ccount[c];
+        double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+        for (int64_t s = b + lane; s < b + n; s += 32) {
+            double ms = smass[s];
+            m += ms;
+            mx += ms * spos[3 * s + 0];
+            my += ms * spos[3 * s + 1];
+            mz += ms * spos[3 * s + 2];
+        }
+        m = warp_sum(m);
+        mx = warp_sum(mx);
+        my = warp_sum(my);
+        mz = warp_sum(mz);
+        const double z[3] = {mx / m, my / m, mz / m};
+        double acc[(NC + 31) / 32];
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = 0.0;
+        double bmax = 0.0, B1 = 0.0, B2 = 0.0;
+        for (int64_t s0 = b; s0 < b + n; s0 += 32) {
+            int64_t s = s0 + lane;
+            bool valid = s < b + n;
+            double d[3] = {0.0, 0.0, 0.0}, ms = 0.0;
+            if (valid) {
+                ms = smass[s];
+                for (int e = 0; e < 3; ++e) d[e] = spos[3 * s + e] - z[e];
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                bmax = fmax(bmax, r);
+                double rp = 1.0;
+                for (int q = 0; q < P + 1; ++q) rp *= r;
+                B1 += ms * rp;
+                B2 += ms * rp * r;
+                prel[s] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)ms);
+            }
+            pm[w][lane] = ms;
+            for (int e = 0; e < 3; ++e) {
+                double v = 1.0;
+                for (int q = 0; q <= P; ++q) {
+                    pw[w][lane][e][q] = v;
+                    v *= d[e];
+                }
+            }
+            __syncwarp();
+            int cnt = (int)((b + n - s0) < 32 ? (b + n - s0) : 32);
+#pragma unroll
+            for (int q = 0; q < (NC + 31) / 32; ++q) {
+                int a = lane + 32 * q;
+                if (a < NC) {
+                    int ax = mi[a][0], ay = mi[a][1], az = mi[a][2];
+                    double t = 0.0;
+                    for (int j = 0; j < cnt; ++j)
+                        t += pm[w][j] * pw[w][j][0][ax] * pw[w][j][1][ay] * pw[w][j][2][az];
+                    acc[q] += t;
+                }
+            }
+            __syncwarp();
+        }
+        bmax = warp_max(bmax);
+        B1 = warp_sum(B1);
+        B2 = warp_sum(B2);
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) {
+            int a = lane + 32 * q;
+            if (a < NC) cmom[c * NC + a] = acc[q];
+        }
+        if (lane == 0) {
+            cmass[c] = m;
+            ccom[3 * c + 0] = z[0];
+            ccom[3 * c + 1] = z[1];
+            ccom[3 * c + 2] = z[2];
+            cbmax[c] = bmax;
+            cB1[c] = B1;
+            cB2[c] = B2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M for the inner cells of one level: one warp per cell, lanes over components.
+// M_a(z) = sum_children sum_{b <= a} C(a,b) M_b(z_ch) (z_ch - z)^{a-b}
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(MW * 32) k_m2m_level(
+    const int32_t *__restrict__ cells, int64_t ncells_lvl, const int32_t *__restrict__ child8,
+    const int32_t *__restrict__ cnchild, double *__restrict__ cmass, double *__restrict__ ccom,
+    double *__restrict__ cmom)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    __shared__ double sd[MW][NC];   // (z_ch - z)^g
+    __shared__ double sm[MW][NC];   // child moments
+    __shared__ unsigned char mi[NC][3];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        mi[k][0] = hot_midx[k][0];
+        mi[k][1] = hot_midx[k][1];
+        mi[k][2] = hot_midx[k][2];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * MW;
+    for (int64_t q0 = (int64_t)blockIdx.x * MW + w; q0 < ncells_lvl; q0 += nw) {
+        const int32_t c = cells[q0];
+        if (cnchild[c] == 0) continue;
+        int32_t ch[8];
+        double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            ch[o] = child8[8 * (int64_t)c + o];
+            if (ch[o] >= 0) {
+                double mc = cmass[ch[o]];
+                m += mc;
+                mx += mc * ccom[3 * (int64_t)ch[o] + 0];
+                my += mc * ccom[3 * (int64_t)ch[o] + 1];
+                mz += mc * ccom[3 * (int64_t)ch[o] + 2];
+            }
+        }
+        const double z[3] = {mx / m, my / m, mz / m};
+        double acc[(NC + 31) / 32];
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = 0.0;
+        for (int o = 0; o < 8; ++o) {
+            const int32_t k = ch[o];
+            if (k < 0) continue;
+            const double d[3] = {ccom[3 * (int64_t)k + 0] - z[0], ccom[3 * (int64_t)k + 1] - z[1],
+                                 ccom[3 * (int64_t)k + 2] - z[2]};
+            for (int g = lane; g < NC; g += 32) {
+                double v = 1.0;
+                for (int e = 0; e < 3; ++e)
+                    for (int t = 0; t < mi[g][e]; ++t) v *= d[e];
+                sd[w][g] = v;
+                sm[w][g] = cmom[(int64_t)k * NC + g];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < (NC + 31) / 32; ++q) {
+                int a = lane + 32 * q;
+                if (a < NC) {
+                    double t = 0.0;
+                    for (int j = m2m_start[a]; j < m2m_start[a + 1]; ++j)
+                        t += m2m_coef[j] * sm[w][m2m_beta[j]] * sd[w][m2m_gamma[j]];
+                    acc[q] += t;
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) {
+            int a = lane + 32 * q;
+            if (a < NC) cmom[(int64_t)c * NC + a] = acc[q];
+        }
+        if (lane == 0) {
+            cmass[c] = m;
+            ccom[3 * (int64_t)c + 0] = z[0];
+            ccom[3 * (int64_t)c + 1] = z[1];
+            ccom[3 * (int64_t)c + 2] = z[2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Acceptance-test aggregates of inner cells from their particles, split into
+// work items of at most CHUNK particles so that large cells spread over the GPU.
+// ---------------------------------------------------------------------------
+__global__ void k_item_count(const int32_t *__restrict__ ccount, const int32_t *__restrict__ cnchild,
+                             int64_t ncell, uint32_t *__restrict__ nitem)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    nitem[c] = cnchild[c] == 0 ? 0u : (uint32_t)((ccount[c] + CHUNK - 1) / CHUNK);
+}
+
+__global__ void k_item_cells(const uint32_t *__restrict__ off, int64_t ncell, int32_t *__restrict__ item_cell)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    for (uint32_t k = off[c]; k < off[c + 1]; ++k) item_cell[k] = (int32_t)c;
+}
+
+template <int P>
+__global__ void __launch_bounds__(MW * 32) k_item_part(
+    const int32_t *__restrict__ item_cell, const uint32_t *__restrict__ off,
+    const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ cbegin,
+    const int32_t *__restrict__ ccount, const double *__restrict__ ccom,
+    const double *__restrict__ spos, const double *__restrict__ smass, double *__restrict__ part)
+{
+    const int64_t nitem = *nitem_p;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * MW;
+    for (int64_t it = (int64_t)blockIdx.x * MW + (threadIdx.x >> 5); it < nitem; it += nw) {
+        const int32_t c = item_cell[it];
+        const int64_t k = it - off[c];
+        const int64_t b = cbegin[c] + k * CHUNK;
+        const int64_t e0 = cbegin[c] + (int64_t)ccount[c];
+        const int64_t e = b + CHUNK < e0 ? b + CHUNK : e0;
+        const double z0 = ccom[3 * (int64_t)c + 0], z1 = ccom[3 * (int64_t)c + 1], z2 = ccom[3 * (int64_t)c + 2];
+        double bmax = 0.0, B1 = 0.0, B2 = 0.0;
+        for (int64_t s = b + lane; s < e; s += 32) {
+            double dx = spos[3 * s + 0] - z0, dy = spos[3 * s + 1] - z1, dz = spos[3 * s + 2] - z2;
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            bmax = fmax(bmax, r);
+            double rp = 1.0;
+#pragma unroll
+            for (int q = 0; q < P + 1; ++q) rp *= r;
+            double ms = smass[s];
+            B1 += ms * rp;
+            B2 += ms * rp * r;
+        }
+        bmax = warp_max(bmax);
+        B1 = warp_sum(B1);
+        B2 = warp_sum(B2);
+        if (lane == 0) {
+            part[3 * it + 0] = bmax;
+            part[3 * it + 1] = B1;
+            part[3 * it + 2] = B2;
+        }
+    }
+}
+
+__global__ void k_item_combine(const uint32_t *__restrict__ off, const int32_t *__restrict__ cnchild,
+                               int64_t ncell, const double *__restrict__ part, double *__restrict__ cbmax,
+                               double *__restrict__ cB1, double *__restrict__ cB2)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell || cnchild[c] == 0) return;
+    double bmax = 0.0, B1 = 0.0, B2 = 0.0;
+    for (uint32_t k = off[c]; k < off[c + 1]; ++k) {
+        bmax = fmax(bmax, part[3 * (int64_t)k + 0]);
+        B1 += part[3 * (int64_t)k + 1];
+        B2 += part[3 * (int64_t)k + 2];
+    }
+    cbmax[c] = bmax;
+    cB1[c] = B1;
+    cB2[c] = B2;
+}
+
+// ---------------------------------------------------------------------------
+// Interaction records: scale s = power of two >= b_max (the cell's size when
+// b_max = 0), so that single-precision coefficients stay O(1).
+// ---------------------------------------------------------------------------
+template <int P, class T>
+__global__ void k_records(const double *__restrict__ cmom, const double *__restrict__ cbmax,
+                          const int32_t *__restrict__ clevel, int64_t ncell, const double *__restrict__ frame,
+                          double G, double eps, int reclen, T *__restrict__ rec)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double L = frame[3];
+    double b = cbmax[c];
+    int e;
+    double inv_s;
+    if (b > 0.0) {
+        frexp(b, &e);
+        inv_s = ldexp(1.0, -e);
+    } else {
+        frexp(L, &e);
+        inv_s = ldexp(1.0, clevel[c] - e);
+    }
+    m2p_record<P, T>(cmom + c * NC, inv_s, G, eps, rec + c * (int64_t)reclen);
+}
+
+template <int P>
+int moments_p(hot_ctx *c)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    cudaStream_t s = c->st;
+    const int64_t ncell = c->ncell, N = c->N;
+    HOT_CK(c->cmass.ensure(ncell, s));
+    HOT_CK(c->ccom.ensure(3 * (size_t)ncell, s));
+    HOT_CK(c->cmom.ensure((size_t)NC * ncell, s));
+    HOT_CK(c->cbmax.ensure(ncell, s));
+    HOT_CK(c->cB1.ensure(ncell, s));
+    HOT_CK(c->cB2.ensure(ncell, s));
+    HOT_CK(c->prel.ensure(N, s));
+    const int grid = c->nsm * 8;
+    k_p2m_leaf<P><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
+                                           c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
+                                           c->cB1.p, c->cB2.p, c->prel.p);
+    for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
+        int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
+        if (n <= 0) continue;
+        int blocks = hot_blocks(n, MW, c->nsm * 16);
+        k_m2m_level<P><<<blocks, MW * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                  c->cmass.p, c->ccom.p, c->cmom.p);
+    }
+    // aggregates of inner cells
+    const int64_t max_items = ncell + N * (c->maxlevel + 1) / CHUNK + 1;
+    HOT_CK(c->item_off.ensure(ncell + 1, s));
+    HOT_CK(c->item_cell.ensure(max_items, s));
+    HOT_CK(c->item_part.ensure(3 * (size_t)max_items, s));
+    HOT_CK(c->gflag.ensure(ncell + 1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ncell + 64), s));
+    k_item_count<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->ccount.p, c->cnchild.p, ncell, c->gflag.p);
+    int r = hot_scan_u32_to_u32(c->gflag.p, c->item_off.p, ncell, c->scan_tmp.p, s);
+    if (r) return r;
+    k_item_cells<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, ncell, c->item_cell.p);
+    k_item_part<P><<<c->nsm * 16, MW * 32, 0, s>>>(c->item_cell.p, c->item_off.p, c->item_off.p + ncell,
+                                                   c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p, c->smass.p,
+                                                   c->item_part.p);
+    k_item_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
+                                                          c->cbmax.p, c->cB1.p, c->cB2.p);
+    // records
+    const int reclen = HOT_REC_LEN[P];
+    c->reclen = reclen;
+    if (c->prm.precision == HOT_FP64) {
+        HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
+        k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+                                                                    c->prm.G, c->prm.eps, reclen, c->rec64.p);
+    } else {
+        HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
+        k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+                                                                   c->prm.G, c->prm.eps, reclen, c->rec32.p);
+    }
+    return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
+}
+
+}  // namespace
+
+int hot_impl_moments(hot_ctx *c, int p)
+{
+    hot_tic(c, 2);
+    int r;
+    switch (p) {
+        case 0: r = moments_p<0>(c); break;
+        case 1: r = moments_p<1>(c); break;
+        case 2: r = moments_p<2>(c); break;
+        case 3: r = moments_p<3>(c); break;
+        case 4: r = moments_p<4>(c); break;
+        case 5: r = moments_p<5>(c); break;
+        case 6: r = moments_p<6>(c); break;
+        default: return HOT_EINVAL;
+    }
+    hot_toc(c, 2);
+    if (r == HOT_OK) {
+        c->p_mom = p;
+        c->stage = 2;
+    }
+    return r;
+}

@@ -1,0 +1,206 @@
+// hot_traverse.cu -- group-wise tree traversal into interaction lists (Warren 2013,
+// Sec. "Improving instruction-level parallelism": a sink cell's n particles share the
+// list of m source cells; Sec. "Multipole Error Bounds" and Fig. "mac": the acceptance
+// test bounds the absolute acceleration error of each cell-body interaction).
+//
+// One warp per sink group.  The warp tests 32 cells of the current frontier at a time;
+// accepted cells go to the M2P list, rejected leaves to the P2P list, and the children
+// of rejected inner cells form the next frontier (kept in per-warp global scratch).  A
+// count pass, a scan and an identical fill pass produce CSR lists.  Every decision
+// depends only on the (cell, group) pair, so the lists equal those of a depth-first
+// traversal as sets; within a list the order is by level, then by parent, then octant.
+#include "hot_common.cuh"
+
+namespace {
+
+constexpr int TW = 8;  // warps per block
+
+// Absolute acceleration error bound of one accepted cell at distance d (d > b):
+// E(d) = G/d^2 (1 - b/d)^-2 [(p+2) B_{p+1}/d^{p+1} - (p+1) B_{p+2}/d^{p+2}]
+__device__ __forceinline__ double mac_bound(double d, double b, double B1, double B2, int p, double G)
+{
+    double q = __dsub_rn(1.0, __ddiv_rn(b, d));
+    double dp1 = 1.0;
+    for (int i = 0; i < p + 1; ++i) dp1 = __dmul_rn(dp1, d);
+    double dp2 = __dmul_rn(dp1, d);
+    double t1 = __ddiv_rn(__dmul_rn((double)(p + 2), B1), dp1);
+    double t2 = __ddiv_rn(__dmul_rn((double)(p + 1), B2), dp2);
+    return __dmul_rn(__ddiv_rn(__ddiv_rn(G, __dmul_rn(d, d)), __dmul_rn(q, q)), __dsub_rn(t1, t2));
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(TW * 32) k_traverse(
+    int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
+    const double *__restrict__ gdmax, const uint64_t *__restrict__ ckey, const int32_t *__restrict__ clevel,
+    const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
+    const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
+    const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol,
+    int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
+    uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
+    int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
+    unsigned *__restrict__ status)
+{
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t *bufA = scratch + gw * 2 * (int64_t)cap;
+    int32_t *bufB = bufA + cap;
+    for (;;) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(work, 1u);
+        const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
+        if (g >= ngroup) break;
+        const int32_t gc = gcell[g];
+        const uint64_t gkey = ckey[gc];
+        const int glev = clevel[gc];
+        const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+        const double dmax = gdmax[g];
+        int64_t om = 0, op = 0;
+        if (FILL) {
+            om = off_m2p[g];
+            op = off_p2p[g];
+        }
+        int32_t *A = bufA, *B = bufB;
+        if (lane == 0) A[0] = 0;
+        __syncwarp();
+        int na = 1;
+        uint32_t nm = 0, np = 0;
+        uint64_t p2p_parts = 0;
+        bool overflow = false;
+        while (na > 0 && !overflow) {
+            int nb = 0;
+            for (int base = 0; base < na; base += 32) {
+                const int i = base + (int)lane;
+                const int32_t c = i < na ? A[i] : -1;
+                int kind = 0;  // 1 M2P, 2 P2P, 3 open
+                if (c >= 0) {
+                    const int lev = clevel[c];
+                    const bool leaf = cnchild[c] == 0;
+                    const bool anc = lev <= glev && (gkey >> (3 * (glev - lev))) == ckey[c];
+                    if (anc) {
+                        kind = leaf ? 2 : 3;
+                    } else {
+                        double dx = __dsub_rn(ccom[3 * (int64_t)c + 0], gx);
+                        double dy = __dsub_rn(ccom[3 * (int64_t)c + 1], gy);
+                        double dz = __dsub_rn(ccom[3 * (int64_t)c + 2], gz);
+                        double dist = __dsqrt_rn(
+                            __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+                        double d = __dsub_rn(dist, dmax);
+                        double b = cbmax[c];
+                        bool acc = false;
+                        if (d > b) acc = mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                        kind = acc ? 1 : (leaf ? 2 : 3);
+                    }
+                }
+                const unsigned mm = __ballot_sync(0xffffffffu, kind == 1);
+                const unsigned pm = __ballot_sync(0xffffffffu, kind == 2);
+                if (FILL) {
+                    if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = c;
+                    if (kind == 2) l_p2p[op + np + __popc(pm & lt)] = c;
+                } else if (kind == 2) {
+                    p2p_parts += (uint64_t)ccount[c];
+                }
+                nm += __popc(mm);
+                np += __popc(pm);
+                const int nch = kind == 3 ? cnchild[c] : 0;
+                const int incl = warp_incl_scan(nch);
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                if (nb + tot > cap) {
+                    overflow = true;
+                    break;
+                }
+                if (kind == 3) {
+                    int k = nb + incl - nch;
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const int32_t ch = child8[8 * (int64_t)c + o];
+                        if (ch >= 0) B[k++] = ch;
+                    }
+                }
+                nb += tot;
+            }
+            __syncwarp();
+            int32_t *t = A;
+            A = B;
+            B = t;
+            na = nb;
+        }
+        if (overflow) {
+            if (lane == 0) hot_flag(status, HOT_ST_FRONTIER);
+            nm = np = 0;
+        }
+        if (!FILL) {
+            p2p_parts = warp_sum(p2p_parts);
+            if (lane == 0) {
+                cnt_m2p[g] = nm;
+                cnt_p2p[g] = np;
+                const uint64_t ns = (uint64_t)ccount[gc];
+                atomicAdd(&stats[0], (unsigned long long)(ns * nm));
+                atomicAdd(&stats[1], (unsigned long long)(ns * p2p_parts));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int hot_impl_traverse(hot_ctx *c, double tol)
+{
+    cudaStream_t s = c->st;
+    const int64_t ng = c->ngroup;
+    hot_tic(c, 3);
+    HOT_CK(c->cnt_m2p.ensure(ng + 1, s));
+    HOT_CK(c->cnt_p2p.ensure(ng + 1, s));
+    HOT_CK(c->off_m2p.ensure(ng + 1, s));
+    HOT_CK(c->off_p2p.ensure(ng + 1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ng + c->ncell + c->N + 64), s));
+    const int blocks = c->nsm * 4;
+    const int64_t nwarps = (int64_t)blocks * TW;
+    unsigned *work = (unsigned *)(c->sizes.p + 50);
+    unsigned long long *stats = (unsigned long long *)(c->sizes.p + 52);
+    int64_t host[4];
+    for (int attempt = 0;; ++attempt) {
+        HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
+        HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
+        k_traverse<false><<<blocks, TW * 32, 0, s>>>(
+            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
+            work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, c->d_status);
+        int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
+        if (r) return r;
+        r = hot_scan_u32_to_i64(c->cnt_p2p.p, c->off_p2p.p, ng, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_CK(cudaMemcpyAsync(host + 0, c->off_m2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 1, c->off_p2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 2, stats, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaStreamSynchronize(s));
+        unsigned st = 0;
+        HOT_CK(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (st & HOT_ST_FRONTIER) {
+            HOT_CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s));
+            if (attempt >= 3) return HOT_EOVERFLOW;
+            c->trav_cap *= 4;
+            continue;
+        }
+        int e = hot_sync_status(c);
+        if (e) return e;
+        break;
+    }
+    c->n_m2p = host[0];
+    c->n_p2p = host[1];
+    c->n_m2p_int = host[2];
+    c->n_pairs = host[3];
+    HOT_CK(c->l_m2p.ensure(c->n_m2p + 1, s));
+    HOT_CK(c->l_p2p.ensure(c->n_p2p + 1, s));
+    HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
+    k_traverse<true><<<blocks, TW * 32, 0, s>>>(
+        ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
+        c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap, work,
+        nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, c->d_status);
+    hot_toc(c, 3);
+    if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
+    c->tol_lists = tol;
+    c->stage = 3;
+    return HOT_OK;
+}

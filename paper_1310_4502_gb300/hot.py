@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libhot.so, the C ABI declared in include/hot.h.
+
+Argument marshalling only: every stage of the force path runs in the CUDA
+kernels of libhot.so.  There is no fallback; if the library is missing or fails
+to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HOT_OK, HOT_EINVAL, HOT_ESTATE, HOT_ENOMEM, HOT_EOVERFLOW, HOT_ECUDA, HOT_EINPUT, HOT_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+HOT_FP32_MIXED, HOT_FP64 = 0, 1
+
+DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
+           CELL_PARENT=7, CELL_NCHILD=8, GROUP_CELL=9, GROUP_CENTRE=10, GROUP_DMAX=11, CELL_MASS=12,
+           CELL_COM=13, MOMENTS=14, CELL_BMAX=15, CELL_B1=16, CELL_B2=17, M2P_OFFSETS=18, M2P_CELLS=19,
+           P2P_OFFSETS=20, P2P_CELLS=21)
+
+EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
+           "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
+           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy")
+
+
+class hot_params(C.Structure):
+    _fields_ = [("p", C.c_int), ("tol", C.c_double), ("eps", C.c_double), ("G", C.c_double),
+                ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int)]
+
+
+class HotError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libhot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.hot_create.argtypes = [C.POINTER(vp), C.POINTER(hot_params), vp]
+    L.hot_set_params.argtypes = [vp, C.POINTER(hot_params)]
+    L.hot_build_tree.argtypes = [vp, vp, vp, C.c_int64]
+    L.hot_compute_moments.argtypes = [vp, C.c_int]
+    L.hot_traverse.argtypes = [vp, C.c_double]
+    L.hot_evaluate_forces.argtypes = [vp, vp, vp]
+    L.hot_adjoint.argtypes = [vp, vp, vp, vp, vp]
+    L.hot_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+    L.hot_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.hot_debug_get.argtypes = [vp, C.c_int, vp, C.c_size_t]
+    L.hot_lookup.argtypes = [vp, vp, C.c_int64, vp]
+    L.hot_fma_peak.argtypes = [vp, C.c_int, C.POINTER(C.c_double)]
+    L.hot_strerror.restype = C.c_char_p
+    L.hot_strerror.argtypes = [C.c_int]
+    L.hot_destroy.argtypes = [vp]
+    L.hot_destroy.restype = None
+    for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
+                 "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
+                 "hot_lookup", "hot_fma_peak"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().hot_strerror(int(code)).decode()
+
+
+def _ck(code, what):
+    if code != HOT_OK:
+        raise HotError(code, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _need(t, shape_last=None):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t
+
+
+def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64, precision="mixed"):
+    prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
+    return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec)
+
+
+class Hot:
+    """One library context: its tree, moments and lists live on the device."""
+
+    def __init__(self, stream=None, **kw):
+        import torch
+        L = load()
+        self.params = make_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _ck(L.hot_create(C.byref(h), C.byref(self.params), C.c_void_p(stream.cuda_stream)), "hot_create")
+        self._h = h
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hot_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, **kw):
+        self.params = make_params(**kw)
+        _ck(load().hot_set_params(self._h, C.byref(self.params)), "hot_set_params")
+
+    def build_tree(self, pos, mass):
+        _need(pos)
+        _need(mass)
+        self.N = int(mass.shape[0])
+        _ck(load().hot_build_tree(self._h, _ptr(pos), _ptr(mass), self.N), "hot_build_tree")
+
+    def compute_moments(self, p=None):
+        p = self.params.p if p is None else p
+        _ck(load().hot_compute_moments(self._h, int(p)), "hot_compute_moments")
+
+    def traverse(self, tol=None):
+        tol = self.params.tol if tol is None else tol
+        _ck(load().hot_traverse(self._h, float(tol)), "hot_traverse")
+
+    def evaluate_forces(self, acc, pot=None):
+        _need(acc)
+        if pot is not None:
+            _need(pot)
+        _ck(load().hot_evaluate_forces(self._h, _ptr(acc), _ptr(pot)), "hot_evaluate_forces")
+
+    def adjoint(self, g_acc, g_pot, g_pos, g_mass):
+        _ck(load().hot_adjoint(self._h, _ptr(g_acc), _ptr(g_pot), _ptr(g_pos), _ptr(g_mass)), "hot_adjoint")
+
+    def stage_times(self):
+        ms = (C.c_float * 6)()
+        _ck(load().hot_stage_times(self._h, ms), "hot_stage_times")
+        return dict(zip(("sort", "build", "moments", "traverse", "interact", "adjoint"), list(ms)))
+
+    def sizes(self):
+        out = (C.c_int64 * 9)()
+        _ck(load().hot_sizes(self._h, out), "hot_sizes")
+        return dict(zip(("N", "ncell", "ngroup", "nleaf", "maxlevel", "n_m2p", "n_p2p", "n_pairs", "n_m2p_int"),
+                        list(out)))
+
+    def debug_get(self, what):
+        s = self.sizes()
+        N, nc, ng = s["N"], s["ncell"], s["ngroup"]
+        ncomp = (self.params.p + 1) * (self.params.p + 2) * (self.params.p + 3) // 6
+        spec = {
+            "FRAME": (np.float64, (4,)), "SORTED_KEYS": (np.uint64, (N,)), "PERM": (np.int32, (N,)),
+            "CELL_KEY": (np.uint64, (nc,)), "CELL_LEVEL": (np.int32, (nc,)), "CELL_BEGIN": (np.int32, (nc,)),
+            "CELL_COUNT": (np.int32, (nc,)), "CELL_PARENT": (np.int32, (nc,)), "CELL_NCHILD": (np.int32, (nc,)),
+            "GROUP_CELL": (np.int32, (ng,)), "GROUP_CENTRE": (np.float64, (ng, 3)),
+            "GROUP_DMAX": (np.float64, (ng,)), "CELL_MASS": (np.float64, (nc,)), "CELL_COM": (np.float64, (nc, 3)),
+            "MOMENTS": (np.float64, (nc, ncomp)), "CELL_BMAX": (np.float64, (nc,)), "CELL_B1": (np.float64, (nc,)),
+            "CELL_B2": (np.float64, (nc,)), "M2P_OFFSETS": (np.int64, (ng + 1,)), "M2P_CELLS": (np.int32, (s["n_m2p"],)),
+            "P2P_OFFSETS": (np.int64, (ng + 1,)), "P2P_CELLS": (np.int32, (s["n_p2p"],)),
+        }[what]
+        out = np.zeros(spec[1], dtype=spec[0])
+        _ck(load().hot_debug_get(self._h, DBG[what], out.ctypes.data_as(C.c_void_p), out.nbytes),
+            f"hot_debug_get({what})")
+        return out
+
+    def lookup(self, keys):
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = np.zeros(len(keys), dtype=np.int32)
+        _ck(load().hot_lookup(self._h, keys.ctypes.data_as(C.c_void_p), len(keys),
+                              out.ctypes.data_as(C.c_void_p)), "hot_lookup")
+        return out
+
+    def fma_peak(self, dbl=False):
+        v = C.c_double()
+        _ck(load().hot_fma_peak(self._h, 1 if dbl else 0, C.byref(v)), "hot_fma_peak")
+        return v.value
+
+
+def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64, precision="mixed",
+               ctx: Hot | None = None, want_pot=True):
+    """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N]."""
+    import torch
+    h = ctx or Hot(p=p, tol=tol, eps=eps, G=G, leaf_max=leaf_max, group_max=group_max, precision=precision)
+    h.build_tree(pos, mass)
+    h.compute_moments(p)
+    h.traverse(tol)
+    acc = torch.empty_like(pos)
+    pot = torch.empty_like(mass) if want_pot else None
+    h.evaluate_forces(acc, pot)
+    return acc, pot

@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact: frame, keys, sort order, tree topology, sink groups and their centres.
+Floating point: moments and acceptance aggregates to ~1e-12 relative; interaction
+lists equal as sets (borderline acceptance decisions excepted); forces within the
+stated tolerances (FP64 path 1e-11, mixed path rms 1e-5 / max 1e-3 relative).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_4502_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1310_4502_gb300 import hot
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def cases():
+    rng = np.random.default_rng(21)
+    out = {}
+    w = W.make("plummer4096")
+    out["plummer4096"] = (w.pos, w.mass, w.eps)
+    n = 1 << 15
+    out["clustered32k"] = (W.clustered(n, seed=3), np.full(n, 1.0 / n), 1e-4)
+    n = 20011  # ragged: not a multiple of any tile
+    x = rng.uniform(-1, 1, (n, 3))
+    x[100:140] = x[99]  # 41 coincident particles -> a level-21 leaf
+    out["ragged_dup"] = (x, rng.uniform(0.5, 1.5, n) / n, 0.01)
+    out["tiny7"] = (rng.standard_normal((7, 3)), np.full(7, 1.0), 0.0)
+    out["one"] = (np.array([[0.3, -0.2, 0.1]]), np.array([2.0]), 0.1)
+    return out
+
+
+CASES = cases()
+
+
+def build(pos, mass, **kw):
+    h = hot.Hot(**kw)
+    P = torch.tensor(pos, device=dev())
+    M = torch.tensor(mass, device=dev())
+    h.build_tree(P, M)
+    return h, P, M
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_keys_sort_topology_groups_bit_exact(name):
+    pos, mass, eps = CASES[name]
+    h, _, _ = build(pos, mass)
+    t = oracle.Tree(pos, mass, 16, 64)
+    lo, L = t.frame()
+    fr = h.debug_get("FRAME")
+    assert np.array_equal(fr[:3], lo) and fr[3] == L
+    k, perm = t.keys()
+    assert np.array_equal(h.debug_get("SORTED_KEYS"), k[perm])
+    assert np.array_equal(h.debug_get("PERM").astype(np.int64), perm)
+    cl = t.cells()
+    assert h.sizes()["ncell"] == len(cl["key"])
+    assert np.array_equal(h.debug_get("CELL_KEY"), cl["key"])
+    assert np.array_equal(h.debug_get("CELL_LEVEL"), cl["level"])
+    assert np.array_equal(h.debug_get("CELL_BEGIN").astype(np.int64), cl["begin"])
+    assert np.array_equal(h.debug_get("CELL_COUNT").astype(np.int64), cl["count"])
+    assert np.array_equal(h.debug_get("CELL_PARENT"), cl["parent"])
+    assert np.array_equal(h.debug_get("CELL_NCHILD"), cl["nchild"])
+    g = t.groups()
+    assert np.array_equal(h.debug_get("GROUP_CELL"), g["cell"])
+    assert np.array_equal(h.debug_get("GROUP_CENTRE"), g["centre"])
+    assert np.array_equal(h.debug_get("GROUP_DMAX"), g["dmax"])
+
+
+@pytest.mark.parametrize("name", ["plummer4096", "ragged_dup"])
+def test_hash_lookup(name):
+    pos, mass, _ = CASES[name]
+    h, _, _ = build(pos, mass)
+    keys = h.debug_get("CELL_KEY")
+    idx = h.lookup(keys)
+    assert np.array_equal(idx, np.arange(len(keys), dtype=np.int32))
+    absent = (keys[1:] << np.uint64(3)) | np.uint64(7)
+    present = set(keys.tolist())
+    absent = np.array([a for a in absent.tolist() if a not in present][:1000], dtype=np.uint64)
+    assert np.all(h.lookup(absent) == -1)
+
+
+@pytest.mark.parametrize("p", [0, 1, 4, 6])
+def test_moments(p):
+    pos, mass, eps = CASES["plummer4096"]
+    h, _, _ = build(pos, mass, p=p)
+    h.compute_moments(p)
+    t = oracle.Tree(pos, mass, 16, 64)
+    t.moments(p)
+    mo = t.get_moments()
+    np.testing.assert_allclose(h.debug_get("CELL_MASS"), mo["mass"], rtol=1e-13)
+    scale_x = np.max(np.abs(pos))
+    np.testing.assert_allclose(h.debug_get("CELL_COM"), mo["com"], rtol=0, atol=1e-13 * scale_x)
+    M = h.debug_get("MOMENTS")
+    bm = mo["bmax"]
+    idx = oracle.multi_indices(p)
+    deg = np.array([sum(a) for a in idx])
+    scale = mo["mass"][:, None] * np.maximum(bm, 1e-300)[:, None] ** deg[None, :] + 1e-300
+    assert np.max(np.abs(M - mo["mom"]) / scale) < 1e-10
+    np.testing.assert_allclose(h.debug_get("CELL_BMAX"), bm, rtol=1e-11, atol=1e-14 * scale_x)
+    np.testing.assert_allclose(h.debug_get("CELL_B1"), mo["B1"], rtol=1e-10, atol=1e-300)
+    np.testing.assert_allclose(h.debug_get("CELL_B2"), mo["B2"], rtol=1e-10, atol=1e-300)
+
+
+def lists_match(h, t, cl):
+    """Per group, the GPU lists equal the oracle's as sets, up to borderline decisions
+    (cells within 1e-9 of a threshold, and their descendants)."""
+    L = t.lists()
+    om, cm = L["m2p"]
+    op, cp = L["p2p"]
+    ob, cb = L["border"]
+    gm_off = h.debug_get("M2P_OFFSETS")
+    gm = h.debug_get("M2P_CELLS")
+    gp_off = h.debug_get("P2P_OFFSETS")
+    gp = h.debug_get("P2P_CELLS")
+    keys = cl["key"]
+    level = cl["level"]
+    bad = 0
+    for g in range(len(om) - 1):
+        a = set(cm[om[g]:om[g + 1]].tolist()) ^ set(gm[gm_off[g]:gm_off[g + 1]].tolist())
+        b = set(cp[op[g]:op[g + 1]].tolist()) ^ set(gp[gp_off[g]:gp_off[g + 1]].tolist())
+        diff = a | b
+        if not diff:
+            continue
+        border = cb[ob[g]:ob[g + 1]]
+        for c in diff:
+            ok = any(level[c] >= level[x] and (int(keys[c]) >> (3 * (level[c] - level[x]))) == int(keys[x])
+                     for x in border)
+            bad += 0 if ok else 1
+    return bad
+
+
+@pytest.mark.parametrize("name", ["plummer4096", "clustered32k", "ragged_dup", "tiny7", "one"])
+@pytest.mark.parametrize("p", [1, 4, 6])
+def test_lists_and_forces(name, p):
+    pos, mass, eps = CASES[name]
+    tol = 1e-4 if name != "ragged_dup" else 1e-5
+    t = oracle.Tree(pos, mass, 16, 64)
+    t.moments(p)
+    t.traverse(tol)
+    ra, rp = t.force(1.0, eps)
+    cl = t.cells()
+    for prec in ("fp64", "mixed"):
+        h, P, M = build(pos, mass, p=p, tol=tol, eps=eps, precision=prec)
+        h.compute_moments(p)
+        h.traverse(tol)
+        assert lists_match(h, t, cl) == 0
+        acc = torch.empty_like(P)
+        pot = torch.empty_like(M)
+        h.evaluate_forces(acc, pot)
+        torch.cuda.synchronize()
+        a = acc.cpu().numpy()
+        ph = pot.cpu().numpy()
+        if len(mass) == 1:
+            assert np.all(a == 0) and np.all(ph == 0)
+            continue
+        na = np.linalg.norm(ra, axis=1)
+        rel = np.linalg.norm(a - ra, axis=1) / na
+        prel = np.abs(ph - rp) / np.abs(rp)
+        if prec == "fp64":
+            assert rel.max() < 1e-11, rel.max()
+            assert prel.max() < 1e-11, prel.max()
+        else:
+            assert np.sqrt(np.mean(rel ** 2)) < 1e-5, np.sqrt(np.mean(rel ** 2))
+            assert rel.max() < 1e-3, rel.max()
+            assert prel.max() < 1e-4, prel.max()
+
+
+def test_call_order_and_bad_arguments():
+    pos, mass, _ = CASES["tiny7"]
+    h = hot.Hot()
+    acc = torch.empty((7, 3), dtype=torch.float64, device=dev())
+    with pytest.raises(hot.HotError) as e:
+        h.evaluate_forces(acc)
+    assert e.value.code == hot.HOT_ESTATE
+    with pytest.raises(hot.HotError) as e:
+        h.compute_moments(4)
+    assert e.value.code == hot.HOT_ESTATE
+    P = torch.tensor(pos, device=dev())
+    M = torch.tensor(mass, device=dev())
+    bad = P.clone()
+    bad[3, 1] = float("nan")
+    with pytest.raises(hot.HotError) as e:
+        h.build_tree(bad, M)
+    assert e.value.code == hot.HOT_EINPUT
+    with pytest.raises(hot.HotError) as e:
+        h.build_tree(P, -M)
+    assert e.value.code == hot.HOT_EINPUT
+    h.build_tree(P, M)
+    with pytest.raises(hot.HotError) as e:
+        h.compute_moments(7)
+    assert e.value.code == hot.HOT_EINVAL
+    h.compute_moments(4)
+    with pytest.raises(hot.HotError) as e:
+        h.traverse(0.0)
+    assert e.value.code == hot.HOT_EINVAL
