@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Tree-force benchmark on one GB300 (or N independent replicas under torchrun).
+
+Workload (the headline configuration): clustered box, N = 2^20 -- 64 Plummer
+spheres (centres uniform in the unit cube, scale radii log-uniform in
+[0.005, 0.05], truncated at 20 scale radii) holding half the particles plus a
+uniform background; equal masses 1/N, Plummer softening 1e-4, open boundaries,
+G = 1, expansion order p = 4, absolute tolerance 1e-4.  Inputs are generated once
+on the host by seeded numpy and are resident in HBM before timing.
+
+One step = the whole force path: bounding cube, keys, radix sort, tree, hash,
+groups, moments, traversal, M2P + P2P interactions, outputs in original order.
+Between timed steps a 256 MiB buffer is written to flush the 129 MB L2.
+
+Printed: one JSON line (rank 0).  ``value`` = particles/s of the mixed-precision
+path (all ranks' particles / max over ranks of the summed step time).
+``--impl reference`` times the CPU FP64 oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_4502_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Tree-force particles/s (mixed vs FP64) at 1e-4 rms force err; adjoint/fwd time"
+
+
+def describe(w):
+    if w.name.startswith("clustered"):
+        return (f"clustered box N=2^{int(math.log2(w.n))}: 64 Plummer spheres (r_s log-uniform [0.005,0.05], "
+                f"truncated at 20 r_s) hold 50%, 50% uniform background; m=1/N, eps={w.eps:g}, G=1, "
+                f"p={w.p}, tol={w.tol:g} (absolute), open boundaries")
+    return f"{w.name}: N={w.n}, eps={w.eps:g}, G=1, p={w.p}, tol={w.tol:g}, open boundaries"
+P2P_FLOPS = 28  # the paper's convention for one softened monopole interaction
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clustered20")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 / p=6 / error legs")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        lr = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(lr)
+        dist.init_process_group("nccl")
+        return dist.get_rank(), ws, lr
+    return 0, 1, 0
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, frac_inv=128, seed=0):
+    """Oracle tree force on a bounded sample: tree + moments on all N, traversal and
+    forces for a seeded random 1/frac_inv of the sink groups; the particles/s figure
+    extrapolates the sampled groups to all of them."""
+    import oracle
+    t0 = time.perf_counter()
+    T = oracle.Tree(w.pos, w.mass)
+    T.moments(w.p)
+    t1 = time.perf_counter()
+    ng = T.info()["ngroup"]
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(ng, max(1, ng // frac_inv), replace=False))
+    T.traverse(w.tol, groups=sel)
+    T.force(1.0, w.eps, groups=sel)
+    t2 = time.perf_counter()
+    g = T.groups()
+    cl = T.cells()
+    sinks = int(cl["count"][g["cell"][sel]].sum())
+    t_full = (t1 - t0) + (t2 - t1) * (w.n / max(sinks, 1))
+    return {"value": w.n / t_full, "unit": "particles/s", "cores": oracle.nthreads(), "kind": "oracle",
+            "sample": (f"CPU FP64 oracle: tree+moments on all {w.n} particles ({t1 - t0:.2f} s), traversal+forces "
+                       f"for {len(sel)} of {ng} sink groups ({sinks} sinks, seed {seed}, {t2 - t1:.2f} s); "
+                       f"time extrapolated to all sinks"),
+            "seconds": t2 - t0}
+
+
+def run_reference(args):
+    rank, ws, _ = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return
+    import oracle
+    w = W.make(args.workload)
+    oracle.build()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(w, frac_inv=512, seed=k)
+        if k >= args.warmup:
+            vals.append(r)
+    v = statistics.median([r["value"] for r in vals])
+    secs = sum(r["seconds"] for r in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w.n / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w), "N": w.n, "p": w.p, "tol": w.tol, "eps": w.eps},
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"].replace("seed 0", "seeds per step")},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "timed_seconds": secs}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, ws, lr = dist_setup(args)
+    from paper_1310_4502_gb300 import hot
+
+    dev = torch.device("cuda", lr)
+    torch.cuda.set_device(dev)
+    w = W.make(args.workload)
+    N = w.n
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    acc = torch.empty_like(P)
+    pot = torch.empty_like(M)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+
+    def step(ctx, p):
+        ctx.build_tree(P, M)
+        ctx.compute_moments(p)
+        ctx.traverse(w.tol)
+        ctx.evaluate_forces(acc, pot)
+
+    def timed(ctx, K, Wm, sampler=None, p=w.p):
+        for _ in range(Wm):
+            step(ctx, p)
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        stages = {}
+        l0 = ctx.sizes()["launches"]
+        if sampler:
+            sampler.start()
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step(ctx, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            for k, v in ctx.stage_times().items():
+                stages[k] = stages.get(k, 0.0) + v
+        clocks = sampler.stop() if sampler else None
+        launches = (ctx.sizes()["launches"] - l0) / K
+        barrier(ws)
+        return tot, {k: v / K for k, v in stages.items()}, launches, clocks
+
+    sampler = ClockSampler(lr)
+    tot, stages, launches, clocks = timed(h, args.steps, args.warmup, sampler)
+    tmax = max_over_ranks(tot, ws)
+    ms_step = tmax / args.steps
+    value = ws * N / (ms_step * 1e-3)
+    sz = h.sizes()
+
+    # roofline of the dominant kernel (interactions): algorithmic flops per launch
+    flops_m2p = sz["n_m2p_int"] * FLOPS_M2P[w.p]
+    flops_p2p = sz["n_pairs"] * P2P_FLOPS
+    t_int = stages["interact"] * 1e-3
+    achieved = (flops_m2p + flops_p2p) / t_int / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fma32 = h.fma_peak(False) / 1e12
+    fma64 = h.fma_peak(True) / 1e12
+    roof = {"kernel": f"k_interact<p={w.p},float>", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(w.p),
+            "peak_note": (f"FP32 non-tensor: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max clock); "
+                          f"FMA microbenchmark measured {fma32:.1f} TFLOP/s"),
+            "flop_convention": f"M2P {FLOPS_M2P[w.p]} flop (generated p={w.p} routine, FMA=2), P2P 28 flop",
+            "m2p_interactions": sz["n_m2p_int"], "p2p_interactions": sz["n_pairs"],
+            "ms_per_launch": stages["interact"],
+            "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int}
+
+    out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": describe(w), "N": N, "p": w.p, "tol": w.tol, "eps": w.eps, "leaf_max": 16,
+                      "group_max": 64, "l2": "flushed between steps (256 MiB write, untimed)",
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "stages_ms": stages, "sizes": {k: v for k, v in sz.items() if k != "launches"},
+           "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+           "fp64_peak_tflops_measured": fma64}
+
+    # end to end through the public API with host buffers
+    pos_h = torch.tensor(w.pos).pin_memory()
+    mass_h = torch.tensor(w.mass).pin_memory()
+    acc_h = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    pot_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        hot.tree_force_host(pos_h, mass_h, acc_h, pot_h, ctx=h, p=w.p, tol=w.tol)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    te = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        hot.tree_force_host(pos_h, mass_h, acc_h, pot_h, ctx=h, p=w.p, tol=w.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te += e0.elapsed_time(e1)
+    te = max_over_ranks(te, ws)
+    out["e2e"] = {"value": ws * N / (te / args.steps * 1e-3), "unit": "particles/s",
+                  "h2d_bytes_per_step": pos_h.nbytes + mass_h.nbytes,
+                  "d2h_bytes_per_step": acc_h.nbytes + pot_h.nbytes}
+
+    if not args.no_extras:
+        mixed_acc = acc.clone()
+        # FP64 path, same lists
+        h64 = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="fp64")
+        k64 = min(args.steps, 2)
+        t64, st64, _, _ = timed(h64, k64, 1)
+        v64 = N / (t64 / k64 * 1e-3)
+        acc64 = acc.clone()
+        rel = torch.linalg.norm(mixed_acc - acc64, dim=1) / torch.linalg.norm(acc64, dim=1)
+        out["fp64"] = {"value": v64, "unit": "particles/s", "ms_per_step": t64 / k64, "stages_ms": st64,
+                       "mixed_speedup": value / ws / v64,
+                       "interact_speedup": st64["interact"] / stages["interact"]}
+        out["error"] = {"mixed_vs_fp64_rms_rel": float(torch.sqrt(torch.mean(rel ** 2))),
+                        "mixed_vs_fp64_max_rel": float(rel.max())}
+        # p = 6
+        h6 = hot.Hot(p=6, tol=w.tol, eps=w.eps, precision="mixed")
+        t6, st6, _, _ = timed(h6, args.steps, 1, p=6)
+        s6 = h6.sizes()
+        out["p6"] = {"value": N / (t6 / args.steps * 1e-3), "unit": "particles/s", "ms_per_step": t6 / args.steps,
+                     "stages_ms": st6, "m2p_interactions": s6["n_m2p_int"], "p2p_interactions": s6["n_pairs"],
+                     "interact_tflops": (s6["n_m2p_int"] * FLOPS_M2P[6] + s6["n_pairs"] * P2P_FLOPS)
+                     / (st6["interact"] * 1e-3) / 1e12}
+        del h64, h6
+        # truncation error of the mixed tree force against the FP64 direct sum on a subsample
+        if rank == 0 and not args.no_cpu:
+            import oracle
+            sub = np.sort(np.random.default_rng(3).choice(N, 4096, replace=False))
+            ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps, sinks=sub)
+            a = mixed_acc.cpu().numpy()[sub]
+            e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            out["error"].update({"tree_vs_direct_rms_rel_4096": float(np.sqrt(np.mean(e ** 2))),
+                                 "tree_vs_direct_max_rel_4096": float(e.max())})
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = {k: v for k, v in oracle_sample(w).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _flops_table():
+    from paper_1310_4502_gb300.csrc.gen_kernels import gen_eval
+    return [gen_eval(p)[3] for p in range(7)]
+
+
+FLOPS_M2P = _flops_table()
+
+# ncu-measured DRAM traffic of the interaction kernel, per launch, on the workload above,
+# with the source hash it was taken on; reported only while the kernel is unchanged.
+TRAFFIC = {}
+
+
+def _kernel_hash():
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("hot_interact.cu", "generated.cuh", "hot_common.cuh"):
+        hsh.update(open(os.path.join(ROOT, "paper_1310_4502_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def traffic_for(p):
+    t = TRAFFIC.get((p, _kernel_hash()))
+    return t
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

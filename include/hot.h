@@ -137,8 +137,9 @@ int hot_stage_times(hot_ctx *ctx, float ms[6]);
 
 /* Sizes after the latest stages: out[0] N, [1] cells, [2] sink groups, [3]
  * leaves, [4] deepest level, [5] M2P list entries, [6] P2P list entries
- * (leaves), [7] P2P particle pairs, [8] M2P interactions (entries x sinks). */
-int hot_sizes(hot_ctx *ctx, int64_t out[9]);
+ * (leaves), [7] P2P particle pairs, [8] M2P interactions (entries x sinks),
+ * [9] kernels launched by the library since it was loaded (all contexts). */
+int hot_sizes(hot_ctx *ctx, int64_t out[10]);
 
 /* Copy an internal array to host memory (for tests).  bytes must equal the
  * array size: see HOT_DBG_* for element type and length.  Synchronises. */

@@ -7,6 +7,8 @@
 
 int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx);
 
+std::atomic<long long> hot_launch_counter{0};
+
 namespace {
 
 int status_code(unsigned bits)
@@ -149,7 +151,7 @@ int hot_stage_times(hot_ctx *c, float ms[6])
     return HOT_OK;
 }
 
-int hot_sizes(hot_ctx *c, int64_t out[9])
+int hot_sizes(hot_ctx *c, int64_t out[10])
 {
     if (!c || !out) return HOT_EINVAL;
     out[0] = c->N;
@@ -161,6 +163,7 @@ int hot_sizes(hot_ctx *c, int64_t out[9])
     out[6] = c->n_p2p;
     out[7] = c->n_pairs;
     out[8] = c->n_m2p_int;
+    out[9] = hot_launch_counter.load();
     return HOT_OK;
 }
 

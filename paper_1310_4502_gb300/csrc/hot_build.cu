@@ -520,8 +520,11 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(c->key2.ensure(N, s));
     HOT_CK(c->idx.ensure(N, s));
     HOT_CK(c->idx2.ensure(N, s));
+    HOT_COUNT_LAUNCH();
     k_bbox_part<<<nbb, BT, 0, s>>>(pos, mass, N, c->part.p, c->d_status);
+    HOT_COUNT_LAUNCH();
     k_bbox_final<<<1, 32, 0, s>>>(c->part.p, nbb, c->frame.p);
+    HOT_COUNT_LAUNCH();
     k_keys<<<hot_blocks(N, BT), BT, 0, s>>>(pos, N, c->frame.p, c->key.p, c->idx.p);
     // radix sort, 8 passes of 8 bits
     int64_t ntiles = (N + RS_TILE - 1) / RS_TILE;
@@ -532,9 +535,11 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     uint32_t *va = c->idx.p, *vb = c->idx2.p;
     for (int pass = 0; pass < 8; ++pass) {
         int shift = 8 * pass;
+        HOT_COUNT_LAUNCH();
         k_rs_hist<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, N, shift, c->hist.p, ntiles);
         int r = hot_scan_u32_to_u32(c->hist.p, c->histoff.p, 256 * ntiles, c->scan_tmp.p, s);
         if (r) return r;
+        HOT_COUNT_LAUNCH();
         k_rs_scatter<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, va, kb, vb, N, shift, c->histoff.p, ntiles);
         uint64_t *tk = ka;
         ka = kb;
@@ -546,6 +551,7 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     // 8 passes: sorted data is back in key/idx
     HOT_CK(c->spos.ensure(3 * (size_t)N, s));
     HOT_CK(c->smass.ensure(N, s));
+    HOT_COUNT_LAUNCH();
     k_gather<<<hot_blocks(N, BT), BT, 0, s>>>(pos, mass, c->idx.p, N, c->spos.p, c->smass.p);
     hot_toc(c, 0);
 
@@ -557,7 +563,9 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(c->sizes.ensure(64, s));
     HOT_CK(cudaMemsetAsync(c->sizes.p, 0, 64 * sizeof(int64_t), s));
     uint8_t *win = (uint8_t *)c->key2.p;  // scratch: key2 is free after the sort
+    HOT_COUNT_LAUNCH();
     k_lcp<<<hot_blocks(N, BT), BT, 0, s>>>(c->key.p, N, leaf_max, c->lcp.p, win);
+    HOT_COUNT_LAUNCH();
     k_leaflevel<<<hot_blocks(N, BT), BT, 0, s>>>(c->lcp.p, win, N, leaf_max, c->leaflev.p, c->ncell_i.p,
                                                    c->sizes.p + 0);
     int r = hot_scan_u32_to_u32(c->ncell_i.p, c->cell_off.p, N, c->scan_tmp.p, s);
@@ -587,6 +595,7 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(c->goff.ensure(ncell + 1, s));
     HOT_CK(c->gcell.ensure(ncell, s));
     HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ncell + N + 256 * ntiles + 64), s));
+    HOT_COUNT_LAUNCH();
     k_cells<<<hot_blocks(N, BT), BT, 0, s>>>(c->key.p, N, c->lcp.p, c->leaflev.p, c->cell_off.p, ncell,
                                               c->ckey.p, c->clevel.p, c->cbegin.p, c->ccount.p, c->cparent.p,
                                               c->cend.p, c->d_status);
@@ -594,9 +603,12 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(cudaMemsetAsync(c->cnchild.p, 0, sizeof(int32_t) * (size_t)ncell, s));
     int32_t *lvlcnt = (int32_t *)(c->sizes.p + 8);     // 24 int32 in sizes[8..20)
     int64_t *levoff = c->sizes.p + 24;                 // 23 int64 in sizes[24..47)
+    HOT_COUNT_LAUNCH();
     k_link<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ckey.p, c->cparent.p, c->clevel.p, ncell, c->child8.p,
                                                  c->cnchild.p, lvlcnt);
+    HOT_COUNT_LAUNCH();
     k_level_off<<<1, 32, 0, s>>>(lvlcnt, levoff, c->sizes.p);
+    HOT_COUNT_LAUNCH();
     k_level_scatter<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->clevel.p, ncell, levoff, lvlcnt, c->level_cells.p);
     // hash table, load <= 1/2
     uint64_t hcap = 1024;
@@ -605,16 +617,20 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(c->hkey.ensure(hcap, s));
     HOT_CK(c->hval.ensure(hcap, s));
     HOT_CK(cudaMemsetAsync(c->hkey.p, 0, sizeof(uint64_t) * hcap, s));
+    HOT_COUNT_LAUNCH();
     k_hash_insert<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ckey.p, ncell, c->hkey.p, c->hval.p, hcap - 1,
                                                         c->d_status);
     // groups
+    HOT_COUNT_LAUNCH();
     k_group_flag<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->ccount.p, c->cparent.p, c->cnchild.p, ncell,
                                                        c->prm.group_max, c->gflag.p, c->sizes.p + 2);
     r = hot_scan_u32_to_u32(c->gflag.p, c->goff.p, ncell, c->scan_tmp.p, s);
     if (r) return r;
+    HOT_COUNT_LAUNCH();
     k_group_write<<<hot_blocks(ncell, BT), BT, 0, s>>>(c->gflag.p, c->goff.p, ncell, c->gcell.p);
     HOT_CK(c->gcen.ensure(3 * (size_t)ncell, s));
     HOT_CK(c->gdmax.ensure(ncell, s));
+    HOT_COUNT_LAUNCH();
     k_group_geom<<<c->nsm * 8, 256, 0, s>>>(c->gcell.p, c->goff.p + ncell, c->cbegin.p, c->ccount.p,
                                              c->spos.p, c->gcen.p, c->gdmax.p);
     HOT_CK(cudaMemcpyAsync(c->sizes.p + 3, c->goff.p + ncell, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
@@ -642,6 +658,7 @@ int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
     HOT_CK(cudaMallocAsync((void **)&dk, sizeof(uint64_t) * (n > 0 ? n : 1), s));
     HOT_CK(cudaMallocAsync((void **)&di, sizeof(int32_t) * (n > 0 ? n : 1), s));
     HOT_CK(cudaMemcpyAsync(dk, keys, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    HOT_COUNT_LAUNCH();
     k_hash_lookup<<<hot_blocks(n, BT), BT, 0, s>>>(dk, n, c->hkey.p, c->hval.p, c->hcap - 1, di);
     HOT_CK(cudaMemcpyAsync(idx, di, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     cudaFreeAsync(dk, s);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -21,6 +22,10 @@
 #define HOT_ST_INTERNAL 16u  // a consistency check failed (index out of range)
 
 #define HOT_MAXLEVEL 21
+
+// Number of kernel launches issued by this library (all contexts), for benchmarks.
+extern std::atomic<long long> hot_launch_counter;
+#define HOT_COUNT_LAUNCH() hot_launch_counter.fetch_add(1, std::memory_order_relaxed)
 
 // ---------------------------------------------------------------------------
 // Grow-only device buffer, stream-ordered allocation.

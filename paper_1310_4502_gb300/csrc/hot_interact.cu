@@ -214,6 +214,7 @@ int forces_pt(hot_ctx *c, double *acc, double *pot)
     if (occ < 1) occ = 1;
     const int blocks = c->nsm * occ;
     const T eps2 = (T)(c->prm.eps * c->prm.eps);
+    HOT_COUNT_LAUNCH();
     kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
                                        c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot);

@@ -312,6 +312,7 @@ int moments_p(hot_ctx *c)
     HOT_CK(c->cB2.ensure(ncell, s));
     HOT_CK(c->prel.ensure(N, s));
     const int grid = c->nsm * 8;
+    HOT_COUNT_LAUNCH();
     k_p2m_leaf<P><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
                                            c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
                                            c->cB1.p, c->cB2.p, c->prel.p);
@@ -319,6 +320,7 @@ int moments_p(hot_ctx *c)
         int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
         if (n <= 0) continue;
         int blocks = hot_blocks(n, MW, c->nsm * 16);
+        HOT_COUNT_LAUNCH();
         k_m2m_level<P><<<blocks, MW * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
                                                   c->cmass.p, c->ccom.p, c->cmom.p);
     }
@@ -329,13 +331,17 @@ int moments_p(hot_ctx *c)
     HOT_CK(c->item_part.ensure(3 * (size_t)max_items, s));
     HOT_CK(c->gflag.ensure(ncell + 1, s));
     HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ncell + 64), s));
+    HOT_COUNT_LAUNCH();
     k_item_count<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->ccount.p, c->cnchild.p, ncell, c->gflag.p);
     int r = hot_scan_u32_to_u32(c->gflag.p, c->item_off.p, ncell, c->scan_tmp.p, s);
     if (r) return r;
+    HOT_COUNT_LAUNCH();
     k_item_cells<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, ncell, c->item_cell.p);
+    HOT_COUNT_LAUNCH();
     k_item_part<P><<<c->nsm * 16, MW * 32, 0, s>>>(c->item_cell.p, c->item_off.p, c->item_off.p + ncell,
                                                    c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p, c->smass.p,
                                                    c->item_part.p);
+    HOT_COUNT_LAUNCH();
     k_item_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
                                                           c->cbmax.p, c->cB1.p, c->cB2.p);
     // records
@@ -343,10 +349,12 @@ int moments_p(hot_ctx *c)
     c->reclen = reclen;
     if (c->prm.precision == HOT_FP64) {
         HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
+        HOT_COUNT_LAUNCH();
         k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                     c->prm.G, c->prm.eps, reclen, c->rec64.p);
     } else {
         HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
+        HOT_COUNT_LAUNCH();
         k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                    c->prm.G, c->prm.eps, reclen, c->rec32.p);
     }

@@ -104,8 +104,11 @@ int scan_impl(const In *in, Out *out, int64_t n, uint64_t *tmp, cudaStream_t s)
 {
     int64_t nb = (n + STILE - 1) / STILE;
     if (nb < 1) nb = 1;
+    HOT_COUNT_LAUNCH();
     k_scan_reduce<In><<<(unsigned)nb, ST, 0, s>>>(in, n, tmp);
+    HOT_COUNT_LAUNCH();
     k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
+    HOT_COUNT_LAUNCH();
     k_scan_tiles<In, Out><<<(unsigned)nb, ST, 0, s>>>(in, out, n, tmp, nb);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }

@@ -163,6 +163,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
+        HOT_COUNT_LAUNCH();
         k_traverse<false><<<blocks, TW * 32, 0, s>>>(
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
             c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
@@ -194,6 +195,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     HOT_CK(c->l_m2p.ensure(c->n_m2p + 1, s));
     HOT_CK(c->l_p2p.ensure(c->n_p2p + 1, s));
     HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
+    HOT_COUNT_LAUNCH();
     k_traverse<true><<<blocks, TW * 32, 0, s>>>(
         ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
         c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap, work,

@@ -162,10 +162,10 @@ class Hot:
         return dict(zip(("sort", "build", "moments", "traverse", "interact", "adjoint"), list(ms)))
 
     def sizes(self):
-        out = (C.c_int64 * 9)()
+        out = (C.c_int64 * 10)()
         _ck(load().hot_sizes(self._h, out), "hot_sizes")
-        return dict(zip(("N", "ncell", "ngroup", "nleaf", "maxlevel", "n_m2p", "n_p2p", "n_pairs", "n_m2p_int"),
-                        list(out)))
+        return dict(zip(("N", "ncell", "ngroup", "nleaf", "maxlevel", "n_m2p", "n_p2p", "n_pairs", "n_m2p_int",
+                         "launches"), list(out)))
 
     def debug_get(self, what):
         s = self.sizes()
@@ -211,3 +211,26 @@ def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=
     pot = torch.empty_like(mass) if want_pot else None
     h.evaluate_forces(acc, pot)
     return acc, pot
+
+
+def tree_force_host(pos_h, mass_h, acc_h, pot_h=None, ctx: Hot | None = None, p=4, tol=1e-4, **kw):
+    """Tree force of host (preferably pinned) float64 tensors: copies the inputs to the
+    device, runs the whole path on the context's stream and copies acc (and pot) back
+    into the given host tensors.  Returns after the results are on the host."""
+    import torch
+    h = ctx or Hot(p=p, tol=tol, **kw)
+    st = h.stream
+    with torch.cuda.stream(st):
+        P = pos_h.to("cuda", non_blocking=True)
+        M = mass_h.to("cuda", non_blocking=True)
+        h.build_tree(P, M)
+        h.compute_moments(p)
+        h.traverse(tol)
+        acc = torch.empty_like(P)
+        pot = torch.empty_like(M) if pot_h is not None else None
+        h.evaluate_forces(acc, pot)
+        acc_h.copy_(acc, non_blocking=True)
+        if pot_h is not None:
+            pot_h.copy_(pot, non_blocking=True)
+    st.synchronize()
+    return acc_h, pot_h
