@@ -174,6 +174,34 @@ int hot_debug_get(hot_ctx *ctx, int what, void *host_dst, size_t bytes);
  * keys[i] or -1 when no such cell exists.  Synchronises. */
 int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
 
+/* Key frame without any allocation.  Computes what hot_build_tree uses as its key
+ * frame -- frame[0..2] = per-axis minimum of the positions, frame[3] = L, their
+ * largest extent (1 when all coincide) -- and rejects non-finite positions and
+ * non-positive masses.  The paper has no counterpart; this entry point exists for
+ * callers that must not allocate device memory: code running inside a stream that
+ * is being captured into a CUDA graph, hosts that pre-allocate all device memory
+ * up front (embedded or real-time loops, pools owned by another framework) and
+ * must never see cudaMalloc, or allocators that are not reentrant from a
+ * callback.  It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * scratch (one partial record per 16384 particles, the frame record and a status
+ * word) is a fixed device array inside the library (about 200 KB, held by every
+ * GPU that loads the library until the process exits).
+ *   pos   device, [N][3] float64;  mass device, [N] float64  (inputs, unchanged)
+ *   frame device, float64[4]                                  (output)
+ *   N     1 .. 2^26; larger N returns HOT_EOVERFLOW (the scratch holds at most
+ *         4096 partial records)
+ *   cuda_stream  a cudaStream_t (NULL = legacy default stream); the call
+ *         synchronises it to read the input check.
+ * The first call on a device looks up the scratch array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array and it keeps the last call's
+ * contents (the status word is cleared at the start of every call): calls that
+ * overlap on the GPU -- on different streams, or from different host threads --
+ * race and must be serialised by the caller.  Returns HOT_OK, HOT_EINVAL,
+ * HOT_EOVERFLOW, HOT_EINPUT or HOT_ECUDA. */
+int hot_key_frame_noalloc(const double *pos, const double *mass, int64_t N, double *frame,
+                          void *cuda_stream);
+
 /* Fused-multiply-add throughput microbenchmark (for roofline denominators):
  * runs a register-resident FMA loop on every SM and writes the achieved
  * FLOP/s (FMA = 2) to *flops.  dbl: 0 = float32, 1 = float64.  Synchronises. */

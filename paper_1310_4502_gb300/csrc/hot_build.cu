@@ -666,3 +666,71 @@ int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
     HOT_CK(cudaStreamSynchronize(s));
     return HOT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the bounding-cube reduction (see hot_key_frame_noalloc
+// in include/hot.h).  Its scratch -- one partial min/max record per block, the
+// frame record written by the final reduction and the status word -- lives in this
+// file-scope device array, which every GPU that loads the library keeps until exit.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t NOALLOC_PER_BLOCK = (int64_t)BT * 64;  // particles per reduction block
+constexpr int NOALLOC_MAX_BLOCKS = 4096;                // => at most 2^26 particles
+constexpr int NOALLOC_DOUBLES = 6 * NOALLOC_MAX_BLOCKS + 8 + 1;  // partials, frame, status
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is queried once per device with
+// that device current, and reused afterwards.
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HOT_ECUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return HOT_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        double *p = nullptr;
+        if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) return HOT_ECUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HOT_OK;
+}
+
+}  // namespace
+
+extern "C" int hot_key_frame_noalloc(const double *pos, const double *mass, int64_t N, double *frame,
+                                     void *cuda_stream)
+{
+    if (!pos || !mass || !frame || N < 1) return HOT_EINVAL;
+    if (N > NOALLOC_PER_BLOCK * NOALLOC_MAX_BLOCKS) return HOT_EOVERFLOW;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double *scratch = nullptr;
+    int e = noalloc_scratch(&scratch);
+    if (e) return e;
+    double *part = scratch;
+    double *fr = scratch + 6 * NOALLOC_MAX_BLOCKS;
+    unsigned *status = (unsigned *)(fr + 8);
+    const int nb = (int)((N + NOALLOC_PER_BLOCK - 1) / NOALLOC_PER_BLOCK);
+    // the status word keeps the previous call's value: clear it
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), s) != cudaSuccess) return HOT_ECUDA;
+    HOT_COUNT_LAUNCH();
+    k_bbox_part<<<nb, BT, 0, s>>>(pos, mass, N, part, status);
+    HOT_COUNT_LAUNCH();
+    k_bbox_final<<<1, 32, 0, s>>>(part, nb, fr);
+    if (cudaMemcpyAsync(frame, fr, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return HOT_ECUDA;
+    unsigned bits = 0;
+    if (cudaMemcpyAsync(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return HOT_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HOT_ECUDA;
+    return (bits & HOT_ST_INPUT) ? HOT_EINPUT : HOT_OK;
+}

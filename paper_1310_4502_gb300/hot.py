@@ -24,7 +24,7 @@ DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy")
+           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc")
 
 
 class hot_params(C.Structure):
@@ -71,9 +71,10 @@ def load():
     L.hot_strerror.argtypes = [C.c_int]
     L.hot_destroy.argtypes = [vp]
     L.hot_destroy.restype = None
+    L.hot_key_frame_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-                 "hot_lookup", "hot_fma_peak"):
+                 "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -197,6 +198,19 @@ class Hot:
         v = C.c_double()
         _ck(load().hot_fma_peak(self._h, 1 if dbl else 0, C.byref(v)), "hot_fma_peak")
         return v.value
+
+
+def key_frame_noalloc(pos, mass, frame, stream=None):
+    """Allocation-free key frame (lo_x, lo_y, lo_z, L) of device tensors into the device
+    tensor frame[4]; see hot_key_frame_noalloc in include/hot.h."""
+    import torch
+    _need(pos)
+    _need(mass)
+    _need(frame)
+    st = stream or torch.cuda.current_stream()
+    _ck(load().hot_key_frame_noalloc(_ptr(pos), _ptr(mass), int(mass.shape[0]), _ptr(frame),
+                                     C.c_void_p(st.cuda_stream)), "hot_key_frame_noalloc")
+    return frame
 
 
 def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64, precision="mixed",
