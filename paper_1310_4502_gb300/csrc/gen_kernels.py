@@ -93,31 +93,22 @@ def g_terms(p):
     return out
 
 
-def gen_eval(p):
-    S = s_terms(p)
-    Gt = g_terms(p)
-    ns, ng = len(S), len(Gt)
-    sidx = {(k, b): 4 + i for i, (k, n, b) in enumerate(S)}
-    gidx = {(k, d, b): 4 + ns + i for i, (k, d, b) in enumerate(Gt)}
+def _eval_stmts(p):
+    """Statements of one M2P interaction with symbolic coefficient references
+    ('@S,k,b@' for C_{b,k}, '@G,k,d,b@' for b_d C_{b,k}) and the flop count."""
     L = []
     fl = 0
-    L.append(f"template <typename T> __device__ __forceinline__ void m2p_eval_{p}("
-             "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {")
-    L.append("  const T is = c[0];")
-    L.append("  rx *= is; ry *= is; rz *= is;")
+    L.append("rx *= is; ry *= is; rz *= is;")
     fl += 3
-    L.append("  const T u = rx * rx + ry * ry + rz * rz + c[1];")
+    L.append("const T u = rx * rx + ry * ry + rz * rz + e2;")
     fl += 6
-    L.append("  const T rho = hot_rsqrt(u);")
+    L.append("const T rho = hot_rsqrt(u);")
     fl += 1
-    L.append("  const T w = rho * rho;")
+    L.append("const T w = rho * rho;")
     fl += 1
-    L.append(f"  const T {mname((1,0,0))} = rx * w, {mname((0,1,0))} = ry * w, {mname((0,0,1))} = rz * w;")
+    L.append(f"const T {mname((1,0,0))} = rx * w, {mname((0,1,0))} = ry * w, {mname((0,0,1))} = rz * w;")
     fl += 3
-    L.append(f"  const T {mname((0,0,0))} = T(1);")
-    # accumulators: S_{k,n}, G_{k,d}
-    have_s = set()
-    have_g = set()
+    have_s, have_g = set(), set()
     for n in range(0, p + 1):
         if n >= 2:
             for a in midx(n)[ncomp(n - 1):]:
@@ -125,26 +116,24 @@ def gen_eval(p):
                 prev = list(a)
                 prev[d] -= 1
                 unit = [mname((1,0,0)), mname((0,1,0)), mname((0,0,1))][d]
-                L.append(f"  const T {mname(a)} = {mname(tuple(prev))} * {unit};")
+                L.append(f"const T {mname(a)} = {mname(tuple(prev))} * {unit};")
                 fl += 1
-        # S terms of degree n
         for k in range(p // 2 + 1):
             if n + 2 * k > p:
                 continue
             acc = f"s{k}_{n}"
             for b in midx(n)[ncomp(n - 1) if n > 0 else 0:]:
-                ci = sidx[(k, b)]
+                ref = f"@S,{k},{b[0]},{b[1]},{b[2]}@"
                 if acc not in have_s:
                     if n == 0:
-                        L.append(f"  T {acc} = c[{ci}];")
+                        L.append(f"T {acc} = {ref};")
                     else:
-                        L.append(f"  T {acc} = c[{ci}] * {mname(b)};")
+                        L.append(f"T {acc} = {ref} * {mname(b)};")
                         fl += 1
                     have_s.add(acc)
                 else:
-                    L.append(f"  {acc} += c[{ci}] * {mname(b)};")
+                    L.append(f"{acc} += {ref} * {mname(b)};")
                     fl += 2
-        # gradient terms whose monomial y^{b-e_d} has degree n
         for k in range(p // 2 + 1):
             if n + 1 + 2 * k > p:
                 continue
@@ -155,61 +144,114 @@ def gen_eval(p):
                     mono = list(b)
                     mono[d] -= 1
                     mono = tuple(mono)
-                    gi = gidx[(k, d, b)]
+                    ref = f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
                     acc = f"g{k}_{d}"
                     if acc not in have_g:
                         if n == 0:
-                            L.append(f"  T {acc} = c[{gi}];")
+                            L.append(f"T {acc} = {ref};")
                         else:
-                            L.append(f"  T {acc} = c[{gi}] * {mname(mono)};")
+                            L.append(f"T {acc} = {ref} * {mname(mono)};")
                             fl += 1
                         have_g.add(acc)
                     else:
-                        L.append(f"  {acc} += c[{gi}] * {mname(mono)};")
+                        L.append(f"{acc} += {ref} * {mname(mono)};")
                         fl += 2
-    # combine: S = sum_k w^k S_k ; Tr = sum_{k,n} w^k (1+2k+2n) S_{k,n} ; Gd = sum_k w^k g_{k,d}
     K = p // 2
     for k in range(K + 1):
         terms = [f"s{k}_{n}" for n in range(p - 2 * k + 1)]
-        L.append(f"  const T S{k} = " + " + ".join(terms) + ";")
+        L.append(f"const T S{k} = " + " + ".join(terms) + ";")
         fl += len(terms) - 1
         tt = [f"T({1 + 2 * k + 2 * n}) * s{k}_{n}" if (1 + 2 * k + 2 * n) != 1 else f"s{k}_{n}"
               for n in range(p - 2 * k + 1)]
-        L.append(f"  const T Q{k} = " + " + ".join(tt) + ";")
-        fl += 2 * (len(tt) - 1) + (0 if len(tt) == 1 else 0)
-    # Horner in w
+        L.append(f"const T Q{k} = " + " + ".join(tt) + ";")
+        fl += 2 * (len(tt) - 1)
+
     def horner(names):
         expr = names[-1]
         for nm in reversed(names[:-1]):
             expr = f"({nm} + w * {expr})"
         return expr
-    L.append(f"  const T S = {horner([f'S{k}' for k in range(K + 1)])};")
-    L.append(f"  const T Q = {horner([f'Q{k}' for k in range(K + 1)])};")
+    L.append(f"const T S = {horner([f'S{k}' for k in range(K + 1)])};")
+    L.append(f"const T Q = {horner([f'Q{k}' for k in range(K + 1)])};")
     fl += 4 * K
+    gk = {(k, d) for (k, d, _) in g_terms(p)}
     for d in range(3):
-        ks = [k for k in range(K + 1) if (k, d) in {(kk, dd) for (kk, dd, _) in Gt}]
+        ks = [k for k in range(K + 1) if (k, d) in gk]
         if ks:
             names = [f"g{k}_{d}" if k in ks else "T(0)" for k in range(max(ks) + 1)]
-            L.append(f"  const T G{d} = {horner(names)};")
+            L.append(f"const T G{d} = {horner(names)};")
             fl += 2 * (len(names) - 1)
         else:
-            L.append(f"  const T G{d} = T(0);")
-    L.append("  phi -= rho * S;")
+            L.append(f"const T G{d} = T(0);")
+    L.append("phi -= rho * S;")
     fl += 2
-    L.append("  const T rs = rho * is;")
+    L.append("const T rs = rho * is;")
     fl += 1
     for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
-        L.append(f"  {an} += rs * (w * G{d} - {yn} * Q);")
+        L.append(f"{an} += rs * (w * G{d} - {yn} * Q);")
         fl += 5
-    L.append("}")
-    return "\n".join(L), ns, ng, fl
+    return L, fl
+
+
+def layout(p):
+    """Record slots in the order the interaction code first reads them (slots 0..3 hold
+    inv_s, eps^2/s^2 and padding), so that vector loads stay close to their use."""
+    L, _ = _eval_stmts(p)
+    order = []
+    seen = set()
+    for st in L:
+        parts = st.split("@")
+        for i in range(1, len(parts), 2):
+            key = parts[i]
+            if key not in seen:
+                seen.add(key)
+                order.append(key)
+    return {key: 4 + i for i, key in enumerate(order)}
+
+
+def gen_eval(p):
+    """Two specialisations: float (float4 loads) and double (double2 loads)."""
+    L, fl = _eval_stmts(p)
+    slot = layout(p)
+    out = []
+    for T, VEC, VW, suf in (("float", "float4", 4, "f32"), ("double", "double2", 2, "f64")):
+        comp = "xyzw"
+        code = [f"__device__ __forceinline__ void m2p_eval_{p}_{suf}(const {T}* __restrict__ c, {T} rx, {T} ry, "
+                f"{T} rz, {T}& phi, {T}& ax, {T}& ay, {T}& az) {{",
+                f"  using T = {T};",
+                f"  const {VEC}* __restrict__ cv = reinterpret_cast<const {VEC}*>(c);"]
+        loaded = set()
+
+        def need(g):
+            if g not in loaded:
+                loaded.add(g)
+                code.append(f"  const {VEC} v{g} = cv[{g}];")
+
+        need(0)
+        if VW == 2:
+            code.append("  const T is = v0.x, e2 = v0.y;")
+        else:
+            code.append("  const T is = v0.x, e2 = v0.y;")
+        for st in L:
+            parts = st.split("@")
+            for i in range(1, len(parts), 2):
+                sl = slot[parts[i]]
+                g = sl // VW
+                need(g)
+                parts[i] = f"v{g}.{comp[sl % VW]}"
+            code.append("  " + "".join(parts))
+        code.append("}")
+        out.append("\n".join(code))
+    ns, ng = len(s_terms(p)), len(g_terms(p))
+    return "\n".join(out), ns, ng, fl
 
 
 def gen_record(p):
-    """Raw moments -> scaled traced coefficients (FP64 arithmetic)."""
+    """Raw moments -> scaled traced coefficients (FP64 arithmetic), in record order."""
     S = s_terms(p)
     Gt = g_terms(p)
     ns = len(S)
+    slot = layout(p)
     idx = {a: i for i, a in enumerate(midx(p))}
     L = []
     L.append(f"template <typename T> __device__ __forceinline__ void m2p_record_{p}("
@@ -219,19 +261,22 @@ def gen_record(p):
     L.append(f"  for (int q = 1; q < {2 * p + 2}; ++q) ip[q] = ip[q - 1] * inv_s;")
     L.append("  rec[0] = T(inv_s); rec[1] = T((eps * inv_s) * (eps * inv_s)); rec[2] = T(0); rec[3] = T(0);")
     L.append(f"  double C[{ns}];")
+    sidx = {}
     for i, (k, n, b) in enumerate(S):
         m = n + k
         const = (-1) ** k * dfact(2 * m - 1) / (2 ** k * fact3(b))
-        # sum over |l| = k of M_{b+2l} / l!
         terms = []
         for l in midx(k)[ncomp(k - 1) if k > 0 else 0:]:
             a = add(b, (2 * l[0], 2 * l[1], 2 * l[2]))
             terms.append(f"M[{idx[a]}] * {1.0 / fact3(l)!r}")
         L.append(f"  C[{i}] = G * ip[{1 + 2 * k + n}] * {const!r} * (" + " + ".join(terms) + ");")
-        L.append(f"  rec[{4 + i}] = T(C[{i}]);")
-    sidx = {(k, b): i for i, (k, n, b) in enumerate(S)}
-    for j, (k, d, b) in enumerate(Gt):
-        L.append(f"  rec[{4 + ns + j}] = T({b[d]}.0 * C[{sidx[(k, b)]}]);")
+        L.append(f"  rec[{slot[f'S,{k},{b[0]},{b[1]},{b[2]}']}] = T(C[{i}]);")
+        sidx[(k, b)] = i
+    for (k, d, b) in Gt:
+        L.append(f"  rec[{slot[f'G,{k},{d},{b[0]},{b[1]},{b[2]}']}] = T({b[d]}.0 * C[{sidx[(k, b)]}]);")
+    rl = (4 + ns + len(Gt) + 3) // 4 * 4
+    for q in range(4 + ns + len(Gt), rl):
+        L.append(f"  rec[{q}] = T(0);")
     L.append("}")
     return "\n".join(L)
 
@@ -293,7 +338,8 @@ def main(out_path):
           "const double* __restrict__ M, double inv_s, double G, double eps, T* __restrict__ rec) {"]
     for p in range(PMAX + 1):
         kw = "if" if p == 0 else "else if"
-        ev.append(f"  {kw} constexpr (P == {p}) m2p_eval_{p}<T>(c, rx, ry, rz, phi, ax, ay, az);")
+        ev.append(f"  {kw} constexpr (P == {p}) {{ if constexpr (sizeof(T) == 4) m2p_eval_{p}_f32(c, rx, ry, rz, phi, ax, ay, az); "
+                  f"else m2p_eval_{p}_f64(c, rx, ry, rz, phi, ax, ay, az); }}")
         rc.append(f"  {kw} constexpr (P == {p}) m2p_record_{p}<T>(M, inv_s, G, eps, rec);")
     ev.append("}")
     rc.append("}")

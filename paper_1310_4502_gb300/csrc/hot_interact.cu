@@ -3,28 +3,89 @@
 // source cells and n sink particles; the source data is reorganised once per block
 // and shared by the n sinks).
 //
-// One warp per sink group (dynamic work counter).  The group's sinks map to lanes; when
-// a group has fewer than 32 sinks, each sink gets floor(32/n) lanes that split the
-// source lists and are combined at the end.  Source cell records and source particles
-// are staged in shared memory per chunk and read as warp-wide broadcasts.
+// One warp per sink group (dynamic work counter).  Groups of up to 32 sinks map one
+// sink to a lane, and when there are fewer than 32 sinks, each sink gets several lanes
+// that split the source lists (combined at the end).  Groups of 33..64 sinks put two
+// sinks on every lane, so each staged coefficient is used twice per load.
 //
-// Mixed precision (T = float): all interaction arithmetic in float32 on coordinates
-// relative to the group centre g.  float64 is used only for the absolute positions and
-// the offsets z_c - g and x_i - g (rounded to float32 afterwards).  Each lane sums a
-// chunk in plain float32 and adds the chunk total into a compensated (Kahan) pair; the
-// pairs are combined in float64.  T = double runs the same code in float64.
+// Cell records (the traced coefficients of every accepted cell) are staged per warp in
+// shared memory by TMA bulk copies (cp.async.bulk, completion on an mbarrier), double
+// buffered: the copies of chunk c+1 are in flight while chunk c is evaluated.  Every
+// wait on an mbarrier is bounded; an expired wait sets the status word and the warp
+// stops.  Source particles of the P2P list are staged by the lanes.
+//
+// Mixed precision (T = float): interaction arithmetic in float32 on coordinates relative
+// to the group centre g; float64 only for the absolute positions and the offsets z_c - g
+// and x_i - g (rounded to float32 afterwards).  Each lane sums a chunk in plain float32
+// and adds the chunk total into a compensated (Kahan) pair; pairs are combined in
+// float64.  T = double runs the same code in float64.
 #include "hot_common.cuh"
 #include "generated.cuh"
 
 namespace {
 
-constexpr int IW = 4;   // warps per block
-constexpr int SRC = 64; // staged source particles per P2P chunk
+constexpr int IW = 4;    // warps per block
+constexpr int SRC = 64;  // staged source particles per P2P chunk
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // try_wait polls before a wait is declared expired
 
-template <int P>
-struct ChunkCells {
-    static constexpr int value = P <= 4 ? 32 : 16;
+template <int P, class T>
+struct Cfg {
+    static constexpr int RL = HOT_REC_LEN[P];
+    static constexpr int CH = sizeof(T) == 4 ? (P <= 4 ? 16 : 8) : (P <= 4 ? 8 : 4);
 };
+
+template <int P, class T>
+struct alignas(16) Smem {
+    static constexpr int RL = Cfg<P, T>::RL;
+    static constexpr int CH = Cfg<P, T>::CH;
+    T rec[2][CH][RL];
+    T off[2][CH][4];
+    T src[SRC][4];
+    double red[32][4];
+    int32_t sidx[SRC];
+    unsigned long long bar[2];
+};
+
+// ---- TMA bulk copy and mbarrier helpers (inline PTX) ----
+__device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sptr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sptr(dst)),
+        "l"(src), "r"(bytes), "r"(sptr(bar))
+        : "memory");
+}
+
+// Warp-collective bounded wait: every lane polls until it has observed the phase
+// completion itself; the result is the same on all lanes.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase)
+{
+    uint32_t done = 0;
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        if (!done)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(sptr(bar)), "r"(phase)
+                : "memory");
+        if (__all_sync(0xffffffffu, done)) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
 {
@@ -35,33 +96,199 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
 }
 __device__ __forceinline__ void kahan_add(double &sum, double &comp, double v) { sum += v; }
 
-template <int P, class T>
-struct Smem {
-    static constexpr int CH = ChunkCells<P>::value;
-    static constexpr int RL = HOT_REC_LEN[P];
-    T rec[CH][RL];
-    T off[CH][4];
-    T src[SRC][4];
-    int32_t sidx[SRC];
-    double red[32][4];
+template <class T>
+struct Acc {
+    T s[4], c[4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) s[d] = c[d] = T(0);
+    }
+    __device__ __forceinline__ void add(T ax, T ay, T az, T ph)
+    {
+        kahan_add(s[0], c[0], ax);
+        kahan_add(s[1], c[1], ay);
+        kahan_add(s[2], c[2], az);
+        kahan_add(s[3], c[3], ph);
+    }
+    __device__ __forceinline__ double get(int d) const { return (double)s[d] - (double)c[d]; }
 };
 
-template <int P, class T>
+struct Group {
+    int64_t gb;      // first sorted slot of the group's sinks
+    int n;           // sinks
+    double gx, gy, gz;
+    int64_t m0, m1;  // M2P list range
+    int64_t p0, p1;  // P2P list range
+};
+
+// M2P over the group's cell list for NS sink positions per lane.  Lane (sink, split sj)
+// evaluates cells sj, sj + nsplit, ... of every staged chunk.  Returns false when a
+// bounded wait expired (status flagged, the warp must stop).
+template <int P, class T, int NS>
+__device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const int32_t *__restrict__ l_m2p,
+                                         const double *__restrict__ ccom, const T *__restrict__ rec,
+                                         const T (&x)[NS][3], int sj, int nsplit, bool active, Acc<T> (&acc)[NS],
+                                         uint32_t (&phase)[2], unsigned *status)
+{
+    constexpr int CH = Cfg<P, T>::CH;
+    constexpr int RL = Cfg<P, T>::RL;
+    constexpr uint32_t RB = RL * sizeof(T);
+    const unsigned lane = lane_id();
+    const int64_t nm = G.m1 - G.m0;
+    const int nch = (int)((nm + CH - 1) / CH);
+    if (nch == 0) return true;
+
+    auto issue = [&](int c, int b) {
+        const int64_t e0 = G.m0 + (int64_t)c * CH;
+        const int ne = (int)(G.m1 - e0 < CH ? G.m1 - e0 : CH);
+        int32_t cell = 0;
+        if ((int)lane < ne) {
+            cell = l_m2p[e0 + lane];
+            sm.off[b][lane][0] = (T)(ccom[3 * (int64_t)cell + 0] - G.gx);
+            sm.off[b][lane][1] = (T)(ccom[3 * (int64_t)cell + 1] - G.gy);
+            sm.off[b][lane][2] = (T)(ccom[3 * (int64_t)cell + 2] - G.gz);
+        }
+        if (lane == 0) mbar_expect_tx(&sm.bar[b], (uint32_t)ne * RB);
+        __syncwarp();
+        if ((int)lane < ne) {
+            fence_async_smem();
+            bulk_g2s(&sm.rec[b][lane][0], rec + (int64_t)cell * RL, RB, &sm.bar[b]);
+        }
+    };
+
+    issue(0, 0);
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        if (c + 1 < nch) issue(c + 1, b ^ 1);
+        if (!mbar_wait(&sm.bar[b], phase[b])) {
+            if (lane == 0) hot_flag(status, HOT_ST_TIMEOUT);
+            mbar_wait(&sm.bar[b], phase[b]);
+            if (c + 1 < nch) mbar_wait(&sm.bar[b ^ 1], phase[b ^ 1]);
+            return false;
+        }
+        phase[b] ^= 1;
+        __syncwarp();
+        const int ne = (int)(nm - (int64_t)c * CH < CH ? nm - (int64_t)c * CH : CH);
+        if (active) {
+            T ph[NS], ax[NS], ay[NS], az[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = T(0);
+            for (int k = sj; k < ne; k += nsplit) {
+                const T *r = &sm.rec[b][k][0];
+                const T ox = sm.off[b][k][0], oy = sm.off[b][k][1], oz = sm.off[b][k][2];
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    m2p_eval<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, ph[s], ax[s], ay[s], az[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) acc[s].add(ax[s], ay[s], az[s], ph[s]);
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// P2P over the group's leaf list: source particles staged SRC at a time by the lanes,
+// positions relative to g (float32: leaf-relative copy + rounded leaf offset).
+template <int P, class T, int NS>
+__device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group &G, const int32_t *__restrict__ l_p2p,
+                                         const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
+                                         const double *__restrict__ ccom, const float4 *__restrict__ prel,
+                                         const double *__restrict__ spos, const double *__restrict__ smass,
+                                         const T (&x)[NS][3], const int32_t (&self)[NS], int sj, int nsplit,
+                                         bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
+{
+    const unsigned lane = lane_id();
+    int fill = 0;
+    auto flush = [&]() {
+        __syncwarp();
+        if (active) {
+            T ph[NS], ax[NS], ay[NS], az[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = T(0);
+            for (int k = sj; k < fill; k += nsplit) {
+                const T sx = sm.src[k][0], sy = sm.src[k][1], sz = sm.src[k][2], m = sm.src[k][3];
+                const int32_t id = sm.sidx[k];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const T dx = sx - x[s][0], dy = sy - x[s][1], dz = sz - x[s][2];
+                    const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+                    const bool ok = (r2 > T(0)) && (id != self[s]);
+                    const T rinv = ok ? hot_rsqrt(r2) : T(0);
+                    const T mr = m * rinv;
+                    const T mr3 = mr * rinv * rinv;
+                    ax[s] += mr3 * dx;
+                    ay[s] += mr3 * dy;
+                    az[s] += mr3 * dz;
+                    ph[s] -= mr;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) acc[s].add(Gt * ax[s], Gt * ay[s], Gt * az[s], Gt * ph[s]);
+        }
+        __syncwarp();
+        fill = 0;
+    };
+    for (int64_t e = G.p0; e < G.p1; ++e) {
+        const int32_t leaf = l_p2p[e];
+        const int64_t lb = cbegin[leaf];
+        const int lc = ccount[leaf];
+        const double ox = ccom[3 * (int64_t)leaf + 0] - G.gx;
+        const double oy = ccom[3 * (int64_t)leaf + 1] - G.gy;
+        const double oz = ccom[3 * (int64_t)leaf + 2] - G.gz;
+        for (int q0 = 0; q0 < lc; q0 += 32) {
+            const int take = lc - q0 < 32 ? lc - q0 : 32;
+            if (fill + take > SRC) flush();
+            if ((int)lane < take) {
+                const int64_t j = lb + q0 + lane;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 v = prel[j];
+                    sm.src[fill + lane][0] = v.x + (float)ox;
+                    sm.src[fill + lane][1] = v.y + (float)oy;
+                    sm.src[fill + lane][2] = v.z + (float)oz;
+                    sm.src[fill + lane][3] = v.w;
+                } else {
+                    sm.src[fill + lane][0] = (T)(spos[3 * j + 0] - G.gx);
+                    sm.src[fill + lane][1] = (T)(spos[3 * j + 1] - G.gy);
+                    sm.src[fill + lane][2] = (T)(spos[3 * j + 2] - G.gz);
+                    sm.src[fill + lane][3] = (T)smass[j];
+                }
+                sm.sidx[fill + lane] = (int32_t)j;
+            }
+            fill += take;
+        }
+    }
+    if (fill > 0) flush();
+}
+
+// cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
+// NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
+// NS = 2: two sinks per lane (slices of 64 sinks).
+template <int P, class T, int NS>
 __global__ void __launch_bounds__(IW * 32) k_interact(
-    int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
+    int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ spos,
     const double *__restrict__ smass, const float4 *__restrict__ prel, const double *__restrict__ ccom,
     const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
-    T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out)
+    T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
+    unsigned *__restrict__ status)
 {
     using S = Smem<P, T>;
-    constexpr int CH = S::CH;
-    constexpr int RL = S::RL;
+    constexpr int CH = Cfg<P, T>::CH;
+    constexpr int SL = 32 * NS;  // sinks per slice
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = reinterpret_cast<S *>(smem_raw)[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     const T Gt = (T)G;
+    if (lane == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    uint32_t phase[2] = {0u, 0u};
 
     for (;;) {
         unsigned g0 = 0;
@@ -69,141 +296,96 @@ __global__ void __launch_bounds__(IW * 32) k_interact(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
-        const int64_t gb = cbegin[gc];
-        const int n = ccount[gc];
-        const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
-        const int64_t m0 = off_m2p[g], m1 = off_m2p[g + 1];
-        const int64_t p0 = off_p2p[g], p1 = off_p2p[g + 1];
-
-        for (int s0 = 0; s0 < n; s0 += 32) {
-            const int ns = n - s0 < 32 ? n - s0 : 32;
-            const int nsplit = 32 / ns;
-            const int si = (int)lane % ns;
-            const int sj = (int)lane / ns;
+        Group Gr;
+        Gr.n = ccount[gc];
+        if ((cls == 1 && Gr.n > 32) || (cls == 2 && Gr.n <= 32)) continue;
+        Gr.gb = cbegin[gc];
+        Gr.gx = gcen[3 * g + 0];
+        Gr.gy = gcen[3 * g + 1];
+        Gr.gz = gcen[3 * g + 2];
+        Gr.m0 = off_m2p[g];
+        Gr.m1 = off_m2p[g + 1];
+        Gr.p0 = off_p2p[g];
+        Gr.p1 = off_p2p[g + 1];
+        for (int s0 = 0; s0 < Gr.n; s0 += SL) {
+            const int rem = Gr.n - s0;
+            int ns, nsplit, si, sj;
+            if (NS == 1) {
+                ns = rem < 32 ? rem : 32;
+                nsplit = 32 / ns;
+                if (nsplit > CH) nsplit = CH;
+                si = (int)lane % ns;
+                sj = (int)lane / ns;
+            } else {
+                ns = rem;
+                nsplit = 1;
+                si = (int)lane;
+                sj = 0;
+            }
             const bool active = sj < nsplit;
-            const int64_t s = gb + s0 + si;
-            const T xi = (T)(spos[3 * s + 0] - gx);
-            const T yi = (T)(spos[3 * s + 1] - gy);
-            const T zi = (T)(spos[3 * s + 2] - gz);
-            T sum[4] = {0, 0, 0, 0}, cmp[4] = {0, 0, 0, 0};
-
-            // ---- M2P over the cell list ----
-            for (int64_t e0 = m0; e0 < m1; e0 += CH) {
-                const int ne = (int)(m1 - e0 < CH ? m1 - e0 : CH);
-                for (int k = 0; k < ne; ++k) {
-                    const int32_t cell = l_m2p[e0 + k];
-                    const T *src = rec + (int64_t)cell * RL;
-                    for (int q = lane; q < RL; q += 32) sm.rec[k][q] = src[q];
-                }
-                if ((int)lane < ne) {
-                    const int32_t cell = l_m2p[e0 + lane];
-                    sm.off[lane][0] = (T)(ccom[3 * (int64_t)cell + 0] - gx);
-                    sm.off[lane][1] = (T)(ccom[3 * (int64_t)cell + 1] - gy);
-                    sm.off[lane][2] = (T)(ccom[3 * (int64_t)cell + 2] - gz);
-                }
+            T x[NS][3];
+            int32_t self[NS];
+            int64_t slot[NS];
+            bool valid[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const int k = si + 32 * q;
+                valid[q] = k < ns;
+                slot[q] = Gr.gb + s0 + (valid[q] ? k : ns - 1);
+                x[q][0] = (T)(spos[3 * slot[q] + 0] - Gr.gx);
+                x[q][1] = (T)(spos[3 * slot[q] + 1] - Gr.gy);
+                x[q][2] = (T)(spos[3 * slot[q] + 2] - Gr.gz);
+                self[q] = (int32_t)slot[q];
+            }
+            Acc<T> acc[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) acc[q].zero();
+            if (!m2p_list<P, T, NS>(sm, Gr, l_m2p, ccom, rec, x, sj, nsplit, active, acc, phase, status)) return;
+            p2p_list<P, T, NS>(sm, Gr, l_p2p, cbegin, ccount, ccom, prel, spos, smass, x, self, sj, nsplit, active,
+                               eps2, Gt, acc);
+            if (NS == 1) {
+                // combine the list splits of each sink in float64
                 __syncwarp();
                 if (active) {
-                    T ph = 0, ax = 0, ay = 0, az = 0;
-                    for (int k = sj; k < ne; k += nsplit)
-                        m2p_eval<P, T>(&sm.rec[k][0], xi - sm.off[k][0], yi - sm.off[k][1], zi - sm.off[k][2], ph,
-                                       ax, ay, az);
-                    kahan_add(sum[0], cmp[0], ax);
-                    kahan_add(sum[1], cmp[1], ay);
-                    kahan_add(sum[2], cmp[2], az);
-                    kahan_add(sum[3], cmp[3], ph);
-                }
-                __syncwarp();
-            }
-
-            // ---- P2P over the leaf list ----
-            int fill = 0;
-            auto flush = [&]() {
-                __syncwarp();
-                if (active) {
-                    T ph = 0, ax = 0, ay = 0, az = 0;
-                    for (int k = sj; k < fill; k += nsplit) {
-                        const T dx = sm.src[k][0] - xi, dy = sm.src[k][1] - yi, dz = sm.src[k][2] - zi;
-                        const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-                        const bool ok = (r2 > T(0)) && (sm.sidx[k] != (int32_t)s);
-                        const T rinv = ok ? hot_rsqrt(r2) : T(0);
-                        const T mr = sm.src[k][3] * rinv;
-                        const T mr3 = mr * rinv * rinv;
-                        ax += mr3 * dx;
-                        ay += mr3 * dy;
-                        az += mr3 * dz;
-                        ph -= mr;
-                    }
-                    kahan_add(sum[0], cmp[0], Gt * ax);
-                    kahan_add(sum[1], cmp[1], Gt * ay);
-                    kahan_add(sum[2], cmp[2], Gt * az);
-                    kahan_add(sum[3], cmp[3], Gt * ph);
-                }
-                __syncwarp();
-                fill = 0;
-            };
-            for (int64_t e = p0; e < p1; ++e) {
-                const int32_t leaf = l_p2p[e];
-                const int64_t lb = cbegin[leaf];
-                const int lc = ccount[leaf];
-                const double ox = ccom[3 * (int64_t)leaf + 0] - gx;
-                const double oy = ccom[3 * (int64_t)leaf + 1] - gy;
-                const double oz = ccom[3 * (int64_t)leaf + 2] - gz;
-                for (int q0 = 0; q0 < lc; q0 += 32) {
-                    const int take = lc - q0 < 32 ? lc - q0 : 32;
-                    if (fill + take > SRC) flush();
-                    if ((int)lane < take) {
-                        const int64_t j = lb + q0 + lane;
-                        if constexpr (sizeof(T) == 4) {
-                            const float4 v = prel[j];
-                            sm.src[fill + lane][0] = v.x + (float)ox;
-                            sm.src[fill + lane][1] = v.y + (float)oy;
-                            sm.src[fill + lane][2] = v.z + (float)oz;
-                            sm.src[fill + lane][3] = v.w;
-                        } else {
-                            sm.src[fill + lane][0] = (T)(spos[3 * j + 0] - gx);
-                            sm.src[fill + lane][1] = (T)(spos[3 * j + 1] - gy);
-                            sm.src[fill + lane][2] = (T)(spos[3 * j + 2] - gz);
-                            sm.src[fill + lane][3] = (T)smass[j];
-                        }
-                        sm.sidx[fill + lane] = (int32_t)j;
-                    }
-                    fill += take;
-                }
-            }
-            if (fill > 0) flush();
-
-            // ---- combine the source splits of each sink in float64, write original order ----
-            __syncwarp();
-            if (active) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) sm.red[lane][d] = (double)sum[d] - (double)cmp[d];
-            }
-            __syncwarp();
-            if (active && sj == 0) {
-                double t[4] = {0, 0, 0, 0};
-                for (int j = 0; j < nsplit; ++j)
+                    for (int d = 0; d < 4; ++d) sm.red[lane][d] = acc[0].get(d);
+                }
+                __syncwarp();
+                if (active && sj == 0) {
+                    double t[4] = {0, 0, 0, 0};
+                    for (int j = 0; j < nsplit; ++j)
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) t[d] += sm.red[si + j * ns][d];
-                const int64_t i = perm[s];
-                acc_out[3 * i + 0] = t[0];
-                acc_out[3 * i + 1] = t[1];
-                acc_out[3 * i + 2] = t[2];
-                if (pot_out) pot_out[i] = t[3];
+                        for (int d = 0; d < 4; ++d) t[d] += sm.red[si + j * ns][d];
+                    const int64_t i = perm[slot[0]];
+                    acc_out[3 * i + 0] = t[0];
+                    acc_out[3 * i + 1] = t[1];
+                    acc_out[3 * i + 2] = t[2];
+                    if (pot_out) pot_out[i] = t[3];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (valid[q]) {
+                        const int64_t i = perm[slot[q]];
+                        acc_out[3 * i + 0] = acc[q].get(0);
+                        acc_out[3 * i + 1] = acc[q].get(1);
+                        acc_out[3 * i + 2] = acc[q].get(2);
+                        if (pot_out) pot_out[i] = acc[q].get(3);
+                    }
             }
             __syncwarp();
         }
     }
 }
 
-template <int P, class T>
-int forces_pt(hot_ctx *c, double *acc, double *pot)
+template <int P, class T, int NS>
+int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *pot)
 {
     cudaStream_t s = c->st;
     const size_t smem = sizeof(Smem<P, T>) * IW;
-    auto kern = k_interact<P, T>;
+    auto kern = k_interact<P, T, NS>;
     HOT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned *work = (unsigned *)(c->sizes.p + 56);
-    HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
+    HOT_CK(cudaMemsetAsync(work, 0, sizeof(unsigned), s));
     const T *rec = nullptr;
     if constexpr (sizeof(T) == 4)
         rec = c->rec32.p;
@@ -215,17 +397,20 @@ int forces_pt(hot_ctx *c, double *acc, double *pot)
     const int blocks = c->nsm * occ;
     const T eps2 = (T)(c->prm.eps * c->prm.eps);
     HOT_COUNT_LAUNCH();
-    kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->spos.p,
+    kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
-                                       c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot);
+                                       c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot, c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }
 
 template <int P>
 int forces_p(hot_ctx *c, double *acc, double *pot)
 {
-    if (c->prm.precision == HOT_FP64) return forces_pt<P, double>(c, acc, pot);
-    return forces_pt<P, float>(c, acc, pot);
+    unsigned *work = (unsigned *)(c->sizes.p + 56);
+    if (c->prm.precision == HOT_FP64) return launch_interact<P, double, 1>(c, 0, work, acc, pot);
+    int r = launch_interact<P, float, 1>(c, 1, work, acc, pot);
+    if (r) return r;
+    return launch_interact<P, float, 2>(c, 2, work + 2, acc, pot);
 }
 
 }  // namespace
