@@ -55,6 +55,12 @@ struct DBuf {
 
 enum { ST_TIMING_EVENTS = 14 };
 
+// Per-cell traversal record: centre of mass and the acceptance radius r_c for the
+// current tolerance (a cell is accepted for a group iff |z - g| - Delta_max >= r_c).
+struct alignas(32) TCell {
+    double x, y, z, rc;
+};
+
 struct hot_ctx {
     hot_params prm;
     cudaStream_t st = nullptr;
@@ -105,6 +111,7 @@ struct hot_ctx {
     DBuf<int64_t> off_m2p, off_p2p;
     DBuf<int32_t> l_m2p, l_p2p;
     DBuf<int32_t> trav_scratch;
+    DBuf<TCell> tcell;
     int trav_cap = 2048;
     DBuf<int64_t> pairs_per_group;
 

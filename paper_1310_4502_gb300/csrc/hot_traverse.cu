@@ -28,10 +28,51 @@ __device__ __forceinline__ double mac_bound(double d, double b, double B1, doubl
     return __dmul_rn(__ddiv_rn(__ddiv_rn(G, __dmul_rn(d, d)), __dmul_rn(q, q)), __dsub_rn(t1, t2));
 }
 
+// Acceptance radius of every cell for the tolerance: E is strictly decreasing on
+// (b_max, inf), so "d > b_max and E(d) <= tol" is "d >= r_c" with E(r_c) = tol, found by
+// doubling and bisection in float64 (r_c = 0 when b_max = 0, where E vanishes).
+__global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
+                             const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
+                             double G, double tol, TCell *__restrict__ tc)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double b = cbmax[c], B1 = cB1[c], B2 = cB2[c];
+    double rc = 0.0;
+    if (b > 0.0) {
+        double lo = b, hi = 2.0 * b;
+        int k = 0;
+        while (!(mac_bound(hi, b, B1, B2, p, G) <= tol) && k < 1100) {
+            lo = hi;
+            hi *= 2.0;
+            ++k;
+        }
+        if (k >= 1100) {
+            rc = INFINITY;
+        } else {
+            for (int it = 0; it < 64; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (!(mid > lo && mid < hi)) break;
+                if (mac_bound(mid, b, B1, B2, p, G) <= tol)
+                    hi = mid;
+                else
+                    lo = mid;
+            }
+            rc = hi;
+        }
+    }
+    TCell t;
+    t.x = ccom[3 * c + 0];
+    t.y = ccom[3 * c + 1];
+    t.z = ccom[3 * c + 2];
+    t.rc = rc;
+    tc[c] = t;
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
-    const double *__restrict__ gdmax, const uint64_t *__restrict__ ckey, const int32_t *__restrict__ clevel,
+    const double *__restrict__ gdmax, const TCell *__restrict__ tcell, const int32_t *__restrict__ cend,
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol,
@@ -51,8 +92,6 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
-        const uint64_t gkey = ckey[gc];
-        const int glev = clevel[gc];
         const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
         const double dmax = gdmax[g];
         int64_t om = 0, op = 0;
@@ -74,21 +113,31 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 const int32_t c = i < na ? A[i] : -1;
                 int kind = 0;  // 1 M2P, 2 P2P, 3 open
                 if (c >= 0) {
-                    const int lev = clevel[c];
                     const bool leaf = cnchild[c] == 0;
-                    const bool anc = lev <= glev && (gkey >> (3 * (glev - lev))) == ckey[c];
+                    // pre-order: c is the group's cell or an ancestor iff gc lies in c's subtree
+                    const bool anc = c <= gc && gc < cend[c];
                     if (anc) {
                         kind = leaf ? 2 : 3;
                     } else {
-                        double dx = __dsub_rn(ccom[3 * (int64_t)c + 0], gx);
-                        double dy = __dsub_rn(ccom[3 * (int64_t)c + 1], gy);
-                        double dz = __dsub_rn(ccom[3 * (int64_t)c + 2], gz);
-                        double dist = __dsqrt_rn(
-                            __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-                        double d = __dsub_rn(dist, dmax);
-                        double b = cbmax[c];
-                        bool acc = false;
-                        if (d > b) acc = mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                        const TCell t = tcell[c];
+                        const double dx = t.x - gx, dy = t.y - gy, dz = t.z - gz;
+                        const double dist2 = dx * dx + dy * dy + dz * dz;
+                        const double thr = dmax + t.rc;
+                        const double thr2 = thr * thr;
+                        bool acc;
+                        if (dist2 > thr2 * (1.0 + 1e-9)) {
+                            acc = true;
+                        } else if (dist2 < thr2 * (1.0 - 1e-9) || !(t.rc < INFINITY)) {
+                            acc = false;
+                        } else {
+                            // within 1e-9 of the threshold: the acceptance test as stated
+                            const double ex = __dsub_rn(t.x, gx), ey = __dsub_rn(t.y, gy), ez = __dsub_rn(t.z, gz);
+                            const double dist = __dsqrt_rn(
+                                __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+                            const double d = __dsub_rn(dist, dmax);
+                            const double b = cbmax[c];
+                            acc = d > b && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                        }
                         kind = acc ? 1 : (leaf ? 2 : 3);
                     }
                 }
@@ -159,13 +208,17 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     const int64_t nwarps = (int64_t)blocks * TW;
     unsigned *work = (unsigned *)(c->sizes.p + 50);
     unsigned long long *stats = (unsigned long long *)(c->sizes.p + 52);
+    HOT_CK(c->tcell.ensure(c->ncell, s));
+    HOT_COUNT_LAUNCH();
+    k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
+                                                            c->p_mom, c->prm.G, tol, c->tcell.p);
     int64_t host[4];
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
         k_traverse<false><<<blocks, TW * 32, 0, s>>>(
-            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
+            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
             c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
             work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
@@ -197,7 +250,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
     HOT_COUNT_LAUNCH();
     k_traverse<true><<<blocks, TW * 32, 0, s>>>(
-        ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->ckey.p, c->clevel.p, c->child8.p, c->cnchild.p, c->ccount.p,
+        ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
         c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap, work,
         nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, c->d_status);
     hot_toc(c, 3);
