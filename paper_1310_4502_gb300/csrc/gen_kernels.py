@@ -36,6 +36,7 @@ import os
 import sys
 
 PMAX = 6
+HDR = 8  # record header slots: inv_s, eps^2/s^2, centre hi (3), centre lo (3)
 
 
 def midx(p):
@@ -121,8 +122,10 @@ def _eval_stmts(p):
         for k in range(p // 2 + 1):
             if n + 2 * k > p:
                 continue
-            acc = f"s{k}_{n}"
-            for b in midx(n)[ncomp(n - 1) if n > 0 else 0:]:
+            betas = midx(n)[ncomp(n - 1) if n > 0 else 0:]
+            nsplit = 2 if len(betas) > 6 else 1  # independent partial chains for ILP
+            for j, b in enumerate(betas):
+                acc = f"s{k}_{n}" if nsplit == 1 else f"s{k}_{n}_{j % nsplit}"
                 ref = f"@S,{k},{b[0]},{b[1]},{b[2]}@"
                 if acc not in have_s:
                     if n == 0:
@@ -134,6 +137,9 @@ def _eval_stmts(p):
                 else:
                     L.append(f"{acc} += {ref} * {mname(b)};")
                     fl += 2
+            if nsplit == 2:
+                L.append(f"const T s{k}_{n} = s{k}_{n}_0 + s{k}_{n}_1;")
+                fl += 1
         for k in range(p // 2 + 1):
             if n + 1 + 2 * k > p:
                 continue
@@ -145,7 +151,7 @@ def _eval_stmts(p):
                     mono[d] -= 1
                     mono = tuple(mono)
                     ref = f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
-                    acc = f"g{k}_{d}"
+                    acc = f"g{k}_{d}_{n}"  # one partial chain per monomial degree
                     if acc not in have_g:
                         if n == 0:
                             L.append(f"T {acc} = {ref};")
@@ -175,6 +181,12 @@ def _eval_stmts(p):
     L.append(f"const T Q = {horner([f'Q{k}' for k in range(K + 1)])};")
     fl += 4 * K
     gk = {(k, d) for (k, d, _) in g_terms(p)}
+    for k in range(K + 1):
+        for d in range(3):
+            parts = [nm for nm in sorted(have_g) if nm.startswith(f"g{k}_{d}_")]
+            if parts:
+                L.append(f"const T g{k}_{d} = " + " + ".join(parts) + ";")
+                fl += len(parts) - 1
     for d in range(3):
         ks = [k for k in range(K + 1) if (k, d) in gk]
         if ks:
@@ -194,8 +206,9 @@ def _eval_stmts(p):
 
 
 def layout(p):
-    """Record slots in the order the interaction code first reads them (slots 0..3 hold
-    inv_s, eps^2/s^2 and padding), so that vector loads stay close to their use."""
+    """Record slots in the order the interaction code first reads them, so that vector
+    loads stay close to their use.  Slots 0..7 hold the header: inv_s, eps^2/s^2, and the
+    cell centre as a hi/lo pair (hi = centre rounded to T, lo = the rounding remainder)."""
     L, _ = _eval_stmts(p)
     order = []
     seen = set()
@@ -206,7 +219,7 @@ def layout(p):
             if key not in seen:
                 seen.add(key)
                 order.append(key)
-    return {key: 4 + i for i, key in enumerate(order)}
+    return {key: HDR + i for i, key in enumerate(order)}
 
 
 def gen_eval(p):
@@ -255,11 +268,13 @@ def gen_record(p):
     idx = {a: i for i, a in enumerate(midx(p))}
     L = []
     L.append(f"template <typename T> __device__ __forceinline__ void m2p_record_{p}("
-             "const double* __restrict__ M, double inv_s, double G, double eps, T* __restrict__ rec) {")
+             "const double* __restrict__ M, const double* __restrict__ z, double inv_s, double G, double eps, "
+             "T* __restrict__ rec) {")
     L.append(f"  double ip[{p + 2 + p}];")
     L.append("  ip[0] = 1.0;")
     L.append(f"  for (int q = 1; q < {2 * p + 2}; ++q) ip[q] = ip[q - 1] * inv_s;")
-    L.append("  rec[0] = T(inv_s); rec[1] = T((eps * inv_s) * (eps * inv_s)); rec[2] = T(0); rec[3] = T(0);")
+    L.append("  rec[0] = T(inv_s); rec[1] = T((eps * inv_s) * (eps * inv_s));")
+    L.append("  for (int d = 0; d < 3; ++d) { const T hi = T(z[d]); rec[2 + d] = hi; rec[5 + d] = T(z[d] - double(hi)); }")
     L.append(f"  double C[{ns}];")
     sidx = {}
     for i, (k, n, b) in enumerate(S):
@@ -274,8 +289,8 @@ def gen_record(p):
         sidx[(k, b)] = i
     for (k, d, b) in Gt:
         L.append(f"  rec[{slot[f'G,{k},{d},{b[0]},{b[1]},{b[2]}']}] = T({b[d]}.0 * C[{sidx[(k, b)]}]);")
-    rl = (4 + ns + len(Gt) + 3) // 4 * 4
-    for q in range(4 + ns + len(Gt), rl):
+    rl = (HDR + ns + len(Gt) + 3) // 4 * 4
+    for q in range(HDR + ns + len(Gt), rl):
         L.append(f"  rec[{q}] = T(0);")
     L.append("}")
     return "\n".join(L)
@@ -309,7 +324,7 @@ def main(out_path):
         code, ns, ng, fl = gen_eval(p)
         evals.append(code)
         records.append(gen_record(p))
-        rl = 4 + ns + ng
+        rl = HDR + ns + ng
         rl = (rl + 3) // 4 * 4
         recl.append(rl)
         nsl.append(ns)
@@ -335,12 +350,13 @@ def main(out_path):
     ev = ["template <int P, typename T> __device__ __forceinline__ void m2p_eval("
           "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {"]
     rc = ["template <int P, typename T> __device__ __forceinline__ void m2p_record("
-          "const double* __restrict__ M, double inv_s, double G, double eps, T* __restrict__ rec) {"]
+          "const double* __restrict__ M, const double* __restrict__ z, double inv_s, double G, double eps, "
+          "T* __restrict__ rec) {"]
     for p in range(PMAX + 1):
         kw = "if" if p == 0 else "else if"
         ev.append(f"  {kw} constexpr (P == {p}) {{ if constexpr (sizeof(T) == 4) m2p_eval_{p}_f32(c, rx, ry, rz, phi, ax, ay, az); "
                   f"else m2p_eval_{p}_f64(c, rx, ry, rz, phi, ax, ay, az); }}")
-        rc.append(f"  {kw} constexpr (P == {p}) m2p_record_{p}<T>(M, inv_s, G, eps, rec);")
+        rc.append(f"  {kw} constexpr (P == {p}) m2p_record_{p}<T>(M, z, inv_s, G, eps, rec);")
     ev.append("}")
     rc.append("}")
     parts.append("\n".join(ev))

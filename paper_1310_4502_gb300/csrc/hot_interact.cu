@@ -3,10 +3,9 @@
 // source cells and n sink particles; the source data is reorganised once per block
 // and shared by the n sinks).
 //
-// One warp per sink group (dynamic work counter).  Groups of up to 32 sinks map one
-// sink to a lane, and when there are fewer than 32 sinks, each sink gets several lanes
-// that split the source lists (combined at the end).  Groups of 33..64 sinks put two
-// sinks on every lane, so each staged coefficient is used twice per load.
+// One warp per sink group (dynamic work counter).  The group's sinks are taken 32 at a
+// time, one sink per lane; when a slice has fewer than 32 sinks, each sink gets several
+// lanes that split the source lists (combined at the end in float64).
 //
 // Cell records (the traced coefficients of every accepted cell) are staged per warp in
 // shared memory by TMA bulk copies (cp.async.bulk, completion on an mbarrier), double
@@ -31,14 +30,17 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;  // try_wait polls before a wait is de
 template <int P, class T>
 struct Cfg {
     static constexpr int RL = HOT_REC_LEN[P];
-    static constexpr int CH = sizeof(T) == 4 ? (P <= 4 ? 16 : 8) : (P <= 4 ? 8 : 4);
+    // shared-memory stride of a staged record: 16 bytes of padding, so that lanes reading
+    // different records at the same offset hit different banks
+    static constexpr int RLS = RL + 16 / (int)sizeof(T);
+    static constexpr int CH = sizeof(T) == 4 ? 8 : 4;
 };
 
 template <int P, class T>
 struct alignas(16) Smem {
-    static constexpr int RL = Cfg<P, T>::RL;
+    static constexpr int RLS = Cfg<P, T>::RLS;
     static constexpr int CH = Cfg<P, T>::CH;
-    T rec[2][CH][RL];
+    T rec[2][CH][RLS];
     T off[2][CH][4];
     T src[SRC][4];
     double red[32][4];
@@ -114,22 +116,34 @@ struct Acc {
     __device__ __forceinline__ double get(int d) const { return (double)s[d] - (double)c[d]; }
 };
 
+template <class T>
 struct Group {
     int64_t gb;      // first sorted slot of the group's sinks
     int n;           // sinks
     double gx, gy, gz;
+    T ghi[3], glo[3];  // group centre as a T pair (hi = rounded, lo = remainder)
     int64_t m0, m1;  // M2P list range
     int64_t p0, p1;  // P2P list range
 };
 
+// Offset z_c - g in T from the hi/lo pairs of the cell (record header slots 2..7) and of
+// the group centre: (z_hi - g_hi) + (z_lo - g_lo).
+template <class T>
+__device__ __forceinline__ void centre_offset(const T *h, const Group<T> &G, T &ox, T &oy, T &oz)
+{
+    ox = (h[2] - G.ghi[0]) + (h[5] - G.glo[0]);
+    oy = (h[3] - G.ghi[1]) + (h[6] - G.glo[1]);
+    oz = (h[4] - G.ghi[2]) + (h[7] - G.glo[2]);
+}
+
 // M2P over the group's cell list for NS sink positions per lane.  Lane (sink, split sj)
-// evaluates cells sj, sj + nsplit, ... of every staged chunk.  Returns false when a
-// bounded wait expired (status flagged, the warp must stop).
+// evaluates cells sj, sj + nsplit, ... of every staged chunk.  Cell indices are loaded
+// one chunk ahead of the copies, which run one chunk ahead of the arithmetic.  Returns
+// false when a bounded wait expired (status flagged, the warp must stop).
 template <int P, class T, int NS>
-__device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const int32_t *__restrict__ l_m2p,
-                                         const double *__restrict__ ccom, const T *__restrict__ rec,
-                                         const T (&x)[NS][3], int sj, int nsplit, bool active, Acc<T> (&acc)[NS],
-                                         uint32_t (&phase)[2], unsigned *status)
+__device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_m2p,
+                                         const T *__restrict__ rec, const T (&x)[NS][3], int sj, int nsplit,
+                                         bool active, Acc<T> (&acc)[NS], uint32_t (&phase)[2], unsigned *status)
 {
     constexpr int CH = Cfg<P, T>::CH;
     constexpr int RL = Cfg<P, T>::RL;
@@ -138,17 +152,12 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const i
     const int64_t nm = G.m1 - G.m0;
     const int nch = (int)((nm + CH - 1) / CH);
     if (nch == 0) return true;
-
-    auto issue = [&](int c, int b) {
-        const int64_t e0 = G.m0 + (int64_t)c * CH;
-        const int ne = (int)(G.m1 - e0 < CH ? G.m1 - e0 : CH);
-        int32_t cell = 0;
-        if ((int)lane < ne) {
-            cell = l_m2p[e0 + lane];
-            sm.off[b][lane][0] = (T)(ccom[3 * (int64_t)cell + 0] - G.gx);
-            sm.off[b][lane][1] = (T)(ccom[3 * (int64_t)cell + 1] - G.gy);
-            sm.off[b][lane][2] = (T)(ccom[3 * (int64_t)cell + 2] - G.gz);
-        }
+    auto chunk_n = [&](int c) { return (int)(nm - (int64_t)c * CH < CH ? nm - (int64_t)c * CH : CH); };
+    auto load_idx = [&](int c) {
+        return (c < nch && (int)lane < chunk_n(c)) ? l_m2p[G.m0 + (int64_t)c * CH + lane] : 0;
+    };
+    auto issue = [&](int c, int b, int32_t cell) {
+        const int ne = chunk_n(c);
         if (lane == 0) mbar_expect_tx(&sm.bar[b], (uint32_t)ne * RB);
         __syncwarp();
         if ((int)lane < ne) {
@@ -157,10 +166,14 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const i
         }
     };
 
-    issue(0, 0);
+    issue(0, 0, load_idx(0));
+    int32_t nxt = load_idx(1);
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
-        if (c + 1 < nch) issue(c + 1, b ^ 1);
+        if (c + 1 < nch) {
+            issue(c + 1, b ^ 1, nxt);
+            nxt = load_idx(c + 2);
+        }
         if (!mbar_wait(&sm.bar[b], phase[b])) {
             if (lane == 0) hot_flag(status, HOT_ST_TIMEOUT);
             mbar_wait(&sm.bar[b], phase[b]);
@@ -168,8 +181,15 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const i
             return false;
         }
         phase[b] ^= 1;
+        const int ne = chunk_n(c);
+        if ((int)lane < ne) {
+            T ox, oy, oz;
+            centre_offset(&sm.rec[b][lane][0], G, ox, oy, oz);
+            sm.off[b][lane][0] = ox;
+            sm.off[b][lane][1] = oy;
+            sm.off[b][lane][2] = oz;
+        }
         __syncwarp();
-        const int ne = (int)(nm - (int64_t)c * CH < CH ? nm - (int64_t)c * CH : CH);
         if (active) {
             T ph[NS], ax[NS], ay[NS], az[NS];
 #pragma unroll
@@ -189,16 +209,19 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group &G, const i
     return true;
 }
 
-// P2P over the group's leaf list: source particles staged SRC at a time by the lanes,
-// positions relative to g (float32: leaf-relative copy + rounded leaf offset).
+// P2P over the group's leaf list.  Leaf metadata (first slot, count, centre offset) is
+// fetched 32 entries at a time, one entry per lane, and broadcast by shuffles; source
+// particles are staged SRC at a time with positions relative to g (float32: the
+// leaf-relative copy plus the leaf offset).
 template <int P, class T, int NS>
-__device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group &G, const int32_t *__restrict__ l_p2p,
+__device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_p2p,
                                          const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
-                                         const double *__restrict__ ccom, const float4 *__restrict__ prel,
+                                         const T *__restrict__ rec, const float4 *__restrict__ prel,
                                          const double *__restrict__ spos, const double *__restrict__ smass,
                                          const T (&x)[NS][3], const int32_t (&self)[NS], int sj, int nsplit,
                                          bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
 {
+    constexpr int RL = Cfg<P, T>::RL;
     const unsigned lane = lane_id();
     int fill = 0;
     auto flush = [&]() {
@@ -230,33 +253,46 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group &G, const i
         __syncwarp();
         fill = 0;
     };
-    for (int64_t e = G.p0; e < G.p1; ++e) {
-        const int32_t leaf = l_p2p[e];
-        const int64_t lb = cbegin[leaf];
-        const int lc = ccount[leaf];
-        const double ox = ccom[3 * (int64_t)leaf + 0] - G.gx;
-        const double oy = ccom[3 * (int64_t)leaf + 1] - G.gy;
-        const double oz = ccom[3 * (int64_t)leaf + 2] - G.gz;
-        for (int q0 = 0; q0 < lc; q0 += 32) {
-            const int take = lc - q0 < 32 ? lc - q0 : 32;
-            if (fill + take > SRC) flush();
-            if ((int)lane < take) {
-                const int64_t j = lb + q0 + lane;
-                if constexpr (sizeof(T) == 4) {
-                    const float4 v = prel[j];
-                    sm.src[fill + lane][0] = v.x + (float)ox;
-                    sm.src[fill + lane][1] = v.y + (float)oy;
-                    sm.src[fill + lane][2] = v.z + (float)oz;
-                    sm.src[fill + lane][3] = v.w;
-                } else {
-                    sm.src[fill + lane][0] = (T)(spos[3 * j + 0] - G.gx);
-                    sm.src[fill + lane][1] = (T)(spos[3 * j + 1] - G.gy);
-                    sm.src[fill + lane][2] = (T)(spos[3 * j + 2] - G.gz);
-                    sm.src[fill + lane][3] = (T)smass[j];
+    for (int64_t e0 = G.p0; e0 < G.p1; e0 += 32) {
+        const int ne = (int)(G.p1 - e0 < 32 ? G.p1 - e0 : 32);
+        int32_t lb = 0, lc = 0;
+        T ox = T(0), oy = T(0), oz = T(0);
+        if ((int)lane < ne) {
+            const int32_t leaf = l_p2p[e0 + lane];
+            lb = cbegin[leaf];
+            lc = ccount[leaf];
+            T h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) h[q] = rec[(int64_t)leaf * RL + q];
+            centre_offset(h, G, ox, oy, oz);
+        }
+        for (int j = 0; j < ne; ++j) {
+            const int32_t b = __shfl_sync(0xffffffffu, lb, j);
+            const int32_t n = __shfl_sync(0xffffffffu, lc, j);
+            const T fx = __shfl_sync(0xffffffffu, ox, j);
+            const T fy = __shfl_sync(0xffffffffu, oy, j);
+            const T fz = __shfl_sync(0xffffffffu, oz, j);
+            for (int q0 = 0; q0 < n; q0 += 32) {
+                const int take = n - q0 < 32 ? n - q0 : 32;
+                if (fill + take > SRC) flush();
+                if ((int)lane < take) {
+                    const int64_t s = (int64_t)b + q0 + lane;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 v = prel[s];
+                        sm.src[fill + lane][0] = v.x + fx;
+                        sm.src[fill + lane][1] = v.y + fy;
+                        sm.src[fill + lane][2] = v.z + fz;
+                        sm.src[fill + lane][3] = v.w;
+                    } else {
+                        sm.src[fill + lane][0] = (T)(spos[3 * s + 0] - G.gx);
+                        sm.src[fill + lane][1] = (T)(spos[3 * s + 1] - G.gy);
+                        sm.src[fill + lane][2] = (T)(spos[3 * s + 2] - G.gz);
+                        sm.src[fill + lane][3] = (T)smass[s];
+                    }
+                    sm.sidx[fill + lane] = (int32_t)s;
                 }
-                sm.sidx[fill + lane] = (int32_t)j;
+                fill += take;
             }
-            fill += take;
         }
     }
     if (fill > 0) flush();
@@ -266,7 +302,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group &G, const i
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
 // NS = 2: two sinks per lane (slices of 64 sinks).
 template <int P, class T, int NS>
-__global__ void __launch_bounds__(IW * 32) k_interact(
+__global__ void __launch_bounds__(IW * 32, 4) k_interact(
     int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ spos,
     const double *__restrict__ smass, const float4 *__restrict__ prel, const double *__restrict__ ccom,
@@ -296,13 +332,21 @@ __global__ void __launch_bounds__(IW * 32) k_interact(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
-        Group Gr;
+        Group<T> Gr;
         Gr.n = ccount[gc];
         if ((cls == 1 && Gr.n > 32) || (cls == 2 && Gr.n <= 32)) continue;
         Gr.gb = cbegin[gc];
         Gr.gx = gcen[3 * g + 0];
         Gr.gy = gcen[3 * g + 1];
         Gr.gz = gcen[3 * g + 2];
+        {
+            const double gv[3] = {Gr.gx, Gr.gy, Gr.gz};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Gr.ghi[d] = (T)gv[d];
+                Gr.glo[d] = (T)(gv[d] - (double)Gr.ghi[d]);
+            }
+        }
         Gr.m0 = off_m2p[g];
         Gr.m1 = off_m2p[g + 1];
         Gr.p0 = off_p2p[g];
@@ -340,8 +384,8 @@ __global__ void __launch_bounds__(IW * 32) k_interact(
             Acc<T> acc[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) acc[q].zero();
-            if (!m2p_list<P, T, NS>(sm, Gr, l_m2p, ccom, rec, x, sj, nsplit, active, acc, phase, status)) return;
-            p2p_list<P, T, NS>(sm, Gr, l_p2p, cbegin, ccount, ccom, prel, spos, smass, x, self, sj, nsplit, active,
+            if (!m2p_list<P, T, NS>(sm, Gr, l_m2p, rec, x, sj, nsplit, active, acc, phase, status)) return;
+            p2p_list<P, T, NS>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, self, sj, nsplit, active,
                                eps2, Gt, acc);
             if (NS == 1) {
                 // combine the list splits of each sink in float64
@@ -408,9 +452,7 @@ int forces_p(hot_ctx *c, double *acc, double *pot)
 {
     unsigned *work = (unsigned *)(c->sizes.p + 56);
     if (c->prm.precision == HOT_FP64) return launch_interact<P, double, 1>(c, 0, work, acc, pot);
-    int r = launch_interact<P, float, 1>(c, 1, work, acc, pot);
-    if (r) return r;
-    return launch_interact<P, float, 2>(c, 2, work + 2, acc, pot);
+    return launch_interact<P, float, 1>(c, 0, work, acc, pot);
 }
 
 }  // namespace

@@ -277,7 +277,8 @@ __global__ void k_item_combine(const uint32_t *__restrict__ off, const int32_t *
 // b_max = 0), so that single-precision coefficients stay O(1).
 // ---------------------------------------------------------------------------
 template <int P, class T>
-__global__ void k_records(const double *__restrict__ cmom, const double *__restrict__ cbmax,
+__global__ void k_records(const double *__restrict__ cmom, const double *__restrict__ ccom,
+                          const double *__restrict__ cbmax,
                           const int32_t *__restrict__ clevel, int64_t ncell, const double *__restrict__ frame,
                           double G, double eps, int reclen, T *__restrict__ rec)
 {
@@ -295,7 +296,7 @@ __global__ void k_records(const double *__restrict__ cmom, const double *__restr
         frexp(L, &e);
         inv_s = ldexp(1.0, clevel[c] - e);
     }
-    m2p_record<P, T>(cmom + c * NC, inv_s, G, eps, rec + c * (int64_t)reclen);
+    m2p_record<P, T>(cmom + c * NC, ccom + 3 * c, inv_s, G, eps, rec + c * (int64_t)reclen);
 }
 
 template <int P>
@@ -350,12 +351,12 @@ int moments_p(hot_ctx *c)
     if (c->prm.precision == HOT_FP64) {
         HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
-        k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+        k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                     c->prm.G, c->prm.eps, reclen, c->rec64.p);
     } else {
         HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
-        k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+        k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                    c->prm.G, c->prm.eps, reclen, c->rec32.p);
     }
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
