@@ -205,6 +205,230 @@ def _eval_stmts(p):
     return L, fl
 
 
+def _tangent_stmts(p):
+    """Forward-mode derivative of the M2P statements along the input direction
+    (ux, uy, uz): the same primal statements interleaved with tangents 'd<name>'.
+    The tangent of the acceleration is (d a / d R) u, the Hessian of the expansion
+    applied to u, which is what the sink side of the adjoint needs."""
+    L, _ = _eval_stmts(p)
+    out = []
+    tmp = [0]
+
+    def dn(nm):
+        nm = nm.strip()
+        if nm.startswith("T("):
+            return "T(0)"
+        return "d" + nm
+
+    def horner_tangent(dst, names):
+        # t = names[-1]; t = names[j] + w * t  (primal and tangent, step by step)
+        t, dt = names[-1], dn(names[-1])
+        for nm in reversed(names[:-1]):
+            tmp[0] += 1
+            k = tmp[0]
+            out.append(f"const T h{k} = {nm} + w * {t};")
+            out.append(f"const T dh{k} = {dn(nm)} + dw * {t} + w * {dt};")
+            t, dt = f"h{k}", f"dh{k}"
+        out.append(f"const T {dst} = {t};")
+        out.append(f"const T d{dst} = {dt};")
+
+    for st in L:
+        if st.startswith("rx *= is"):
+            out.append(st)
+            out.append("const T drx = ux * is, dry = uy * is, drz = uz * is;")
+        elif st.startswith("const T u ="):
+            out.append(st)
+            out.append("const T du = T(2) * (rx * drx + ry * dry + rz * drz);")
+        elif st.startswith("const T rho ="):
+            out.append(st)
+        elif st.startswith("const T w ="):
+            out.append(st)
+            out.append("const T drho = T(-0.5) * rho * w * du;")
+            out.append("const T dw = T(2) * rho * drho;")
+        elif st.startswith("const T y100 = rx * w"):
+            out.append(st)
+            out.append("const T dy100 = drx * w + rx * dw, dy010 = dry * w + ry * dw, dy001 = drz * w + rz * dw;")
+        elif st.startswith("const T y") and " * y" in st:
+            # monomial: const T yABC = yDEF * yGHI;
+            lhs, rhs = st[len("const T "):-1].split(" = ")
+            a, b = rhs.split(" * ")
+            out.append(st)
+            out.append(f"const T d{lhs} = d{a} * {b} + {a} * d{b};")
+        elif st.startswith("T ") and "@" in st:
+            # T acc = REF;  or  T acc = REF * mono;
+            lhs, rhs = st[2:-1].split(" = ")
+            out.append(st)
+            if " * " in rhs:
+                ref, mono = rhs.split(" * ")
+                out.append(f"T d{lhs} = {ref} * d{mono};")
+            else:
+                out.append(f"T d{lhs} = T(0);")
+        elif "+=" in st and "@" in st:
+            lhs, rhs = st[:-1].split(" += ")
+            ref, mono = rhs.split(" * ")
+            out.append(st)
+            out.append(f"d{lhs} += {ref} * d{mono};")
+        elif st.startswith("const T S =") or st.startswith("const T Q =") or \
+                (st.startswith("const T G") and "w *" in st):
+            lhs = st[len("const T "):].split(" = ")[0]
+            expr = st.split(" = ", 1)[1][:-1]
+            # parse the Horner form (n0 + w * (n1 + w * (...)))
+            names = [x.strip(" ()") for x in expr.replace("w *", "|").replace("+", "|").split("|")]
+            names = [x for x in names if x]
+            horner_tangent(lhs, names)
+        elif st.startswith("const T rs"):
+            out.append(st)
+            out.append("const T drs = drho * is;")
+        elif st.startswith("const T G") and st.endswith("T(0);"):
+            lhs = st[len("const T "):].split(" = ")[0]
+            out.append(st)
+            out.append(f"const T d{lhs} = T(0);")
+        elif st.startswith("const T "):
+            # linear combination: const T X = a + T(c) * b + ...;
+            lhs, rhs = st[len("const T "):-1].split(" = ")
+            terms = [t.strip() for t in rhs.split(" + ")]
+            dterms = []
+            for t in terms:
+                if " * " in t:
+                    c, nm = t.split(" * ")
+                    dterms.append(f"{c} * d{nm}")
+                else:
+                    dterms.append(dn(t))
+            out.append(st)
+            out.append(f"const T d{lhs} = " + " + ".join(dterms) + ";")
+        elif st.startswith("phi -="):
+            out.append(st)
+        elif st.startswith("ax +=") or st.startswith("ay +=") or st.startswith("az +="):
+            an = st[:2]
+            comp = {"ax": ("G0", "y100"), "ay": ("G1", "y010"), "az": ("G2", "y001")}[an]
+            Gd, yd = comp
+            out.append(st)
+            out.append(f"d{an} += drs * (w * {Gd} - {yd} * Q) + rs * (dw * {Gd} + w * d{Gd} - d{yd} * Q - {yd} * dQ);")
+        else:
+            raise ValueError("unhandled statement: " + st)
+    return out
+
+
+def gen_tangent(p):
+    L = _tangent_stmts(p)
+    slot = layout(p)
+    out = []
+    for T, VEC, VW, suf in (("float", "float4", 4, "f32"), ("double", "double2", 2, "f64")):
+        comp = "xyzw"
+        code = [f"__device__ __forceinline__ void m2p_tangent_{p}_{suf}(const {T}* __restrict__ c, {T} rx, {T} ry, "
+                f"{T} rz, {T} ux, {T} uy, {T} uz, {T}& phi, {T}& ax, {T}& ay, {T}& az, {T}& dax, {T}& day, "
+                f"{T}& daz) {{",
+                f"  using T = {T};",
+                f"  const {VEC}* __restrict__ cv = reinterpret_cast<const {VEC}*>(c);"]
+        loaded = set()
+
+        def need(g):
+            if g not in loaded:
+                loaded.add(g)
+                code.append(f"  const {VEC} v{g} = cv[{g}];")
+
+        need(0)
+        code.append("  const T is = v0.x, e2 = v0.y;")
+        for st in L:
+            parts = st.split("@")
+            for i in range(1, len(parts), 2):
+                sl = slot[parts[i]]
+                g = sl // VW
+                need(g)
+                parts[i] = f"v{g}.{comp[sl % VW]}"
+            code.append("  " + "".join(parts))
+        code.append("}")
+        out.append("\n".join(code))
+    return "\n".join(out)
+
+
+def gen_cbar(p):
+    """Adjoint of one interaction with respect to the record coefficients C_{b,k}
+    (the accelerations and potential are linear in them): with output weights u (for
+    the acceleration) and v (for the potential),
+        dL/dC_{b,k} = A_{k,n} y^b + B_k D_u(y^b),
+        A_{k,n} = -w^k (v rho + rs (1+2k+2n) (u.y)),   B_k = rs w^{k+1},
+    D_u(y^b) = sum_d u_d b_d y^{b-e_d}; accumulated into cb[] in s_terms order."""
+    S = s_terms(p)
+    K = p // 2
+    out = []
+    for T, suf in (("float", "f32"), ("double", "f64")):
+        L = [f"__device__ __forceinline__ void m2p_cbar_{p}_{suf}({T} is, {T} e2, {T} rx, {T} ry, {T} rz, "
+             f"{T} ux, {T} uy, {T} uz, {T} v, {T}* __restrict__ cb) {{",
+             f"  using T = {T};",
+             "  rx *= is; ry *= is; rz *= is;",
+             "  const T u = rx * rx + ry * ry + rz * rz + e2;",
+             "  const T rho = hot_rsqrt(u);",
+             "  const T w = rho * rho;",
+             "  const T rs = rho * is;",
+             "  const T y100 = rx * w, y010 = ry * w, y001 = rz * w;",
+             "  const T Dy100 = ux, Dy010 = uy, Dy001 = uz;",
+             "  const T uy_ = ux * y100 + uy * y010 + uz * y001;",
+             "  const T y000 = T(1), Dy000 = T(0);",
+             "  T wk[%d];" % (K + 2),
+             "  wk[0] = T(1);",
+             f"  for (int q = 1; q < {K + 2}; ++q) wk[q] = wk[q - 1] * w;"]
+        for n in range(2, p + 1):
+            for a in midx(n)[ncomp(n - 1):]:
+                d = 0 if a[0] > 0 else (1 if a[1] > 0 else 2)
+                prev = list(a)
+                prev[d] -= 1
+                prev = mname(tuple(prev))
+                unit = [mname((1, 0, 0)), mname((0, 1, 0)), mname((0, 0, 1))][d]
+                ud = ["ux", "uy", "uz"][d]
+                L.append(f"  const T {mname(a)} = {prev} * {unit};")
+                L.append(f"  const T D{mname(a)} = D{prev} * {unit} + {prev} * {ud};")
+        for k in range(K + 1):
+            L.append(f"  const T B{k} = rs * wk[{k + 1}];")
+            for n in range(p - 2 * k + 1):
+                L.append(f"  const T A{k}_{n} = -wk[{k}] * (v * rho + rs * T({1 + 2 * k + 2 * n}) * uy_);")
+        for i, (k, n, b) in enumerate(S):
+            L.append(f"  cb[{i}] += A{k}_{n} * {mname(b)} + B{k} * D{mname(b)};")
+        L.append("}")
+        out.append("\n".join(L))
+    return "\n".join(out)
+
+
+def gen_record_adjoint(p):
+    """Transpose of the moments -> coefficients map of m2p_record: given dL/dC_{b,k}
+    (s_terms order), accumulate dL/dM_a (FP64)."""
+    S = s_terms(p)
+    idx = {a: i for i, a in enumerate(midx(p))}
+    L = [f"__device__ __forceinline__ void m2p_record_adjoint_{p}(const double* __restrict__ cb, double inv_s, "
+         "double G, double* __restrict__ Mbar) {",
+         f"  double ip[{2 * p + 2}];",
+         "  ip[0] = 1.0;",
+         f"  for (int q = 1; q < {2 * p + 2}; ++q) ip[q] = ip[q - 1] * inv_s;"]
+    for i, (k, n, b) in enumerate(S):
+        m = n + k
+        const = (-1) ** k * dfact(2 * m - 1) / (2 ** k * fact3(b))
+        L.append(f"  {{ const double t = G * ip[{1 + 2 * k + n}] * {const!r} * cb[{i}];")
+        for l in midx(k)[ncomp(k - 1) if k > 0 else 0:]:
+            a = add(b, (2 * l[0], 2 * l[1], 2 * l[2]))
+            L.append(f"    Mbar[{idx[a]}] += t * {1.0 / fact3(l)!r};")
+        L.append("  }")
+    L.append("}")
+    return "\n".join(L)
+
+
+def m2m_transposed(p):
+    """For each b: the pairs (a >= b, C(a,b), g = a - b) of the translation, so that
+    dL/dM_b(child) += sum_a C(a,b) (z_child - z_parent)^{a-b} dL/dM_a(parent)."""
+    ia = midx(p)
+    idx = {a: i for i, a in enumerate(ia)}
+    start, aidx, gidx, coef = [], [], [], []
+    for b in ia:
+        start.append(len(aidx))
+        for a in ia:
+            if all(b[d] <= a[d] for d in range(3)):
+                g = (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+                aidx.append(idx[a])
+                gidx.append(idx[g])
+                coef.append(math.comb(a[0], b[0]) * math.comb(a[1], b[1]) * math.comb(a[2], b[2]))
+    start.append(len(aidx))
+    return start, aidx, gidx, coef
+
+
 def layout(p):
     """Record slots in the order the interaction code first reads them, so that vector
     loads stay close to their use.  Slots 0..7 hold the header: inv_s, eps^2/s^2, and the
@@ -347,6 +571,33 @@ def main(out_path):
     parts.append(f"__device__ const double m2m_coef[{len(co)}] = {{{', '.join(repr(float(c)) for c in co)}}};")
     parts.extend(evals)
     parts.extend(records)
+    ts, ta, tg, tc = m2m_transposed(PMAX)
+    parts.append(f"__device__ const unsigned short m2mt_start[{len(ts)}] = {{{', '.join(map(str, ts))}}};")
+    parts.append(f"__device__ const unsigned char m2mt_alpha[{len(ta)}] = {{{', '.join(map(str, ta))}}};")
+    parts.append(f"__device__ const unsigned char m2mt_gamma[{len(tg)}] = {{{', '.join(map(str, tg))}}};")
+    parts.append(f"__device__ const double m2mt_coef[{len(tc)}] = {{{', '.join(repr(float(c)) for c in tc)}}};")
+    parts.append("static constexpr int HOT_NS[%d] = {%s};" % (PMAX + 1, ", ".join(str(len(s_terms(q))) for q in range(PMAX + 1))))
+    for q in range(PMAX + 1):
+        parts.append(gen_tangent(q))
+        parts.append(gen_cbar(q))
+        parts.append(gen_record_adjoint(q))
+    tw = ["template <int P, typename T> __device__ __forceinline__ void m2p_tangent(const T* __restrict__ c, "
+          "T rx, T ry, T rz, T ux, T uy, T uz, T& phi, T& ax, T& ay, T& az, T& dax, T& day, T& daz) {"]
+    cw = ["template <int P, typename T> __device__ __forceinline__ void m2p_cbar(T is, T e2, T rx, T ry, T rz, "
+          "T ux, T uy, T uz, T v, T* __restrict__ cb) {"]
+    aw = ["template <int P> __device__ __forceinline__ void m2p_record_adjoint(const double* __restrict__ cb, "
+          "double inv_s, double G, double* __restrict__ Mbar) {"]
+    for q in range(PMAX + 1):
+        kw = "if" if q == 0 else "else if"
+        tw.append(f"  {kw} constexpr (P == {q}) {{ if constexpr (sizeof(T) == 4) m2p_tangent_{q}_f32(c, rx, ry, rz, ux, uy, uz, "
+                  f"phi, ax, ay, az, dax, day, daz); else m2p_tangent_{q}_f64(c, rx, ry, rz, ux, uy, uz, phi, ax, ay, az, "
+                  f"dax, day, daz); }}")
+        cw.append(f"  {kw} constexpr (P == {q}) {{ if constexpr (sizeof(T) == 4) m2p_cbar_{q}_f32(is, e2, rx, ry, rz, "
+                  f"ux, uy, uz, v, cb); else m2p_cbar_{q}_f64(is, e2, rx, ry, rz, ux, uy, uz, v, cb); }}")
+        aw.append(f"  {kw} constexpr (P == {q}) m2p_record_adjoint_{q}(cb, inv_s, G, Mbar);")
+    for w_ in (tw, cw, aw):
+        w_.append("}")
+        parts.append("\n".join(w_))
     ev = ["template <int P, typename T> __device__ __forceinline__ void m2p_eval("
           "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {"]
     rc = ["template <int P, typename T> __device__ __forceinline__ void m2p_record("

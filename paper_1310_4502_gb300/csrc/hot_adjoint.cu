@@ -1,0 +1,548 @@
+// hot_adjoint.cu -- adjoint of the tree force through frozen lists and frozen
+// expansion centres: for L = sum_i u_i . a_i + v_i phi_i, dL/dx and dL/dm of every
+// particle, where each cell's moments stay functions of its particles' positions and
+// masses (moment tensor definition, about the frozen centre).
+//
+//   sink side    : d/dx_i of every interaction of sink i -- the forward-mode derivative
+//                  of the M2P routine along u_i (the Hessian of the expansion applied to
+//                  u_i) minus v_i a_i, and the P2P pair terms (interaction kernel, MODE 1)
+//   source, M2P  : the interactions are linear in a cell's record coefficients, so
+//                  dL/dC accumulates A y^b + B D_u(y^b) over every (sink, cell) pair; the
+//                  lists are transposed (cell -> groups) by a stable radix sort so that
+//                  each cell's sum is formed by one warp per chunk, in a fixed order;
+//                  then dL/dM = (record map)^T dL/dC, pushed down the tree with the
+//                  transposed binomial translation and onto the particles with the
+//                  transposed P2M at the leaves (float64)
+//   source, P2P  : the pair terms seen from the source particle, over the transposed
+//                  (leaf -> groups) lists, one warp per leaf
+// Every sum has a fixed order: results are reproducible run to run.
+#include "hot_common.cuh"
+#include "generated.cuh"
+
+namespace {
+
+constexpr int AW = 4;    // warps per block
+constexpr int KG = 32;   // groups per source-side work item
+
+template <int P, class T>
+struct ACfg {
+    static constexpr int RL = HOT_REC_LEN[P];
+    static constexpr int NS = HOT_NS[P];
+    static constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+};
+
+// Sorted-order sink weights (u, v) and float hi/lo positions.
+template <class T>
+__global__ void k_adj_prep(const double *__restrict__ g_acc, const double *__restrict__ g_pot,
+                           const uint32_t *__restrict__ perm, const double *__restrict__ spos, int64_t N,
+                           T *__restrict__ w, float *__restrict__ xhl)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int64_t i = perm[s];
+    w[4 * s + 0] = (T)g_acc[3 * i + 0];
+    w[4 * s + 1] = (T)g_acc[3 * i + 1];
+    w[4 * s + 2] = (T)g_acc[3 * i + 2];
+    w[4 * s + 3] = g_pot ? (T)g_pot[i] : T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double x = spos[3 * s + d];
+        const float hi = (float)x;
+        xhl[8 * s + d] = hi;
+        xhl[8 * s + 4 + d] = (float)(x - (double)hi);
+    }
+}
+
+// (key = target cell, value = group) for every entry of a CSR list, in list order.
+__global__ void k_expand_pairs(const int64_t *__restrict__ off, const int32_t *__restrict__ list, int64_t ng,
+                               uint64_t *__restrict__ key, uint32_t *__restrict__ val)
+{
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= ng) return;
+    for (int64_t e = off[g] + lane_id(); e < off[g + 1]; e += 32) {
+        key[e] = (uint64_t)(uint32_t)list[e];
+        val[e] = (uint32_t)g;
+    }
+}
+
+// Range [start, end) of every target in the sorted pair array.
+__global__ void k_ranges(const uint64_t *__restrict__ key, int64_t n, int64_t *__restrict__ start,
+                         int64_t *__restrict__ end)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const uint64_t k = key[e];
+    if (e == 0 || key[e - 1] != k) start[k] = e;
+    if (e == n - 1 || key[e + 1] != k) end[k] = e + 1;
+}
+
+__global__ void k_item_count_adj(const int64_t *__restrict__ start, const int64_t *__restrict__ end, int64_t ncell,
+                                 uint32_t *__restrict__ cnt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    cnt[c] = (uint32_t)((end[c] - start[c] + KG - 1) / KG);
+}
+
+__global__ void k_item_fill_adj(const int64_t *__restrict__ start, const int64_t *__restrict__ end,
+                                const uint32_t *__restrict__ ioff, int64_t ncell, int32_t *__restrict__ icell,
+                                int64_t *__restrict__ ia, int64_t *__restrict__ ib)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int64_t a = start[c];
+    const int64_t e = end[c];
+    for (uint32_t it = ioff[c]; it < ioff[c + 1]; ++it) {
+        icell[it] = (int32_t)c;
+        ia[it] = a;
+        ib[it] = a + KG < e ? a + KG : e;
+        a += KG;
+    }
+}
+
+// Source side of M2P: one warp per item (one cell, up to KG groups that list it); the
+// sinks of all the item's groups are spread over the lanes.  Each lane accumulates the
+// coefficient adjoints in registers; the warp sum goes to part[item].
+template <int P, class T>
+__global__ void __launch_bounds__(AW * 32) k_adj_src(
+    const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
+    const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const T *__restrict__ rec,
+    const T *__restrict__ w, const float *__restrict__ xhl, const double *__restrict__ spos, T *__restrict__ part)
+{
+    constexpr int RL = ACfg<P, T>::RL;
+    constexpr int NS = ACfg<P, T>::NS;
+    __shared__ int32_t sbeg[AW][32], spre[AW][33];
+    const int wi = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nitem = *nitem_p;
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t it = (int64_t)blockIdx.x * AW + wi; it < nitem; it += nw) {
+        const int32_t c = icell[it];
+        const int64_t a = ia[it], b = ib[it];
+        const int ng = (int)(b - a);
+        const T *h = rec + (int64_t)c * RL;
+        const T is = h[0], e2 = h[1];
+        int32_t gb = 0, gn = 0;
+        if ((int)lane < ng) {
+            const int32_t gcl = gcell[tval[a + lane]];
+            gb = cbegin[gcl];
+            gn = ccount[gcl];
+        }
+        const int incl = warp_incl_scan(gn);
+        sbeg[wi][lane] = gb;
+        spre[wi][lane + 1] = incl;
+        if (lane == 0) spre[wi][0] = 0;
+        __syncwarp();
+        const int total = spre[wi][ng];
+        T cb[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) cb[q] = T(0);
+        for (int t = lane; t < total; t += 32) {
+            int lo = 0, hi = ng;  // find j with spre[j] <= t < spre[j+1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (spre[wi][mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int64_t s = (int64_t)sbeg[wi][lo] + (t - spre[wi][lo]);
+            T rx, ry, rz;
+            if constexpr (sizeof(T) == 4) {
+                rx = (xhl[8 * s + 0] - h[2]) + (xhl[8 * s + 4] - h[5]);
+                ry = (xhl[8 * s + 1] - h[3]) + (xhl[8 * s + 5] - h[6]);
+                rz = (xhl[8 * s + 2] - h[4]) + (xhl[8 * s + 6] - h[7]);
+            } else {
+                rx = spos[3 * s + 0] - h[2];
+                ry = spos[3 * s + 1] - h[3];
+                rz = spos[3 * s + 2] - h[4];
+            }
+            m2p_cbar<P, T>(is, e2, rx, ry, rz, w[4 * s + 0], w[4 * s + 1], w[4 * s + 2], w[4 * s + 3], cb);
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const T v = warp_sum(cb[q]);
+            if (lane == 0) part[it * NS + q] = v;
+        }
+        __syncwarp();
+    }
+}
+
+// dL/dC of every cell = sum of its items (fixed order, float64), then dL/dM through the
+// transposed record map.  One thread per cell; Mbar must be zero on entry.
+template <int P, class T>
+__global__ void k_adj_cells(int64_t ncell, const uint32_t *__restrict__ ioff,
+                            const T *__restrict__ part, const T *__restrict__ rec, double G,
+                            double *__restrict__ Mbar)
+{
+    constexpr int RL = ACfg<P, T>::RL;
+    constexpr int NS = ACfg<P, T>::NS;
+    constexpr int NC = ACfg<P, T>::NC;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    if (ioff[c] == ioff[c + 1]) return;
+    double cb[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) cb[q] = 0.0;
+    for (uint32_t it = ioff[c]; it < ioff[c + 1]; ++it)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) cb[q] += (double)part[(int64_t)it * NS + q];
+    const double inv_s = (double)rec[c * (int64_t)RL];
+    m2p_record_adjoint<P>(cb, inv_s, G, Mbar + c * (int64_t)NC);
+}
+
+// Top-down: dL/dM of a cell += transposed translation of its parent's dL/dM
+// (M_parent = sum_children shift(M_child) with frozen centres).  One warp per cell of
+// the level; the parent level is complete.
+template <int P>
+__global__ void __launch_bounds__(AW * 32) k_adj_l2l(const int32_t *__restrict__ cells, int64_t n,
+                                                     const int32_t *__restrict__ cparent,
+                                                     const double *__restrict__ ccom, double *__restrict__ Mbar)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    __shared__ double sd[AW][NC], sp[AW][NC];
+    __shared__ unsigned char mi[NC][3];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        mi[k][0] = hot_midx[k][0];
+        mi[k][1] = hot_midx[k][1];
+        mi[k][2] = hot_midx[k][2];
+    }
+    __syncthreads();
+    const int wi = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t q0 = (int64_t)blockIdx.x * AW + wi; q0 < n; q0 += nw) {
+        const int32_t c = cells[q0];
+        const int32_t p = cparent[c];
+        if (p < 0) continue;
+        const double d[3] = {ccom[3 * (int64_t)c + 0] - ccom[3 * (int64_t)p + 0],
+                             ccom[3 * (int64_t)c + 1] - ccom[3 * (int64_t)p + 1],
+                             ccom[3 * (int64_t)c + 2] - ccom[3 * (int64_t)p + 2]};
+        for (int g = lane; g < NC; g += 32) {
+            double v = 1.0;
+            for (int e = 0; e < 3; ++e)
+                for (int t = 0; t < mi[g][e]; ++t) v *= d[e];
+            sd[wi][g] = v;
+            sp[wi][g] = Mbar[(int64_t)p * NC + g];
+        }
+        __syncwarp();
+        for (int b = lane; b < NC; b += 32) {
+            double t = 0.0;
+            // the table is of order 6; for each b its alpha run in canonical order, so the
+            // ones of this order (alpha < NC) come first
+            for (int j = m2mt_start[b]; j < m2mt_start[b + 1] && m2mt_alpha[j] < NC; ++j)
+                t += m2mt_coef[j] * sd[wi][m2mt_gamma[j]] * sp[wi][m2mt_alpha[j]];
+            Mbar[(int64_t)c * NC + b] += t;
+        }
+        __syncwarp();
+    }
+}
+
+// Source side of P2P: one warp per leaf, lanes = (leaf particle, split of the sinks).
+// For a pair (sink i, source j), d = x_j - x_i, s^2 = |d|^2 + eps^2:
+//   dL/dx_j += G m_j [u_i/s^3 - 3 d (d.u_i)/s^5 + v_i d/s^3]
+//   dL/dm_j += G [u_i.d/s^3 - v_i/s]
+template <class T>
+__global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
+    int64_t ncell, const int32_t *__restrict__ cnchild, const int64_t *__restrict__ start,
+    const int64_t *__restrict__ end, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ ccom,
+    const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
+    const float *__restrict__ xhl, const T *__restrict__ w, T eps2, double G, double *__restrict__ gout)
+{
+    __shared__ T ss[AW][64][4];
+    __shared__ T sw[AW][64][4];
+    __shared__ int32_t sid[AW][64];
+    __shared__ double red[AW][32][4];
+    const int wi = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t L = (int64_t)blockIdx.x * AW + wi; L < ncell; L += nw) {
+        if (cnchild[L] != 0 || end[L] <= start[L]) continue;
+        const int64_t lb = cbegin[L];
+        const int lc = ccount[L];
+        const double zx = ccom[3 * L + 0], zy = ccom[3 * L + 1], zz = ccom[3 * L + 2];
+        const float zhi[3] = {(float)zx, (float)zy, (float)zz};
+        const float zlo[3] = {(float)(zx - (double)zhi[0]), (float)(zy - (double)zhi[1]), (float)(zz - (double)zhi[2])};
+        for (int j0 = 0; j0 < lc; j0 += 32) {
+            const int nj = lc - j0 < 32 ? lc - j0 : 32;
+            const int nsplit = 32 / nj;
+            const int jj = (int)lane % nj, sj = (int)lane / nj;
+            const bool active = sj < nsplit;
+            const int64_t sj_slot = lb + j0 + jj;
+            T xj[3], mj;
+            if constexpr (sizeof(T) == 4) {
+                const float4 v = prel[sj_slot];
+                xj[0] = v.x;
+                xj[1] = v.y;
+                xj[2] = v.z;
+                mj = v.w;
+            } else {
+                xj[0] = spos[3 * sj_slot + 0] - zx;
+                xj[1] = spos[3 * sj_slot + 1] - zy;
+                xj[2] = spos[3 * sj_slot + 2] - zz;
+                mj = smass[sj_slot];
+            }
+            T gx = 0, gy = 0, gz = 0, gm = 0;
+            int fill = 0;
+            auto flush = [&]() {
+                __syncwarp();
+                if (active) {
+                    for (int k = sj; k < fill; k += nsplit) {
+                        const T dx = xj[0] - ss[wi][k][0], dy = xj[1] - ss[wi][k][1], dz = xj[2] - ss[wi][k][2];
+                        const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+                        const bool ok = (r2 > T(0)) && (sid[wi][k] != (int32_t)sj_slot);
+                        const T ri = ok ? hot_rsqrt(r2) : T(0);
+                        const T r3 = ri * ri * ri;
+                        const T ux = sw[wi][k][0], uy = sw[wi][k][1], uz = sw[wi][k][2], vv = sw[wi][k][3];
+                        const T du = dx * ux + dy * uy + dz * uz;
+                        const T c1 = T(3) * r3 * ri * ri * du;
+                        gx += r3 * ux - c1 * dx + vv * r3 * dx;
+                        gy += r3 * uy - c1 * dy + vv * r3 * dy;
+                        gz += r3 * uz - c1 * dz + vv * r3 * dz;
+                        gm += du * r3 - vv * ri;
+                    }
+                }
+                __syncwarp();
+                fill = 0;
+            };
+            for (int64_t e = start[L]; e < end[L]; ++e) {
+                const int32_t gc = gcell[tval[e]];
+                const int64_t gb = cbegin[gc];
+                const int gn = ccount[gc];
+                for (int q0 = 0; q0 < gn; q0 += 32) {
+                    const int take = gn - q0 < 32 ? gn - q0 : 32;
+                    if (fill + take > 64) flush();
+                    if ((int)lane < take) {
+                        const int64_t s = gb + q0 + lane;
+                        if constexpr (sizeof(T) == 4) {
+                            ss[wi][fill + lane][0] = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
+                            ss[wi][fill + lane][1] = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
+                            ss[wi][fill + lane][2] = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
+                        } else {
+                            ss[wi][fill + lane][0] = spos[3 * s + 0] - zx;
+                            ss[wi][fill + lane][1] = spos[3 * s + 1] - zy;
+                            ss[wi][fill + lane][2] = spos[3 * s + 2] - zz;
+                        }
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) sw[wi][fill + lane][d] = w[4 * s + d];
+                        sid[wi][fill + lane] = (int32_t)s;
+                    }
+                    fill += take;
+                }
+            }
+            if (fill > 0) flush();
+            __syncwarp();
+            if (active) {
+                red[wi][lane][0] = (double)gx;
+                red[wi][lane][1] = (double)gy;
+                red[wi][lane][2] = (double)gz;
+                red[wi][lane][3] = (double)gm;
+            }
+            __syncwarp();
+            if (active && sj == 0) {
+                double t[4] = {0, 0, 0, 0};
+                for (int q = 0; q < nsplit; ++q)
+                    for (int d = 0; d < 4; ++d) t[d] += red[wi][jj + q * nj][d];
+                gout[4 * sj_slot + 0] = G * (double)mj * t[0];
+                gout[4 * sj_slot + 1] = G * (double)mj * t[1];
+                gout[4 * sj_slot + 2] = G * (double)mj * t[2];
+                gout[4 * sj_slot + 3] = G * t[3];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Leaves: transposed P2M of dL/dM onto the particles (float64), plus the sink-side and
+// P2P source-side parts; written in original order.
+template <int P>
+__global__ void __launch_bounds__(AW * 32) k_adj_leaf(
+    int64_t ncell, const int32_t *__restrict__ cnchild, const int32_t *__restrict__ cbegin,
+    const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ spos,
+    const double *__restrict__ smass, const double *__restrict__ Mbar, const double *__restrict__ gsink,
+    const double *__restrict__ gp2p, const uint32_t *__restrict__ perm, double *__restrict__ g_pos,
+    double *__restrict__ g_mass)
+{
+    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+    __shared__ double sm[AW][NC];
+    __shared__ unsigned char mi[NC][3];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        mi[k][0] = hot_midx[k][0];
+        mi[k][1] = hot_midx[k][1];
+        mi[k][2] = hot_midx[k][2];
+    }
+    __syncthreads();
+    const int wi = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t c = (int64_t)blockIdx.x * AW + wi; c < ncell; c += nw) {
+        if (cnchild[c] != 0) continue;
+        for (int g = lane; g < NC; g += 32) sm[wi][g] = Mbar[c * NC + g];
+        __syncwarp();
+        const int64_t b = cbegin[c], n = ccount[c];
+        for (int64_t s = b + lane; s < b + n; s += 32) {
+            double pw[3][P + 1];
+            for (int e = 0; e < 3; ++e) {
+                const double d = spos[3 * s + e] - ccom[3 * c + e];
+                pw[e][0] = 1.0;
+                for (int q = 1; q <= P; ++q) pw[e][q] = pw[e][q - 1] * d;
+            }
+            double gm = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+            for (int a = 0; a < NC; ++a) {
+                const int i = mi[a][0], j = mi[a][1], k = mi[a][2];
+                const double mb = sm[wi][a];
+                gm += mb * pw[0][i] * pw[1][j] * pw[2][k];
+                if (i) gx += mb * i * pw[0][i - 1] * pw[1][j] * pw[2][k];
+                if (j) gy += mb * j * pw[0][i] * pw[1][j - 1] * pw[2][k];
+                if (k) gz += mb * k * pw[0][i] * pw[1][j] * pw[2][k - 1];
+            }
+            const double m = smass[s];
+            const int64_t o = perm[s];
+            g_pos[3 * o + 0] = m * gx + gsink[3 * s + 0] + gp2p[4 * s + 0];
+            g_pos[3 * o + 1] = m * gy + gsink[3 * s + 1] + gp2p[4 * s + 1];
+            g_pos[3 * o + 2] = m * gz + gsink[3 * s + 2] + gp2p[4 * s + 2];
+            g_mass[o] = gm + gp2p[4 * s + 3];
+        }
+        __syncwarp();
+    }
+}
+
+template <int P, class T>
+int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
+{
+    constexpr int NS = ACfg<P, T>::NS;
+    constexpr int NC = ACfg<P, T>::NC;
+    cudaStream_t s = c->st;
+    const int64_t N = c->N, nc = c->ncell, ng = c->ngroup;
+    const T *rec = nullptr;
+    if constexpr (sizeof(T) == 4)
+        rec = c->rec32.p;
+    else
+        rec = c->rec64.p;
+
+    // weights and positions in sorted order
+    HOT_CK(c->adj_w.ensure(4 * sizeof(T) * (size_t)N, s));
+    HOT_CK(c->adj_xhl.ensure(8 * (size_t)N, s));
+    T *w = (T *)c->adj_w.p;
+    HOT_COUNT_LAUNCH();
+    k_adj_prep<T><<<hot_blocks(N, 256), 256, 0, s>>>(g_acc, g_pot, c->idx.p, c->spos.p, N, w, c->adj_xhl.p);
+
+    // sink side (interaction kernel in adjoint mode)
+    HOT_CK(c->adj_gsink.ensure(3 * (size_t)N, s));
+    int r = hot_impl_adjoint_sink(c, w, c->adj_gsink.p);
+    if (r) return r;
+
+    // source side of M2P: transpose the lists, coefficient adjoints per item
+    const int64_t nm = c->n_m2p;
+    int bits = 1;
+    while ((int64_t(1) << bits) <= nc) ++bits;
+    HOT_CK(c->tp_key.ensure(nm + 1, s));
+    HOT_CK(c->tp_key2.ensure(nm + 1, s));
+    HOT_CK(c->tp_val.ensure(nm + 1, s));
+    HOT_CK(c->tp_val2.ensure(nm + 1, s));
+    HOT_CK(c->tp_start.ensure(nc + 1, s));
+    HOT_CK(c->tp_end.ensure(nc + 1, s));
+    HOT_CK(c->it_cnt.ensure(nc + 1, s));
+    HOT_CK(c->it_off.ensure(nc + 1, s));
+    HOT_CK(c->adj_mbar.ensure((size_t)NC * nc, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(nc + 64), s));
+    HOT_CK(cudaMemsetAsync(c->adj_mbar.p, 0, sizeof(double) * NC * (size_t)nc, s));
+    if (nm > 0) {
+        HOT_COUNT_LAUNCH();
+        k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_m2p.p, c->l_m2p.p, ng, c->tp_key.p, c->tp_val.p);
+        r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, nm, bits);
+        if (r) return r;
+        HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
+        HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
+        HOT_COUNT_LAUNCH();
+        k_ranges<<<hot_blocks(nm, 256), 256, 0, s>>>(c->tp_key.p, nm, c->tp_start.p, c->tp_end.p);
+        HOT_COUNT_LAUNCH();
+        k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
+        r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
+        if (r) return r;
+        const int64_t max_items = nm / KG + nc + 1;
+        HOT_CK(c->it_cell.ensure(max_items, s));
+        HOT_CK(c->it_a.ensure(max_items, s));
+        HOT_CK(c->it_b.ensure(max_items, s));
+        HOT_CK(c->it_part.ensure(sizeof(T) * NS * (size_t)max_items, s));
+        HOT_COUNT_LAUNCH();
+        k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
+                                                            c->it_a.p, c->it_b.p);
+        T *part = (T *)c->it_part.p;
+        HOT_COUNT_LAUNCH();
+        k_adj_src<P, T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
+                                                      c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, rec, w,
+                                                      c->adj_xhl.p, c->spos.p, part);
+        HOT_COUNT_LAUNCH();
+        k_adj_cells<P, T><<<hot_blocks(nc, 128), 128, 0, s>>>(nc, c->it_off.p, part, rec, c->prm.G,
+                                                             c->adj_mbar.p);
+    }
+    // push dL/dM down the tree, level by level
+    for (int l = 1; l <= (int)c->maxlevel; ++l) {
+        const int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
+        if (n <= 0) continue;
+        HOT_COUNT_LAUNCH();
+        k_adj_l2l<P><<<hot_blocks(n, AW, c->nsm * 16), AW * 32, 0, s>>>(c->level_cells.p + a, n, c->cparent.p,
+                                                                       c->ccom.p, c->adj_mbar.p);
+    }
+
+    // source side of P2P: transpose the leaf lists
+    const int64_t np = c->n_p2p;
+    HOT_CK(c->adj_gp2p.ensure(4 * (size_t)N, s));
+    HOT_CK(cudaMemsetAsync(c->adj_gp2p.p, 0, sizeof(double) * 4 * (size_t)N, s));
+    if (np > 0) {
+        HOT_CK(c->tp_key.ensure(np + 1, s));
+        HOT_CK(c->tp_key2.ensure(np + 1, s));
+        HOT_CK(c->tp_val.ensure(np + 1, s));
+        HOT_CK(c->tp_val2.ensure(np + 1, s));
+        HOT_COUNT_LAUNCH();
+        k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_p2p.p, c->l_p2p.p, ng, c->tp_key.p, c->tp_val.p);
+        r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, np, bits);
+        if (r) return r;
+        HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
+        HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
+        HOT_COUNT_LAUNCH();
+        k_ranges<<<hot_blocks(np, 256), 256, 0, s>>>(c->tp_key.p, np, c->tp_start.p, c->tp_end.p);
+        HOT_COUNT_LAUNCH();
+        k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(nc, c->cnchild.p, c->tp_start.p, c->tp_end.p, c->tp_val.p,
+                                                        c->gcell.p, c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p,
+                                                        c->smass.p, c->prel.p, c->adj_xhl.p, w,
+                                                        (T)(c->prm.eps * c->prm.eps), c->prm.G, c->adj_gp2p.p);
+    }
+
+    // leaves: transposed P2M and the final sums, original order
+    HOT_COUNT_LAUNCH();
+    k_adj_leaf<P><<<c->nsm * 8, AW * 32, 0, s>>>(nc, c->cnchild.p, c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p,
+                                                c->smass.p, c->adj_mbar.p, c->adj_gsink.p, c->adj_gp2p.p, c->idx.p,
+                                                g_pos, g_mass);
+    return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
+}
+
+template <int P>
+int adjoint_p(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
+{
+    if (c->prm.precision == HOT_FP64) return adjoint_pt<P, double>(c, g_acc, g_pot, g_pos, g_mass);
+    return adjoint_pt<P, float>(c, g_acc, g_pot, g_pos, g_mass);
+}
+
+}  // namespace
+
+int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
+{
+    hot_tic(c, 5);
+    int r;
+    switch (c->p_mom) {
+        case 0: r = adjoint_p<0>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 1: r = adjoint_p<1>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 2: r = adjoint_p<2>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 3: r = adjoint_p<3>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 4: r = adjoint_p<4>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 5: r = adjoint_p<5>(c, g_acc, g_pot, g_pos, g_mass); break;
+        case 6: r = adjoint_p<6>(c, g_acc, g_pot, g_pos, g_mass); break;
+        default: return HOT_ESTATE;
+    }
+    hot_toc(c, 5);
+    return r;
+}

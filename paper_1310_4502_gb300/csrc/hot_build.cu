@@ -734,3 +734,40 @@ extern "C" int hot_key_frame_noalloc(const double *pos, const double *mass, int6
     if (cudaStreamSynchronize(s) != cudaSuccess) return HOT_ECUDA;
     return (bits & HOT_ST_INPUT) ? HOT_EINPUT : HOT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Stable sort of (key, value) pairs by the low `bits` bits of the key (LSD passes of
+// 8 bits); used to transpose interaction lists.  The result is left in keys/vals.
+// ---------------------------------------------------------------------------
+int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, int64_t n, int bits)
+{
+    cudaStream_t s = c->st;
+    if (n <= 0) return HOT_OK;
+    const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    HOT_CK(c->hist.ensure(256 * (size_t)ntiles + 1, s));
+    HOT_CK(c->histoff.ensure(256 * (size_t)ntiles + 1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(256 * ntiles + 64), s));
+    const int passes = (bits + 7) / 8;
+    uint64_t *ka = keys, *kb = ktmp;
+    uint32_t *va = vals, *vb = vtmp;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        HOT_COUNT_LAUNCH();
+        k_rs_hist<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, n, shift, c->hist.p, ntiles);
+        int r = hot_scan_u32_to_u32(c->hist.p, c->histoff.p, 256 * ntiles, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_COUNT_LAUNCH();
+        k_rs_scatter<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, va, kb, vb, n, shift, c->histoff.p, ntiles);
+        uint64_t *tk = ka;
+        ka = kb;
+        kb = tk;
+        uint32_t *tv = va;
+        va = vb;
+        vb = tv;
+    }
+    if (ka != keys) {
+        HOT_CK(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        HOT_CK(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
+}

@@ -112,6 +112,18 @@ struct hot_ctx {
     DBuf<int32_t> l_m2p, l_p2p;
     DBuf<int32_t> trav_scratch;
     DBuf<TCell> tcell;
+
+    // adjoint
+    DBuf<unsigned char> adj_w;   // sink weights (u, v) per sorted slot, T4
+    DBuf<float> adj_xhl;         // sorted positions as float hi/lo pairs [N][8]
+    DBuf<double> adj_gsink, adj_gp2p, adj_mbar, adj_cbar;
+    DBuf<uint64_t> tp_key, tp_key2;
+    DBuf<uint32_t> tp_val, tp_val2;
+    DBuf<int64_t> tp_start, tp_end;
+    DBuf<uint32_t> it_cnt, it_off;
+    DBuf<int32_t> it_cell;
+    DBuf<int64_t> it_a, it_b;
+    DBuf<unsigned char> it_part;
     int trav_cap = 2048;
     DBuf<int64_t> pairs_per_group;
 
@@ -172,6 +184,8 @@ int hot_impl_traverse(hot_ctx *c, double tol);
 int hot_impl_forces(hot_ctx *c, double *acc, double *pot);
 int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos,
                      double *g_mass);
+int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink);
+int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, int64_t n, int bits);
 
 // ---------------------------------------------------------------------------
 // Device helpers

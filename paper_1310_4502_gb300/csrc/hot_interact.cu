@@ -140,10 +140,11 @@ __device__ __forceinline__ void centre_offset(const T *h, const Group<T> &G, T &
 // evaluates cells sj, sj + nsplit, ... of every staged chunk.  Cell indices are loaded
 // one chunk ahead of the copies, which run one chunk ahead of the arithmetic.  Returns
 // false when a bounded wait expired (status flagged, the warp must stop).
-template <int P, class T, int NS>
+template <int P, class T, int NS, int MODE>
 __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_m2p,
-                                         const T *__restrict__ rec, const T (&x)[NS][3], int sj, int nsplit,
-                                         bool active, Acc<T> (&acc)[NS], uint32_t (&phase)[2], unsigned *status)
+                                         const T *__restrict__ rec, const T (&x)[NS][3], const T (&wt)[NS][4],
+                                         int sj, int nsplit, bool active, Acc<T> (&acc)[NS], uint32_t (&phase)[2],
+                                         unsigned *status)
 {
     constexpr int CH = Cfg<P, T>::CH;
     constexpr int RL = Cfg<P, T>::RL;
@@ -191,18 +192,28 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         }
         __syncwarp();
         if (active) {
-            T ph[NS], ax[NS], ay[NS], az[NS];
+            T ph[NS], ax[NS], ay[NS], az[NS], dx[NS], dy[NS], dz[NS];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = T(0);
+            for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = dx[s] = dy[s] = dz[s] = T(0);
             for (int k = sj; k < ne; k += nsplit) {
                 const T *r = &sm.rec[b][k][0];
                 const T ox = sm.off[b][k][0], oy = sm.off[b][k][1], oz = sm.off[b][k][2];
 #pragma unroll
-                for (int s = 0; s < NS; ++s)
-                    m2p_eval<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, ph[s], ax[s], ay[s], az[s]);
+                for (int s = 0; s < NS; ++s) {
+                    if constexpr (MODE == 0)
+                        m2p_eval<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, ph[s], ax[s], ay[s], az[s]);
+                    else
+                        m2p_tangent<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, wt[s][0], wt[s][1], wt[s][2],
+                                          ph[s], ax[s], ay[s], az[s], dx[s], dy[s], dz[s]);
+                }
             }
 #pragma unroll
-            for (int s = 0; s < NS; ++s) acc[s].add(ax[s], ay[s], az[s], ph[s]);
+            for (int s = 0; s < NS; ++s) {
+                if constexpr (MODE == 0)
+                    acc[s].add(ax[s], ay[s], az[s], ph[s]);
+                else  // d/dx_i (u.a + v phi) over these cells = (da/dR) u - v a
+                    acc[s].add(dx[s] - wt[s][3] * ax[s], dy[s] - wt[s][3] * ay[s], dz[s] - wt[s][3] * az[s], T(0));
+            }
         }
         __syncwarp();
     }
@@ -213,13 +224,13 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 // fetched 32 entries at a time, one entry per lane, and broadcast by shuffles; source
 // particles are staged SRC at a time with positions relative to g (float32: the
 // leaf-relative copy plus the leaf offset).
-template <int P, class T, int NS>
+template <int P, class T, int NS, int MODE>
 __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_p2p,
                                          const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
                                          const T *__restrict__ rec, const float4 *__restrict__ prel,
                                          const double *__restrict__ spos, const double *__restrict__ smass,
-                                         const T (&x)[NS][3], const int32_t (&self)[NS], int sj, int nsplit,
-                                         bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
+                                         const T (&x)[NS][3], const T (&wt)[NS][4], const int32_t (&self)[NS],
+                                         int sj, int nsplit, bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
 {
     constexpr int RL = Cfg<P, T>::RL;
     const unsigned lane = lane_id();
@@ -241,10 +252,20 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     const T rinv = ok ? hot_rsqrt(r2) : T(0);
                     const T mr = m * rinv;
                     const T mr3 = mr * rinv * rinv;
-                    ax[s] += mr3 * dx;
-                    ay[s] += mr3 * dy;
-                    az[s] += mr3 * dz;
-                    ph[s] -= mr;
+                    if constexpr (MODE == 0) {
+                        ax[s] += mr3 * dx;
+                        ay[s] += mr3 * dy;
+                        az[s] += mr3 * dz;
+                        ph[s] -= mr;
+                    } else {
+                        // d/dx_i (u.a_i + v phi_i) = -G m [u/s^3 - 3 d (d.u)/s^5 + v d/s^3], d = x_j - x_i
+                        const T du = dx * wt[s][0] + dy * wt[s][1] + dz * wt[s][2];
+                        const T c1 = T(3) * mr3 * rinv * rinv * du;
+                        const T c2 = mr3 * wt[s][3];
+                        ax[s] -= mr3 * wt[s][0] - c1 * dx + c2 * dx;
+                        ay[s] -= mr3 * wt[s][1] - c1 * dy + c2 * dy;
+                        az[s] -= mr3 * wt[s][2] - c1 * dz + c2 * dz;
+                    }
                 }
             }
 #pragma unroll
@@ -301,7 +322,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 // cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
 // NS = 2: two sinks per lane (slices of 64 sinks).
-template <int P, class T, int NS>
+template <int P, class T, int NS, int MODE>
 __global__ void __launch_bounds__(IW * 32, 4) k_interact(
     int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ spos,
@@ -309,7 +330,7 @@ __global__ void __launch_bounds__(IW * 32, 4) k_interact(
     const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
     T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
-    unsigned *__restrict__ status)
+    const T *__restrict__ wsink, double *__restrict__ gsink, unsigned *__restrict__ status)
 {
     using S = Smem<P, T>;
     constexpr int CH = Cfg<P, T>::CH;
@@ -367,7 +388,7 @@ __global__ void __launch_bounds__(IW * 32, 4) k_interact(
                 sj = 0;
             }
             const bool active = sj < nsplit;
-            T x[NS][3];
+            T x[NS][3], wt[NS][4];
             int32_t self[NS];
             int64_t slot[NS];
             bool valid[NS];
@@ -380,12 +401,14 @@ __global__ void __launch_bounds__(IW * 32, 4) k_interact(
                 x[q][1] = (T)(spos[3 * slot[q] + 1] - Gr.gy);
                 x[q][2] = (T)(spos[3 * slot[q] + 2] - Gr.gz);
                 self[q] = (int32_t)slot[q];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) wt[q][d] = MODE == 0 ? T(0) : wsink[4 * slot[q] + d];
             }
             Acc<T> acc[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) acc[q].zero();
-            if (!m2p_list<P, T, NS>(sm, Gr, l_m2p, rec, x, sj, nsplit, active, acc, phase, status)) return;
-            p2p_list<P, T, NS>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, self, sj, nsplit, active,
+            if (!m2p_list<P, T, NS, MODE>(sm, Gr, l_m2p, rec, x, wt, sj, nsplit, active, acc, phase, status)) return;
+            p2p_list<P, T, NS, MODE>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, wt, self, sj, nsplit, active,
                                eps2, Gt, acc);
             if (NS == 1) {
                 // combine the list splits of each sink in float64
@@ -400,11 +423,17 @@ __global__ void __launch_bounds__(IW * 32, 4) k_interact(
                     for (int j = 0; j < nsplit; ++j)
 #pragma unroll
                         for (int d = 0; d < 4; ++d) t[d] += sm.red[si + j * ns][d];
-                    const int64_t i = perm[slot[0]];
-                    acc_out[3 * i + 0] = t[0];
-                    acc_out[3 * i + 1] = t[1];
-                    acc_out[3 * i + 2] = t[2];
-                    if (pot_out) pot_out[i] = t[3];
+                    if constexpr (MODE == 0) {
+                        const int64_t i = perm[slot[0]];
+                        acc_out[3 * i + 0] = t[0];
+                        acc_out[3 * i + 1] = t[1];
+                        acc_out[3 * i + 2] = t[2];
+                        if (pot_out) pot_out[i] = t[3];
+                    } else {
+                        gsink[3 * slot[0] + 0] = t[0];
+                        gsink[3 * slot[0] + 1] = t[1];
+                        gsink[3 * slot[0] + 2] = t[2];
+                    }
                 }
             } else {
 #pragma unroll
@@ -422,12 +451,12 @@ __global__ void __launch_bounds__(IW * 32, 4) k_interact(
     }
 }
 
-template <int P, class T, int NS>
-int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *pot)
+template <int P, class T, int NS, int MODE>
+int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *pot, const T *wsink, double *gsink)
 {
     cudaStream_t s = c->st;
     const size_t smem = sizeof(Smem<P, T>) * IW;
-    auto kern = k_interact<P, T, NS>;
+    auto kern = k_interact<P, T, NS, MODE>;
     HOT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HOT_CK(cudaMemsetAsync(work, 0, sizeof(unsigned), s));
     const T *rec = nullptr;
@@ -443,7 +472,8 @@ int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *po
     HOT_COUNT_LAUNCH();
     kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
-                                       c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot, c->d_status);
+                                       c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot, wsink, gsink,
+                                       c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }
 
@@ -451,8 +481,9 @@ template <int P>
 int forces_p(hot_ctx *c, double *acc, double *pot)
 {
     unsigned *work = (unsigned *)(c->sizes.p + 56);
-    if (c->prm.precision == HOT_FP64) return launch_interact<P, double, 1>(c, 0, work, acc, pot);
-    return launch_interact<P, float, 1>(c, 0, work, acc, pot);
+    if (c->prm.precision == HOT_FP64)
+        return launch_interact<P, double, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
+    return launch_interact<P, float, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
 }
 
 }  // namespace
@@ -475,4 +506,27 @@ int hot_impl_forces(hot_ctx *c, double *acc, double *pot)
     return r;
 }
 
-int hot_impl_adjoint(hot_ctx *, const double *, const double *, double *, double *) { return HOT_ESTATE; }
+// Sink side of the adjoint: for every sink, d/dx_i of sum over its interactions of
+// (u_i . a_i + v_i phi_i), with (u_i, v_i) = wsink[slot] (T4, sorted order); written to
+// gsink [N][3] (float64, sorted order).
+int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink)
+{
+    unsigned *work = (unsigned *)(c->sizes.p + 56);
+#define HOT_ADJ_SINK(PP)                                                                                 \
+    case PP:                                                                                             \
+        if (c->prm.precision == HOT_FP64)                                                                \
+            return launch_interact<PP, double, 1, 1>(c, 0, work, nullptr, nullptr, (const double *)wsink, \
+                                                     gsink);                                             \
+        return launch_interact<PP, float, 1, 1>(c, 0, work, nullptr, nullptr, (const float *)wsink, gsink);
+    switch (c->p_mom) {
+        HOT_ADJ_SINK(0)
+        HOT_ADJ_SINK(1)
+        HOT_ADJ_SINK(2)
+        HOT_ADJ_SINK(3)
+        HOT_ADJ_SINK(4)
+        HOT_ADJ_SINK(5)
+        HOT_ADJ_SINK(6)
+        default: return HOT_ESTATE;
+    }
+#undef HOT_ADJ_SINK
+}

@@ -1,0 +1,125 @@
+"""GPU adjoint (dL/dx, dL/dm through frozen lists and centres) against the oracle.
+
+L = sum_i w_i . a_i + sum_i v_i phi_i.  References:
+* central finite differences of the oracle's frozen-structure loss (same lists, same
+  expansion centres, moments recomputed from the perturbed particles), taken on the
+  partial loss of the perturbed particle (identical differences, less cancellation);
+* L is linear in the masses, so sum_j m_j dL/dm_j = L exactly;
+* at a tolerance so tight that every interaction is P2P, the frozen tree is the direct
+  sum, whose analytic gradient the oracle provides.
+Tolerances: FP64 path 1e-7, mixed path 1e-5 relative (|g - g_fd| / max(|g_fd|, rms g_fd)).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_4502_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1310_4502_gb300 import hot
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def gpu_adjoint(pos, mass, w, v, p, tol, eps, prec):
+    h = hot.Hot(p=p, tol=tol, eps=eps, precision=prec)
+    P = torch.tensor(pos, device=dev())
+    M = torch.tensor(mass, device=dev())
+    h.build_tree(P, M)
+    h.compute_moments(p)
+    h.traverse(tol)
+    acc = torch.empty_like(P)
+    pot = torch.empty_like(M)
+    h.evaluate_forces(acc, pot)
+    gw = torch.tensor(w, device=dev())
+    gv = None if v is None else torch.tensor(v, device=dev())
+    gx = torch.empty_like(P)
+    gm = torch.empty_like(M)
+    h.adjoint(gw, gv, gx, gm)
+    torch.cuda.synchronize()
+    return acc.cpu().numpy(), pot.cpu().numpy(), gx.cpu().numpy(), gm.cpu().numpy()
+
+
+def fd_reference(pos, mass, w, v, p, tol, eps, ks, h=1e-6):
+    t = oracle.Tree(pos, mass)
+    t.moments(p)
+    t.traverse(tol)
+    gx = np.zeros((len(ks), 3))
+    gm = np.zeros(len(ks))
+    for r, k in enumerate(ks):
+        for d in range(3):
+            vals = []
+            for sgn in (1, -1, 2, -2):
+                x = pos.copy()
+                x[k, d] += sgn * h
+                vals.append(t.frozen_loss(x, mass, w, v, 1.0, eps, k))
+            # fourth-order central difference
+            gx[r, d] = (8 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12 * h)
+        hm = 1e-3 * mass[k]
+        m1 = mass.copy()
+        m1[k] += hm
+        m2 = mass.copy()
+        m2[k] -= hm
+        gm[r] = (t.frozen_loss(pos, m1, w, v, 1.0, eps, k) - t.frozen_loss(pos, m2, w, v, 1.0, eps, k)) / (2 * hm)
+    return gx, gm
+
+
+CASES = {
+    "plummer4096": lambda: (W.make("plummer4096").pos, W.make("plummer4096").mass, 0.01),
+    "clustered16k": lambda: (W.clustered(1 << 14, seed=4), np.full(1 << 14, 1.0 / (1 << 14)), 1e-3),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("p", [1, 4])
+def test_adjoint_against_finite_differences(name, p):
+    pos, mass, eps = CASES[name]()
+    n = len(mass)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((n, 3))
+    v = rng.standard_normal(n)
+    ks = np.sort(np.random.default_rng(2).choice(n, 12, replace=False))
+    tol = 1e-4
+    fx, fm = fd_reference(pos, mass, w, v, p, tol, eps, ks)
+    sx = np.sqrt(np.mean(np.sum(fx ** 2, 1)))
+    sm = np.sqrt(np.mean(fm ** 2))
+    for prec, bound in (("fp64", 1e-7), ("mixed", 1e-5)):
+        a, ph, gx, gm = gpu_adjoint(pos, mass, w, v, p, tol, eps, prec)
+        ex = np.linalg.norm(gx[ks] - fx, axis=1) / np.maximum(np.linalg.norm(fx, axis=1), sx)
+        em = np.abs(gm[ks] - fm) / np.maximum(np.abs(fm), sm)
+        assert ex.max() < bound, (prec, ex.max())
+        assert em.max() < bound, (prec, em.max())
+        # L is linear in the masses
+        L = np.sum(w * a) + np.sum(v * ph)
+        assert np.sum(mass * gm) == pytest.approx(L, rel=10 * bound)
+
+
+def test_adjoint_all_p2p_is_direct_gradient():
+    w_ = W.make("plummer4096")
+    pos, mass, eps = w_.pos[:2000], w_.mass[:2000], 0.05
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal((2000, 3))
+    v = rng.standard_normal(2000)
+    rx, rm = oracle.direct_grad(pos, mass, w, v, 1.0, eps)
+    for prec, bound in (("fp64", 1e-10), ("mixed", 1e-5)):
+        _, _, gx, gm = gpu_adjoint(pos, mass, w, v, 4, 1e-300, eps, prec)
+        sx = np.sqrt(np.mean(np.sum(rx ** 2, 1)))
+        assert np.max(np.linalg.norm(gx - rx, axis=1) / np.maximum(np.linalg.norm(rx, axis=1), sx)) < bound
+        assert np.max(np.abs(gm - rm) / np.maximum(np.abs(rm), np.sqrt(np.mean(rm ** 2)))) < bound
+
+
+def test_adjoint_without_potential_weights():
+    pos, mass, eps = CASES["plummer4096"]()
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((len(mass), 3))
+    a, _, gx, gm = gpu_adjoint(pos, mass, w, None, 4, 1e-4, eps, "fp64")
+    assert np.sum(mass * gm) == pytest.approx(np.sum(w * a), rel=1e-9)
+    ks = [3, 700, 4000]
+    fx, fm = fd_reference(pos, mass, w, None, 4, 1e-4, eps, ks)
+    sx = np.sqrt(np.mean(np.sum(fx ** 2, 1)))
+    assert np.max(np.linalg.norm(gx[ks] - fx, axis=1) / np.maximum(np.linalg.norm(fx, axis=1), sx)) < 1e-7
