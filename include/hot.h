@@ -202,6 +202,12 @@ int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
 int hot_key_frame_noalloc(const double *pos, const double *mass, int64_t N, double *frame,
                           void *cuda_stream);
 
+/* y[k] += alpha * x[k] for k < n (device float64 arrays, asynchronous on the
+ * context stream).  The kick (v += dt/2 a) and drift (x += dt v) of the
+ * kick-drift-kick leapfrog of Sec. "Time Integration", and their adjoints, are
+ * this update.  x and y may not overlap unless equal. */
+int hot_axpy(hot_ctx *ctx, double *y, const double *x, double alpha, int64_t n);
+
 /* Fused-multiply-add throughput microbenchmark (for roofline denominators):
  * runs a register-resident FMA loop on every SM and writes the achieved
  * FLOP/s (FMA = 2) to *flops.  dbl: 0 = float32, 1 = float64.  Synchronises. */

@@ -87,6 +87,8 @@ def lib():
         L.orc_tree_force.restype = C.c_int
         L.orc_tree_force.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int64,
                                      C.c_void_p, _d, C.c_void_p]
+        L.orc_frozen_force.restype = C.c_int
+        L.orc_frozen_force.argtypes = [C.c_void_p, _d, _d, C.c_double, C.c_double, _d, C.c_void_p]
         L.orc_frozen_loss.restype = C.c_double
         L.orc_frozen_loss.argtypes = [C.c_void_p, _d, _d, C.c_double, C.c_double, _d,
                                       C.c_void_p, C.c_int64]
@@ -288,10 +290,34 @@ class Tree:
             raise ValueError("force needs lists")
         return acc, pot
 
+    def frozen_force(self, pos, mass, G=1.0, eps=0.0):
+        """Force with this tree's lists and centres frozen, moments from the given particles."""
+        n = len(self.mass)
+        acc = np.zeros((n, 3))
+        pot = np.zeros(n)
+        if lib().orc_frozen_force(self._h, _c(pos), _c(mass), G, eps, acc, _ptr(pot)) != 0:
+            raise ValueError("frozen_force needs lists")
+        return acc, pot
+
     def frozen_loss(self, pos, mass, w, v=None, G=1.0, eps=0.0, k=-1):
         vv = None if v is None else _c(v)
         return float(lib().orc_frozen_loss(self._h, _c(pos), _c(mass), G, eps, _c(w), _ptr(vv),
                                            int(k)))
+
+
+def frozen_leapfrog(trees, x0, v0, mass, dt, G=1.0, eps=0.0):
+    """Kick-drift-kick leapfrog (Sec. "Time Integration": v += dt/2 a; x += dt v;
+    v += dt/2 a) whose force at step point k uses trees[k] frozen (its lists and
+    centres), moments recomputed from the current particles.  len(trees) = steps + 1."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    v = np.array(v0, dtype=np.float64, copy=True)
+    a, _ = trees[0].frozen_force(x, mass, G, eps)
+    for k in range(1, len(trees)):
+        v += 0.5 * dt * a
+        x += dt * v
+        a, _ = trees[k].frozen_force(x, mass, G, eps)
+        v += 0.5 * dt * a
+    return x, v
 
 
 def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64):

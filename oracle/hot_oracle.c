@@ -921,3 +921,40 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
     free(mom);
     return L;
 }
+
+/* Frozen-structure force: the tree's sorted order, cell ranges, lists and expansion
+ * centres, with every cell's moments recomputed about its frozen centre from the given
+ * positions and masses (original order).  acc [N][3], pot [N] or NULL, original order.
+ * At the tree's own positions this is the tree force. */
+int orc_frozen_force(const orc_tree *t, const double *pos, const double *mass, double G, double eps,
+                     double *acc, double *pot)
+{
+    if (!t->lm2p) return -1;
+    int64_t N = t->N;
+    int p = t->p, nc = ncomp(p);
+    int tab[200][3];
+    midx_table(p, tab);
+    double eps2 = eps * eps;
+    double *spos = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *smass = (double *)malloc(sizeof(double) * (size_t)N);
+    double *ph = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int64_t s = 0; s < N; s++) {
+        int64_t i = t->perm[s];
+        for (int d = 0; d < 3; d++) spos[3 * s + d] = pos[3 * i + d];
+        smass[s] = mass[i];
+    }
+    double *mom = (double *)malloc(sizeof(double) * (size_t)nc * (size_t)t->ncell);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < t->ncell; c++)
+        moments_about(spos, smass, t->cbegin[c], t->ccount[c], t->ccom + 3 * c, p, (const int(*)[3])tab,
+                      mom + (size_t)nc * c);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t g = 0; g < t->ngroup; g++)
+        group_force(t, g, spos, smass, mom, (const int(*)[3])tab, G, eps2, acc, ph);
+    if (pot) memcpy(pot, ph, sizeof(double) * (size_t)N);
+    free(spos);
+    free(smass);
+    free(ph);
+    free(mom);
+    return 0;
+}

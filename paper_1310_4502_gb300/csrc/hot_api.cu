@@ -47,6 +47,12 @@ __global__ void k_fma(T *out, int iters, T a, T b)
     if (s == (T)-12345.0) out[0] = s;  // keeps the chains alive
 }
 
+__global__ void k_axpy(double *__restrict__ y, const double *__restrict__ x, double alpha, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        y[k] += alpha * x[k];
+}
+
 }  // namespace
 
 int hot_sync_status(hot_ctx *c)
@@ -214,6 +220,15 @@ int hot_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
     if (c->stage < 1) return HOT_ESTATE;
     if (n == 0) return HOT_OK;
     return hot_impl_lookup(c, keys, n, idx);
+}
+
+int hot_axpy(hot_ctx *c, double *y, const double *x, double alpha, int64_t n)
+{
+    if (!c || n < 0 || (n > 0 && (!y || !x))) return HOT_EINVAL;
+    if (n == 0) return HOT_OK;
+    HOT_COUNT_LAUNCH();
+    k_axpy<<<hot_blocks(n, 256, c->nsm * 32), 256, 0, c->st>>>(y, x, alpha, n);
+    return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }
 
 int hot_fma_peak(hot_ctx *c, int dbl, double *flops)

@@ -24,7 +24,7 @@ DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc")
+           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy")
 
 
 class hot_params(C.Structure):
@@ -72,9 +72,10 @@ def load():
     L.hot_destroy.argtypes = [vp]
     L.hot_destroy.restype = None
     L.hot_key_frame_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.hot_axpy.argtypes = [vp, vp, vp, C.c_double, C.c_int64]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-                 "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc"):
+                 "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -193,6 +194,14 @@ class Hot:
         _ck(load().hot_lookup(self._h, keys.ctypes.data_as(C.c_void_p), len(keys),
                               out.ctypes.data_as(C.c_void_p)), "hot_lookup")
         return out
+
+    def axpy(self, y, x, alpha):
+        """y += alpha * x on the device (float64 CUDA tensors of equal size)."""
+        _need(y)
+        _need(x)
+        if y.numel() != x.numel():
+            raise ValueError("size mismatch")
+        _ck(load().hot_axpy(self._h, _ptr(y), _ptr(x), float(alpha), int(y.numel())), "hot_axpy")
 
     def fma_peak(self, dbl=False):
         v = C.c_double()

@@ -517,3 +517,69 @@ def test_mac_bound_is_exact_for_collinear_particle(p):
     assert E == pytest.approx(tail, rel=1e-12)
     assert err == pytest.approx(E, rel=1e-9)
     assert abs(a[1]) < 1e-15 and abs(a[2]) < 1e-15
+
+
+def test_frozen_force_is_tree_force_at_its_own_positions():
+    rng = np.random.default_rng(14)
+    n = 900
+    pos = np.concatenate([rng.standard_normal((n // 2, 3)) * 0.05, rng.uniform(-1, 1, (n - n // 2, 3))])
+    mass = rng.uniform(0.5, 1.5, n) / n
+    t = oracle.Tree(pos, mass)
+    t.moments(4)
+    t.traverse(1e-5)
+    a0, p0 = t.force(1.0, 0.01)
+    a1, p1 = t.frozen_force(pos, mass, 1.0, 0.01)
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(p1, p0)
+    # and the frozen loss is the weighted sum of the frozen force at moved positions
+    x = pos + rng.standard_normal(pos.shape) * 1e-3
+    w = rng.standard_normal((n, 3))
+    a2, _ = t.frozen_force(x, mass, 1.0, 0.01)
+    assert t.frozen_loss(x, mass, w, None, 1.0, 0.01) == pytest.approx(np.sum(w * a2), rel=1e-12)
+
+
+def _tree(x, m):
+    t = oracle.Tree(x, m)
+    t.moments(0)
+    t.traverse(1e-3)
+    return t
+
+
+def _rebuild_step(x, v, m, dt):
+    """One kick-drift-kick step with the tree rebuilt at both force points."""
+    t0 = _tree(x, m)
+    a0, _ = t0.force(1.0, 0.0)
+    t1 = _tree(x + dt * (v + 0.5 * dt * a0), m)
+    return oracle.frozen_leapfrog([t0, t1], x, v, m, dt)
+
+
+def test_leapfrog_two_body_energy_order_and_reversibility():
+    """Two equal masses on an eccentric orbit (e about 0.5): the kick-drift-kick scheme of Sec. "Time
+    Integration" keeps the energy error bounded at second order in dt over an orbit (the
+    largest deviation is taken: at a full period the symplectic error nearly cancels) and
+    is time reversible."""
+    m = np.array([0.5, 0.5])
+    x0 = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    vc = np.sqrt(0.5 / 2.0)  # circular speed: v^2/r = G m / d^2 with r = 0.5, d = 1
+    v0 = np.array([[0.0, 0.7 * vc, 0.0], [0.0, -0.7 * vc, 0.0]])
+    period = 2 * np.pi * 0.5 / vc  # covers more than one eccentric orbit
+
+    def energy(x, v):
+        return 0.5 * np.sum(m[:, None] * v * v) - m[0] * m[1] / np.linalg.norm(x[0] - x[1])
+
+    errs = []
+    for nsteps in (400, 800):
+        x, v = x0.copy(), v0.copy()
+        worst = 0.0
+        for _ in range(nsteps):
+            x, v = _rebuild_step(x, v, m, period / nsteps)
+            worst = max(worst, abs(energy(x, v) - energy(x0, v0)))
+        errs.append(worst)
+    assert 3.0 < errs[0] / errs[1] < 5.0  # halving dt quarters the error
+    x, v = x0.copy(), v0.copy()
+    for _ in range(50):
+        x, v = _rebuild_step(x, v, m, 0.01)
+    v = -v
+    for _ in range(50):
+        x, v = _rebuild_step(x, v, m, 0.01)
+    assert np.max(np.abs(x - x0)) < 1e-12 and np.max(np.abs(v + v0)) < 1e-12
