@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="clustered20")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / p=6 / error legs")
+    ap.add_argument("--no-leapfrog", action="store_true", help="skip the 8-step leapfrog forward+backward leg")
+    ap.add_argument("--leapfrog-workload", default="zeldovich256")
     return ap.parse_args()
 
 
@@ -202,6 +204,70 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+def _ev_ms(stream, fn, flush=None):
+    import torch
+    if flush is not None:
+        flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def adjoint_leg(h, fwd, N, dev, K, flush, stream):
+    """Forward step vs adjoint (dL/dx, dL/dm of L = sum_i w_i . a_i, w seeded N(0,1)^3)
+    through the forward's frozen lists, alternating, L2 flushed before each."""
+    import torch
+    gw = torch.tensor(W.loss_weights(N), device=dev)
+    gx = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    gm = torch.empty(N, dtype=torch.float64, device=dev)
+    fwd()
+    h.adjoint(gw, None, gx, gm)
+    tf = ta = 0.0
+    for _ in range(K):
+        tf += _ev_ms(stream, fwd, flush)[0]
+        ta += _ev_ms(stream, lambda: h.adjoint(gw, None, gx, gm), flush)[0]
+    return {"fwd_ms": tf / K, "adjoint_ms": ta / K, "ratio": ta / tf, "steps": K,
+            "loss": "L = sum_i w_i . a_i, w ~ N(0,1)^3 (seed 1); outputs dL/dx [N,3], dL/dm [N]"}
+
+
+def leapfrog_leg(wname, dev, stream, steps=8, dt=1e-3):
+    """S kick-drift-kick steps with the tree rebuilt at every force point, then the
+    backward through all of them by checkpoint-and-recompute; one timed pass each
+    after one untimed force evaluation that sizes the library's buffers."""
+    import torch
+    from paper_1310_4502_gb300 import hot, leapfrog as LF
+    w = W.make(wname)
+    N = w.n
+    X = torch.tensor(w.pos, device=dev)
+    V = torch.zeros_like(X)
+    M = torch.tensor(w.mass, device=dev)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    h.force(X, M, torch.empty_like(X))
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    hot.memory_stats(reset_peak=True)
+    integ = LF.KDK(h, dt, steps)
+    l0 = h.sizes()["launches"]
+    t_fwd, (xs, vs) = _ev_ms(stream, lambda: integ.forward(X, V, M))
+    gx = torch.tensor(W.loss_weights(N), device=dev)
+    gv = torch.tensor(W.loss_weights(N, seed=2), device=dev)
+    t_bwd, _ = _ev_ms(stream, lambda: integ.backward(gx, gv))
+    launches = h.sizes()["launches"] - l0
+    lib_peak = hot.memory_stats()[1]
+    torch_peak = torch.cuda.max_memory_allocated(dev)
+    return {"workload": describe(w) + f"; {steps} KDK steps dt={dt:g}, v0 = 0, tree rebuilt every step; "
+            "L = wx.x_S + wv.v_S (w ~ N(0,1)^3, seeds 1, 2)",
+            "N": N, "p": w.p, "steps": steps, "fwd_ms": t_fwd, "bwd_ms": t_bwd, "ratio": t_bwd / t_fwd,
+            "fwd_particle_steps_per_s": N * steps / (t_fwd * 1e-3), "gpu_launches": launches,
+            "peak_device_bytes": lib_peak + torch_peak, "peak_library_bytes": lib_peak,
+            "peak_torch_bytes": torch_peak}
+
+
 def run_ours(args):
     import torch
 
@@ -290,6 +356,9 @@ def run_ours(args):
            "gpu_launches": launches, "roofline": roof, "clocks": clocks,
            "fp64_peak_tflops_measured": fma64}
 
+    out["adjoint"] = adjoint_leg(h, lambda: step(h, w.p), N, dev, args.steps, flush, stream)
+    out["adjoint"]["workload"] = describe(w)
+
     # end to end through the public API with host buffers
     pos_h = torch.tensor(w.pos).pin_memory()
     mass_h = torch.tensor(w.mass).pin_memory()
@@ -337,6 +406,17 @@ def run_ours(args):
                      "interact_tflops": (s6["n_m2p_int"] * FLOPS_M2P[6] + s6["n_pairs"] * P2P_FLOPS)
                      / (st6["interact"] * 1e-3) / 1e12}
         del h64, h6
+        # the differentiation configuration: clustered recipe at N = 2^18
+        wd = W.make("clustered18")
+        Pd = torch.tensor(wd.pos, device=dev)
+        Md = torch.tensor(wd.mass, device=dev)
+        ad = torch.empty_like(Pd)
+        hd = hot.Hot(p=wd.p, tol=wd.tol, eps=wd.eps, precision="mixed")
+        out["adjoint_2e18"] = adjoint_leg(hd, lambda: hd.force(Pd, Md, ad), wd.n, dev, args.steps, flush, stream)
+        out["adjoint_2e18"]["workload"] = describe(wd)
+        del hd
+    if not args.no_leapfrog:
+        out["leapfrog"] = leapfrog_leg(args.leapfrog_workload, dev, stream)
         # truncation error of the mixed tree force against the FP64 direct sum on a subsample
         if rank == 0 and not args.no_cpu:
             import oracle

@@ -208,6 +208,13 @@ int hot_key_frame_noalloc(const double *pos, const double *mass, int64_t N, doub
  * this update.  x and y may not overlap unless equal. */
 int hot_axpy(hot_ctx *ctx, double *y, const double *x, double alpha, int64_t n);
 
+/* Device memory held by the library's own buffers (tree, moments, records, lists,
+ * scratch) over all contexts: out[0] bytes held now, out[1] the largest value since
+ * the library was loaded or the peak was last reset; reset_peak != 0 then sets the
+ * peak to the current value.  Host-side bookkeeping only (no device call).  The
+ * paper has no counterpart: it serves the memory report of multi-step runs. */
+int hot_memory_stats(int64_t out[2], int reset_peak);
+
 /* Fused-multiply-add throughput microbenchmark (for roofline denominators):
  * runs a register-resident FMA loop on every SM and writes the achieved
  * FLOP/s (FMA = 2) to *flops.  dbl: 0 = float32, 1 = float64.  Synchronises. */

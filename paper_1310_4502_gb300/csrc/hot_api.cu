@@ -8,6 +8,7 @@
 int hot_impl_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx);
 
 std::atomic<long long> hot_launch_counter{0};
+std::atomic<long long> hot_bytes_held{0}, hot_bytes_peak{0};
 
 namespace {
 
@@ -303,3 +304,12 @@ void hot_destroy(hot_ctx *c)
 }
 
 }  // extern "C"
+
+extern "C" int hot_memory_stats(int64_t out[2], int reset_peak)
+{
+    if (!out) return HOT_EINVAL;
+    out[0] = hot_bytes_held.load();
+    out[1] = hot_bytes_peak.load();
+    if (reset_peak) hot_bytes_peak.store(out[0]);
+    return HOT_OK;
+}

@@ -27,6 +27,16 @@
 extern std::atomic<long long> hot_launch_counter;
 #define HOT_COUNT_LAUNCH() hot_launch_counter.fetch_add(1, std::memory_order_relaxed)
 
+// Device bytes held in DBufs by all contexts, and the largest value since the last reset.
+extern std::atomic<long long> hot_bytes_held, hot_bytes_peak;
+inline void hot_bytes_add(long long d)
+{
+    long long now = hot_bytes_held.fetch_add(d, std::memory_order_relaxed) + d;
+    long long pk = hot_bytes_peak.load(std::memory_order_relaxed);
+    while (now > pk && !hot_bytes_peak.compare_exchange_weak(pk, now, std::memory_order_relaxed)) {
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Grow-only device buffer, stream-ordered allocation.
 // ---------------------------------------------------------------------------
@@ -37,17 +47,21 @@ struct DBuf {
     cudaError_t ensure(size_t n, cudaStream_t s)
     {
         if (n <= cap && p) return cudaSuccess;
-        if (p) cudaFreeAsync(p, s);
-        p = nullptr;
-        cap = 0;
+        release(s);
         size_t want = n + n / 8 + 64;
         cudaError_t e = cudaMallocAsync((void **)&p, want * sizeof(T), s);
-        if (e == cudaSuccess) cap = want;
+        if (e == cudaSuccess) {
+            cap = want;
+            hot_bytes_add((long long)(want * sizeof(T)));
+        }
         return e;
     }
     void release(cudaStream_t s)
     {
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            cudaFreeAsync(p, s);
+            hot_bytes_add(-(long long)(cap * sizeof(T)));
+        }
         p = nullptr;
         cap = 0;
     }

@@ -24,7 +24,8 @@ DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy")
+           "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy",
+           "hot_memory_stats")
 
 
 class hot_params(C.Structure):
@@ -73,9 +74,11 @@ def load():
     L.hot_destroy.restype = None
     L.hot_key_frame_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.hot_axpy.argtypes = [vp, vp, vp, C.c_double, C.c_int64]
+    L.hot_memory_stats.argtypes = [C.POINTER(C.c_int64), C.c_int]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
-                 "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy"):
+                 "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy",
+           "hot_memory_stats"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -122,6 +125,7 @@ class Hot:
         _ck(L.hot_create(C.byref(h), C.byref(self.params), C.c_void_p(stream.cuda_stream)), "hot_create")
         self._h = h
         self.N = 0
+        self.generation = 0  # bumped by every build_tree: names the tree the context holds
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -139,6 +143,7 @@ class Hot:
         _need(pos)
         _need(mass)
         self.N = int(mass.shape[0])
+        self.generation += 1
         _ck(load().hot_build_tree(self._h, _ptr(pos), _ptr(mass), self.N), "hot_build_tree")
 
     def compute_moments(self, p=None):
@@ -155,7 +160,19 @@ class Hot:
             _need(pot)
         _ck(load().hot_evaluate_forces(self._h, _ptr(acc), _ptr(pot)), "hot_evaluate_forces")
 
+    def force(self, pos, mass, acc, pot=None):
+        """The whole forward path at this context's parameters: build, moments,
+        traversal, interactions into the given device tensors."""
+        self.build_tree(pos, mass)
+        self.compute_moments(self.params.p)
+        self.traverse(self.params.tol)
+        self.evaluate_forces(acc, pot)
+
     def adjoint(self, g_acc, g_pot, g_pos, g_mass):
+        for t in (g_acc, g_pos, g_mass):
+            _need(t)
+        if g_pot is not None:
+            _need(g_pot)
         _ck(load().hot_adjoint(self._h, _ptr(g_acc), _ptr(g_pot), _ptr(g_pos), _ptr(g_mass)), "hot_adjoint")
 
     def stage_times(self):
@@ -207,6 +224,13 @@ class Hot:
         v = C.c_double()
         _ck(load().hot_fma_peak(self._h, 1 if dbl else 0, C.byref(v)), "hot_fma_peak")
         return v.value
+
+
+def memory_stats(reset_peak=False):
+    """(bytes the library holds on the device now, peak bytes since load or last reset)."""
+    out = (C.c_int64 * 2)()
+    _ck(load().hot_memory_stats(out, 1 if reset_peak else 0), "hot_memory_stats")
+    return int(out[0]), int(out[1])
 
 
 def key_frame_noalloc(pos, mass, frame, stream=None):

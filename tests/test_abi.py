@@ -33,6 +33,8 @@ def test_library_loads_and_reports_errors_without_gpu():
         assert hasattr(L, name)
     assert hot.strerror(hot.HOT_EINVAL) == "invalid argument"
     assert hot.strerror(hot.HOT_ESTATE) == "call out of order"
+    # host-side bookkeeping only: callable without a device, nothing held yet
+    assert hot.memory_stats() == (0, 0)
 
 
 def test_binding_rejects_cpu_tensors():
