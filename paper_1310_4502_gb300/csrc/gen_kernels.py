@@ -411,6 +411,28 @@ def gen_record_adjoint(p):
     return "\n".join(L)
 
 
+def record_adjoint_table(p):
+    """The map of gen_record_adjoint gathered per moment a: dL/dM_a = G sum_j f_j inv_s^e_j
+    dL/dC[q_j], terms in statement order.  Returns (start[ncomp+1], q, e, f)."""
+    S = s_terms(p)
+    idx = {a: i for i, a in enumerate(midx(p))}
+    terms = [[] for _ in range(ncomp(p))]
+    for i, (k, n, b) in enumerate(S):
+        m = n + k
+        const = (-1) ** k * dfact(2 * m - 1) / (2 ** k * fact3(b))
+        for l in midx(k)[ncomp(k - 1) if k > 0 else 0:]:
+            a = add(b, (2 * l[0], 2 * l[1], 2 * l[2]))
+            terms[idx[a]].append((i, 1 + 2 * k + n, const * (1.0 / fact3(l))))
+    start, q, e, f = [0], [], [], []
+    for t in terms:
+        for (i, ee, ff) in t:
+            q.append(i)
+            e.append(ee)
+            f.append(ff)
+        start.append(len(q))
+    return start, q, e, f
+
+
 def m2m_transposed(p):
     """For each b: the pairs (a >= b, C(a,b), g = a - b) of the translation, so that
     dL/dM_b(child) += sum_a C(a,b) (z_child - z_parent)^{a-b} dL/dM_a(parent)."""
@@ -577,6 +599,21 @@ def main(out_path):
     parts.append(f"__device__ const unsigned char m2mt_gamma[{len(tg)}] = {{{', '.join(map(str, tg))}}};")
     parts.append(f"__device__ const double m2mt_coef[{len(tc)}] = {{{', '.join(repr(float(c)) for c in tc)}}};")
     parts.append("static constexpr int HOT_NS[%d] = {%s};" % (PMAX + 1, ", ".join(str(len(s_terms(q))) for q in range(PMAX + 1))))
+    # record-adjoint gather tables of every order, concatenated (per-order bases)
+    sb, eb, rs, rq, re_, rf = [], [], [], [], [], []
+    for q in range(PMAX + 1):
+        st, qq, ee, ff = record_adjoint_table(q)
+        sb.append(len(rs))
+        eb.append(len(rq))
+        rs.extend(x + len(rq) for x in st)
+        rq.extend(qq)
+        re_.extend(ee)
+        rf.extend(ff)
+    parts.append("static constexpr int RADJ_SBASE[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, sb))))
+    parts.append(f"__device__ const unsigned short radj_start[{len(rs)}] = {{{', '.join(map(str, rs))}}};")
+    parts.append(f"__device__ const unsigned short radj_q[{len(rq)}] = {{{', '.join(map(str, rq))}}};")
+    parts.append(f"__device__ const unsigned char radj_e[{len(re_)}] = {{{', '.join(map(str, re_))}}};")
+    parts.append(f"__device__ const double radj_f[{len(rf)}] = {{{', '.join(repr(float(x)) for x in rf)}}};")
     for q in range(PMAX + 1):
         parts.append(gen_tangent(q))
         parts.append(gen_cbar(q))

@@ -172,24 +172,47 @@ __global__ void __launch_bounds__(AW * 32) k_adj_src(
 // dL/dC of every cell = sum of its items (fixed order, float64), then dL/dM through the
 // transposed record map.  One thread per cell; Mbar must be zero on entry.
 template <int P, class T>
-__global__ void k_adj_cells(int64_t ncell, const uint32_t *__restrict__ ioff,
-                            const T *__restrict__ part, const T *__restrict__ rec, double G,
-                            double *__restrict__ Mbar)
+__global__ void __launch_bounds__(AW * 32) k_adj_cells(int64_t ncell, const uint32_t *__restrict__ ioff,
+                                                       const T *__restrict__ part, const T *__restrict__ rec,
+                                                       double G, double *__restrict__ Mbar)
 {
+    // One warp per cell: the lanes sum the coefficient adjoints of the cell's items
+    // (coalesced rows, FP64, items in order), then each lane gathers the moment
+    // adjoints it owns through the record-adjoint table (terms in a fixed order).
     constexpr int RL = ACfg<P, T>::RL;
     constexpr int NS = ACfg<P, T>::NS;
     constexpr int NC = ACfg<P, T>::NC;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    if (ioff[c] == ioff[c + 1]) return;
-    double cb[NS];
-#pragma unroll
-    for (int q = 0; q < NS; ++q) cb[q] = 0.0;
-    for (uint32_t it = ioff[c]; it < ioff[c + 1]; ++it)
-#pragma unroll
-        for (int q = 0; q < NS; ++q) cb[q] += (double)part[(int64_t)it * NS + q];
-    const double inv_s = (double)rec[c * (int64_t)RL];
-    m2p_record_adjoint<P>(cb, inv_s, G, Mbar + c * (int64_t)NC);
+    constexpr int NE = 2 * P + 2;
+    __shared__ double scb[AW][NS];
+    __shared__ double sip[AW][NE];
+    const int wi = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t c = (int64_t)blockIdx.x * AW + wi; c < ncell; c += nw) {
+        const uint32_t i0 = ioff[c], i1 = ioff[c + 1];
+        if (i0 == i1) continue;
+        for (int q = lane; q < NS; q += 32) {
+            double t = 0.0;
+            for (uint32_t it = i0; it < i1; ++it) t += (double)part[(int64_t)it * NS + q];
+            scb[wi][q] = t;
+        }
+        if (lane == 0) {
+            const double inv_s = (double)rec[c * (int64_t)RL];
+            double v = 1.0;
+            for (int e = 0; e < NE; ++e) {
+                sip[wi][e] = v;
+                v *= inv_s;
+            }
+        }
+        __syncwarp();
+        for (int a = lane; a < NC; a += 32) {
+            double t = 0.0;
+            const int j0 = radj_start[RADJ_SBASE[P] + a], j1 = radj_start[RADJ_SBASE[P] + a + 1];
+            for (int j = j0; j < j1; ++j) t += radj_f[j] * sip[wi][radj_e[j]] * scb[wi][radj_q[j]];
+            Mbar[c * NC + a] = G * t;
+        }
+        __syncwarp();
+    }
 }
 
 // Top-down: dL/dM of a cell += transposed translation of its parent's dL/dM
@@ -355,8 +378,20 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
     }
 }
 
+// Position of multi-index (i, j, k) in the moment order (degree ascending, then i
+// descending, then j descending).
+__host__ __device__ constexpr int moment_index(int i, int j, int k)
+{
+    const int n = i + j + k;
+    return n * (n + 1) * (n + 2) / 6 + (n - i) * (n - i + 1) / 2 + (n - i - j);
+}
+
 // Leaves: transposed P2M of dL/dM onto the particles (float64), plus the sink-side and
-// P2P source-side parts; written in original order.
+// P2P source-side parts; written in original order.  A half-warp per leaf, a lane per
+// particle; with (d = x - z) the sums
+//   dL/dm = sum_a Mbar_a d^a,   dL/dx = m sum_a Mbar_a grad(d^a)
+// are taken in factorised form (z innermost, then y, then x), fully unrolled so that
+// the powers stay in registers.
 template <int P>
 __global__ void __launch_bounds__(AW * 32) k_adj_leaf(
     int64_t ncell, const int32_t *__restrict__ cnchild, const int32_t *__restrict__ cbegin,
@@ -366,37 +401,46 @@ __global__ void __launch_bounds__(AW * 32) k_adj_leaf(
     double *__restrict__ g_mass)
 {
     constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
-    __shared__ double sm[AW][NC];
-    __shared__ unsigned char mi[NC][3];
-    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
-        mi[k][0] = hot_midx[k][0];
-        mi[k][1] = hot_midx[k][1];
-        mi[k][2] = hot_midx[k][2];
-    }
-    __syncthreads();
-    const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    const int64_t nw = (int64_t)gridDim.x * AW;
-    for (int64_t c = (int64_t)blockIdx.x * AW + wi; c < ncell; c += nw) {
+    const int half = (int)(lane >> 4), hl = (int)(lane & 15);
+    const int64_t nh = (int64_t)gridDim.x * AW * 2;
+    for (int64_t c = ((int64_t)blockIdx.x * AW + (threadIdx.x >> 5)) * 2 + half; c < ncell; c += nh) {
         if (cnchild[c] != 0) continue;
-        for (int g = lane; g < NC; g += 32) sm[wi][g] = Mbar[c * NC + g];
-        __syncwarp();
+        const double *__restrict__ mb = Mbar + c * NC;
         const int64_t b = cbegin[c], n = ccount[c];
-        for (int64_t s = b + lane; s < b + n; s += 32) {
-            double pw[3][P + 1];
-            for (int e = 0; e < 3; ++e) {
-                const double d = spos[3 * s + e] - ccom[3 * c + e];
-                pw[e][0] = 1.0;
-                for (int q = 1; q <= P; ++q) pw[e][q] = pw[e][q - 1] * d;
+        for (int64_t s = b + hl; s < b + n; s += 16) {
+            double px[P + 1], py[P + 1], pz[P + 1];
+            px[0] = py[0] = pz[0] = 1.0;
+            const double dx = spos[3 * s + 0] - ccom[3 * c + 0];
+            const double dy = spos[3 * s + 1] - ccom[3 * c + 1];
+            const double dz = spos[3 * s + 2] - ccom[3 * c + 2];
+#pragma unroll
+            for (int q = 1; q <= P; ++q) {
+                px[q] = px[q - 1] * dx;
+                py[q] = py[q - 1] * dy;
+                pz[q] = pz[q - 1] * dz;
             }
             double gm = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-            for (int a = 0; a < NC; ++a) {
-                const int i = mi[a][0], j = mi[a][1], k = mi[a][2];
-                const double mb = sm[wi][a];
-                gm += mb * pw[0][i] * pw[1][j] * pw[2][k];
-                if (i) gx += mb * i * pw[0][i - 1] * pw[1][j] * pw[2][k];
-                if (j) gy += mb * j * pw[0][i] * pw[1][j - 1] * pw[2][k];
-                if (k) gz += mb * k * pw[0][i] * pw[1][j] * pw[2][k - 1];
+#pragma unroll
+            for (int i = 0; i <= P; ++i) {
+                double T0 = 0.0, Ty = 0.0, Tz = 0.0;
+#pragma unroll
+                for (int j = 0; j <= P - i; ++j) {
+                    double S0 = 0.0, Sz = 0.0;
+#pragma unroll
+                    for (int k = 0; k <= P - i - j; ++k) {
+                        const double m = __ldg(mb + moment_index(i, j, k));
+                        S0 += m * pz[k];
+                        if (k > 0) Sz += (double)k * m * pz[k - 1];
+                    }
+                    T0 += py[j] * S0;
+                    Tz += py[j] * Sz;
+                    if (j > 0) Ty += (double)j * py[j - 1] * S0;
+                }
+                gm += px[i] * T0;
+                gy += px[i] * Ty;
+                gz += px[i] * Tz;
+                if (i > 0) gx += (double)i * px[i - 1] * T0;
             }
             const double m = smass[s];
             const int64_t o = perm[s];
@@ -405,7 +449,6 @@ __global__ void __launch_bounds__(AW * 32) k_adj_leaf(
             g_pos[3 * o + 2] = m * gz + gsink[3 * s + 2] + gp2p[4 * s + 2];
             g_mass[o] = gm + gp2p[4 * s + 3];
         }
-        __syncwarp();
     }
 }
 
@@ -476,8 +519,8 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
                                                       c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, rec, w,
                                                       c->adj_xhl.p, c->spos.p, part);
         HOT_COUNT_LAUNCH();
-        k_adj_cells<P, T><<<hot_blocks(nc, 128), 128, 0, s>>>(nc, c->it_off.p, part, rec, c->prm.G,
-                                                             c->adj_mbar.p);
+        k_adj_cells<P, T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(nc, c->it_off.p, part, rec,
+                                                                              c->prm.G, c->adj_mbar.p);
     }
     // push dL/dM down the tree, level by level
     for (int l = 1; l <= (int)c->maxlevel; ++l) {

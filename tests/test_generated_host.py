@@ -84,6 +84,20 @@ static double dpow(const double *d, int g)
         for (int t = 0; t < hot_midx[g][e]; ++t) v *= d[e];
     return v;
 }
+void g_radj(int p, const double *cb, double is, double G, double *serial, double *table)
+{
+    for (int a = 0; a < HOT_NCOMP[p]; ++a) serial[a] = 0.0;
+    DISPATCH(m2p_record_adjoint, cb, is, G, serial)
+    double ip[16];
+    ip[0] = 1.0;
+    for (int e = 1; e < 16; ++e) ip[e] = ip[e - 1] * is;
+    for (int a = 0; a < HOT_NCOMP[p]; ++a) {
+        double t = 0.0;
+        for (int j = radj_start[RADJ_SBASE[p] + a]; j < radj_start[RADJ_SBASE[p] + a + 1]; ++j)
+            t += radj_f[j] * ip[radj_e[j]] * cb[radj_q[j]];
+        table[a] = G * t;
+    }
+}
 void g_m2m(int p, const double *Mc, const double *d, double *Mp)
 {
     for (int a = 0; a < HOT_NCOMP[p]; ++a) {
@@ -120,8 +134,9 @@ def gen(tmp_path_factory):
     L.g_eval.argtypes = [C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
     L.g_tangent.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp, dp, C.c_double, dp]
     L.g_m2m.argtypes = [C.c_int, dp, dp, dp]
+    L.g_radj.argtypes = [C.c_int, dp, C.c_double, C.c_double, dp, dp]
     L.g_m2mt.argtypes = [C.c_int, dp, dp, dp]
-    for f in (L.g_eval, L.g_tangent, L.g_m2m, L.g_m2mt):
+    for f in (L.g_eval, L.g_tangent, L.g_m2m, L.g_m2mt, L.g_radj):
         f.restype = None
     return L
 
@@ -208,3 +223,16 @@ def test_m2m_tables_translate_moments(gen, p):
         gen.g_m2m(p, x, d, Tx)
         gen.g_m2mt(p, y, d, Tty)
         assert y @ Tx == pytest.approx(Tty @ x, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("p", range(7))
+def test_record_adjoint_gather_table_equals_generated_map(gen, p):
+    """The per-moment gather table the cell kernel uses is the same linear map as the
+    straight-line record adjoint (itself pinned against the oracle above)."""
+    rng = np.random.default_rng(400 + p)
+    nc = oracle.ncomp(p)
+    cb = rng.standard_normal(200)
+    a = np.zeros(nc)
+    b = np.zeros(nc)
+    gen.g_radj(p, cb, 0.25, 1.7, a, b)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))

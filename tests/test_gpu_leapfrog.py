@@ -97,7 +97,10 @@ def test_time_reversible_fp64():
     assert np.max(np.abs(-v2 - v)) < 1e-11
 
 
-def _fd(trees, x, v, m, wx, wv, dt, eps, ks, h=1e-6):
+def _fd(trees, x, v, m, wx, wv, dt, eps, ks, h=1e-4):
+    """Fourth-order central differences.  The loss difference sums 3N coordinates of two
+    separately rounded trajectories, about 1e-13 of noise, so h = 1e-6 would leave ~1e-8
+    in the derivative; at h = 1e-4 noise and truncation (h^4 terms) are both ~1e-10."""
     def L(x_, v_, m_):
         xs, vs = oracle.frozen_leapfrog(trees, x_, v_, m_, dt, 1.0, eps)
         return xs, vs
@@ -118,7 +121,7 @@ def _fd(trees, x, v, m, wx, wv, dt, eps, ks, h=1e-6):
                     (xx if which == 0 else vv)[k, d] += s * h
                     res.append(L(xx, vv, m))
                 out[r, d] = (8 * dL(res[0], 0, res[1], 0) - dL(res[2], 0, res[3], 0)) / (12 * h)
-        hm = 1e-3 * m[k]
+        hm = 1e-2 * m[k]
         res = []
         for s in (1, -1, 2, -2):
             mm = m.copy()
@@ -149,9 +152,7 @@ def test_backward_against_finite_differences(fd_ref, prec, bound):
     # whole gradient, relative
     for g, f in ((gx, fx), (gv, fv)):
         assert np.max(np.linalg.norm(g - f, axis=1) / np.linalg.norm(f, axis=1)) < bound
-    # dL/dm: the difference of two loss values of size |w| sqrt(N) carries about 1e-8 of
-    # absolute noise, so the relative bound is floored at 1e-7
-    assert np.max(np.abs(gm - fm) / np.abs(fm)) < max(bound, 1e-7)
+    assert np.max(np.abs(gm - fm) / np.abs(fm)) < bound
     # force-induced part, relative to its own size
     free_x, free_v = wx[ks], S * dt * wx[ks] + wv[ks]
     for g, f, free in ((gx, fx, free_x), (gv, fv, free_v)):
