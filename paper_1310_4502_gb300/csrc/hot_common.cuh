@@ -23,6 +23,9 @@
 
 #define HOT_MAXLEVEL 21
 
+// Device memory the one-pass traversal may hold in per-group list slots (bytes).
+#define HOT_SLOT_BUDGET (16.0 * 1024 * 1024 * 1024)
+
 // Number of kernel launches issued by this library (all contexts), for benchmarks.
 extern std::atomic<long long> hot_launch_counter;
 #define HOT_COUNT_LAUNCH() hot_launch_counter.fetch_add(1, std::memory_order_relaxed)
@@ -139,6 +142,9 @@ struct hot_ctx {
     DBuf<int64_t> it_a, it_b;
     DBuf<unsigned char> it_part;
     int trav_cap = 2048;
+    // per-group slot capacities of the one-pass traversal (grown from the counts seen)
+    int64_t slot_capm = 2048, slot_capp = 512;
+    DBuf<int32_t> slot_m2p, slot_p2p;
     DBuf<int64_t> pairs_per_group;
 
     // status

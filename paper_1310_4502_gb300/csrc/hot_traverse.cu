@@ -28,9 +28,27 @@ __device__ __forceinline__ double mac_bound(double d, double b, double B1, doubl
     return __dmul_rn(__ddiv_rn(__ddiv_rn(G, __dmul_rn(d, d)), __dmul_rn(q, q)), __dsub_rn(t1, t2));
 }
 
+// ln E(d) - ln tol and its derivative in ln d, for the radius solver (any rounding: the
+// traversal re-takes decisions near the threshold with mac_bound itself).  With
+// T(d) d^{p+2} = (p+2) B_{p+1} d - (p+1) B_{p+2} > 0 on (b, inf):
+//   d (ln E)'(d) = -2 - 2b/(d - b) - (p+1)(p+2)(B_{p+1} d - B_{p+2}) / ((p+2) B_{p+1} d - (p+1) B_{p+2})
+__device__ __forceinline__ void mac_log_newton(double d, double b, double B1, double B2, int p, double G,
+                                               double ltol, double &f, double &df)
+{
+    const double q = 1.0 - b / d;
+    const double tn = (p + 2) * B1 * d - (p + 1) * B2;  // T(d) d^{p+2}
+    // ln E = ln G - 2 ln d - 2 ln q + ln tn - (p+2) ln d
+    f = log(G) - (p + 4) * log(d) - 2.0 * log(q) + log(tn) - ltol;
+    df = -2.0 - 2.0 * b / (d - b) - (double)((p + 1) * (p + 2)) * (B1 * d - B2) / tn;
+}
+
 // Acceptance radius of every cell for the tolerance: E is strictly decreasing on
-// (b_max, inf), so "d > b_max and E(d) <= tol" is "d >= r_c" with E(r_c) = tol, found by
-// doubling and bisection in float64 (r_c = 0 when b_max = 0, where E vanishes).
+// (b_max, inf), so "d > b_max and E(d) <= tol" is "d >= r_c" with E(r_c) = tol.  A
+// bracket [lo, hi] with E(lo) > tol >= E(hi) is found by doubling, then Newton steps
+// in ln d on ln E - ln tol (which is nearly linear in ln d), falling back to bisection
+// whenever a step leaves the bracket, until a step or the bracket is below 1e-13
+// relative (r_c = 0 when b_max = 0, where E vanishes).  That accuracy is far inside the
+// 1e-9 band in which the traversal re-takes decisions with the bound itself.
 __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
                              const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
                              double G, double tol, TCell *__restrict__ tc)
@@ -50,15 +68,29 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
         if (k >= 1100) {
             rc = INFINITY;
         } else {
-            for (int it = 0; it < 64; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (!(mid > lo && mid < hi)) break;
-                if (mac_bound(mid, b, B1, B2, p, G) <= tol)
-                    hi = mid;
+            const double ltol = log(tol);
+            double d = hi;
+            for (int it = 0; it < 60; ++it) {
+                double f, df;
+                mac_log_newton(d, b, B1, B2, p, G, ltol, f, df);
+                double dn = d * exp(-f / df);
+                if (fabs(dn - d) <= 1e-13 * d) {  // converged (possibly onto a bracket end)
+                    d = dn;
+                    break;
+                }
+                if (!(dn > lo && dn < hi)) dn = 0.5 * (lo + hi);
+                if (!(dn > lo && dn < hi)) break;
+                if (mac_bound(dn, b, B1, B2, p, G) <= tol)
+                    hi = dn;
                 else
-                    lo = mid;
+                    lo = dn;
+                d = dn;
+                if (hi - lo <= 1e-13 * hi) {
+                    d = hi;
+                    break;
+                }
             }
-            rc = hi;
+            rc = d;
         }
     }
     TCell t;
@@ -69,7 +101,13 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
     tc[c] = t;
 }
 
-template <bool FILL>
+// MODE 0: count the entries of every group's lists (and the interaction totals);
+// MODE 1: fill the CSR lists at the scanned offsets;
+// MODE 2: one pass for both -- the entries go to fixed-capacity per-group slots (capm,
+// capp entries), the counts and totals as in MODE 0, and the largest counts to maxc[2];
+// a group whose lists do not fit sets *slot_over and keeps counting.  MODE 0 also
+// records the largest counts.
+template <int MODE>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const double *__restrict__ gdmax, const TCell *__restrict__ tcell, const int32_t *__restrict__ cend,
@@ -79,8 +117,10 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
+    int64_t capm, int64_t capp, unsigned long long *__restrict__ maxc, unsigned *__restrict__ slot_over,
     unsigned *__restrict__ status)
 {
+    constexpr bool FILL = MODE == 1, SLOTS = MODE == 2;
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -98,6 +138,9 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
         if (FILL) {
             om = off_m2p[g];
             op = off_p2p[g];
+        } else if (SLOTS) {
+            om = g * capm;
+            op = g * capp;
         }
         int32_t *A = bufA, *B = bufB;
         if (lane == 0) A[0] = 0;
@@ -146,8 +189,13 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 if (FILL) {
                     if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = c;
                     if (kind == 2) l_p2p[op + np + __popc(pm & lt)] = c;
-                } else if (kind == 2) {
-                    p2p_parts += (uint64_t)ccount[c];
+                } else {
+                    if (SLOTS) {
+                        const int64_t im = nm + __popc(mm & lt), ip = np + __popc(pm & lt);
+                        if (kind == 1 && im < capm) l_m2p[om + im] = c;
+                        if (kind == 2 && ip < capp) l_p2p[op + ip] = c;
+                    }
+                    if (kind == 2) p2p_parts += (uint64_t)ccount[c];
                 }
                 nm += __popc(mm);
                 np += __popc(pm);
@@ -186,10 +234,28 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 const uint64_t ns = (uint64_t)ccount[gc];
                 atomicAdd(&stats[0], (unsigned long long)(ns * nm));
                 atomicAdd(&stats[1], (unsigned long long)(ns * p2p_parts));
+                atomicMax(&maxc[0], (unsigned long long)nm);
+                atomicMax(&maxc[1], (unsigned long long)np);
+                if (SLOTS && ((int64_t)nm > capm || (int64_t)np > capp)) atomicOr(slot_over, 1u);
             }
         }
         __syncwarp();
     }
+}
+
+// Copy every group's slot entries to its CSR range (one warp per group, in order).
+__global__ void k_compact_lists(int64_t ngroup, int64_t capm, int64_t capp, const int32_t *__restrict__ sm,
+                                const int32_t *__restrict__ sp, const int64_t *__restrict__ off_m2p,
+                                const int64_t *__restrict__ off_p2p, int32_t *__restrict__ l_m2p,
+                                int32_t *__restrict__ l_p2p)
+{
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= ngroup) return;
+    const unsigned lane = lane_id();
+    const int64_t m0 = off_m2p[g], nm = off_m2p[g + 1] - m0;
+    const int64_t p0 = off_p2p[g], np = off_p2p[g + 1] - p0;
+    for (int64_t k = lane; k < nm; k += 32) l_m2p[m0 + k] = sm[g * capm + k];
+    for (int64_t k = lane; k < np; k += 32) l_p2p[p0 + k] = sp[g * capp + k];
 }
 
 }  // namespace
@@ -208,19 +274,38 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     const int64_t nwarps = (int64_t)blocks * TW;
     unsigned *work = (unsigned *)(c->sizes.p + 50);
     unsigned long long *stats = (unsigned long long *)(c->sizes.p + 52);
+    unsigned long long *maxc = (unsigned long long *)(c->sizes.p + 58);
+    unsigned *slot_over = (unsigned *)(c->sizes.p + 60);
     HOT_CK(c->tcell.ensure(c->ncell, s));
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
                                                             c->p_mom, c->prm.G, tol, c->tcell.p);
-    int64_t host[4];
+    // One pass into per-group slots when their capacities (the largest counts of the
+    // previous traversal plus headroom) fit the budget; otherwise count, scan, fill.
+    const int64_t capm = c->slot_capm, capp = c->slot_capp;
+    const bool slots = (double)ng * (double)(capm + capp) * sizeof(int32_t) <= HOT_SLOT_BUDGET;
+    if (slots) {
+        HOT_CK(c->slot_m2p.ensure((size_t)ng * capm, s));
+        HOT_CK(c->slot_p2p.ensure((size_t)ng * capp, s));
+    }
+    int64_t host[7];
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
+        HOT_CK(cudaMemsetAsync(c->sizes.p + 58, 0, 3 * sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
-        k_traverse<false><<<blocks, TW * 32, 0, s>>>(
-            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
-            work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, c->d_status);
+        if (slots)
+            k_traverse<2><<<blocks, TW * 32, 0, s>>>(
+                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
+                c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
+                capm, capp, maxc, slot_over, c->d_status);
+        else
+            k_traverse<0><<<blocks, TW * 32, 0, s>>>(
+                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
+                c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
+                slot_over, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
         if (r) return r;
         r = hot_scan_u32_to_i64(c->cnt_p2p.p, c->off_p2p.p, ng, c->scan_tmp.p, s);
@@ -228,6 +313,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_CK(cudaMemcpyAsync(host + 0, c->off_m2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaMemcpyAsync(host + 1, c->off_p2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaMemcpyAsync(host + 2, stats, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 4, c->sizes.p + 58, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaStreamSynchronize(s));
         unsigned st = 0;
         HOT_CK(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -245,14 +331,26 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     c->n_p2p = host[1];
     c->n_m2p_int = host[2];
     c->n_pairs = host[3];
+    const bool fits = slots && (host[6] & 0xffffffffll) == 0;
+    auto round_cap = [](int64_t n) { return ((n + n / 4 + 256) + 255) / 256 * 256; };
+    c->slot_capm = round_cap(host[4]);
+    c->slot_capp = round_cap(host[5]);
     HOT_CK(c->l_m2p.ensure(c->n_m2p + 1, s));
     HOT_CK(c->l_p2p.ensure(c->n_p2p + 1, s));
-    HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
-    HOT_COUNT_LAUNCH();
-    k_traverse<true><<<blocks, TW * 32, 0, s>>>(
-        ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-        c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap, work,
-        nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, c->d_status);
+    if (fits) {
+        HOT_COUNT_LAUNCH();
+        k_compact_lists<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(ng, capm, capp, c->slot_m2p.p, c->slot_p2p.p,
+                                                                  c->off_m2p.p, c->off_p2p.p, c->l_m2p.p,
+                                                                  c->l_p2p.p);
+    } else {
+        HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
+        HOT_COUNT_LAUNCH();
+        k_traverse<1><<<blocks, TW * 32, 0, s>>>(
+            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
+            work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
+            slot_over, c->d_status);
+    }
     hot_toc(c, 3);
     if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     c->tol_lists = tol;

@@ -123,3 +123,17 @@ def test_adjoint_without_potential_weights():
     fx, fm = fd_reference(pos, mass, w, None, 4, 1e-4, eps, ks)
     sx = np.sqrt(np.mean(np.sum(fx ** 2, 1)))
     assert np.max(np.linalg.norm(gx[ks] - fx, axis=1) / np.maximum(np.linalg.norm(fx, axis=1), sx)) < 1e-7
+
+
+def test_context_destroy_returns_all_device_memory():
+    """Every buffer a context grows (tree, moments, lists, list slots, adjoint scratch)
+    is released by hot_destroy: the library's byte counter returns to its prior value."""
+    pos, mass, eps = CASES["plummer4096"]()
+    torch.cuda.synchronize()
+    before = hot.memory_stats()[0]
+    rng = np.random.default_rng(9)
+    gpu_adjoint(pos, mass, rng.standard_normal((len(mass), 3)), None, 4, 1e-4, eps, "mixed")
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    assert hot.memory_stats()[0] == before
