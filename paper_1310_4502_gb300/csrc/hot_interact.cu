@@ -45,6 +45,8 @@ struct alignas(16) Smem {
     T src[SRC][4];
     double red[32][4];
     int32_t sidx[SRC];
+    int32_t lex[33], lbeg[32];  // P2P batch: scanned particle offsets and first slots
+    T loff[32][3];              // P2P batch: leaf centre offsets
     unsigned long long bar[2];
 };
 
@@ -274,6 +276,9 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         __syncwarp();
         fill = 0;
     };
+    // 32 list entries at a time: their particle counts are scanned across the lanes, then
+    // every lane loads particles of the batch (finding its leaf by binary search in the
+    // scanned offsets), so the loads of all 32 leaves are in flight together.
     for (int64_t e0 = G.p0; e0 < G.p1; e0 += 32) {
         const int ne = (int)(G.p1 - e0 < 32 ? G.p1 - e0 : 32);
         int32_t lb = 0, lc = 0;
@@ -287,36 +292,46 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             for (int q = 0; q < 8; ++q) h[q] = rec[(int64_t)leaf * RL + q];
             centre_offset(h, G, ox, oy, oz);
         }
-        for (int j = 0; j < ne; ++j) {
-            const int32_t b = __shfl_sync(0xffffffffu, lb, j);
-            const int32_t n = __shfl_sync(0xffffffffu, lc, j);
-            const T fx = __shfl_sync(0xffffffffu, ox, j);
-            const T fy = __shfl_sync(0xffffffffu, oy, j);
-            const T fz = __shfl_sync(0xffffffffu, oz, j);
-            for (int q0 = 0; q0 < n; q0 += 32) {
-                const int take = n - q0 < 32 ? n - q0 : 32;
-                if (fill + take > SRC) flush();
-                if ((int)lane < take) {
-                    const int64_t s = (int64_t)b + q0 + lane;
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 v = prel[s];
-                        sm.src[fill + lane][0] = v.x + fx;
-                        sm.src[fill + lane][1] = v.y + fy;
-                        sm.src[fill + lane][2] = v.z + fz;
-                        sm.src[fill + lane][3] = v.w;
-                    } else {
-                        sm.src[fill + lane][0] = (T)(spos[3 * s + 0] - G.gx);
-                        sm.src[fill + lane][1] = (T)(spos[3 * s + 1] - G.gy);
-                        sm.src[fill + lane][2] = (T)(spos[3 * s + 2] - G.gz);
-                        sm.src[fill + lane][3] = (T)smass[s];
-                    }
-                    sm.sidx[fill + lane] = (int32_t)s;
+        const int incl = warp_incl_scan(lc);
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        sm.lex[lane + 1] = incl;
+        if (lane == 0) sm.lex[0] = 0;
+        sm.lbeg[lane] = lb;
+        sm.loff[lane][0] = ox;
+        sm.loff[lane][1] = oy;
+        sm.loff[lane][2] = oz;
+        __syncwarp();
+        for (int t0 = 0; t0 < tot; t0 += SRC) {
+            const int take = tot - t0 < SRC ? tot - t0 : SRC;
+            for (int u = lane; u < take; u += 32) {
+                const int t = t0 + u;
+                int lo = 0, hi = ne;  // leaf j with lex[j] <= t < lex[j + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.lex[mid] <= t)
+                        lo = mid;
+                    else
+                        hi = mid;
                 }
-                fill += take;
+                const int64_t s = (int64_t)sm.lbeg[lo] + (t - sm.lex[lo]);
+                if constexpr (sizeof(T) == 4) {
+                    const float4 v = prel[s];
+                    sm.src[u][0] = v.x + sm.loff[lo][0];
+                    sm.src[u][1] = v.y + sm.loff[lo][1];
+                    sm.src[u][2] = v.z + sm.loff[lo][2];
+                    sm.src[u][3] = v.w;
+                } else {
+                    sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx);
+                    sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy);
+                    sm.src[u][2] = (T)(spos[3 * s + 2] - G.gz);
+                    sm.src[u][3] = (T)smass[s];
+                }
+                sm.sidx[u] = (int32_t)s;
             }
+            fill = take;
+            flush();
         }
     }
-    if (fill > 0) flush();
 }
 
 // cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.

@@ -14,8 +14,12 @@ constexpr int CHUNK = 2048;  // particles per aggregate work item
 // ---------------------------------------------------------------------------
 // P2M at leaves: one warp per leaf.  Also b_max, B_{p+1}, B_{p+2} of the leaf and
 // the leaf-relative single-precision particle copy used by the P2P interactions.
+// The centre of mass and the acceptance aggregates are float64 (they decide the
+// acceptance test); the moment sums run in T on the leaf-relative offsets (float32 in
+// the mixed mode, which only feeds float32 interaction records and the float64 M2M)
+// and are stored as float64.
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, class T>
 __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
     const int32_t *__restrict__ cnchild, int64_t ncell, const double *__restrict__ spos,
@@ -24,8 +28,8 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
     double *__restrict__ cB2, float4 *__restrict__ prel)
 {
     constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
-    __shared__ double pw[MW][32][3][P + 1];
-    __shared__ double pm[MW][32];
+    __shared__ T pw[MW][32][3][P + 1];
+    __shared__ T pm[MW][32];
     __shared__ unsigned char mi[NC][3];
     for (int k = threadIdx.x; k < NC; k += blockDim.x) {
         mi[k][0] = hot_midx[k][0];
@@ -52,9 +56,9 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
         my = warp_sum(my);
         mz = warp_sum(mz);
         const double z[3] = {mx / m, my / m, mz / m};
-        double acc[(NC + 31) / 32];
+        T acc[(NC + 31) / 32];
 #pragma unroll
-        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = 0.0;
+        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = T(0);
         double bmax = 0.0, B1 = 0.0, B2 = 0.0;
         for (int64_t s0 = b; s0 < b + n; s0 += 32) {
             int64_t s = s0 + lane;
@@ -71,12 +75,13 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
                 B2 += ms * rp * r;
                 prel[s] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)ms);
             }
-            pm[w][lane] = ms;
+            pm[w][lane] = (T)ms;
             for (int e = 0; e < 3; ++e) {
-                double v = 1.0;
+                const T de = (T)d[e];
+                T v = T(1);
                 for (int q = 0; q <= P; ++q) {
                     pw[w][lane][e][q] = v;
-                    v *= d[e];
+                    v *= de;
                 }
             }
             __syncwarp();
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
                 int a = lane + 32 * q;
                 if (a < NC) {
                     int ax = mi[a][0], ay = mi[a][1], az = mi[a][2];
-                    double t = 0.0;
+                    T t = T(0);
                     for (int j = 0; j < cnt; ++j)
                         t += pm[w][j] * pw[w][j][0][ax] * pw[w][j][1][ay] * pw[w][j][2][az];
                     acc[q] += t;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
 #pragma unroll
         for (int q = 0; q < (NC + 31) / 32; ++q) {
             int a = lane + 32 * q;
-            if (a < NC) cmom[c * NC + a] = acc[q];
+            if (a < NC) cmom[c * NC + a] = (double)acc[q];
         }
         if (lane == 0) {
             cmass[c] = m;
@@ -314,9 +319,14 @@ int moments_p(hot_ctx *c)
     HOT_CK(c->prel.ensure(N, s));
     const int grid = c->nsm * 8;
     HOT_COUNT_LAUNCH();
-    k_p2m_leaf<P><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
-                                           c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
-                                           c->cB1.p, c->cB2.p, c->prel.p);
+    if (c->prm.precision == HOT_FP64)
+        k_p2m_leaf<P, double><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
+                                                       c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
+                                                       c->cB1.p, c->cB2.p, c->prel.p);
+    else
+        k_p2m_leaf<P, float><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
+                                                      c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
+                                                      c->cB1.p, c->cB2.p, c->prel.p);
     for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
         int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
         if (n <= 0) continue;
