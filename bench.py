@@ -360,8 +360,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": describe(w), "N": N, "p": w.p, "tol": w.tol, "eps": w.eps, "leaf_max": 16,
-                      "group_max": 64, "l2": "flushed between steps (256 MiB write, untimed)",
+           "config": {"workload": describe(w), "N": N, "p": w.p, "tol": w.tol, "eps": w.eps, "leaf_max": h.params.leaf_max,
+                      "group_max": h.params.group_max, "l2": "flushed between steps (256 MiB write, untimed)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "stages_ms": stages, "sizes": {k: v for k, v in sz.items() if k != "launches"},
            "gpu_launches": launches, "roofline": roof, "clocks": clocks,

@@ -189,7 +189,7 @@ def mac_bound(d, b, B1, B2, p, G=1.0):
 class Tree:
     """Oracle tree: keys, stable sort, pre-order cells, groups, moments, lists, forces."""
 
-    def __init__(self, pos, mass, leaf_max=16, group_max=64):
+    def __init__(self, pos, mass, leaf_max=64, group_max=128):
         self.pos = _c(pos)
         self.mass = _c(mass)
         self.leaf_max, self.group_max = leaf_max, group_max
@@ -320,7 +320,7 @@ def frozen_leapfrog(trees, x0, v0, mass, dt, G=1.0, eps=0.0):
     return x, v
 
 
-def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64):
+def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128):
     t = Tree(pos, mass, leaf_max, group_max)
     t.moments(p)
     t.traverse(tol, G)

@@ -100,6 +100,18 @@ __global__ void k_item_fill_adj(const int64_t *__restrict__ start, const int64_t
     }
 }
 
+// Partial rows of the P2P source side: a leaf with entries gets (its items) x (its
+// particles) rows.
+__global__ void k_item_rows(const int64_t *__restrict__ start, const int64_t *__restrict__ end,
+                            const int32_t *__restrict__ ccount, const int32_t *__restrict__ cnchild, int64_t ncell,
+                            uint32_t *__restrict__ rows)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int64_t ne = end[c] - start[c];
+    rows[c] = (cnchild[c] != 0 || ne <= 0) ? 0u : (uint32_t)(((ne + KG - 1) / KG) * (int64_t)ccount[c]);
+}
+
 // Source side of M2P: one warp per item (one cell, up to KG groups that list it); the
 // sinks of all the item's groups are spread over the lanes.  Each lane accumulates the
 // coefficient adjoints in registers; the warp sum goes to part[item].
@@ -262,118 +274,208 @@ __global__ void __launch_bounds__(AW * 32) k_adj_l2l(const int32_t *__restrict__
     }
 }
 
-// Source side of P2P: one warp per leaf, lanes = (leaf particle, split of the sinks).
-// For a pair (sink i, source j), d = x_j - x_i, s^2 = |d|^2 + eps^2:
-//   dL/dx_j += G m_j [u_i/s^3 - 3 d (d.u_i)/s^5 + v_i d/s^3]
-//   dL/dm_j += G [u_i.d/s^3 - v_i/s]
+// Source side of P2P: work items of one leaf and up to KG of the groups that list it (a
+// leaf in a dense region is listed by thousands of groups, so whole leaves would leave
+// a long tail).  One warp per item, taken from a work counter; lanes = leaf particles
+// (two per lane when the leaf has more than 32, otherwise one per lane with the staged
+// sinks split across the spare lanes).  The sinks of the item's groups are staged PS at
+// a time, all their loads in flight together (a scan of the group sizes, then every lane
+// loads sinks of the batch).  Per item and leaf particle the sums
+//   gx = sum_i [u_i/s^3 - 3 d (d.u_i)/s^5 + v_i d/s^3],  gm = sum_i [u_i.d/s^3 - v_i/s]
+// (d = x_j - x_i, s^2 = |d|^2 + eps^2) go to row roff[leaf] + k n_leaf + j of part (k:
+// the item's rank within its leaf); k_adj_p2p_combine adds the items of each leaf in
+// order: dL/dx_j += G m_j gx, dL/dm_j += G gm.
+constexpr int PS = 128;
+constexpr int LMAX = 64;  // leaf particles per pass (two per lane)
 template <class T>
 __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
-    int64_t ncell, const int32_t *__restrict__ cnchild, const int64_t *__restrict__ start,
-    const int64_t *__restrict__ end, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
+    const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
+    const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ ccom,
     const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
-    const float *__restrict__ xhl, const T *__restrict__ w, T eps2, double G, double *__restrict__ gout)
+    const float *__restrict__ xhl, const T *__restrict__ w, T eps2, const uint32_t *__restrict__ ioff,
+    const int64_t *__restrict__ roff, unsigned *__restrict__ work, T *__restrict__ part)
 {
-    __shared__ T ss[AW][64][4];
-    __shared__ T sw[AW][64][4];
-    __shared__ int32_t sid[AW][64];
+    __shared__ T ss[AW][PS][4];
+    __shared__ T sw[AW][PS][4];
+    __shared__ int32_t sid[AW][PS];
+    __shared__ int32_t sex[AW][33], sgb[AW][32];
     __shared__ double red[AW][32][4];
     const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    const int64_t nw = (int64_t)gridDim.x * AW;
-    for (int64_t L = (int64_t)blockIdx.x * AW + wi; L < ncell; L += nw) {
-        if (cnchild[L] != 0 || end[L] <= start[L]) continue;
+    const int64_t nitem = *nitem_p;
+    for (;;) {
+        unsigned I0 = 0;
+        if (lane == 0) I0 = atomicAdd(work, 1u);
+        const int64_t it = __shfl_sync(0xffffffffu, I0, 0);
+        if (it >= nitem) break;
+        const int64_t L = icell[it];
+        const int64_t ea = ia[it], eb = ib[it];
         const int64_t lb = cbegin[L];
+        T *pout = part + (roff[L] + (it - (int64_t)ioff[L]) * (int64_t)ccount[L]) * 4;
         const int lc = ccount[L];
         const double zx = ccom[3 * L + 0], zy = ccom[3 * L + 1], zz = ccom[3 * L + 2];
         const float zhi[3] = {(float)zx, (float)zy, (float)zz};
         const float zlo[3] = {(float)(zx - (double)zhi[0]), (float)(zy - (double)zhi[1]), (float)(zz - (double)zhi[2])};
-        for (int j0 = 0; j0 < lc; j0 += 32) {
-            const int nj = lc - j0 < 32 ? lc - j0 : 32;
-            const int nsplit = 32 / nj;
-            const int jj = (int)lane % nj, sj = (int)lane / nj;
+        for (int j0 = 0; j0 < lc; j0 += LMAX) {
+            const int nj = lc - j0 < LMAX ? lc - j0 : LMAX;
+            const bool two = nj > 32;
+            const int nsplit = two ? 1 : 32 / nj;
+            const int jj = two ? (int)lane : (int)lane % nj, sj = two ? 0 : (int)lane / nj;
             const bool active = sj < nsplit;
-            const int64_t sj_slot = lb + j0 + jj;
-            T xj[3], mj;
-            if constexpr (sizeof(T) == 4) {
-                const float4 v = prel[sj_slot];
-                xj[0] = v.x;
-                xj[1] = v.y;
-                xj[2] = v.z;
-                mj = v.w;
-            } else {
-                xj[0] = spos[3 * sj_slot + 0] - zx;
-                xj[1] = spos[3 * sj_slot + 1] - zy;
-                xj[2] = spos[3 * sj_slot + 2] - zz;
-                mj = smass[sj_slot];
+            bool val[2];
+            int64_t slot[2];
+            T xj[2][3], mj[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int jq = jj + 32 * q;
+                val[q] = active && jq < nj && (q == 0 || two);
+                slot[q] = lb + j0 + (val[q] ? jq : 0);
+                if constexpr (sizeof(T) == 4) {
+                    const float4 v = prel[slot[q]];
+                    xj[q][0] = v.x;
+                    xj[q][1] = v.y;
+                    xj[q][2] = v.z;
+                    mj[q] = v.w;
+                } else {
+                    xj[q][0] = spos[3 * slot[q] + 0] - zx;
+                    xj[q][1] = spos[3 * slot[q] + 1] - zy;
+                    xj[q][2] = spos[3 * slot[q] + 2] - zz;
+                    mj[q] = smass[slot[q]];
+                }
             }
-            T gx = 0, gy = 0, gz = 0, gm = 0;
-            int fill = 0;
-            auto flush = [&]() {
+            T gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0}, gm[2] = {0, 0};
+            auto flush = [&](int fill) {
                 __syncwarp();
                 if (active) {
                     for (int k = sj; k < fill; k += nsplit) {
-                        const T dx = xj[0] - ss[wi][k][0], dy = xj[1] - ss[wi][k][1], dz = xj[2] - ss[wi][k][2];
-                        const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-                        const bool ok = (r2 > T(0)) && (sid[wi][k] != (int32_t)sj_slot);
-                        const T ri = ok ? hot_rsqrt(r2) : T(0);
-                        const T r3 = ri * ri * ri;
+                        const T sx = ss[wi][k][0], sy = ss[wi][k][1], sz = ss[wi][k][2];
                         const T ux = sw[wi][k][0], uy = sw[wi][k][1], uz = sw[wi][k][2], vv = sw[wi][k][3];
-                        const T du = dx * ux + dy * uy + dz * uz;
-                        const T c1 = T(3) * r3 * ri * ri * du;
-                        gx += r3 * ux - c1 * dx + vv * r3 * dx;
-                        gy += r3 * uy - c1 * dy + vv * r3 * dy;
-                        gz += r3 * uz - c1 * dz + vv * r3 * dz;
-                        gm += du * r3 - vv * ri;
+                        const int32_t id = sid[wi][k];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            if (!val[q]) continue;
+                            const T dx = xj[q][0] - sx, dy = xj[q][1] - sy, dz = xj[q][2] - sz;
+                            const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+                            const bool ok = (r2 > T(0)) && (id != (int32_t)slot[q]);
+                            const T ri = ok ? hot_rsqrt(r2) : T(0);
+                            const T r3 = ri * ri * ri;
+                            const T du = dx * ux + dy * uy + dz * uz;
+                            const T c1 = T(3) * r3 * ri * ri * du;
+                            gx[q] += r3 * ux - c1 * dx + vv * r3 * dx;
+                            gy[q] += r3 * uy - c1 * dy + vv * r3 * dy;
+                            gz[q] += r3 * uz - c1 * dz + vv * r3 * dz;
+                            gm[q] += du * r3 - vv * ri;
+                        }
                     }
                 }
                 __syncwarp();
-                fill = 0;
             };
-            for (int64_t e = start[L]; e < end[L]; ++e) {
-                const int32_t gc = gcell[tval[e]];
-                const int64_t gb = cbegin[gc];
-                const int gn = ccount[gc];
-                for (int q0 = 0; q0 < gn; q0 += 32) {
-                    const int take = gn - q0 < 32 ? gn - q0 : 32;
-                    if (fill + take > 64) flush();
-                    if ((int)lane < take) {
-                        const int64_t s = gb + q0 + lane;
+            for (int64_t e0 = ea; e0 < eb; e0 += 32) {
+                const int ne = (int)(eb - e0 < 32 ? eb - e0 : 32);
+                int32_t gb = 0, gn = 0;
+                if ((int)lane < ne) {
+                    const int32_t gc = gcell[tval[e0 + lane]];
+                    gb = cbegin[gc];
+                    gn = ccount[gc];
+                }
+                const int incl = warp_incl_scan(gn);
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                sex[wi][lane + 1] = incl;
+                if (lane == 0) sex[wi][0] = 0;
+                sgb[wi][lane] = gb;
+                __syncwarp();
+                for (int t0 = 0; t0 < tot; t0 += PS) {
+                    const int take = tot - t0 < PS ? tot - t0 : PS;
+                    for (int u = lane; u < take; u += 32) {
+                        const int t = t0 + u;
+                        int lo = 0, hi = ne;  // entry with sex[lo] <= t < sex[lo + 1]
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sex[wi][mid] <= t)
+                                lo = mid;
+                            else
+                                hi = mid;
+                        }
+                        const int64_t s = (int64_t)sgb[wi][lo] + (t - sex[wi][lo]);
                         if constexpr (sizeof(T) == 4) {
-                            ss[wi][fill + lane][0] = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
-                            ss[wi][fill + lane][1] = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
-                            ss[wi][fill + lane][2] = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
+                            ss[wi][u][0] = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
+                            ss[wi][u][1] = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
+                            ss[wi][u][2] = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
                         } else {
-                            ss[wi][fill + lane][0] = spos[3 * s + 0] - zx;
-                            ss[wi][fill + lane][1] = spos[3 * s + 1] - zy;
-                            ss[wi][fill + lane][2] = spos[3 * s + 2] - zz;
+                            ss[wi][u][0] = spos[3 * s + 0] - zx;
+                            ss[wi][u][1] = spos[3 * s + 1] - zy;
+                            ss[wi][u][2] = spos[3 * s + 2] - zz;
                         }
 #pragma unroll
-                        for (int d = 0; d < 4; ++d) sw[wi][fill + lane][d] = w[4 * s + d];
-                        sid[wi][fill + lane] = (int32_t)s;
+                        for (int d = 0; d < 4; ++d) sw[wi][u][d] = w[4 * s + d];
+                        sid[wi][u] = (int32_t)s;
                     }
-                    fill += take;
+                    flush(take);
                 }
             }
-            if (fill > 0) flush();
-            __syncwarp();
-            if (active) {
-                red[wi][lane][0] = (double)gx;
-                red[wi][lane][1] = (double)gy;
-                red[wi][lane][2] = (double)gz;
-                red[wi][lane][3] = (double)gm;
+            if (two) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (val[q]) {
+                        T *o = pout + 4 * (int64_t)(slot[q] - lb);
+                        o[0] = gx[q];
+                        o[1] = gy[q];
+                        o[2] = gz[q];
+                        o[3] = gm[q];
+                    }
+            } else {
+                if (active) {
+                    red[wi][lane][0] = (double)gx[0];
+                    red[wi][lane][1] = (double)gy[0];
+                    red[wi][lane][2] = (double)gz[0];
+                    red[wi][lane][3] = (double)gm[0];
+                }
+                __syncwarp();
+                if (active && sj == 0) {
+                    double t[4] = {0, 0, 0, 0};
+                    for (int q = 0; q < nsplit; ++q)
+                        for (int d = 0; d < 4; ++d) t[d] += red[wi][jj + q * nj][d];
+                    T *o = pout + 4 * (int64_t)(slot[0] - lb);
+                    for (int d = 0; d < 4; ++d) o[d] = (T)t[d];
+                }
             }
             __syncwarp();
-            if (active && sj == 0) {
-                double t[4] = {0, 0, 0, 0};
-                for (int q = 0; q < nsplit; ++q)
-                    for (int d = 0; d < 4; ++d) t[d] += red[wi][jj + q * nj][d];
-                gout[4 * sj_slot + 0] = G * (double)mj * t[0];
-                gout[4 * sj_slot + 1] = G * (double)mj * t[1];
-                gout[4 * sj_slot + 2] = G * (double)mj * t[2];
-                gout[4 * sj_slot + 3] = G * t[3];
+        }
+    }
+}
+
+// dL/dx_j, dL/dm_j of the P2P source side: the partial sums of a leaf's items, added in
+// item order (float64).  One warp per leaf, lanes over its particles.
+template <class T>
+__global__ void __launch_bounds__(AW * 32) k_adj_p2p_combine(int64_t ncell, const int32_t *__restrict__ cnchild,
+                                                             const uint32_t *__restrict__ ioff,
+                                                             const int64_t *__restrict__ roff,
+                                                             const int32_t *__restrict__ cbegin,
+                                                             const int32_t *__restrict__ ccount,
+                                                             const double *__restrict__ smass, const T *__restrict__ part,
+                                                             double G, double *__restrict__ gout)
+{
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * AW;
+    for (int64_t L = (int64_t)blockIdx.x * AW + (threadIdx.x >> 5); L < ncell; L += nw) {
+        if (cnchild[L] != 0) continue;
+        const uint32_t i0 = ioff[L], i1 = ioff[L + 1];
+        if (i0 == i1) continue;
+        const int64_t lb = cbegin[L];
+        const int lc = ccount[L];
+        for (int j = lane; j < lc; j += 32) {
+            double t[4] = {0, 0, 0, 0};
+            for (uint32_t it = i0; it < i1; ++it) {
+                const T *o = part + (roff[L] + (int64_t)(it - i0) * lc + j) * 4;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) t[d] += (double)o[d];
             }
-            __syncwarp();
+            const double m = smass[lb + j];
+            gout[4 * (lb + j) + 0] = G * m * t[0];
+            gout[4 * (lb + j) + 1] = G * m * t[1];
+            gout[4 * (lb + j) + 2] = G * m * t[2];
+            gout[4 * (lb + j) + 3] = G * t[3];
         }
     }
 }
@@ -548,11 +650,40 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
         HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
         HOT_COUNT_LAUNCH();
         k_ranges<<<hot_blocks(np, 256), 256, 0, s>>>(c->tp_key.p, np, c->tp_start.p, c->tp_end.p);
+        // work items: a leaf and up to KG of the groups that list it
+        const int64_t max_items = np / KG + nc + 1;
+        // rows: sum over leaves of items x particles <= (source-particle visits) / KG + N
+        const int64_t max_rows = c->n_p2p_src / KG + N + 1;
+        HOT_CK(c->it_cell.ensure(max_items, s));
+        HOT_CK(c->it_a.ensure(max_items, s));
+        HOT_CK(c->it_b.ensure(max_items, s));
+        HOT_CK(c->adj_roff.ensure(nc + 1, s));
+        HOT_CK(c->adj_pp.ensure(sizeof(T) * 4 * (size_t)max_rows, s));
         HOT_COUNT_LAUNCH();
-        k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(nc, c->cnchild.p, c->tp_start.p, c->tp_end.p, c->tp_val.p,
-                                                        c->gcell.p, c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p,
-                                                        c->smass.p, c->prel.p, c->adj_xhl.p, w,
-                                                        (T)(c->prm.eps * c->prm.eps), c->prm.G, c->adj_gp2p.p);
+        k_item_rows<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->ccount.p, c->cnchild.p, nc,
+                                                        c->it_cnt.p + 0);
+        r = hot_scan_u32_to_i64(c->it_cnt.p, c->adj_roff.p, nc, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_COUNT_LAUNCH();
+        k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
+        r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_COUNT_LAUNCH();
+        k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
+                                                            c->it_a.p, c->it_b.p);
+        unsigned *pwork = (unsigned *)(c->sizes.p + 62);
+        HOT_CK(cudaMemsetAsync(pwork, 0, sizeof(unsigned), s));
+        T *pp = (T *)c->adj_pp.p;
+        HOT_COUNT_LAUNCH();
+        k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
+                                                        c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->ccom.p,
+                                                        c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
+                                                        (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
+                                                        pwork, pp);
+        HOT_COUNT_LAUNCH();
+        k_adj_p2p_combine<T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(
+            nc, c->cnchild.p, c->it_off.p, c->adj_roff.p, c->cbegin.p, c->ccount.p, c->smass.p, pp, c->prm.G,
+            c->adj_gp2p.p);
     }
 
     // leaves: transposed P2M and the final sums, original order

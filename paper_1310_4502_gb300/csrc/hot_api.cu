@@ -301,7 +301,7 @@ void hot_destroy(hot_ctx *c)
     c->adj_mbar.release(s); c->adj_cbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);
     c->tp_val.release(s); c->tp_val2.release(s); c->tp_start.release(s); c->tp_end.release(s);
     c->it_cnt.release(s); c->it_off.release(s); c->it_cell.release(s); c->it_a.release(s); c->it_b.release(s);
-    c->it_part.release(s);
+    c->it_part.release(s); c->adj_pp.release(s); c->adj_roff.release(s);
     cudaStreamSynchronize(s);
     if (c->d_status) cudaFree(c->d_status);
     for (int k = 0; k < ST_TIMING_EVENTS; ++k)

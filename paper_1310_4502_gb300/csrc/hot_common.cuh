@@ -124,6 +124,7 @@ struct hot_ctx {
     // lists
     double tol_lists = 0;
     int64_t n_m2p = 0, n_p2p = 0, n_pairs = 0, n_m2p_int = 0;
+    int64_t n_p2p_src = 0;  // P2P source-particle visits: sum over groups of listed leaf sizes
     DBuf<uint32_t> cnt_m2p, cnt_p2p;
     DBuf<int64_t> off_m2p, off_p2p;
     DBuf<int32_t> l_m2p, l_p2p;
@@ -141,6 +142,8 @@ struct hot_ctx {
     DBuf<int32_t> it_cell;
     DBuf<int64_t> it_a, it_b;
     DBuf<unsigned char> it_part;
+    DBuf<unsigned char> adj_pp;  // P2P source-side partial sums per work item and leaf particle
+    DBuf<int64_t> adj_roff;      // first partial row of every leaf
     int trav_cap = 2048;
     // per-group slot capacities of the one-pass traversal (grown from the counts seen)
     int64_t slot_capm = 2048, slot_capp = 512;

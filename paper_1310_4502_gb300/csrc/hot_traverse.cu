@@ -106,7 +106,8 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
 // MODE 2: one pass for both -- the entries go to fixed-capacity per-group slots (capm,
 // capp entries), the counts and totals as in MODE 0, and the largest counts to maxc[2];
 // a group whose lists do not fit sets *slot_over and keeps counting.  MODE 0 also
-// records the largest counts.
+// records the largest counts.  Both add the P2P source-particle visits (the particles
+// of every listed leaf, summed over groups) to maxc[3].
 template <int MODE>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 atomicAdd(&stats[1], (unsigned long long)(ns * p2p_parts));
                 atomicMax(&maxc[0], (unsigned long long)nm);
                 atomicMax(&maxc[1], (unsigned long long)np);
+                atomicAdd(&maxc[3], (unsigned long long)p2p_parts);  // source-particle visits
                 if (SLOTS && ((int64_t)nm > capm || (int64_t)np > capp)) atomicOr(slot_over, 1u);
             }
         }
@@ -288,11 +290,11 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_CK(c->slot_m2p.ensure((size_t)ng * capm, s));
         HOT_CK(c->slot_p2p.ensure((size_t)ng * capp, s));
     }
-    int64_t host[7];
+    int64_t host[8];
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
-        HOT_CK(cudaMemsetAsync(c->sizes.p + 58, 0, 3 * sizeof(int64_t), s));
+        HOT_CK(cudaMemsetAsync(c->sizes.p + 58, 0, 4 * sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
         if (slots)
             k_traverse<2><<<blocks, TW * 32, 0, s>>>(
@@ -313,7 +315,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_CK(cudaMemcpyAsync(host + 0, c->off_m2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaMemcpyAsync(host + 1, c->off_p2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaMemcpyAsync(host + 2, stats, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        HOT_CK(cudaMemcpyAsync(host + 4, c->sizes.p + 58, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 4, c->sizes.p + 58, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         HOT_CK(cudaStreamSynchronize(s));
         unsigned st = 0;
         HOT_CK(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -331,6 +333,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     c->n_p2p = host[1];
     c->n_m2p_int = host[2];
     c->n_pairs = host[3];
+    c->n_p2p_src = host[7];
     const bool fits = slots && (host[6] & 0xffffffffll) == 0;
     auto round_cap = [](int64_t n) { return ((n + n / 4 + 256) + 255) / 256 * 256; };
     c->slot_capm = round_cap(host[4]);

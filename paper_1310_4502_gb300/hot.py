@@ -106,7 +106,7 @@ def _need(t, shape_last=None):
     return t
 
 
-def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64, precision="mixed"):
+def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed"):
     prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
     return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec)
 
@@ -246,7 +246,7 @@ def key_frame_noalloc(pos, mass, frame, stream=None):
     return frame
 
 
-def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=16, group_max=64, precision="mixed",
+def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
                ctx: Hot | None = None, want_pot=True):
     """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N]."""
     import torch

@@ -50,10 +50,11 @@ def build(pos, mass, **kw):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_keys_sort_topology_groups_bit_exact(name):
+@pytest.mark.parametrize("leaf_max,group_max", [(64, 128), (16, 64), (1, 8)])
+def test_keys_sort_topology_groups_bit_exact(name, leaf_max, group_max):
     pos, mass, eps = CASES[name]
-    h, _, _ = build(pos, mass)
-    t = oracle.Tree(pos, mass, 16, 64)
+    h, _, _ = build(pos, mass, leaf_max=leaf_max, group_max=group_max)
+    t = oracle.Tree(pos, mass, leaf_max, group_max)
     lo, L = t.frame()
     fr = h.debug_get("FRAME")
     assert np.array_equal(fr[:3], lo) and fr[3] == L
@@ -97,7 +98,7 @@ def test_moments(p, prec, mtol):
     pos, mass, eps = CASES["plummer4096"]
     h, _, _ = build(pos, mass, p=p, precision=prec)
     h.compute_moments(p)
-    t = oracle.Tree(pos, mass, 16, 64)
+    t = oracle.Tree(pos, mass)  # the default leaf and group sizes on both sides
     t.moments(p)
     mo = t.get_moments()
     np.testing.assert_allclose(h.debug_get("CELL_MASS"), mo["mass"], rtol=1e-13)
@@ -147,7 +148,7 @@ def lists_match(h, t, cl):
 def test_lists_and_forces(name, p):
     pos, mass, eps = CASES[name]
     tol = 1e-4 if name != "ragged_dup" else 1e-5
-    t = oracle.Tree(pos, mass, 16, 64)
+    t = oracle.Tree(pos, mass)  # the default leaf and group sizes on both sides
     t.moments(p)
     t.traverse(tol)
     ra, rp = t.force(1.0, eps)

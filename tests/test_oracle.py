@@ -207,9 +207,10 @@ def test_tree_topology_brute_force(leaf_max):
     assert np.all(np.diff(cl["begin"]) >= 0)
 
 
-def test_groups_partition_and_extent():
+@pytest.mark.parametrize("leaf_max,group_max", [(16, 64), (64, 128)])
+def test_groups_partition_and_extent(leaf_max, group_max):
     w = W.make("plummer4096")
-    t = oracle.Tree(w.pos, w.mass)
+    t = oracle.Tree(w.pos, w.mass, leaf_max, group_max)
     cl = t.cells()
     g = t.groups()
     cov = np.zeros(w.n, dtype=int)
@@ -218,8 +219,8 @@ def test_groups_partition_and_extent():
     for c, cen, dm in zip(g["cell"], g["centre"], g["dmax"]):
         b, n = cl["begin"][c], cl["count"][c]
         cov[b:b + n] += 1
-        assert n <= 64 or cl["nchild"][c] == 0
-        assert cl["parent"][c] < 0 or cl["count"][cl["parent"][c]] > 64
+        assert n <= group_max or cl["nchild"][c] == 0
+        assert cl["parent"][c] < 0 or cl["count"][cl["parent"][c]] > group_max
         x = sp[b:b + n]
         np.testing.assert_allclose(cen, 0.5 * (x.min(0) + x.max(0)), rtol=0, atol=1e-15)
         assert abs(dm - np.linalg.norm(x - cen, axis=1).max()) <= 1e-15 * max(dm, 1e-300)
