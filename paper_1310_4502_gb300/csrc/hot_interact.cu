@@ -335,10 +335,13 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 }
 
 // cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
+// Occupancy: 4 CTAs per SM (128 registers) up to p = 4; the larger expansions of p >= 5
+// run faster with more registers and fewer CTAs (3 for the forces, 2 for the adjoint's
+// tangent evaluation), measured on the clustered 2^20 and lattice 128^3 workloads.
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
 // NS = 2: two sinks per lane (slices of 64 sinks).
 template <int P, class T, int NS, int MODE>
-__global__ void __launch_bounds__(IW * 32, 4) k_interact(
+__global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_interact(
     int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ spos,
     const double *__restrict__ smass, const float4 *__restrict__ prel, const double *__restrict__ ccom,
