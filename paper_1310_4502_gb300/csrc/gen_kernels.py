@@ -94,223 +94,136 @@ def g_terms(p):
     return out
 
 
-def _eval_stmts(p):
-    """Statements of one M2P interaction with symbolic coefficient references
-    ('@S,k,b@' for C_{b,k}, '@G,k,d,b@' for b_d C_{b,k}) and the flop count."""
-    L = []
-    fl = 0
-    L.append("rx *= is; ry *= is; rz *= is;")
-    fl += 3
-    L.append("const T u = rx * rx + ry * ry + rz * rz + e2;")
-    fl += 6
-    L.append("const T rho = hot_rsqrt(u);")
-    fl += 1
-    L.append("const T w = rho * rho;")
-    fl += 1
-    L.append(f"const T {mname((1,0,0))} = rx * w, {mname((0,1,0))} = ry * w, {mname((0,0,1))} = rz * w;")
-    fl += 3
-    have_s, have_g = set(), set()
-    for n in range(0, p + 1):
-        if n >= 2:
-            for a in midx(n)[ncomp(n - 1):]:
-                d = 0 if a[0] > 0 else (1 if a[1] > 0 else 2)
-                prev = list(a)
-                prev[d] -= 1
-                unit = [mname((1,0,0)), mname((0,1,0)), mname((0,0,1))][d]
-                L.append(f"const T {mname(a)} = {mname(tuple(prev))} * {unit};")
-                fl += 1
-        for k in range(p // 2 + 1):
-            if n + 2 * k > p:
-                continue
-            betas = midx(n)[ncomp(n - 1) if n > 0 else 0:]
-            nsplit = 2 if len(betas) > 6 else 1  # independent partial chains for ILP
-            for j, b in enumerate(betas):
-                acc = f"s{k}_{n}" if nsplit == 1 else f"s{k}_{n}_{j % nsplit}"
-                ref = f"@S,{k},{b[0]},{b[1]},{b[2]}@"
-                if acc not in have_s:
-                    if n == 0:
-                        L.append(f"T {acc} = {ref};")
-                    else:
-                        L.append(f"T {acc} = {ref} * {mname(b)};")
-                        fl += 1
-                    have_s.add(acc)
-                else:
-                    L.append(f"{acc} += {ref} * {mname(b)};")
-                    fl += 2
-            if nsplit == 2:
-                L.append(f"const T s{k}_{n} = s{k}_{n}_0 + s{k}_{n}_1;")
-                fl += 1
-        for k in range(p // 2 + 1):
-            if n + 1 + 2 * k > p:
-                continue
-            for b in midx(n + 1)[ncomp(n):]:
-                for d in range(3):
-                    if b[d] < 1:
-                        continue
-                    mono = list(b)
-                    mono[d] -= 1
-                    mono = tuple(mono)
-                    ref = f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
-                    acc = f"g{k}_{d}_{n}"  # one partial chain per monomial degree
-                    if acc not in have_g:
-                        if n == 0:
-                            L.append(f"T {acc} = {ref};")
-                        else:
-                            L.append(f"T {acc} = {ref} * {mname(mono)};")
-                            fl += 1
-                        have_g.add(acc)
-                    else:
-                        L.append(f"{acc} += {ref} * {mname(mono)};")
-                        fl += 2
-    K = p // 2
-    for k in range(K + 1):
-        terms = [f"s{k}_{n}" for n in range(p - 2 * k + 1)]
-        L.append(f"const T S{k} = " + " + ".join(terms) + ";")
-        fl += len(terms) - 1
-        tt = [f"T({1 + 2 * k + 2 * n}) * s{k}_{n}" if (1 + 2 * k + 2 * n) != 1 else f"s{k}_{n}"
-              for n in range(p - 2 * k + 1)]
-        L.append(f"const T Q{k} = " + " + ".join(tt) + ";")
-        fl += 2 * (len(tt) - 1)
-
-    def horner(names):
-        expr = names[-1]
-        for nm in reversed(names[:-1]):
-            expr = f"({nm} + w * {expr})"
-        return expr
-    L.append(f"const T S = {horner([f'S{k}' for k in range(K + 1)])};")
-    L.append(f"const T Q = {horner([f'Q{k}' for k in range(K + 1)])};")
-    fl += 4 * K
-    gk = {(k, d) for (k, d, _) in g_terms(p)}
-    for k in range(K + 1):
-        for d in range(3):
-            parts = [nm for nm in sorted(have_g) if nm.startswith(f"g{k}_{d}_")]
-            if parts:
-                L.append(f"const T g{k}_{d} = " + " + ".join(parts) + ";")
-                fl += len(parts) - 1
-    for d in range(3):
-        ks = [k for k in range(K + 1) if (k, d) in gk]
-        if ks:
-            names = [f"g{k}_{d}" if k in ks else "T(0)" for k in range(max(ks) + 1)]
-            L.append(f"const T G{d} = {horner(names)};")
-            fl += 2 * (len(names) - 1)
-        else:
-            L.append(f"const T G{d} = T(0);")
-    L.append("phi -= rho * S;")
-    fl += 2
-    L.append("const T rs = rho * is;")
-    fl += 1
-    for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
-        L.append(f"{an} += rs * (w * G{d} - {yn} * Q);")
-        fl += 5
-    return L, fl
+# Flops per M2P interaction used as the roofline convention (FMA = 2, rsqrt = 1): the
+# operation count of the traced expansion evaluated with explicit monomials (the first
+# form of this routine).  The Horner form below does the same mathematics with fewer
+# instructions; the convention stays fixed so that rates stay comparable.
+M2P_FLOP_CONVENTION = [32, 40, 82, 164, 307, 534, 874]
 
 
-def _tangent_stmts(p):
-    """Forward-mode derivative of the M2P statements along the input direction
-    (ux, uy, uz): the same primal statements interleaved with tangents 'd<name>'.
-    The tangent of the acceleration is (d a / d R) u, the Hessian of the expansion
-    applied to u, which is what the sink side of the adjoint needs."""
-    L, _ = _eval_stmts(p)
+def _horner_poly(X, n, ref, tangent):
+    """Statements for the polynomial X(y) = sum_{|g| <= n} c_g y^g, nested Horner in y_z,
+    then y_y, then y_x, so that every coefficient is consumed by one fused multiply-add
+    (chains over z are independent of each other).  With tangent, the derivative along
+    (dy100, dy010, dy001) is carried as dX."""
     out = []
-    tmp = [0]
-
-    def dn(nm):
-        nm = nm.strip()
-        if nm.startswith("T("):
-            return "T(0)"
-        return "d" + nm
-
-    def horner_tangent(dst, names):
-        # t = names[-1]; t = names[j] + w * t  (primal and tangent, step by step)
-        t, dt = names[-1], dn(names[-1])
-        for nm in reversed(names[:-1]):
-            tmp[0] += 1
-            k = tmp[0]
-            out.append(f"const T h{k} = {nm} + w * {t};")
-            out.append(f"const T dh{k} = {dn(nm)} + dw * {t} + w * {dt};")
-            t, dt = f"h{k}", f"dh{k}"
-        out.append(f"const T {dst} = {t};")
-        out.append(f"const T d{dst} = {dt};")
-
-    for st in L:
-        if st.startswith("rx *= is"):
-            out.append(st)
-            out.append("const T drx = ux * is, dry = uy * is, drz = uz * is;")
-        elif st.startswith("const T u ="):
-            out.append(st)
-            out.append("const T du = T(2) * (rx * drx + ry * dry + rz * drz);")
-        elif st.startswith("const T rho ="):
-            out.append(st)
-        elif st.startswith("const T w ="):
-            out.append(st)
-            out.append("const T drho = T(-0.5) * rho * w * du;")
-            out.append("const T dw = T(2) * rho * drho;")
-        elif st.startswith("const T y100 = rx * w"):
-            out.append(st)
-            out.append("const T dy100 = drx * w + rx * dw, dy010 = dry * w + ry * dw, dy001 = drz * w + rz * dw;")
-        elif st.startswith("const T y") and " * y" in st:
-            # monomial: const T yABC = yDEF * yGHI;
-            lhs, rhs = st[len("const T "):-1].split(" = ")
-            a, b = rhs.split(" * ")
-            out.append(st)
-            out.append(f"const T d{lhs} = d{a} * {b} + {a} * d{b};")
-        elif st.startswith("T ") and "@" in st:
-            # T acc = REF;  or  T acc = REF * mono;
-            lhs, rhs = st[2:-1].split(" = ")
-            out.append(st)
-            if " * " in rhs:
-                ref, mono = rhs.split(" * ")
-                out.append(f"T d{lhs} = {ref} * d{mono};")
-            else:
-                out.append(f"T d{lhs} = T(0);")
-        elif "+=" in st and "@" in st:
-            lhs, rhs = st[:-1].split(" += ")
-            ref, mono = rhs.split(" * ")
-            out.append(st)
-            out.append(f"d{lhs} += {ref} * d{mono};")
-        elif st.startswith("const T S =") or st.startswith("const T Q =") or \
-                (st.startswith("const T G") and "w *" in st):
-            lhs = st[len("const T "):].split(" = ")[0]
-            expr = st.split(" = ", 1)[1][:-1]
-            # parse the Horner form (n0 + w * (n1 + w * (...)))
-            names = [x.strip(" ()") for x in expr.replace("w *", "|").replace("+", "|").split("|")]
-            names = [x for x in names if x]
-            horner_tangent(lhs, names)
-        elif st.startswith("const T rs"):
-            out.append(st)
-            out.append("const T drs = drho * is;")
-        elif st.startswith("const T G") and st.endswith("T(0);"):
-            lhs = st[len("const T "):].split(" = ")[0]
-            out.append(st)
-            out.append(f"const T d{lhs} = T(0);")
-        elif st.startswith("const T "):
-            # linear combination: const T X = a + T(c) * b + ...;
-            lhs, rhs = st[len("const T "):-1].split(" = ")
-            terms = [t.strip() for t in rhs.split(" + ")]
-            dterms = []
-            for t in terms:
-                if " * " in t:
-                    c, nm = t.split(" * ")
-                    dterms.append(f"{c} * d{nm}")
-                else:
-                    dterms.append(dn(t))
-            out.append(st)
-            out.append(f"const T d{lhs} = " + " + ".join(dterms) + ";")
-        elif st.startswith("phi -="):
-            out.append(st)
-        elif st.startswith("ax +=") or st.startswith("ay +=") or st.startswith("az +="):
-            an = st[:2]
-            comp = {"ax": ("G0", "y100"), "ay": ("G1", "y010"), "az": ("G2", "y001")}[an]
-            Gd, yd = comp
-            out.append(st)
-            out.append(f"d{an} += drs * (w * {Gd} - {yd} * Q) + rs * (dw * {Gd} + w * d{Gd} - d{yd} * Q - {yd} * dQ);")
-        else:
-            raise ValueError("unhandled statement: " + st)
+    for i in range(n + 1):
+        for j in range(n - i + 1):
+            m = n - i - j
+            h = f"h{X}_{i}_{j}"
+            out.append(f"T {h} = {ref(i, j, m)};")
+            if tangent:
+                out.append(f"T d{h} = T(0);")
+            for l in range(m - 1, -1, -1):
+                if tangent:
+                    out.append(f"d{h} = dy001 * {h} + y001 * d{h};")
+                out.append(f"{h} = {ref(i, j, l)} + y001 * {h};")
+        t = f"t{X}_{i}"
+        out.append(f"T {t} = h{X}_{i}_{n - i};")
+        if tangent:
+            out.append(f"T d{t} = dh{X}_{i}_{n - i};")
+        for j in range(n - i - 1, -1, -1):
+            if tangent:
+                out.append(f"d{t} = dh{X}_{i}_{j} + dy010 * {t} + y010 * d{t};")
+            out.append(f"{t} = h{X}_{i}_{j} + y010 * {t};")
+    out.append(f"T {X} = t{X}_{n};")
+    if tangent:
+        out.append(f"T d{X} = dt{X}_{n};")
+    for i in range(n - 1, -1, -1):
+        if tangent:
+            out.append(f"d{X} = dt{X}_{i} + dy100 * {X} + y100 * d{X};")
+        out.append(f"{X} = t{X}_{i} + y100 * {X};")
     return out
 
 
+def _horner_w(dst, names, tangent):
+    """dst = names[0] + w (names[1] + w (...)), with its tangent when asked."""
+    out = []
+
+    def dn(nm):
+        return "T(0)" if nm.startswith("T(") else "d" + nm
+
+    t, dt = names[-1], dn(names[-1])
+    for q, nm in enumerate(reversed(names[:-1])):
+        v = f"w{dst}_{q}"
+        out.append(f"const T {v} = {nm} + w * {t};")
+        if tangent:
+            out.append(f"const T d{v} = {dn(nm)} + dw * {t} + w * {dt};")
+        t, dt = v, "d" + v
+    out.append(f"const T {dst} = {t};")
+    if tangent:
+        out.append(f"const T d{dst} = {dt};")
+    return out
+
+
+def _eval_stmts(p, tangent=False):
+    """Statements of one M2P interaction with symbolic coefficient references
+    ('@S,k,b@' for C_{b,k}, '@G,k,d,b@' for b_d C_{b,k}), and the flop convention.
+    Phi = rho sum_k w^k S_k(y); the gradient needs dS_k/dy_d (polynomials with the
+    coefficients b_d C_{b,k}) and Q = sum_k w^k sum_n (1+2k+2n) S_{k,n}, which by
+    Euler's theorem for the degree-n parts is sum_k w^k [(1+2k) S_k + 2 y . grad S_k].
+    With tangent, the forward-mode derivative along the input direction (ux, uy, uz) is
+    carried alongside: (d a / d R) u, the Hessian of the expansion applied to u."""
+    L = ["rx *= is; ry *= is; rz *= is;"]
+    if tangent:
+        L.append("const T drx = ux * is, dry = uy * is, drz = uz * is;")
+    L.append("const T u = rx * rx + ry * ry + rz * rz + e2;")
+    if tangent:
+        L.append("const T du = T(2) * (rx * drx + ry * dry + rz * drz);")
+    L.append("const T rho = hot_rsqrt(u);")
+    L.append("const T w = rho * rho;")
+    if tangent:
+        L.append("const T drho = T(-0.5) * rho * w * du;")
+        L.append("const T dw = T(2) * rho * drho;")
+    L.append(f"const T {mname((1,0,0))} = rx * w, {mname((0,1,0))} = ry * w, {mname((0,0,1))} = rz * w;")
+    if tangent:
+        L.append("const T dy100 = drx * w + rx * dw, dy010 = dry * w + ry * dw, dy001 = drz * w + rz * dw;")
+    K = p // 2
+    for k in range(K + 1):
+        n = p - 2 * k
+        L += _horner_poly(f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@", tangent)
+        if n >= 1:
+            for d in range(3):
+                def gref(i, j, l, d=d, k=k):
+                    b = [i, j, l]
+                    b[d] += 1
+                    return f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
+                L += _horner_poly(f"G{k}_{d}", n - 1, gref, tangent)
+            L.append(f"const T yg{k} = y100 * G{k}_0 + y010 * G{k}_1 + y001 * G{k}_2;")
+            if tangent:
+                L.append(f"const T dyg{k} = dy100 * G{k}_0 + y100 * dG{k}_0 + dy010 * G{k}_1 + y010 * dG{k}_1 + "
+                         f"dy001 * G{k}_2 + y001 * dG{k}_2;")
+            L.append(f"const T Q{k} = T({1 + 2 * k}) * S{k} + T(2) * yg{k};")
+            if tangent:
+                L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k} + T(2) * dyg{k};")
+        else:
+            L.append(f"const T Q{k} = T({1 + 2 * k}) * S{k};")
+            if tangent:
+                L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k};")
+    L += _horner_w("S", [f"S{k}" for k in range(K + 1)], tangent)
+    L += _horner_w("Q", [f"Q{k}" for k in range(K + 1)], tangent)
+    for d in range(3):
+        ks = [k for k in range(K + 1) if p - 2 * k >= 1]
+        if ks:
+            L += _horner_w(f"Gs{d}", [f"G{k}_{d}" for k in range(max(ks) + 1)], tangent)
+        else:
+            L.append(f"const T Gs{d} = T(0);")
+            if tangent:
+                L.append(f"const T dGs{d} = T(0);")
+    L.append("phi -= rho * S;")
+    L.append("const T rs = rho * is;")
+    if tangent:
+        L.append("const T drs = drho * is;")
+    for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
+        L.append(f"{an} += rs * (w * Gs{d} - {yn} * Q);")
+        if tangent:
+            L.append(f"d{an} += drs * (w * Gs{d} - {yn} * Q) + rs * (dw * Gs{d} + w * dGs{d} - d{yn} * Q - "
+                     f"{yn} * dQ);")
+    return L, M2P_FLOP_CONVENTION[p]
+
+
 def gen_tangent(p):
-    L = _tangent_stmts(p)
+    L, _ = _eval_stmts(p, tangent=True)
     slot = layout(p)
     out = []
     for T, VEC, VW, suf in (("float", "float4", 4, "f32"), ("double", "double2", 2, "f64")):
