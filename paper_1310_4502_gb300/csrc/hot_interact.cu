@@ -18,6 +18,8 @@
 // and x_i - g (rounded to float32 afterwards).  Each lane sums a chunk in plain float32
 // and adds the chunk total into a compensated (Kahan) pair; pairs are combined in
 // float64.  T = double runs the same code in float64.
+#include <type_traits>
+
 #include "hot_common.cuh"
 #include "generated.cuh"
 
@@ -126,6 +128,7 @@ struct Group {
     T ghi[3], glo[3];  // group centre as a T pair (hi = rounded, lo = remainder)
     int64_t m0, m1;  // M2P list range
     int64_t p0, p1;  // P2P list range
+    int32_t own0, own1;  // pre-order range of the group's cell: its own leaves
 };
 
 // Offset z_c - g in T from the hi/lo pairs of the cell (record header slots 2..7) and of
@@ -237,21 +240,32 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
     constexpr int RL = Cfg<P, T>::RL;
     const unsigned lane = lane_id();
     int fill = 0;
-    auto flush = [&]() {
+    // A sink can meet itself, or a source at zero separation, only in a batch holding one
+    // of the group's own leaves or when eps = 0; other batches take the loop without the
+    // per-pair tests.
+    auto flush = [&](bool checked) {
         __syncwarp();
         if (active) {
             T ph[NS], ax[NS], ay[NS], az[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = T(0);
+            auto sweep = [&](auto ck) {
+                constexpr bool CK = decltype(ck)::value;
+#pragma unroll 2
             for (int k = sj; k < fill; k += nsplit) {
                 const T sx = sm.src[k][0], sy = sm.src[k][1], sz = sm.src[k][2], m = sm.src[k][3];
-                const int32_t id = sm.sidx[k];
+                const int32_t id = CK ? sm.sidx[k] : 0;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     const T dx = sx - x[s][0], dy = sy - x[s][1], dz = sz - x[s][2];
                     const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-                    const bool ok = (r2 > T(0)) && (id != self[s]);
-                    const T rinv = ok ? hot_rsqrt(r2) : T(0);
+                    T rinv;
+                    if constexpr (CK) {
+                        const bool ok = (r2 > T(0)) && (id != self[s]);
+                        rinv = ok ? hot_rsqrt(r2) : T(0);
+                    } else {
+                        rinv = hot_rsqrt(r2);
+                    }
                     const T mr = m * rinv;
                     const T mr3 = mr * rinv * rinv;
                     if constexpr (MODE == 0) {
@@ -270,6 +284,11 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     }
                 }
             }
+            };
+            if (checked)
+                sweep(std::true_type{});
+            else
+                sweep(std::false_type{});
 #pragma unroll
             for (int s = 0; s < NS; ++s) acc[s].add(Gt * ax[s], Gt * ay[s], Gt * az[s], Gt * ph[s]);
         }
@@ -283,8 +302,10 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         const int ne = (int)(G.p1 - e0 < 32 ? G.p1 - e0 : 32);
         int32_t lb = 0, lc = 0;
         T ox = T(0), oy = T(0), oz = T(0);
+        bool own = false;
         if ((int)lane < ne) {
             const int32_t leaf = l_p2p[e0 + lane];
+            own = leaf >= G.own0 && leaf < G.own1;
             lb = cbegin[leaf];
             lc = ccount[leaf];
             T h[8];
@@ -292,6 +313,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             for (int q = 0; q < 8; ++q) h[q] = rec[(int64_t)leaf * RL + q];
             centre_offset(h, G, ox, oy, oz);
         }
+        const bool checked = __any_sync(0xffffffffu, own) || !(eps2 > T(0));
         const int incl = warp_incl_scan(lc);
         const int tot = __shfl_sync(0xffffffffu, incl, 31);
         sm.lex[lane + 1] = incl;
@@ -329,7 +351,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 sm.sidx[u] = (int32_t)s;
             }
             fill = take;
-            flush();
+            flush(checked);
         }
     }
 }
@@ -343,9 +365,9 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 template <int P, class T, int NS, int MODE>
 __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_interact(
     int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
-    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ spos,
-    const double *__restrict__ smass, const float4 *__restrict__ prel, const double *__restrict__ ccom,
-    const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const int32_t *__restrict__ cend,
+    const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
+    const double *__restrict__ ccom, const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
     T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
     const T *__restrict__ wsink, double *__restrict__ gsink, unsigned *__restrict__ status)
@@ -390,6 +412,8 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
         Gr.m1 = off_m2p[g + 1];
         Gr.p0 = off_p2p[g];
         Gr.p1 = off_p2p[g + 1];
+        Gr.own0 = gc;
+        Gr.own1 = cend[gc];
         for (int s0 = 0; s0 < Gr.n; s0 += SL) {
             const int rem = Gr.n - s0;
             int ns, nsplit, si, sj;
@@ -488,7 +512,8 @@ int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *po
     const int blocks = c->nsm * occ;
     const T eps2 = (T)(c->prm.eps * c->prm.eps);
     HOT_COUNT_LAUNCH();
-    kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->spos.p,
+    kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->cend.p,
+                                       c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
                                        c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot, wsink, gsink,
                                        c->d_status);
@@ -501,6 +526,13 @@ int forces_p(hot_ctx *c, double *acc, double *pot)
     unsigned *work = (unsigned *)(c->sizes.p + 56);
     if (c->prm.precision == HOT_FP64)
         return launch_interact<P, double, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
+    if constexpr (P >= 5) {
+        // large expansions: groups of more than 32 sinks run two sinks per lane, so that
+        // every coefficient read from shared memory feeds two independent evaluations
+        int r = launch_interact<P, float, 1, 0>(c, 1, work, acc, pot, nullptr, nullptr);
+        if (r) return r;
+        return launch_interact<P, float, 2, 0>(c, 2, work, acc, pot, nullptr, nullptr);
+    }
     return launch_interact<P, float, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
 }
 

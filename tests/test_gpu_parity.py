@@ -27,6 +27,7 @@ def cases():
     out = {}
     w = W.make("plummer4096")
     out["plummer4096"] = (w.pos, w.mass, w.eps)
+    out["plummer_eps0"] = (w.pos, w.mass, 0.0)  # unsoftened: every pair takes the tested path
     n = 1 << 15
     out["clustered32k"] = (W.clustered(n, seed=3), np.full(n, 1.0 / n), 1e-4)
     n = 20011  # ragged: not a multiple of any tile
@@ -143,7 +144,7 @@ def lists_match(h, t, cl):
     return bad
 
 
-@pytest.mark.parametrize("name", ["plummer4096", "clustered32k", "ragged_dup", "tiny7", "one"])
+@pytest.mark.parametrize("name", ["plummer4096", "plummer_eps0", "clustered32k", "ragged_dup", "tiny7", "one"])
 @pytest.mark.parametrize("p", [1, 4, 6])
 def test_lists_and_forces(name, p):
     pos, mass, eps = CASES[name]
