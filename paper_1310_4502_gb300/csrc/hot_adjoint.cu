@@ -16,6 +16,8 @@
 //   source, P2P  : the pair terms seen from the source particle, over the transposed
 //                  (leaf -> groups) lists, one warp per leaf
 // Every sum has a fixed order: results are reproducible run to run.
+#include <type_traits>
+
 #include "hot_common.cuh"
 #include "generated.cuh"
 
@@ -291,9 +293,10 @@ template <class T>
 __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
     const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
     const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
-    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ ccom,
-    const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
-    const float *__restrict__ xhl, const T *__restrict__ w, T eps2, const uint32_t *__restrict__ ioff,
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const int32_t *__restrict__ cend,
+    const double *__restrict__ ccom, const double *__restrict__ spos, const double *__restrict__ smass,
+    const float4 *__restrict__ prel, const float *__restrict__ xhl, const T *__restrict__ w, T eps2,
+    const uint32_t *__restrict__ ioff,
     const int64_t *__restrict__ roff, unsigned *__restrict__ work, T *__restrict__ part)
 {
     __shared__ T ss[AW][PS][4];
@@ -345,20 +348,30 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                 }
             }
             T gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0}, gm[2] = {0, 0};
-            auto flush = [&](int fill) {
+            // the self pair, or a zero separation, can only occur in a batch holding the group
+            // whose cell contains this leaf, or when eps = 0: other batches skip the tests
+            auto flush = [&](int fill, bool checked) {
                 __syncwarp();
                 if (active) {
+                    auto sweep = [&](auto ck) {
+                        constexpr bool CK = decltype(ck)::value;
+#pragma unroll 2
                     for (int k = sj; k < fill; k += nsplit) {
                         const T sx = ss[wi][k][0], sy = ss[wi][k][1], sz = ss[wi][k][2];
                         const T ux = sw[wi][k][0], uy = sw[wi][k][1], uz = sw[wi][k][2], vv = sw[wi][k][3];
-                        const int32_t id = sid[wi][k];
+                        const int32_t id = CK ? sid[wi][k] : 0;
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
                             if (!val[q]) continue;
                             const T dx = xj[q][0] - sx, dy = xj[q][1] - sy, dz = xj[q][2] - sz;
                             const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-                            const bool ok = (r2 > T(0)) && (id != (int32_t)slot[q]);
-                            const T ri = ok ? hot_rsqrt(r2) : T(0);
+                            T ri;
+                            if constexpr (CK) {
+                                const bool ok = (r2 > T(0)) && (id != (int32_t)slot[q]);
+                                ri = ok ? hot_rsqrt(r2) : T(0);
+                            } else {
+                                ri = hot_rsqrt(r2);
+                            }
                             const T r3 = ri * ri * ri;
                             const T du = dx * ux + dy * uy + dz * uz;
                             const T c1 = T(3) * r3 * ri * ri * du;
@@ -368,17 +381,25 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                             gm[q] += du * r3 - vv * ri;
                         }
                     }
+                    };
+                    if (checked)
+                        sweep(std::true_type{});
+                    else
+                        sweep(std::false_type{});
                 }
                 __syncwarp();
             };
             for (int64_t e0 = ea; e0 < eb; e0 += 32) {
                 const int ne = (int)(eb - e0 < 32 ? eb - e0 : 32);
                 int32_t gb = 0, gn = 0;
+                bool own = false;
                 if ((int)lane < ne) {
                     const int32_t gc = gcell[tval[e0 + lane]];
                     gb = cbegin[gc];
                     gn = ccount[gc];
+                    own = L >= gc && L < cend[gc];
                 }
+                const bool checked = __any_sync(0xffffffffu, own) || !(eps2 > T(0));
                 const int incl = warp_incl_scan(gn);
                 const int tot = __shfl_sync(0xffffffffu, incl, 31);
                 sex[wi][lane + 1] = incl;
@@ -411,7 +432,7 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                         for (int d = 0; d < 4; ++d) sw[wi][u][d] = w[4 * s + d];
                         sid[wi][u] = (int32_t)s;
                     }
-                    flush(take);
+                    flush(take, checked);
                 }
             }
             if (two) {
@@ -676,8 +697,8 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
         T *pp = (T *)c->adj_pp.p;
         HOT_COUNT_LAUNCH();
         k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
-                                                        c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->ccom.p,
-                                                        c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
+                                                        c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
+                                                        c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
                                                         (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
                                                         pwork, pp);
         HOT_COUNT_LAUNCH();

@@ -71,6 +71,7 @@ def fd_reference(pos, mass, w, v, p, tol, eps, ks, h=1e-6):
 
 CASES = {
     "plummer4096": lambda: (W.make("plummer4096").pos, W.make("plummer4096").mass, 0.01),
+    "plummer_eps0": lambda: (W.make("plummer4096").pos, W.make("plummer4096").mass, 0.0),
     "clustered16k": lambda: (W.clustered(1 << 14, seed=4), np.full(1 << 14, 1.0 / (1 << 14)), 1e-3),
 }
 
