@@ -148,6 +148,8 @@ struct hot_ctx {
     // per-group slot capacities of the one-pass traversal (grown from the counts seen)
     int64_t slot_capm = 2048, slot_capp = 512;
     DBuf<int32_t> slot_m2p, slot_p2p;
+    DBuf<uint64_t> gkey, gkey2;      // per-group interaction cost keys (largest first)
+    DBuf<uint32_t> gorder, gorder2;  // groups in the order the interaction kernels take them
     DBuf<int64_t> pairs_per_group;
 
     // status

@@ -191,9 +191,13 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         if ((int)lane < ne) {
             T ox, oy, oz;
             centre_offset(&sm.rec[b][lane][0], G, ox, oy, oz);
-            sm.off[b][lane][0] = ox;
-            sm.off[b][lane][1] = oy;
-            sm.off[b][lane][2] = oz;
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(&sm.off[b][lane][0]) = make_float4(ox, oy, oz, 0.f);
+            } else {
+                sm.off[b][lane][0] = ox;
+                sm.off[b][lane][1] = oy;
+                sm.off[b][lane][2] = oz;
+            }
         }
         __syncwarp();
         if (active) {
@@ -338,10 +342,10 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 const int64_t s = (int64_t)sm.lbeg[lo] + (t - sm.lex[lo]);
                 if constexpr (sizeof(T) == 4) {
                     const float4 v = prel[s];
-                    sm.src[u][0] = v.x + sm.loff[lo][0];
-                    sm.src[u][1] = v.y + sm.loff[lo][1];
-                    sm.src[u][2] = v.z + sm.loff[lo][2];
-                    sm.src[u][3] = v.w;
+                    // one 16-byte store per source (scalar stores at a 16-byte lane stride
+                    // would meet four lanes in each bank)
+                    *reinterpret_cast<float4 *>(&sm.src[u][0]) =
+                        make_float4(v.x + sm.loff[lo][0], v.y + sm.loff[lo][1], v.z + sm.loff[lo][2], v.w);
                 } else {
                     sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx);
                     sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy);
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
     const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
     const double *__restrict__ ccom, const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
-    T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
+    const uint32_t *__restrict__ gorder, T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
     const T *__restrict__ wsink, double *__restrict__ gsink, unsigned *__restrict__ status)
 {
     using S = Smem<P, T>;
@@ -390,8 +394,9 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
     for (;;) {
         unsigned g0 = 0;
         if (lane == 0) g0 = atomicAdd(work, 1u);
-        const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
-        if (g >= ngroup) break;
+        const int64_t gi = __shfl_sync(0xffffffffu, g0, 0);
+        if (gi >= ngroup) break;
+        const int64_t g = gorder[gi];  // largest interaction cost first
         const int32_t gc = gcell[g];
         Group<T> Gr;
         Gr.n = ccount[gc];
@@ -515,7 +520,8 @@ int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *po
     kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->cend.p,
                                        c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
-                                       c->l_p2p.p, c->idx.p, eps2, c->prm.G, work, acc, pot, wsink, gsink,
+                                       c->l_p2p.p, c->idx.p, c->gorder.p, eps2, c->prm.G, work, acc, pot, wsink,
+                                       gsink,
                                        c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }

@@ -107,7 +107,7 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
 // capp entries), the counts and totals as in MODE 0, and the largest counts to maxc[2];
 // a group whose lists do not fit sets *slot_over and keeps counting.  MODE 0 also
 // records the largest counts.  Both add the P2P source-particle visits (the particles
-// of every listed leaf, summed over groups) to maxc[3].
+// of every listed leaf, summed over groups) to maxc[3] and write each group's cost key.
 template <int MODE>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
     int64_t capm, int64_t capp, unsigned long long *__restrict__ maxc, unsigned *__restrict__ slot_over,
-    unsigned *__restrict__ status)
+    uint64_t *__restrict__ gkey, unsigned *__restrict__ status)
 {
     constexpr bool FILL = MODE == 1, SLOTS = MODE == 2;
     const unsigned lane = lane_id();
@@ -238,11 +238,21 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 atomicMax(&maxc[0], (unsigned long long)nm);
                 atomicMax(&maxc[1], (unsigned long long)np);
                 atomicAdd(&maxc[3], (unsigned long long)p2p_parts);  // source-particle visits
+                // interaction cost of the group (one M2P evaluation ~ 10 P2P source visits per
+                // 32-sink slice), as an ascending sort key for largest-first processing
+                const uint64_t cost = (ns + 31) / 32 * (10ull * nm + p2p_parts);
+                gkey[g] = 0xffffffffull - (cost < 0xffffffffull ? cost : 0xffffffffull);
                 if (SLOTS && ((int64_t)nm > capm || (int64_t)np > capp)) atomicOr(slot_over, 1u);
             }
         }
         __syncwarp();
     }
+}
+
+__global__ void k_iota(uint32_t *__restrict__ v, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
 }
 
 // Copy every group's slot entries to its CSR range (one warp per group, in order).
@@ -279,6 +289,10 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     unsigned long long *maxc = (unsigned long long *)(c->sizes.p + 58);
     unsigned *slot_over = (unsigned *)(c->sizes.p + 60);
     HOT_CK(c->tcell.ensure(c->ncell, s));
+    HOT_CK(c->gkey.ensure(ng + 1, s));
+    HOT_CK(c->gkey2.ensure(ng + 1, s));
+    HOT_CK(c->gorder.ensure(ng + 1, s));
+    HOT_CK(c->gorder2.ensure(ng + 1, s));
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
                                                             c->p_mom, c->prm.G, tol, c->tcell.p);
@@ -301,13 +315,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
                 c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
-                capm, capp, maxc, slot_over, c->d_status);
+                capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
             k_traverse<0><<<blocks, TW * 32, 0, s>>>(
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
                 c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
-                slot_over, c->d_status);
+                slot_over, c->gkey.p, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
         if (r) return r;
         r = hot_scan_u32_to_i64(c->cnt_p2p.p, c->off_p2p.p, ng, c->scan_tmp.p, s);
@@ -352,8 +366,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
             c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
-            slot_over, c->d_status);
+            slot_over, nullptr, c->d_status);
     }
+    // group order for the interactions: largest cost first (stable, so ties keep index order)
+    HOT_COUNT_LAUNCH();
+    k_iota<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, ng);
+    int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 32);
+    if (rs) return rs;
     hot_toc(c, 3);
     if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     c->tol_lists = tol;
