@@ -181,7 +181,9 @@ def _eval_stmts(p, tangent=False):
     K = p // 2
     for k in range(K + 1):
         n = p - 2 * k
-        L += _horner_poly(f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@", tangent)
+        # the tangent of S_k is grad S_k . dy, and grad S_k = (G_k0, G_k1, G_k2) is evaluated
+        # below, so S_k itself needs no tangent chain
+        L += _horner_poly(f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@", False)
         if n >= 1:
             for d in range(3):
                 def gref(i, j, l, d=d, k=k):
@@ -189,6 +191,8 @@ def _eval_stmts(p, tangent=False):
                     b[d] += 1
                     return f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
                 L += _horner_poly(f"G{k}_{d}", n - 1, gref, tangent)
+            if tangent:
+                L.append(f"const T dS{k} = G{k}_0 * dy100 + G{k}_1 * dy010 + G{k}_2 * dy001;")
             L.append(f"const T yg{k} = y100 * G{k}_0 + y010 * G{k}_1 + y001 * G{k}_2;")
             if tangent:
                 L.append(f"const T dyg{k} = dy100 * G{k}_0 + y100 * dG{k}_0 + dy010 * G{k}_1 + y010 * dG{k}_1 + "
@@ -197,6 +201,8 @@ def _eval_stmts(p, tangent=False):
             if tangent:
                 L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k} + T(2) * dyg{k};")
         else:
+            if tangent:
+                L.append(f"const T dS{k} = T(0);")
             L.append(f"const T Q{k} = T({1 + 2 * k}) * S{k};")
             if tangent:
                 L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k};")

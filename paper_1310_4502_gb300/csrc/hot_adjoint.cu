@@ -114,15 +114,17 @@ __global__ void k_item_rows(const int64_t *__restrict__ start, const int64_t *__
     rows[c] = (cnchild[c] != 0 || ne <= 0) ? 0u : (uint32_t)(((ne + KG - 1) / KG) * (int64_t)ccount[c]);
 }
 
-// Source side of M2P: one warp per item (one cell, up to KG groups that list it); the
-// sinks of all the item's groups are spread over the lanes.  Each lane accumulates the
+// Source side of M2P: one warp per item (one cell, up to KG groups that list it), taken
+// from a work counter in the given order (largest first); the sinks of all the item's
+// groups are spread over the lanes.  Each lane accumulates the
 // coefficient adjoints in registers; the warp sum goes to part[item].
 template <int P, class T>
 __global__ void __launch_bounds__(AW * 32) k_adj_src(
     const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
     const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const T *__restrict__ rec,
-    const T *__restrict__ w, const float *__restrict__ xhl, const double *__restrict__ spos, T *__restrict__ part)
+    const T *__restrict__ w, const float *__restrict__ xhl, const double *__restrict__ spos,
+    const uint32_t *__restrict__ iorder, unsigned *__restrict__ work, T *__restrict__ part)
 {
     constexpr int RL = ACfg<P, T>::RL;
     constexpr int NS = ACfg<P, T>::NS;
@@ -130,8 +132,12 @@ __global__ void __launch_bounds__(AW * 32) k_adj_src(
     const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t nitem = *nitem_p;
-    const int64_t nw = (int64_t)gridDim.x * AW;
-    for (int64_t it = (int64_t)blockIdx.x * AW + wi; it < nitem; it += nw) {
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(work, 1u);
+        const int64_t ii = __shfl_sync(0xffffffffu, i0, 0);
+        if (ii >= nitem) break;
+        const int64_t it = iorder ? (int64_t)iorder[ii] : ii;
         const int32_t c = icell[it];
         const int64_t a = ia[it], b = ib[it];
         const int ng = (int)(b - a);
@@ -637,10 +643,12 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
         k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
                                                             c->it_a.p, c->it_b.p);
         T *part = (T *)c->it_part.p;
+        unsigned *swork = (unsigned *)(c->sizes.p + 63);
+        HOT_CK(cudaMemsetAsync(swork, 0, sizeof(unsigned), s));
         HOT_COUNT_LAUNCH();
         k_adj_src<P, T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
                                                       c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, rec, w,
-                                                      c->adj_xhl.p, c->spos.p, part);
+                                                      c->adj_xhl.p, c->spos.p, nullptr, swork, part);
         HOT_COUNT_LAUNCH();
         k_adj_cells<P, T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(nc, c->it_off.p, part, rec,
                                                                               c->prm.G, c->adj_mbar.p);

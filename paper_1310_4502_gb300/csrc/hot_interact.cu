@@ -253,6 +253,8 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             T ph[NS], ax[NS], ay[NS], az[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = T(0);
+            // adjoint: the sink's u is the same for all its sources, so sum_j m/s^3 u is
+            // carried as u sum_j m/s^3 (ph holds that sum in this mode)
             auto sweep = [&](auto ck) {
                 constexpr bool CK = decltype(ck)::value;
 #pragma unroll 2
@@ -279,12 +281,13 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                         ph[s] -= mr;
                     } else {
                         // d/dx_i (u.a_i + v phi_i) = -G m [u/s^3 - 3 d (d.u)/s^5 + v d/s^3], d = x_j - x_i
+                        //   = -G [u sum_j m/s^3 + sum_j (v m/s^3 - 3 m (d.u)/s^5) d]
                         const T du = dx * wt[s][0] + dy * wt[s][1] + dz * wt[s][2];
-                        const T c1 = T(3) * mr3 * rinv * rinv * du;
-                        const T c2 = mr3 * wt[s][3];
-                        ax[s] -= mr3 * wt[s][0] - c1 * dx + c2 * dx;
-                        ay[s] -= mr3 * wt[s][1] - c1 * dy + c2 * dy;
-                        az[s] -= mr3 * wt[s][2] - c1 * dz + c2 * dz;
+                        const T cc = mr3 * wt[s][3] - T(3) * mr3 * rinv * rinv * du;
+                        ph[s] += mr3;
+                        ax[s] += cc * dx;
+                        ay[s] += cc * dy;
+                        az[s] += cc * dz;
                     }
                 }
             }
@@ -294,7 +297,14 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             else
                 sweep(std::false_type{});
 #pragma unroll
-            for (int s = 0; s < NS; ++s) acc[s].add(Gt * ax[s], Gt * ay[s], Gt * az[s], Gt * ph[s]);
+            for (int s = 0; s < NS; ++s) {
+                if constexpr (MODE == 0) {
+                    acc[s].add(Gt * ax[s], Gt * ay[s], Gt * az[s], Gt * ph[s]);
+                } else {
+                    acc[s].add(-Gt * (wt[s][0] * ph[s] + ax[s]), -Gt * (wt[s][1] * ph[s] + ay[s]),
+                               -Gt * (wt[s][2] * ph[s] + az[s]), T(0));
+                }
+            }
         }
         __syncwarp();
         fill = 0;
