@@ -456,8 +456,8 @@ FLOPS_M2P = _flops_table()
 # with the source hash it was taken on; reported only while the kernel is unchanged.
 # (p, hash): dram__bytes_read.sum + dram__bytes_write.sum of the timed step's force
 # launch, one-pass capture of "python bench.py --steps 1 --warmup 1 --no-cpu --no-extras
-# --no-leapfrog" (clustered 2^20, p = 4): 314.51 MB read + 54.31 MB written.
-TRAFFIC = {(4, "f214b8dd630f90bb"): 368.82e6}
+# --no-leapfrog" (clustered 2^20, p = 4): 417.62 MB read + 67.09 MB written.
+TRAFFIC = {(4, "4777edfafb412068"): 484.71e6}
 
 
 def _kernel_hash():
