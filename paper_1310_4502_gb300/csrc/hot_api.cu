@@ -296,7 +296,7 @@ void hot_destroy(hot_ctx *c)
     c->item_cell.release(s); c->item_part.release(s); c->rec32.release(s); c->rec64.release(s); c->prel.release(s);
     c->cnt_m2p.release(s); c->cnt_p2p.release(s); c->off_m2p.release(s); c->off_p2p.release(s);
     c->l_m2p.release(s); c->l_p2p.release(s); c->trav_scratch.release(s); c->pairs_per_group.release(s);
-    c->tcell.release(s); c->slot_m2p.release(s); c->slot_p2p.release(s);
+    c->tcell.release(s); c->tcellf.release(s); c->slot_m2p.release(s); c->slot_p2p.release(s);
     c->gkey.release(s); c->gkey2.release(s); c->gorder.release(s); c->gorder2.release(s);
     c->adj_w.release(s); c->adj_xhl.release(s); c->adj_gsink.release(s); c->adj_gp2p.release(s);
     c->adj_mbar.release(s); c->adj_cbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);

@@ -61,20 +61,21 @@ __global__ void k_bbox_part(const double *__restrict__ pos, const double *__rest
     }
 }
 
-// frame = lo[3], L, 2^21/L
+// frame = lo[3], L, 2^21/L.  One warp: lanes take the block partials in turn, then a warp
+// reduction (min and max are exact, so the order does not matter).
 __global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ frame)
 {
-    if (threadIdx.x != 0) return;
-    double lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = part[d];
-        hi[d] = part[3 + d];
-    }
-    for (int b = 1; b < nb; ++b)
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nb; b += 32)
         for (int d = 0; d < 3; ++d) {
             lo[d] = fmin(lo[d], part[6 * b + d]);
             hi[d] = fmax(hi[d], part[6 * b + 3 + d]);
         }
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = warp_min(lo[d]);
+        hi[d] = warp_max(hi[d]);
+    }
+    if (threadIdx.x != 0) return;
     double ext = 0.0;
     for (int d = 0; d < 3; ++d) {
         double e = __dsub_rn(hi[d], lo[d]);

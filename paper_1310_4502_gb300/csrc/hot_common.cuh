@@ -78,6 +78,12 @@ struct alignas(32) TCell {
     double x, y, z, rc;
 };
 
+// The same in float32 for the traversal's pre-test: the centre as a hi/lo pair (hi =
+// rounded, lo = remainder) and r_c rounded.
+struct alignas(32) TCellF {
+    float hx, hy, hz, lx, ly, lz, rc, pad;
+};
+
 struct hot_ctx {
     hot_params prm;
     cudaStream_t st = nullptr;
@@ -130,6 +136,7 @@ struct hot_ctx {
     DBuf<int32_t> l_m2p, l_p2p;
     DBuf<int32_t> trav_scratch;
     DBuf<TCell> tcell;
+    DBuf<TCellF> tcellf;
 
     // adjoint
     DBuf<unsigned char> adj_w;   // sink weights (u, v) per sorted slot, T4

@@ -51,7 +51,7 @@ __device__ __forceinline__ void mac_log_newton(double d, double b, double B1, do
 // 1e-9 band in which the traversal re-takes decisions with the bound itself.
 __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
                              const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
-                             double G, double tol, TCell *__restrict__ tc)
+                             double G, double tol, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -99,6 +99,16 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
     t.z = ccom[3 * c + 2];
     t.rc = rc;
     tc[c] = t;
+    TCellF f;
+    f.hx = (float)t.x;
+    f.hy = (float)t.y;
+    f.hz = (float)t.z;
+    f.lx = (float)(t.x - (double)f.hx);
+    f.ly = (float)(t.y - (double)f.hy);
+    f.lz = (float)(t.z - (double)f.hz);
+    f.rc = (float)rc;
+    f.pad = 0.f;
+    tcf[c] = f;
 }
 
 // MODE 0: count the entries of every group's lists (and the interaction totals);
@@ -111,7 +121,8 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
 template <int MODE>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
-    const double *__restrict__ gdmax, const TCell *__restrict__ tcell, const int32_t *__restrict__ cend,
+    const double *__restrict__ gdmax, const TCell *__restrict__ tcell, const TCellF *__restrict__ tcf,
+    const int32_t *__restrict__ cend,
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol,
@@ -135,6 +146,9 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
         const int32_t gc = gcell[g];
         const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
         const double dmax = gdmax[g];
+        const float ghx = (float)gx, ghy = (float)gy, ghz = (float)gz;
+        const float glx = (float)(gx - (double)ghx), gly = (float)(gy - (double)ghy), glz = (float)(gz - (double)ghz);
+        const float dmaxf = (float)dmax;
         int64_t om = 0, op = 0;
         if (FILL) {
             om = off_m2p[g];
@@ -163,12 +177,26 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                     if (anc) {
                         kind = leaf ? 2 : 3;
                     } else {
+                        // float32 pre-test on hi/lo offsets (relative error below 1e-6): decisions
+                        // outside a 1e-5 band are those of the float64 test; inside it, that test
+                        const TCellF f = tcf[c];
+                        const float ox = (f.hx - ghx) + (f.lx - glx);
+                        const float oy = (f.hy - ghy) + (f.ly - gly);
+                        const float oz = (f.hz - ghz) + (f.lz - glz);
+                        const float d2f = ox * ox + oy * oy + oz * oz;
+                        const float thf = dmaxf + f.rc;
+                        const float th2f = thf * thf;
+                        bool acc;
+                        if (d2f > th2f * 1.00001f) {
+                            acc = true;
+                        } else if (d2f < th2f * 0.99999f || !(f.rc < INFINITY)) {
+                            acc = false;
+                        } else {
                         const TCell t = tcell[c];
                         const double dx = t.x - gx, dy = t.y - gy, dz = t.z - gz;
                         const double dist2 = dx * dx + dy * dy + dz * dz;
                         const double thr = dmax + t.rc;
                         const double thr2 = thr * thr;
-                        bool acc;
                         if (dist2 > thr2 * (1.0 + 1e-9)) {
                             acc = true;
                         } else if (dist2 < thr2 * (1.0 - 1e-9) || !(t.rc < INFINITY)) {
@@ -181,6 +209,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                             const double d = __dsub_rn(dist, dmax);
                             const double b = cbmax[c];
                             acc = d > b && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                        }
                         }
                         kind = acc ? 1 : (leaf ? 2 : 3);
                     }
@@ -289,13 +318,14 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     unsigned long long *maxc = (unsigned long long *)(c->sizes.p + 58);
     unsigned *slot_over = (unsigned *)(c->sizes.p + 60);
     HOT_CK(c->tcell.ensure(c->ncell, s));
+    HOT_CK(c->tcellf.ensure(c->ncell, s));
     HOT_CK(c->gkey.ensure(ng + 1, s));
     HOT_CK(c->gkey2.ensure(ng + 1, s));
     HOT_CK(c->gorder.ensure(ng + 1, s));
     HOT_CK(c->gorder2.ensure(ng + 1, s));
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
-                                                            c->p_mom, c->prm.G, tol, c->tcell.p);
+                                                            c->p_mom, c->prm.G, tol, c->tcell.p, c->tcellf.p);
     // One pass into per-group slots when their capacities (the largest counts of the
     // previous traversal plus headroom) fit the budget; otherwise count, scan, fill.
     const int64_t capm = c->slot_capm, capp = c->slot_capp;
@@ -312,13 +342,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_COUNT_LAUNCH();
         if (slots)
             k_traverse<2><<<blocks, TW * 32, 0, s>>>(
-                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
+                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
                 c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
                 capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
             k_traverse<0><<<blocks, TW * 32, 0, s>>>(
-                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p,
+                ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
                 c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
                 slot_over, c->gkey.p, c->d_status);
@@ -363,7 +393,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
         k_traverse<1><<<blocks, TW * 32, 0, s>>>(
-            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
+            ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
             c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
