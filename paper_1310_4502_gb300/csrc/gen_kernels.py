@@ -461,23 +461,6 @@ def gen_record(p):
     return "\n".join(L)
 
 
-def m2m_pairs(p):
-    """Pairs (alpha, beta <= alpha): M_alpha(z') += C(alpha,beta) M_beta(z) (z - z')^{alpha-beta}."""
-    ia = midx(p)
-    idx = {a: i for i, a in enumerate(ia)}
-    start, bidx, gidx, coef = [], [], [], []
-    for a in ia:
-        start.append(len(bidx))
-        for b in ia:
-            if all(b[d] <= a[d] for d in range(3)):
-                g = (a[0] - b[0], a[1] - b[1], a[2] - b[2])
-                bidx.append(idx[b])
-                gidx.append(idx[g])
-                coef.append(math.comb(a[0], b[0]) * math.comb(a[1], b[1]) * math.comb(a[2], b[2]))
-    start.append(len(bidx))
-    return start, bidx, gidx, coef
-
-
 def main(out_path):
     parts = []
     parts.append("// Generated by gen_kernels.py -- do not edit by hand.\n#pragma once\n")
@@ -502,14 +485,6 @@ def main(out_path):
     ia = midx(PMAX)
     parts.append("__device__ __constant__ unsigned char hot_midx[%d][3] = {%s};" % (
         len(ia), ", ".join("{%d,%d,%d}" % a for a in ia)))
-    # translation pairs of order PMAX; components are ordered so that every lower
-    # order is a prefix (alpha with |alpha| <= p come first and only reference such beta)
-    st, bi, gi, co = m2m_pairs(PMAX)
-    parts.append(f"static constexpr int M2M_NPAIR = {len(bi)};")
-    parts.append(f"__device__ const unsigned short m2m_start[{len(st)}] = {{{', '.join(map(str, st))}}};")
-    parts.append(f"__device__ const unsigned char m2m_beta[{len(bi)}] = {{{', '.join(map(str, bi))}}};")
-    parts.append(f"__device__ const unsigned char m2m_gamma[{len(gi)}] = {{{', '.join(map(str, gi))}}};")
-    parts.append(f"__device__ const double m2m_coef[{len(co)}] = {{{', '.join(repr(float(c)) for c in co)}}};")
     parts.extend(evals)
     parts.extend(records)
     ts, ta, tg, tc = m2m_transposed(PMAX)

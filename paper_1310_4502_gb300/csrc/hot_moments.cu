@@ -121,8 +121,18 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
 
 // ---------------------------------------------------------------------------
 // M2M for the inner cells of one level: one warp per cell, lanes over components.
-// M_a(z) = sum_children sum_{b <= a} C(a,b) M_b(z_ch) (z_ch - z)^{a-b}
+// M_a(z) = sum_children sum_{b <= a} C(a,b) M_b(z_ch) (z_ch - z)^{a-b}.  The binomial
+// translation factorises over the axes, so it is applied as three one-dimensional
+// translations (x, then y, then z):
+//   T1(i,j,k) = sum_{i' <= i} C(i,i') dx^{i-i'} M(i',j,k),  then likewise in j and in k,
+// at most p+1 terms per component and pass (float64 throughout).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int mom_index(int i, int j, int k)
+{
+    const int n = i + j + k;
+    return n * (n + 1) * (n + 2) / 6 + (n - i) * (n - i + 1) / 2 + (n - i - j);
+}
+
 template <int P>
 __global__ void __launch_bounds__(MW * 32) k_m2m_level(
     const int32_t *__restrict__ cells, int64_t ncells_lvl, const int32_t *__restrict__ child8,
@@ -130,13 +140,24 @@ __global__ void __launch_bounds__(MW * 32) k_m2m_level(
     double *__restrict__ cmom)
 {
     constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
-    __shared__ double sd[MW][NC];   // (z_ch - z)^g
-    __shared__ double sm[MW][NC];   // child moments
+    constexpr int NQ = (NC + 31) / 32;
+    __shared__ double sa[MW][NC], sb[MW][NC];  // child moments, then the partial translations
+    __shared__ double sp[MW][3][P + 1];        // powers of the offset z_ch - z
     __shared__ unsigned char mi[NC][3];
+    __shared__ double binom[P + 1][P + 1];
     for (int k = threadIdx.x; k < NC; k += blockDim.x) {
         mi[k][0] = hot_midx[k][0];
         mi[k][1] = hot_midx[k][1];
         mi[k][2] = hot_midx[k][2];
+    }
+    for (int k = threadIdx.x; k < (P + 1) * (P + 1); k += blockDim.x) {
+        const int n = k / (P + 1), r = k % (P + 1);
+        double v = 0.0;
+        if (r <= n) {
+            v = 1.0;
+            for (int t = 1; t <= r; ++t) v = v * (double)(n - r + t) / (double)t;
+        }
+        binom[n][r] = v;
     }
     __syncthreads();
     const int w = threadIdx.x >> 5;
@@ -159,36 +180,61 @@ __global__ void __launch_bounds__(MW * 32) k_m2m_level(
             }
         }
         const double z[3] = {mx / m, my / m, mz / m};
-        double acc[(NC + 31) / 32];
+        double acc[NQ];
 #pragma unroll
-        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = 0.0;
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
         for (int o = 0; o < 8; ++o) {
             const int32_t k = ch[o];
             if (k < 0) continue;
-            const double d[3] = {ccom[3 * (int64_t)k + 0] - z[0], ccom[3 * (int64_t)k + 1] - z[1],
-                                 ccom[3 * (int64_t)k + 2] - z[2]};
-            for (int g = lane; g < NC; g += 32) {
+            if (lane < 3) {
+                const double d = ccom[3 * (int64_t)k + lane] - z[lane];
                 double v = 1.0;
-                for (int e = 0; e < 3; ++e)
-                    for (int t = 0; t < mi[g][e]; ++t) v *= d[e];
-                sd[w][g] = v;
-                sm[w][g] = cmom[(int64_t)k * NC + g];
+                for (int e = 0; e <= P; ++e) {
+                    sp[w][lane][e] = v;
+                    v *= d;
+                }
+            }
+            for (int g = lane; g < NC; g += 32) sa[w][g] = cmom[(int64_t)k * NC + g];
+            __syncwarp();
+            // pass 1 (x): sa -> sb
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int a = lane + 32 * q;
+                if (a < NC) {
+                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
+                    double t = 0.0;
+                    for (int i2 = 0; i2 <= i; ++i2) t += binom[i][i2] * sp[w][0][i - i2] * sa[w][mom_index(i2, j, kk)];
+                    sb[w][a] = t;
+                }
             }
             __syncwarp();
+            // pass 2 (y): sb -> sa
 #pragma unroll
-            for (int q = 0; q < (NC + 31) / 32; ++q) {
-                int a = lane + 32 * q;
+            for (int q = 0; q < NQ; ++q) {
+                const int a = lane + 32 * q;
                 if (a < NC) {
+                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
                     double t = 0.0;
-                    for (int j = m2m_start[a]; j < m2m_start[a + 1]; ++j)
-                        t += m2m_coef[j] * sm[w][m2m_beta[j]] * sd[w][m2m_gamma[j]];
+                    for (int j2 = 0; j2 <= j; ++j2) t += binom[j][j2] * sp[w][1][j - j2] * sb[w][mom_index(i, j2, kk)];
+                    sa[w][a] = t;
+                }
+            }
+            __syncwarp();
+            // pass 3 (z): sa -> accumulated parent moments
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int a = lane + 32 * q;
+                if (a < NC) {
+                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
+                    double t = 0.0;
+                    for (int k2 = 0; k2 <= kk; ++k2) t += binom[kk][k2] * sp[w][2][kk - k2] * sa[w][mom_index(i, j, k2)];
                     acc[q] += t;
                 }
             }
             __syncwarp();
         }
 #pragma unroll
-        for (int q = 0; q < (NC + 31) / 32; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             int a = lane + 32 * q;
             if (a < NC) cmom[(int64_t)c * NC + a] = acc[q];
         }

@@ -9,8 +9,9 @@ g++ and checked without a GPU:
   difference of the oracle's M2P;
 * m2p_cbar + m2p_record_adjoint: dL/dM of L = u.a + v phi, which is linear in M, against
   L evaluated by the oracle on unit moment vectors;
-* the M2M tables: the translated moments against the oracle's moments taken directly
-  about the new centre; the transposed tables against <y, T x> = <T^T y, x>.
+* the moment translation (in the kernel's three one-dimensional passes): the translated
+  moments against the oracle's moments taken directly about the new centre; the adjoint's
+  transposed translation tables against <y, T x> = <T^T y, x>.
 """
 import ctypes as C
 import os
@@ -98,13 +99,40 @@ void g_radj(int p, const double *cb, double is, double G, double *serial, double
         table[a] = G * t;
     }
 }
+static int mom_index(int i, int j, int k)
+{
+    const int n = i + j + k;
+    return n * (n + 1) * (n + 2) / 6 + (n - i) * (n - i + 1) / 2 + (n - i - j);
+}
+static double binom(int n, int r)
+{
+    double v = 1.0;
+    for (int t = 1; t <= r; ++t) v = v * (double)(n - r + t) / (double)t;
+    return v;
+}
+// the moment translation as the moments kernel applies it: three one-dimensional passes
 void g_m2m(int p, const double *Mc, const double *d, double *Mp)
 {
-    for (int a = 0; a < HOT_NCOMP[p]; ++a) {
-        double t = 0.0;
-        for (int j = m2m_start[a]; j < m2m_start[a + 1]; ++j) t += m2m_coef[j] * Mc[m2m_beta[j]] * dpow(d, m2m_gamma[j]);
-        Mp[a] = t;
+    const int nc = HOT_NCOMP[p];
+    double a[84], b[84];
+    for (int q = 0; q < nc; ++q) a[q] = Mc[q];
+    for (int e = 0; e < 3; ++e) {
+        for (int q = 0; q < nc; ++q) {
+            int x[3] = {hot_midx[q][0], hot_midx[q][1], hot_midx[q][2]};
+            double t = 0.0, pw = 1.0;
+            const int top = x[e];
+            // sum over x_e' <= x_e of C(x_e, x_e') d_e^(x_e - x_e') a(.., x_e', ..)
+            for (int r = top; r >= 0; --r) {
+                int y[3] = {x[0], x[1], x[2]};
+                y[e] = r;
+                t += binom(top, r) * pw * a[mom_index(y[0], y[1], y[2])];
+                pw *= d[e];
+            }
+            b[q] = t;
+        }
+        for (int q = 0; q < nc; ++q) a[q] = b[q];
     }
+    for (int q = 0; q < nc; ++q) Mp[q] = a[q];
 }
 void g_m2mt(int p, const double *Mbp, const double *d, double *Mbc)
 {
