@@ -496,11 +496,17 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
 #pragma unroll
                 for (int q = 0; q < NS; ++q)
                     if (valid[q]) {
-                        const int64_t i = perm[slot[q]];
-                        acc_out[3 * i + 0] = acc[q].get(0);
-                        acc_out[3 * i + 1] = acc[q].get(1);
-                        acc_out[3 * i + 2] = acc[q].get(2);
-                        if (pot_out) pot_out[i] = acc[q].get(3);
+                        if constexpr (MODE == 0) {
+                            const int64_t i = perm[slot[q]];
+                            acc_out[3 * i + 0] = acc[q].get(0);
+                            acc_out[3 * i + 1] = acc[q].get(1);
+                            acc_out[3 * i + 2] = acc[q].get(2);
+                            if (pot_out) pot_out[i] = acc[q].get(3);
+                        } else {
+                            gsink[3 * slot[q] + 0] = acc[q].get(0);
+                            gsink[3 * slot[q] + 1] = acc[q].get(1);
+                            gsink[3 * slot[q] + 2] = acc[q].get(2);
+                        }
                     }
             }
             __syncwarp();
