@@ -287,22 +287,32 @@ def gen_cbar(p):
              "  T wk[%d];" % (K + 2),
              "  wk[0] = T(1);",
              f"  for (int q = 1; q < {K + 2}; ++q) wk[q] = wk[q - 1] * w;"]
-        for n in range(2, p + 1):
-            for a in midx(n)[ncomp(n - 1):]:
-                d = 0 if a[0] > 0 else (1 if a[1] > 0 else 2)
-                prev = list(a)
-                prev[d] -= 1
-                prev = mname(tuple(prev))
-                unit = [mname((1, 0, 0)), mname((0, 1, 0)), mname((0, 0, 1))][d]
-                ud = ["ux", "uy", "uz"][d]
-                L.append(f"  const T {mname(a)} = {prev} * {unit};")
-                L.append(f"  const T D{mname(a)} = D{prev} * {unit} + {prev} * {ud};")
+        # A_{k,n} = a_k + n b_k with a_k = -w^k (v rho + rs (1+2k) u.y), b_k = -2 w^k rs u.y
         for k in range(K + 1):
             L.append(f"  const T B{k} = rs * wk[{k + 1}];")
-            for n in range(p - 2 * k + 1):
-                L.append(f"  const T A{k}_{n} = -wk[{k}] * (v * rho + rs * T({1 + 2 * k + 2 * n}) * uy_);")
-        for i, (k, n, b) in enumerate(S):
-            L.append(f"  cb[{i}] += A{k}_{n} * {mname(b)} + B{k} * D{mname(b)};")
+            L.append(f"  const T a{k} = -wk[{k}] * (v * rho + rs * T({1 + 2 * k}) * uy_);")
+            L.append(f"  const T b{k} = T(-2) * wk[{k}] * rs * uy_;")
+        sidx = {(k, n, b): i for i, (k, n, b) in enumerate(S)}
+        # degree by degree: the monomials of degree n (and their derivatives along u) are
+        # formed from those of degree n-1 and consumed at once, so that only two degrees
+        # are live together
+        for n in range(0, p + 1):
+            if n >= 2:
+                for a in midx(n)[ncomp(n - 1):]:
+                    d = 0 if a[0] > 0 else (1 if a[1] > 0 else 2)
+                    prev = list(a)
+                    prev[d] -= 1
+                    prev = mname(tuple(prev))
+                    unit = [mname((1, 0, 0)), mname((0, 1, 0)), mname((0, 0, 1))][d]
+                    ud = ["ux", "uy", "uz"][d]
+                    L.append(f"  const T {mname(a)} = {prev} * {unit};")
+                    L.append(f"  const T D{mname(a)} = D{prev} * {unit} + {prev} * {ud};")
+            for k in range(K + 1):
+                if n > p - 2 * k:
+                    continue
+                L.append(f"  const T A{k}_{n} = a{k} + T({n}) * b{k};")
+                for b in (midx(n)[ncomp(n - 1):] if n > 0 else [(0, 0, 0)]):
+                    L.append(f"  cb[{sidx[(k, n, b)]}] += A{k}_{n} * {mname(b)} + B{k} * D{mname(b)};")
         L.append("}")
         out.append("\n".join(L))
     return "\n".join(out)
