@@ -202,6 +202,35 @@ int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
 int hot_key_frame_noalloc(const double *pos, const double *mass, int64_t N, double *frame,
                           void *cuda_stream);
 
+/* Synchronise the context stream and return the device status of the calls made since
+ * the last synchronisation point: HOT_OK, or HOT_EINPUT, HOT_EOVERFLOW, HOT_ETIMEOUT
+ * (a bounded wait of the interaction kernels expired; the kernel skipped the rest of that
+ * group's work and the context stays usable), HOT_ECUDA.  The status word is cleared.
+ * hot_evaluate_forces and hot_adjoint are asynchronous: their status is reported here or
+ * at the next hot_build_tree / hot_traverse. */
+int hot_synchronize(hot_ctx *ctx);
+
+/* Test knobs (no counterpart in the paper): they force the library's overflow and
+ * timeout paths on small inputs.  Values persist on the context until changed.
+ *   HOT_DBGSET_FRONTIER_CAP  per-warp traversal frontier capacity in cells (>= 1); an
+ *                            overflow makes hot_traverse retry with 4x the capacity, at
+ *                            most three times, then return HOT_EOVERFLOW
+ *   HOT_DBGSET_SLOT_CAP      capacity (entries, >= 1) of each group's list slots in the
+ *                            one-pass traversal; a group that does not fit makes that call
+ *                            fall back to the count/scan/fill passes (the next call sizes
+ *                            the slots from the counts)
+ *   HOT_DBGSET_WAIT_POLLS    poll limit of the interaction kernels' wait for each staged
+ *                            chunk (>= 1; 0 restores the default of 2^22): on expiry the
+ *                            warp flags HOT_ETIMEOUT, waits (with the default limit) for
+ *                            its copies in flight and leaves its group
+ *   HOT_DBGSET_WAIT_PROBE    1: before its first copy, every group's M2P pass waits on a
+ *                            barrier that nothing completes (at most min(poll limit, 4096)
+ *                            polls), so the wait runs out, HOT_ETIMEOUT is flagged and the
+ *                            group is left with no copy in flight; 0: off (default)
+ * Returns HOT_OK or HOT_EINVAL. */
+enum { HOT_DBGSET_FRONTIER_CAP = 0, HOT_DBGSET_SLOT_CAP = 1, HOT_DBGSET_WAIT_POLLS = 2, HOT_DBGSET_WAIT_PROBE = 3 };
+int hot_debug_set(hot_ctx *ctx, int what, int64_t value);
+
 /* y[k] += alpha * x[k] for k < n (device float64 arrays, asynchronous on the
  * context stream).  The kick (v += dt/2 a) and drift (x += dt v) of the
  * kick-drift-kick leapfrog of Sec. "Time Integration", and their adjoints, are

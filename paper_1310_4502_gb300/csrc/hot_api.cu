@@ -320,3 +320,34 @@ extern "C" int hot_memory_stats(int64_t out[2], int reset_peak)
     if (reset_peak) hot_bytes_peak.store(out[0]);
     return HOT_OK;
 }
+
+extern "C" int hot_synchronize(hot_ctx *c)
+{
+    if (!c) return HOT_EINVAL;
+    return hot_sync_status(c);
+}
+
+extern "C" int hot_debug_set(hot_ctx *c, int what, int64_t value)
+{
+    if (!c) return HOT_EINVAL;
+    switch (what) {
+        case HOT_DBGSET_FRONTIER_CAP:
+            if (value < 1 || value > (1 << 24)) return HOT_EINVAL;
+            c->trav_cap = (int)value;
+            return HOT_OK;
+        case HOT_DBGSET_SLOT_CAP:
+            if (value < 1 || value > (1 << 24)) return HOT_EINVAL;
+            c->slot_capm = c->slot_capp = value;
+            return HOT_OK;
+        case HOT_DBGSET_WAIT_POLLS:
+            if (value < 0 || value > 0xffffffffll) return HOT_EINVAL;
+            c->wait_polls = (uint32_t)value;
+            return HOT_OK;
+        case HOT_DBGSET_WAIT_PROBE:
+            if (value != 0 && value != 1) return HOT_EINVAL;
+            c->wait_probe = (int)value;
+            return HOT_OK;
+        default:
+            return HOT_EINVAL;
+    }
+}

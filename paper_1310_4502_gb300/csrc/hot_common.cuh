@@ -152,6 +152,9 @@ struct hot_ctx {
     DBuf<unsigned char> adj_pp;  // P2P source-side partial sums per work item and leaf particle
     DBuf<int64_t> adj_roff;      // first partial row of every leaf
     int trav_cap = 2048;
+    uint32_t wait_polls = 0;  // interaction kernels' chunk-wait poll limit (0: default)
+    int wait_probe = 0;       // test setting: every group's M2P list first waits on a barrier
+                              // that nothing completes
     // per-group slot capacities of the one-pass traversal (grown from the counts seen)
     int64_t slot_capm = 2048, slot_capp = 512;
     DBuf<int32_t> slot_m2p, slot_p2p;

@@ -50,6 +50,7 @@ struct alignas(16) Smem {
     int32_t lex[33], lbeg[32];  // P2P batch: scanned particle offsets and first slots
     T loff[32][3];              // P2P batch: leaf centre offsets
     unsigned long long bar[2];
+    unsigned long long probe;   // test setting: a barrier nothing ever arrives on
 };
 
 // ---- TMA bulk copy and mbarrier helpers (inline PTX) ----
@@ -75,17 +76,28 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // Warp-collective bounded wait: every lane polls until it has observed the phase
-// completion itself; the result is the same on all lanes.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase)
+// completion itself; the result is the same on all lanes.  Polls use try_wait (which
+// may suspend the thread for a while); a limit below the default (a test setting) polls
+// with the non-blocking test_wait, so that the limit counts polls of no duration.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase, uint32_t limit = WAIT_LIMIT)
 {
     uint32_t done = 0;
-    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
-        if (!done)
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(done)
-                : "r"(sptr(bar)), "r"(phase)
-                : "memory");
+    const bool quick = limit < WAIT_LIMIT;
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (!done) {
+            if (quick)
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(done)
+                    : "r"(sptr(bar)), "r"(phase)
+                    : "memory");
+            else
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(done)
+                    : "r"(sptr(bar)), "r"(phase)
+                    : "memory");
+        }
         if (__all_sync(0xffffffffu, done)) return true;
     }
     return false;
@@ -149,7 +161,7 @@ template <int P, class T, int NS, int MODE>
 __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_m2p,
                                          const T *__restrict__ rec, const T (&x)[NS][3], const T (&wt)[NS][4],
                                          int sj, int nsplit, bool active, Acc<T> (&acc)[NS], uint32_t (&phase)[2],
-                                         unsigned *status)
+                                         uint32_t wait_limit, bool probe, unsigned *status)
 {
     constexpr int CH = Cfg<P, T>::CH;
     constexpr int RL = Cfg<P, T>::RL;
@@ -158,6 +170,14 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
     const int64_t nm = G.m1 - G.m0;
     const int nch = (int)((nm + CH - 1) / CH);
     if (nch == 0) return true;
+    if (probe) {
+        // test setting: a wait that cannot complete, taken before any copy is issued (so
+        // nothing is in flight when it runs out); at most 4096 polls
+        if (!mbar_wait(&sm.probe, 0, wait_limit < 4096u ? wait_limit : 4096u)) {
+            if (lane == 0) hot_flag(status, HOT_ST_TIMEOUT);
+            return false;
+        }
+    }
     auto chunk_n = [&](int c) { return (int)(nm - (int64_t)c * CH < CH ? nm - (int64_t)c * CH : CH); };
     auto load_idx = [&](int c) {
         return (c < nch && (int)lane < chunk_n(c)) ? l_m2p[G.m0 + (int64_t)c * CH + lane] : 0;
@@ -180,7 +200,9 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             issue(c + 1, b ^ 1, nxt);
             nxt = load_idx(c + 2);
         }
-        if (!mbar_wait(&sm.bar[b], phase[b])) {
+        if (!mbar_wait(&sm.bar[b], phase[b], wait_limit)) {
+            // the wait ran out: flag it, let the copies in flight land (default limit) and
+            // leave the group
             if (lane == 0) hot_flag(status, HOT_ST_TIMEOUT);
             mbar_wait(&sm.bar[b], phase[b]);
             if (c + 1 < nch) mbar_wait(&sm.bar[b ^ 1], phase[b ^ 1]);
@@ -384,7 +406,8 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
     const double *__restrict__ ccom, const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
     const uint32_t *__restrict__ gorder, T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
-    const T *__restrict__ wsink, double *__restrict__ gsink, unsigned *__restrict__ status)
+    const T *__restrict__ wsink, double *__restrict__ gsink, uint32_t wait_limit, int probe,
+    unsigned *__restrict__ status)
 {
     using S = Smem<P, T>;
     constexpr int CH = Cfg<P, T>::CH;
@@ -396,6 +419,7 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
+        mbar_init(&sm.probe, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
@@ -464,7 +488,9 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
             Acc<T> acc[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) acc[q].zero();
-            if (!m2p_list<P, T, NS, MODE>(sm, Gr, l_m2p, rec, x, wt, sj, nsplit, active, acc, phase, status)) return;
+            if (!m2p_list<P, T, NS, MODE>(sm, Gr, l_m2p, rec, x, wt, sj, nsplit, active, acc, phase, wait_limit,
+                                          probe != 0, status))
+                return;
             p2p_list<P, T, NS, MODE>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, wt, self, sj, nsplit, active,
                                eps2, Gt, acc);
             if (NS == 1) {
@@ -537,7 +563,7 @@ int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *po
                                        c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
                                        c->l_p2p.p, c->idx.p, c->gorder.p, eps2, c->prm.G, work, acc, pot, wsink,
-                                       gsink,
+                                       gsink, c->wait_polls ? c->wait_polls : WAIT_LIMIT, c->wait_probe,
                                        c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }

@@ -16,6 +16,7 @@ from . import build as _build
 HOT_OK, HOT_EINVAL, HOT_ESTATE, HOT_ENOMEM, HOT_EOVERFLOW, HOT_ECUDA, HOT_EINPUT, HOT_ETIMEOUT = (
     0, -1, -2, -3, -4, -5, -6, -7)
 HOT_FP32_MIXED, HOT_FP64 = 0, 1
+HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS, HOT_DBGSET_WAIT_PROBE = 0, 1, 2, 3
 
 DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
            CELL_PARENT=7, CELL_NCHILD=8, GROUP_CELL=9, GROUP_CENTRE=10, GROUP_DMAX=11, CELL_MASS=12,
@@ -25,7 +26,7 @@ DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
            "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats")
+           "hot_memory_stats", "hot_synchronize", "hot_debug_set")
 
 
 class hot_params(C.Structure):
@@ -75,10 +76,12 @@ def load():
     L.hot_key_frame_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.hot_axpy.argtypes = [vp, vp, vp, C.c_double, C.c_int64]
     L.hot_memory_stats.argtypes = [C.POINTER(C.c_int64), C.c_int]
+    L.hot_synchronize.argtypes = [vp]
+    L.hot_debug_set.argtypes = [vp, C.c_int, C.c_int64]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
                  "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats"):
+           "hot_memory_stats", "hot_synchronize", "hot_debug_set"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -219,6 +222,16 @@ class Hot:
         if y.numel() != x.numel():
             raise ValueError("size mismatch")
         _ck(load().hot_axpy(self._h, _ptr(y), _ptr(x), float(alpha), int(y.numel())), "hot_axpy")
+
+    def synchronize(self):
+        """Wait for the context stream; raises HotError for a device-side status (for the
+        asynchronous calls: moments, forces, adjoint)."""
+        _ck(load().hot_synchronize(self._h), "hot_synchronize")
+
+    def debug_set(self, what, value):
+        """Test knobs: HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS,
+        HOT_DBGSET_WAIT_PROBE (see include/hot.h)."""
+        _ck(load().hot_debug_set(self._h, int(what), int(value)), "hot_debug_set")
 
     def fma_peak(self, dbl=False):
         v = C.c_double()
