@@ -355,7 +355,17 @@ def run_ours(args):
             "flop_convention": f"M2P {FLOPS_M2P[w.p]} flop (generated p={w.p} routine, FMA=2), P2P 28 flop",
             "m2p_interactions": sz["n_m2p_int"], "p2p_interactions": sz["n_pairs"],
             "ms_per_launch": stages["interact"],
-            "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int}
+            "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int,
+            "m2p_interactions_per_s": sz["n_m2p_int"] / t_int, "p2p_pairs_per_s": sz["n_pairs"] / t_int}
+    # the HBM-bound integer stages against the measured copy bandwidth, with algorithmic
+    # bytes per particle: bounding cube + keys (read positions twice and masses, write key
+    # and index: 68 B), eight 8-bit LSD passes over (key, index) (192 B), gather of
+    # positions and masses into key order (64 B); tree build from the sorted keys (12 B)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_stages = {}
+    for name, stage, bpp in (("keys_sort", "sort", 68 + 192 + 64), ("build", "build", 12)):
+        gbs = N * bpp / (stages[stage] * 1e-3) / 1e9
+        hbm_stages[name] = {"bytes_per_particle": bpp, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
 
     out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -364,7 +374,7 @@ def run_ours(args):
                       "group_max": h.params.group_max, "l2": "flushed between steps (256 MiB write, untimed)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "stages_ms": stages, "sizes": {k: v for k, v in sz.items() if k != "launches"},
-           "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+           "gpu_launches": launches, "roofline": roof, "clocks": clocks, "hbm_stages": hbm_stages,
            "fp64_peak_tflops_measured": fma64}
 
     out["adjoint"] = adjoint_leg(h, lambda: step(h, w.p), N, dev, args.steps, flush, stream)
@@ -416,6 +426,18 @@ def run_ours(args):
                      "interact_tflops": (s6["n_m2p_int"] * FLOPS_M2P[6] + s6["n_pairs"] * P2P_FLOPS)
                      / (st6["interact"] * 1e-3) / 1e12}
         del h64, h6
+        # the paper's science tolerance on the same box
+        h5 = hot.Hot(p=w.p, tol=1e-5, eps=w.eps, precision="mixed")
+        h5.force(P, M, acc)
+        t5 = 0.0
+        for _ in range(args.steps):
+            t5 += _ev_ms(stream, lambda: h5.force(P, M, acc), flush)[0]
+        s5 = h5.sizes()
+        out["tol1e5"] = {"value": N / (t5 / args.steps * 1e-3), "unit": "particles/s",
+                         "ms_per_step": t5 / args.steps, "m2p_interactions": s5["n_m2p_int"],
+                         "p2p_interactions": s5["n_pairs"]}
+        acc_tol5 = acc.clone()
+        del h5
         # the differentiation configuration: clustered recipe at N = 2^18
         wd = W.make("clustered18")
         Pd = torch.tensor(wd.pos, device=dev)
@@ -436,6 +458,9 @@ def run_ours(args):
             e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
             out["error"].update({"tree_vs_direct_rms_rel_4096": float(np.sqrt(np.mean(e ** 2))),
                                  "tree_vs_direct_max_rel_4096": float(e.max())})
+            e5 = np.linalg.norm(acc_tol5.cpu().numpy()[sub] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            out["tol1e5"].update({"tree_vs_direct_rms_rel_4096": float(np.sqrt(np.mean(e5 ** 2))),
+                                  "tree_vs_direct_max_rel_4096": float(e5.max())})
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = {k: v for k, v in oracle_sample(w).items() if k != "seconds"}
     if rank == 0:
