@@ -471,8 +471,8 @@ def run_ours(args):
 
 
 def _flops_table():
-    from paper_1310_4502_gb300.csrc.gen_kernels import gen_eval
-    return [gen_eval(p)[3] for p in range(7)]
+    from paper_1310_4502_gb300.csrc.gen_kernels import M2P_FLOP_CONVENTION
+    return list(M2P_FLOP_CONVENTION)
 
 
 FLOPS_M2P = _flops_table()

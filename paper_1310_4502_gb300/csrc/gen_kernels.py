@@ -22,8 +22,10 @@ every order p = 0..6:
 * ``m2p_record<P>(M, inv_s, G, eps, rec)`` -- raw moments (FP64) to the record
   read by ``m2p_eval``: every coefficient is scaled by a power of two
   s = 1/inv_s (exact), so that R' = R/s and the coefficients stay O(1) in
-  single precision; G/s is folded in.  Layout: [inv_s, eps^2/s^2, 0, 0,
-  C_{b,k} ..., gradient coefficients b_d C_{b,k} ...].
+  single precision; G/s is folded in.  Layout: [inv_s, eps^2/s^2, centre hi (3),
+  centre lo (3), C_{b,k} ... in the order the evaluation reads them].  The gradient
+  polynomials dS_k/dy_d are not stored: the evaluation forms them from the C_{b,k}
+  by derivative-carrying Horner chains.
 * the moment-translation (M2M) pair tables and multi-index tables.
 
 The flop count of each ``m2p_eval<P>`` (FMA = 2, the rsqrt as 1) is emitted as
@@ -82,18 +84,6 @@ def s_terms(p):
     return out
 
 
-def g_terms(p):
-    """(k, d, beta) with beta_d >= 1: coefficient beta_d C_{beta,k} of dS_k/dy_d."""
-    out = []
-    for k in range(p // 2 + 1):
-        for n in range(1, p - 2 * k + 1):
-            for b in midx(n)[ncomp(n - 1):]:
-                for d in range(3):
-                    if b[d] >= 1:
-                        out.append((k, d, b))
-    return out
-
-
 # Flops per M2P interaction used as the roofline convention (FMA = 2, rsqrt = 1): the
 # operation count of the traced expansion evaluated with explicit monomials (the first
 # form of this routine).  The Horner form below does the same mathematics with fewer
@@ -101,39 +91,62 @@ def g_terms(p):
 M2P_FLOP_CONVENTION = [32, 40, 82, 164, 307, 534, 874]
 
 
-def _horner_poly(X, n, ref, tangent):
-    """Statements for the polynomial X(y) = sum_{|g| <= n} c_g y^g, nested Horner in y_z,
-    then y_y, then y_x, so that every coefficient is consumed by one fused multiply-add
-    (chains over z are independent of each other).  With tangent, the derivative along
-    (dy100, dy010, dy001) is carried as dX."""
-    out = []
-    for i in range(n + 1):
-        for j in range(n - i + 1):
+class _Prog:
+    """Straight-line code in SSA form built from steps v = a + m * b (one fused
+    multiply-add), m one of the Horner variables y100, y010, y001.  Operands are
+    variable names, coefficient references ('@...@', constant) or None (zero).  With
+    tangent, every variable v gets dv = da + dm b + m db, the forward-mode derivative
+    along (dy100, dy010, dy001)."""
+
+    def __init__(self, tangent):
+        self.L = []
+        self.tangent = tangent
+        self.var = set()
+
+    def d(self, x):
+        return "d" + x if x in self.var else None
+
+    def fma(self, name, a, m, b):
+        if b is None:
+            return a
+        self.L.append(f"const T {name} = " + (f"{m} * {b};" if a is None else f"{a} + {m} * {b};"))
+        self.var.add(name)
+        if self.tangent:
+            terms = [t for t in (self.d(a) if a is not None else None, f"d{m} * {b}",
+                                 f"{m} * {self.d(b)}" if self.d(b) else None) if t]
+            self.L.append(f"const T d{name} = " + " + ".join(terms) + ";")
+        return name
+
+
+def _horner_grad(P, X, n, ref):
+    """The polynomial X(y) = sum_{|g| <= n} c_g y^g and its gradient from the
+    coefficients c_g alone: nested Horner in y_z (inner), y_y, y_x (outer), each chain
+    carrying its derivative in its own variable (d <- d y + h before h <- h y + c), and
+    the y_z- and y_y-derivatives of the inner chains carried through the outer ones.
+    Returns the names of X, dX/dy_x, dX/dy_y, dX/dy_z (None where identically zero)."""
+    S = Sx = Sy = Sz = None
+    for i in range(n, -1, -1):
+        t = ty = tz = None
+        for j in range(n - i, -1, -1):
             m = n - i - j
-            h = f"h{X}_{i}_{j}"
-            out.append(f"T {h} = {ref(i, j, m)};")
-            if tangent:
-                out.append(f"T d{h} = T(0);")
+            h, hz = ref(i, j, m), None
             for l in range(m - 1, -1, -1):
-                if tangent:
-                    out.append(f"d{h} = dy001 * {h} + y001 * d{h};")
-                out.append(f"{h} = {ref(i, j, l)} + y001 * {h};")
-        t = f"t{X}_{i}"
-        out.append(f"T {t} = h{X}_{i}_{n - i};")
-        if tangent:
-            out.append(f"T d{t} = dh{X}_{i}_{n - i};")
-        for j in range(n - i - 1, -1, -1):
-            if tangent:
-                out.append(f"d{t} = dh{X}_{i}_{j} + dy010 * {t} + y010 * d{t};")
-            out.append(f"{t} = h{X}_{i}_{j} + y010 * {t};")
-    out.append(f"T {X} = t{X}_{n};")
-    if tangent:
-        out.append(f"T d{X} = dt{X}_{n};")
-    for i in range(n - 1, -1, -1):
-        if tangent:
-            out.append(f"d{X} = dt{X}_{i} + dy100 * {X} + y100 * d{X};")
-        out.append(f"{X} = t{X}_{i} + y100 * {X};")
-    return out
+                hz = h if hz is None else P.fma(f"hz{X}_{i}_{j}_{l}", h, "y001", hz)
+                h = P.fma(f"h{X}_{i}_{j}_{l}", ref(i, j, l), "y001", h)
+            if t is None:
+                t, tz = h, hz
+            else:
+                ty = t if ty is None else P.fma(f"ty{X}_{i}_{j}", t, "y010", ty)
+                t = P.fma(f"t{X}_{i}_{j}", h, "y010", t)
+                tz = hz if tz is None else P.fma(f"tz{X}_{i}_{j}", hz, "y010", tz)
+        if S is None:
+            S, Sy, Sz = t, ty, tz
+        else:
+            Sx = S if Sx is None else P.fma(f"sx{X}_{i}", S, "y100", Sx)
+            S = P.fma(f"s{X}_{i}", t, "y100", S)
+            Sy = ty if Sy is None else P.fma(f"sy{X}_{i}", ty, "y100", Sy)
+            Sz = tz if Sz is None else P.fma(f"sz{X}_{i}", tz, "y100", Sz)
+    return S, Sx, Sy, Sz
 
 
 def _horner_w(dst, names, tangent):
@@ -158,12 +171,13 @@ def _horner_w(dst, names, tangent):
 
 def _eval_stmts(p, tangent=False):
     """Statements of one M2P interaction with symbolic coefficient references
-    ('@S,k,b@' for C_{b,k}, '@G,k,d,b@' for b_d C_{b,k}), and the flop convention.
-    Phi = rho sum_k w^k S_k(y); the gradient needs dS_k/dy_d (polynomials with the
-    coefficients b_d C_{b,k}) and Q = sum_k w^k sum_n (1+2k+2n) S_{k,n}, which by
-    Euler's theorem for the degree-n parts is sum_k w^k [(1+2k) S_k + 2 y . grad S_k].
-    With tangent, the forward-mode derivative along the input direction (ux, uy, uz) is
-    carried alongside: (d a / d R) u, the Hessian of the expansion applied to u."""
+    ('@S,k,i,j,l@' for C_{b,k}, b = (i, j, l)), and the flop convention.
+    Phi = rho sum_k w^k S_k(y); the gradient needs dS_k/dy_d, formed alongside S_k by
+    the derivative-carrying Horner chains of _horner_grad, and Q = sum_k w^k sum_n
+    (1+2k+2n) S_{k,n}, which by Euler's theorem for the degree-n parts is sum_k w^k
+    [(1+2k) S_k + 2 y . grad S_k].  With tangent, the forward-mode derivative along the
+    input direction (ux, uy, uz) is carried alongside: (d a / d R) u, the Hessian of the
+    expansion applied to u."""
     L = ["rx *= is; ry *= is; rz *= is;"]
     if tangent:
         L.append("const T drx = ux * is, dry = uy * is, drz = uz * is;")
@@ -181,18 +195,15 @@ def _eval_stmts(p, tangent=False):
     K = p // 2
     for k in range(K + 1):
         n = p - 2 * k
-        # the tangent of S_k is grad S_k . dy, and grad S_k = (G_k0, G_k1, G_k2) is evaluated
-        # below, so S_k itself needs no tangent chain
-        L += _horner_poly(f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@", False)
-        if n >= 1:
-            for d in range(3):
-                def gref(i, j, l, d=d, k=k):
-                    b = [i, j, l]
-                    b[d] += 1
-                    return f"@G,{k},{d},{b[0]},{b[1]},{b[2]}@"
-                L += _horner_poly(f"G{k}_{d}", n - 1, gref, tangent)
+        P = _Prog(tangent)
+        names = _horner_grad(P, f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@")
+        L += P.L
+        for nm, v in zip([f"S{k}", f"G{k}_0", f"G{k}_1", f"G{k}_2"], names):
+            L.append(f"const T {nm} = {v if v is not None else 'T(0)'};")
             if tangent:
-                L.append(f"const T dS{k} = G{k}_0 * dy100 + G{k}_1 * dy010 + G{k}_2 * dy001;")
+                dv = P.d(v) if v is not None else None
+                L.append(f"const T d{nm} = {dv if dv else 'T(0)'};")
+        if n >= 1:
             L.append(f"const T yg{k} = y100 * G{k}_0 + y010 * G{k}_1 + y001 * G{k}_2;")
             if tangent:
                 L.append(f"const T dyg{k} = dy100 * G{k}_0 + y100 * dG{k}_0 + dy010 * G{k}_1 + y010 * dG{k}_1 + "
@@ -201,8 +212,6 @@ def _eval_stmts(p, tangent=False):
             if tangent:
                 L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k} + T(2) * dyg{k};")
         else:
-            if tangent:
-                L.append(f"const T dS{k} = T(0);")
             L.append(f"const T Q{k} = T({1 + 2 * k}) * S{k};")
             if tangent:
                 L.append(f"const T dQ{k} = T({1 + 2 * k}) * dS{k};")
@@ -430,14 +439,12 @@ def gen_eval(p):
             code.append("  " + "".join(parts))
         code.append("}")
         out.append("\n".join(code))
-    ns, ng = len(s_terms(p)), len(g_terms(p))
-    return "\n".join(out), ns, ng, fl
+    return "\n".join(out), len(s_terms(p)), fl
 
 
 def gen_record(p):
     """Raw moments -> scaled traced coefficients (FP64 arithmetic), in record order."""
     S = s_terms(p)
-    Gt = g_terms(p)
     ns = len(S)
     slot = layout(p)
     idx = {a: i for i, a in enumerate(midx(p))}
@@ -451,7 +458,6 @@ def gen_record(p):
     L.append("  rec[0] = T(inv_s); rec[1] = T((eps * inv_s) * (eps * inv_s));")
     L.append("  for (int d = 0; d < 3; ++d) { const T hi = T(z[d]); rec[2 + d] = hi; rec[5 + d] = T(z[d] - double(hi)); }")
     L.append(f"  double C[{ns}];")
-    sidx = {}
     for i, (k, n, b) in enumerate(S):
         m = n + k
         const = (-1) ** k * dfact(2 * m - 1) / (2 ** k * fact3(b))
@@ -461,11 +467,8 @@ def gen_record(p):
             terms.append(f"M[{idx[a]}] * {1.0 / fact3(l)!r}")
         L.append(f"  C[{i}] = G * ip[{1 + 2 * k + n}] * {const!r} * (" + " + ".join(terms) + ");")
         L.append(f"  rec[{slot[f'S,{k},{b[0]},{b[1]},{b[2]}']}] = T(C[{i}]);")
-        sidx[(k, b)] = i
-    for (k, d, b) in Gt:
-        L.append(f"  rec[{slot[f'G,{k},{d},{b[0]},{b[1]},{b[2]}']}] = T({b[d]}.0 * C[{sidx[(k, b)]}]);")
-    rl = (HDR + ns + len(Gt) + 3) // 4 * 4
-    for q in range(HDR + ns + len(Gt), rl):
+    rl = (HDR + ns + 3) // 4 * 4
+    for q in range(HDR + ns, rl):
         L.append(f"  rec[{q}] = T(0);")
     L.append("}")
     return "\n".join(L)
@@ -476,17 +479,13 @@ def main(out_path):
     parts.append("// Generated by gen_kernels.py -- do not edit by hand.\n#pragma once\n")
     parts.append(f"#define HOT_PMAX {PMAX}")
     parts.append(f"#define HOT_NCOMP_MAX {ncomp(PMAX)}")
-    recl, nsl, ngl, fll = [], [], [], []
+    recl, fll = [], []
     evals, records = [], []
     for p in range(PMAX + 1):
-        code, ns, ng, fl = gen_eval(p)
+        code, ns, fl = gen_eval(p)
         evals.append(code)
         records.append(gen_record(p))
-        rl = HDR + ns + ng
-        rl = (rl + 3) // 4 * 4
-        recl.append(rl)
-        nsl.append(ns)
-        ngl.append(ng)
+        recl.append((HDR + ns + 3) // 4 * 4)
         fll.append(fl)
     parts.append("static constexpr int HOT_REC_LEN[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, recl))))
     parts.append("static constexpr int M2P_FLOPS[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, fll))))
