@@ -320,8 +320,15 @@ def gen_cbar(p):
                 if n > p - 2 * k:
                     continue
                 L.append(f"  const T A{k}_{n} = a{k} + T({n}) * b{k};")
+                # two separate accumulations, each one fused multiply-add (a single
+                # expression would be evaluated as multiply, multiply-add and add)
                 for b in (midx(n)[ncomp(n - 1):] if n > 0 else [(0, 0, 0)]):
-                    L.append(f"  cb[{sidx[(k, n, b)]}] += A{k}_{n} * {mname(b)} + B{k} * D{mname(b)};")
+                    i = sidx[(k, n, b)]
+                    if n > 0:
+                        L.append(f"  cb[{i}] += A{k}_{n} * {mname(b)};")
+                        L.append(f"  cb[{i}] += B{k} * D{mname(b)};")
+                    else:
+                        L.append(f"  cb[{i}] += A{k}_{n};")
         L.append("}")
         out.append("\n".join(L))
     return "\n".join(out)

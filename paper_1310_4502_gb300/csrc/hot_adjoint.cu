@@ -119,9 +119,11 @@ __global__ void k_item_rows(const int64_t *__restrict__ start, const int64_t *__
 // groups are spread over the lanes.  Each lane accumulates the
 // coefficient adjoints in registers; the warp sum goes to part[item].
 // At p = 6 the 130 coefficient adjoints a lane accumulates fill every register; capped at
-// 168 (3 CTAs per SM) the kernel spills a few bytes and runs 6% faster than at 255.
+// 168 (3 CTAs per SM) the kernel spills a few bytes and runs 6% faster than at 255 (and
+// 15% faster than at 4 CTAs).  At p <= 4 (float) 4 CTAs per SM fit without spills and run
+// 8% faster than 1-3 (clustered 2^20).
 template <int P, class T>
-__global__ void __launch_bounds__(AW * 32, P >= 6 ? 3 : 1) k_adj_src(
+__global__ void __launch_bounds__(AW * 32, P >= 6 ? 3 : (P <= 4 && sizeof(T) == 4 ? 4 : 1)) k_adj_src(
     const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
     const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const T *__restrict__ rec,
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(AW * 32, P >= 6 ? 3 : 1) k_adj_src(
     constexpr int RL = ACfg<P, T>::RL;
     constexpr int NS = ACfg<P, T>::NS;
     __shared__ int32_t sbeg[AW][32], spre[AW][33];
+    __shared__ T red[AW][32][33];  // transpose of 32 lanes x 32 coefficients (padded row)
     const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t nitem = *nitem_p;
@@ -160,34 +163,51 @@ __global__ void __launch_bounds__(AW * 32, P >= 6 ? 3 : 1) k_adj_src(
         T cb[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) cb[q] = T(0);
+        // group of sink t: spre[j] <= t < spre[j+1]; t grows, so j only advances (and
+        // stays below ng, as t < total = spre[ng])
+        int j = 0;
         for (int t = lane; t < total; t += 32) {
-            int lo = 0, hi = ng;  // find j with spre[j] <= t < spre[j+1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (spre[wi][mid] <= t)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            const int64_t s = (int64_t)sbeg[wi][lo] + (t - spre[wi][lo]);
-            T rx, ry, rz;
+            while (spre[wi][j + 1] <= t) ++j;
+            const int64_t s = (int64_t)sbeg[wi][j] + (t - spre[wi][j]);
+            T rx, ry, rz, wx, wy, wz, wv;
             if constexpr (sizeof(T) == 4) {
-                rx = (xhl[8 * s + 0] - h[2]) + (xhl[8 * s + 4] - h[5]);
-                ry = (xhl[8 * s + 1] - h[3]) + (xhl[8 * s + 5] - h[6]);
-                rz = (xhl[8 * s + 2] - h[4]) + (xhl[8 * s + 6] - h[7]);
+                const float4 hi = reinterpret_cast<const float4 *>(xhl)[2 * s];
+                const float4 lo = reinterpret_cast<const float4 *>(xhl)[2 * s + 1];
+                rx = (hi.x - h[2]) + (lo.x - h[5]);
+                ry = (hi.y - h[3]) + (lo.y - h[6]);
+                rz = (hi.z - h[4]) + (lo.z - h[7]);
+                const float4 ww = reinterpret_cast<const float4 *>(w)[s];
+                wx = ww.x;
+                wy = ww.y;
+                wz = ww.z;
+                wv = ww.w;
             } else {
                 rx = spos[3 * s + 0] - h[2];
                 ry = spos[3 * s + 1] - h[3];
                 rz = spos[3 * s + 2] - h[4];
+                wx = w[4 * s + 0];
+                wy = w[4 * s + 1];
+                wz = w[4 * s + 2];
+                wv = w[4 * s + 3];
             }
-            m2p_cbar<P, T>(is, e2, rx, ry, rz, w[4 * s + 0], w[4 * s + 1], w[4 * s + 2], w[4 * s + 3], cb);
+            m2p_cbar<P, T>(is, e2, rx, ry, rz, wx, wy, wz, wv, cb);
         }
+        // warp sums, 32 coefficients at a time through shared memory: lane l writes its
+        // row, then sums column l (the 32 lanes' values of coefficient c0 + l, in lane order)
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            const T v = warp_sum(cb[q]);
-            if (lane == 0) part[it * NS + q] = v;
+        for (int c0 = 0; c0 < NS; c0 += 32) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (c0 + q < NS) red[wi][lane][q] = cb[c0 + q];
+            __syncwarp();
+            if (c0 + (int)lane < NS) {
+                T v = T(0);
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) v += red[wi][l][lane];
+                part[it * NS + c0 + lane] = v;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -603,119 +623,130 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
     HOT_COUNT_LAUNCH();
     k_adj_prep<T><<<hot_blocks(N, 256), 256, 0, s>>>(g_acc, g_pot, c->idx.p, c->spos.p, N, w, c->adj_xhl.p);
 
-    // sink side (interaction kernel in adjoint mode)
+    // sink side (interaction kernel in adjoint mode) on the second stream, concurrent with
+    // the source side below (they share no buffer the other writes): each fills the
+    // other's tail of idle SMs
     HOT_CK(c->adj_gsink.ensure(3 * (size_t)N, s));
-    int r = hot_impl_adjoint_sink(c, w, c->adj_gsink.p);
+    HOT_CK(cudaEventRecord(c->ev_fork, s));
+    HOT_CK(cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+    int r = hot_impl_adjoint_sink(c, w, c->adj_gsink.p, c->st2);
+    auto source_side = [&]() -> int {
+        int r = HOT_OK;
+        // source side of M2P: transpose the lists, coefficient adjoints per item
+        const int64_t nm = c->n_m2p;
+        int bits = 1;
+        while ((int64_t(1) << bits) <= nc) ++bits;
+        HOT_CK(c->tp_key.ensure(nm + 1, s));
+        HOT_CK(c->tp_key2.ensure(nm + 1, s));
+        HOT_CK(c->tp_val.ensure(nm + 1, s));
+        HOT_CK(c->tp_val2.ensure(nm + 1, s));
+        HOT_CK(c->tp_start.ensure(nc + 1, s));
+        HOT_CK(c->tp_end.ensure(nc + 1, s));
+        HOT_CK(c->it_cnt.ensure(nc + 1, s));
+        HOT_CK(c->it_off.ensure(nc + 1, s));
+        HOT_CK(c->adj_mbar.ensure((size_t)NC * nc, s));
+        HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(nc + 64), s));
+        HOT_CK(cudaMemsetAsync(c->adj_mbar.p, 0, sizeof(double) * NC * (size_t)nc, s));
+        if (nm > 0) {
+            HOT_COUNT_LAUNCH();
+            k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_m2p.p, c->l_m2p.p, ng, c->tp_key.p, c->tp_val.p);
+            r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, nm, bits);
+            if (r) return r;
+            HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
+            HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
+            HOT_COUNT_LAUNCH();
+            k_ranges<<<hot_blocks(nm, 256), 256, 0, s>>>(c->tp_key.p, nm, c->tp_start.p, c->tp_end.p);
+            HOT_COUNT_LAUNCH();
+            k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
+            r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
+            if (r) return r;
+            const int64_t max_items = nm / KG + nc + 1;
+            HOT_CK(c->it_cell.ensure(max_items, s));
+            HOT_CK(c->it_a.ensure(max_items, s));
+            HOT_CK(c->it_b.ensure(max_items, s));
+            HOT_CK(c->it_part.ensure(sizeof(T) * NS * (size_t)max_items, s));
+            HOT_COUNT_LAUNCH();
+            k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
+                                                                c->it_a.p, c->it_b.p);
+            T *part = (T *)c->it_part.p;
+            unsigned *swork = (unsigned *)(c->sizes.p + 63);
+            HOT_CK(cudaMemsetAsync(swork, 0, sizeof(unsigned), s));
+            HOT_COUNT_LAUNCH();
+            k_adj_src<P, T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
+                                                          c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, rec, w,
+                                                          c->adj_xhl.p, c->spos.p, nullptr, swork, part);
+            HOT_COUNT_LAUNCH();
+            k_adj_cells<P, T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(nc, c->it_off.p, part, rec,
+                                                                                  c->prm.G, c->adj_mbar.p);
+        }
+        // push dL/dM down the tree, level by level
+        for (int l = 1; l <= (int)c->maxlevel; ++l) {
+            const int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
+            if (n <= 0) continue;
+            HOT_COUNT_LAUNCH();
+            k_adj_l2l<P><<<hot_blocks(n, AW, c->nsm * 16), AW * 32, 0, s>>>(c->level_cells.p + a, n, c->cparent.p,
+                                                                           c->ccom.p, c->adj_mbar.p);
+        }
+
+        // source side of P2P: transpose the leaf lists
+        const int64_t np = c->n_p2p;
+        HOT_CK(c->adj_gp2p.ensure(4 * (size_t)N, s));
+        HOT_CK(cudaMemsetAsync(c->adj_gp2p.p, 0, sizeof(double) * 4 * (size_t)N, s));
+        if (np > 0) {
+            HOT_CK(c->tp_key.ensure(np + 1, s));
+            HOT_CK(c->tp_key2.ensure(np + 1, s));
+            HOT_CK(c->tp_val.ensure(np + 1, s));
+            HOT_CK(c->tp_val2.ensure(np + 1, s));
+            HOT_COUNT_LAUNCH();
+            k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_p2p.p, c->l_p2p.p, ng, c->tp_key.p, c->tp_val.p);
+            r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, np, bits);
+            if (r) return r;
+            HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
+            HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
+            HOT_COUNT_LAUNCH();
+            k_ranges<<<hot_blocks(np, 256), 256, 0, s>>>(c->tp_key.p, np, c->tp_start.p, c->tp_end.p);
+            // work items: a leaf and up to KG of the groups that list it
+            const int64_t max_items = np / KG + nc + 1;
+            // rows: sum over leaves of items x particles <= (source-particle visits) / KG + N
+            const int64_t max_rows = c->n_p2p_src / KG + N + 1;
+            HOT_CK(c->it_cell.ensure(max_items, s));
+            HOT_CK(c->it_a.ensure(max_items, s));
+            HOT_CK(c->it_b.ensure(max_items, s));
+            HOT_CK(c->adj_roff.ensure(nc + 1, s));
+            HOT_CK(c->adj_pp.ensure(sizeof(T) * 4 * (size_t)max_rows, s));
+            HOT_COUNT_LAUNCH();
+            k_item_rows<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->ccount.p, c->cnchild.p, nc,
+                                                            c->it_cnt.p + 0);
+            r = hot_scan_u32_to_i64(c->it_cnt.p, c->adj_roff.p, nc, c->scan_tmp.p, s);
+            if (r) return r;
+            HOT_COUNT_LAUNCH();
+            k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
+            r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
+            if (r) return r;
+            HOT_COUNT_LAUNCH();
+            k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
+                                                                c->it_a.p, c->it_b.p);
+            unsigned *pwork = (unsigned *)(c->sizes.p + 62);
+            HOT_CK(cudaMemsetAsync(pwork, 0, sizeof(unsigned), s));
+            T *pp = (T *)c->adj_pp.p;
+            HOT_COUNT_LAUNCH();
+            k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
+                                                            c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
+                                                            c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
+                                                            (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
+                                                            pwork, pp);
+            HOT_COUNT_LAUNCH();
+            k_adj_p2p_combine<T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(
+                nc, c->cnchild.p, c->it_off.p, c->adj_roff.p, c->cbegin.p, c->ccount.p, c->smass.p, pp, c->prm.G,
+                c->adj_gp2p.p);
+        }
+        return HOT_OK;
+    };
+    if (r == HOT_OK) r = source_side();
+    // join (also after an error, so that no work of this call is left behind on st2)
+    HOT_CK(cudaEventRecord(c->ev_join, c->st2));
+    HOT_CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     if (r) return r;
-
-    // source side of M2P: transpose the lists, coefficient adjoints per item
-    const int64_t nm = c->n_m2p;
-    int bits = 1;
-    while ((int64_t(1) << bits) <= nc) ++bits;
-    HOT_CK(c->tp_key.ensure(nm + 1, s));
-    HOT_CK(c->tp_key2.ensure(nm + 1, s));
-    HOT_CK(c->tp_val.ensure(nm + 1, s));
-    HOT_CK(c->tp_val2.ensure(nm + 1, s));
-    HOT_CK(c->tp_start.ensure(nc + 1, s));
-    HOT_CK(c->tp_end.ensure(nc + 1, s));
-    HOT_CK(c->it_cnt.ensure(nc + 1, s));
-    HOT_CK(c->it_off.ensure(nc + 1, s));
-    HOT_CK(c->adj_mbar.ensure((size_t)NC * nc, s));
-    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(nc + 64), s));
-    HOT_CK(cudaMemsetAsync(c->adj_mbar.p, 0, sizeof(double) * NC * (size_t)nc, s));
-    if (nm > 0) {
-        HOT_COUNT_LAUNCH();
-        k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_m2p.p, c->l_m2p.p, ng, c->tp_key.p, c->tp_val.p);
-        r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, nm, bits);
-        if (r) return r;
-        HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
-        HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
-        HOT_COUNT_LAUNCH();
-        k_ranges<<<hot_blocks(nm, 256), 256, 0, s>>>(c->tp_key.p, nm, c->tp_start.p, c->tp_end.p);
-        HOT_COUNT_LAUNCH();
-        k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
-        r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
-        if (r) return r;
-        const int64_t max_items = nm / KG + nc + 1;
-        HOT_CK(c->it_cell.ensure(max_items, s));
-        HOT_CK(c->it_a.ensure(max_items, s));
-        HOT_CK(c->it_b.ensure(max_items, s));
-        HOT_CK(c->it_part.ensure(sizeof(T) * NS * (size_t)max_items, s));
-        HOT_COUNT_LAUNCH();
-        k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
-                                                            c->it_a.p, c->it_b.p);
-        T *part = (T *)c->it_part.p;
-        unsigned *swork = (unsigned *)(c->sizes.p + 63);
-        HOT_CK(cudaMemsetAsync(swork, 0, sizeof(unsigned), s));
-        HOT_COUNT_LAUNCH();
-        k_adj_src<P, T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
-                                                      c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, rec, w,
-                                                      c->adj_xhl.p, c->spos.p, nullptr, swork, part);
-        HOT_COUNT_LAUNCH();
-        k_adj_cells<P, T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(nc, c->it_off.p, part, rec,
-                                                                              c->prm.G, c->adj_mbar.p);
-    }
-    // push dL/dM down the tree, level by level
-    for (int l = 1; l <= (int)c->maxlevel; ++l) {
-        const int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
-        if (n <= 0) continue;
-        HOT_COUNT_LAUNCH();
-        k_adj_l2l<P><<<hot_blocks(n, AW, c->nsm * 16), AW * 32, 0, s>>>(c->level_cells.p + a, n, c->cparent.p,
-                                                                       c->ccom.p, c->adj_mbar.p);
-    }
-
-    // source side of P2P: transpose the leaf lists
-    const int64_t np = c->n_p2p;
-    HOT_CK(c->adj_gp2p.ensure(4 * (size_t)N, s));
-    HOT_CK(cudaMemsetAsync(c->adj_gp2p.p, 0, sizeof(double) * 4 * (size_t)N, s));
-    if (np > 0) {
-        HOT_CK(c->tp_key.ensure(np + 1, s));
-        HOT_CK(c->tp_key2.ensure(np + 1, s));
-        HOT_CK(c->tp_val.ensure(np + 1, s));
-        HOT_CK(c->tp_val2.ensure(np + 1, s));
-        HOT_COUNT_LAUNCH();
-        k_expand_pairs<<<hot_blocks(ng * 32, 256), 256, 0, s>>>(c->off_p2p.p, c->l_p2p.p, ng, c->tp_key.p, c->tp_val.p);
-        r = hot_sort_pairs(c, c->tp_key.p, c->tp_val.p, c->tp_key2.p, c->tp_val2.p, np, bits);
-        if (r) return r;
-        HOT_CK(cudaMemsetAsync(c->tp_start.p, 0, sizeof(int64_t) * (nc + 1), s));
-        HOT_CK(cudaMemsetAsync(c->tp_end.p, 0, sizeof(int64_t) * (nc + 1), s));
-        HOT_COUNT_LAUNCH();
-        k_ranges<<<hot_blocks(np, 256), 256, 0, s>>>(c->tp_key.p, np, c->tp_start.p, c->tp_end.p);
-        // work items: a leaf and up to KG of the groups that list it
-        const int64_t max_items = np / KG + nc + 1;
-        // rows: sum over leaves of items x particles <= (source-particle visits) / KG + N
-        const int64_t max_rows = c->n_p2p_src / KG + N + 1;
-        HOT_CK(c->it_cell.ensure(max_items, s));
-        HOT_CK(c->it_a.ensure(max_items, s));
-        HOT_CK(c->it_b.ensure(max_items, s));
-        HOT_CK(c->adj_roff.ensure(nc + 1, s));
-        HOT_CK(c->adj_pp.ensure(sizeof(T) * 4 * (size_t)max_rows, s));
-        HOT_COUNT_LAUNCH();
-        k_item_rows<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->ccount.p, c->cnchild.p, nc,
-                                                        c->it_cnt.p + 0);
-        r = hot_scan_u32_to_i64(c->it_cnt.p, c->adj_roff.p, nc, c->scan_tmp.p, s);
-        if (r) return r;
-        HOT_COUNT_LAUNCH();
-        k_item_count_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, nc, c->it_cnt.p);
-        r = hot_scan_u32_to_u32(c->it_cnt.p, c->it_off.p, nc, c->scan_tmp.p, s);
-        if (r) return r;
-        HOT_COUNT_LAUNCH();
-        k_item_fill_adj<<<hot_blocks(nc, 256), 256, 0, s>>>(c->tp_start.p, c->tp_end.p, c->it_off.p, nc, c->it_cell.p,
-                                                            c->it_a.p, c->it_b.p);
-        unsigned *pwork = (unsigned *)(c->sizes.p + 62);
-        HOT_CK(cudaMemsetAsync(pwork, 0, sizeof(unsigned), s));
-        T *pp = (T *)c->adj_pp.p;
-        HOT_COUNT_LAUNCH();
-        k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
-                                                        c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
-                                                        c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
-                                                        (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
-                                                        pwork, pp);
-        HOT_COUNT_LAUNCH();
-        k_adj_p2p_combine<T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(
-            nc, c->cnchild.p, c->it_off.p, c->adj_roff.p, c->cbegin.p, c->ccount.p, c->smass.p, pp, c->prm.G,
-            c->adj_gp2p.p);
-    }
 
     // leaves: transposed P2M and the final sums, original order
     HOT_COUNT_LAUNCH();

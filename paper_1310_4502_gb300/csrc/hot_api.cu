@@ -89,6 +89,12 @@ int hot_create(hot_ctx **out, const hot_params *prm, void *cuda_stream)
     cudaMemset(c->d_status, 0, sizeof(unsigned));
     c->h_status = nullptr;
     for (int k = 0; k < ST_TIMING_EVENTS; ++k) cudaEventCreate(&c->ev[k]);
+    if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        hot_destroy(c);
+        return HOT_ECUDA;
+    }
     *out = c;
     return HOT_OK;
 }
@@ -298,6 +304,7 @@ void hot_destroy(hot_ctx *c)
     c->l_m2p.release(s); c->l_p2p.release(s); c->trav_scratch.release(s); c->pairs_per_group.release(s);
     c->tcell.release(s); c->tcellf.release(s); c->slot_m2p.release(s); c->slot_p2p.release(s);
     c->gkey.release(s); c->gkey2.release(s); c->gorder.release(s); c->gorder2.release(s);
+    c->slice_cnt.release(s); c->slice_off.release(s); c->items.release(s);
     c->adj_w.release(s); c->adj_xhl.release(s); c->adj_gsink.release(s); c->adj_gp2p.release(s);
     c->adj_mbar.release(s); c->adj_cbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);
     c->tp_val.release(s); c->tp_val2.release(s); c->tp_start.release(s); c->tp_end.release(s);
@@ -307,6 +314,12 @@ void hot_destroy(hot_ctx *c)
     if (c->d_status) cudaFree(c->d_status);
     for (int k = 0; k < ST_TIMING_EVENTS; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->st2) {
+        cudaStreamSynchronize(c->st2);
+        cudaStreamDestroy(c->st2);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -87,6 +87,10 @@ struct alignas(32) TCellF {
 struct hot_ctx {
     hot_params prm;
     cudaStream_t st = nullptr;
+    // second stream: the adjoint's sink pass runs on it beside the source side, forked from
+    // and joined back into st by the two events
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int dev = 0, nsm = 0;
     int stage = 0;  // 0 created, 1 tree, 2 moments, 3 lists
     int64_t N = 0;
@@ -158,8 +162,10 @@ struct hot_ctx {
     // per-group slot capacities of the one-pass traversal (grown from the counts seen)
     int64_t slot_capm = 2048, slot_capp = 512;
     DBuf<int32_t> slot_m2p, slot_p2p;
-    DBuf<uint64_t> gkey, gkey2;      // per-group interaction cost keys (largest first)
-    DBuf<uint32_t> gorder, gorder2;  // groups in the order the interaction kernels take them
+    DBuf<uint64_t> gkey, gkey2;      // per-group cost keys of one 32-sink slice (largest first)
+    DBuf<uint32_t> gorder, gorder2;  // groups in descending slice cost
+    DBuf<uint32_t> slice_cnt, slice_off;  // 32-sink slices per group (sorted order), offsets
+    DBuf<uint64_t> items;            // work items of the interaction kernels: group << 32 | first sink
     DBuf<int64_t> pairs_per_group;
 
     // status
@@ -219,7 +225,7 @@ int hot_impl_traverse(hot_ctx *c, double tol);
 int hot_impl_forces(hot_ctx *c, double *acc, double *pot);
 int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos,
                      double *g_mass);
-int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink);
+int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink, cudaStream_t s);
 int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, int64_t n, int bits);
 
 // ---------------------------------------------------------------------------

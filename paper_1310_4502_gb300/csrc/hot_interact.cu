@@ -3,9 +3,11 @@
 // source cells and n sink particles; the source data is reorganised once per block
 // and shared by the n sinks).
 //
-// One warp per sink group (dynamic work counter).  The group's sinks are taken 32 at a
-// time, one sink per lane; when a slice has fewer than 32 sinks, each sink gets several
-// lanes that split the source lists (combined at the end in float64).
+// One warp per work item, a slice of 32 sinks of one group (dynamic work counter over
+// the items, which come in descending order of their cost), one sink per lane; when a
+// slice has fewer than 32 sinks, each sink gets several lanes that split the source
+// lists (combined at the end in float64).  Taking slices rather than whole groups as
+// items keeps one large group from being a single warp's work at the end of the launch.
 //
 // Cell records (the traced coefficients of every accepted cell) are staged per warp in
 // shared memory by TMA bulk copies (cp.async.bulk, completion on an mbarrier), double
@@ -393,19 +395,19 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 }
 
 // cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
-// Occupancy: 4 CTAs per SM (128 registers) up to p = 4; the larger expansions of p >= 5
-// run faster with more registers and fewer CTAs (3 for the forces, 2 for the adjoint's
-// tangent evaluation), measured on the clustered 2^20 and lattice 128^3 workloads.
+// Occupancy (measured on the clustered 2^20 and lattice 128^3 workloads): the forces run
+// at 5 CTAs per SM (102 registers; 4% faster than 4 at p = 4, 3% at p = 6); the adjoint's
+// tangent evaluation at 4 up to p = 4 and at 2 for p >= 5 (no faster at 3 or 4).
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
-// NS = 2: two sinks per lane (slices of 64 sinks).
+// NS = 2: two sinks per lane (slices of 64 sinks: the items at even 32-sink positions).
 template <int P, class T, int NS, int MODE>
-__global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_interact(
-    int64_t ngroup, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
+__global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : 5) k_interact(
+    const uint32_t *__restrict__ nitem_p, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const int32_t *__restrict__ cend,
     const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
     const double *__restrict__ ccom, const T *__restrict__ rec, const int64_t *__restrict__ off_m2p, const int32_t *__restrict__ l_m2p,
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
-    const uint32_t *__restrict__ gorder, T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
+    const uint64_t *__restrict__ items, T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
     const T *__restrict__ wsink, double *__restrict__ gsink, uint32_t wait_limit, int probe,
     unsigned *__restrict__ status)
 {
@@ -425,12 +427,16 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
     __syncwarp();
     uint32_t phase[2] = {0u, 0u};
 
+    const int64_t nitem = *nitem_p;
     for (;;) {
-        unsigned g0 = 0;
-        if (lane == 0) g0 = atomicAdd(work, 1u);
-        const int64_t gi = __shfl_sync(0xffffffffu, g0, 0);
-        if (gi >= ngroup) break;
-        const int64_t g = gorder[gi];  // largest interaction cost first
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(work, 1u);
+        const int64_t ii = __shfl_sync(0xffffffffu, i0, 0);
+        if (ii >= nitem) break;
+        const uint64_t item = items[ii];  // largest slice cost first
+        const int64_t g = (int64_t)(item >> 32);
+        const int s0 = (int)(uint32_t)item;
+        if (s0 % SL != 0) continue;  // two sinks per lane: one item per 64-sink slice
         const int32_t gc = gcell[g];
         Group<T> Gr;
         Gr.n = ccount[gc];
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
         Gr.p1 = off_p2p[g + 1];
         Gr.own0 = gc;
         Gr.own1 = cend[gc];
-        for (int s0 = 0; s0 < Gr.n; s0 += SL) {
+        {
             const int rem = Gr.n - s0;
             int ns, nsplit, si, sj;
             if (NS == 1) {
@@ -541,9 +547,9 @@ __global__ void __launch_bounds__(IW * 32, P >= 5 ? (MODE == 1 ? 2 : 3) : 4) k_i
 }
 
 template <int P, class T, int NS, int MODE>
-int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *pot, const T *wsink, double *gsink)
+int launch_interact(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double *acc, double *pot, const T *wsink,
+                    double *gsink)
 {
-    cudaStream_t s = c->st;
     const size_t smem = sizeof(Smem<P, T>) * IW;
     auto kern = k_interact<P, T, NS, MODE>;
     HOT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -559,10 +565,10 @@ int launch_interact(hot_ctx *c, int cls, unsigned *work, double *acc, double *po
     const int blocks = c->nsm * occ;
     const T eps2 = (T)(c->prm.eps * c->prm.eps);
     HOT_COUNT_LAUNCH();
-    kern<<<blocks, IW * 32, smem, s>>>(c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->cend.p,
+    kern<<<blocks, IW * 32, smem, s>>>(c->slice_off.p + c->ngroup, cls, c->gcell.p, c->gcen.p, c->cbegin.p, c->ccount.p, c->cend.p,
                                        c->spos.p,
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
-                                       c->l_p2p.p, c->idx.p, c->gorder.p, eps2, c->prm.G, work, acc, pot, wsink,
+                                       c->l_p2p.p, c->idx.p, c->items.p, eps2, c->prm.G, work, acc, pot, wsink,
                                        gsink, c->wait_polls ? c->wait_polls : WAIT_LIMIT, c->wait_probe,
                                        c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
@@ -573,15 +579,15 @@ int forces_p(hot_ctx *c, double *acc, double *pot)
 {
     unsigned *work = (unsigned *)(c->sizes.p + 56);
     if (c->prm.precision == HOT_FP64)
-        return launch_interact<P, double, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
+        return launch_interact<P, double, 1, 0>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
     if constexpr (P >= 5) {
         // large expansions: groups of more than 32 sinks run two sinks per lane, so that
         // every coefficient read from shared memory feeds two independent evaluations
-        int r = launch_interact<P, float, 1, 0>(c, 1, work, acc, pot, nullptr, nullptr);
+        int r = launch_interact<P, float, 1, 0>(c, c->st, 1, work, acc, pot, nullptr, nullptr);
         if (r) return r;
-        return launch_interact<P, float, 2, 0>(c, 2, work, acc, pot, nullptr, nullptr);
+        return launch_interact<P, float, 2, 0>(c, c->st, 2, work, acc, pot, nullptr, nullptr);
     }
-    return launch_interact<P, float, 1, 0>(c, 0, work, acc, pot, nullptr, nullptr);
+    return launch_interact<P, float, 1, 0>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
 }
 
 }  // namespace
@@ -606,16 +612,16 @@ int hot_impl_forces(hot_ctx *c, double *acc, double *pot)
 
 // Sink side of the adjoint: for every sink, d/dx_i of sum over its interactions of
 // (u_i . a_i + v_i phi_i), with (u_i, v_i) = wsink[slot] (T4, sorted order); written to
-// gsink [N][3] (float64, sorted order).
-int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink)
+// gsink [N][3] (float64, sorted order).  Launched on stream s.
+int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink, cudaStream_t s)
 {
     unsigned *work = (unsigned *)(c->sizes.p + 56);
 #define HOT_ADJ_SINK(PP)                                                                                 \
     case PP:                                                                                             \
         if (c->prm.precision == HOT_FP64)                                                                \
-            return launch_interact<PP, double, 1, 1>(c, 0, work, nullptr, nullptr, (const double *)wsink, \
+            return launch_interact<PP, double, 1, 1>(c, s, 0, work, nullptr, nullptr, (const double *)wsink, \
                                                      gsink);                                             \
-        return launch_interact<PP, float, 1, 1>(c, 0, work, nullptr, nullptr, (const float *)wsink, gsink);
+        return launch_interact<PP, float, 1, 1>(c, s, 0, work, nullptr, nullptr, (const float *)wsink, gsink);
     switch (c->p_mom) {
         HOT_ADJ_SINK(0)
         HOT_ADJ_SINK(1)

@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 atomicMax(&maxc[0], (unsigned long long)nm);
                 atomicMax(&maxc[1], (unsigned long long)np);
                 atomicAdd(&maxc[3], (unsigned long long)p2p_parts);  // source-particle visits
-                // interaction cost of the group (one M2P evaluation ~ 10 P2P source visits per
-                // 32-sink slice), as an ascending sort key for largest-first processing
-                const uint64_t cost = (ns + 31) / 32 * (10ull * nm + p2p_parts);
+                // interaction cost of one 32-sink slice of the group (one M2P evaluation ~ 10
+                // P2P source visits), as an ascending sort key for largest-first processing
+                const uint64_t cost = 10ull * nm + p2p_parts;
                 gkey[g] = 0xffffffffull - (cost < 0xffffffffull ? cost : 0xffffffffull);
                 if (SLOTS && ((int64_t)nm > capm || (int64_t)np > capp)) atomicOr(slot_over, 1u);
             }
@@ -282,6 +282,25 @@ __global__ void k_iota(uint32_t *__restrict__ v, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = (uint32_t)i;
+}
+
+// Number of 32-sink slices of every group, in the sorted group order.
+__global__ void k_slice_count(const uint32_t *__restrict__ gorder, const int32_t *__restrict__ gcell,
+                              const int32_t *__restrict__ ccount, int64_t ng, uint32_t *__restrict__ cnt)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < ng) cnt[j] = (uint32_t)((ccount[gcell[gorder[j]]] + 31) / 32);
+}
+
+// Work items: the slices of every group, groups in the sorted order, each item the group
+// index (high word) and its first sink within the group (low word).
+__global__ void k_slice_fill(const uint32_t *__restrict__ gorder, const uint32_t *__restrict__ off, int64_t ng,
+                             uint64_t *__restrict__ items)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ng) return;
+    const uint64_t g = gorder[j];
+    for (uint32_t q = off[j]; q < off[j + 1]; ++q) items[q] = (g << 32) | (uint64_t)((q - off[j]) * 32u);
 }
 
 // Copy every group's slot entries to its CSR range (one warp per group, in order).
@@ -398,11 +417,22 @@ int hot_impl_traverse(hot_ctx *c, double tol)
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }
-    // group order for the interactions: largest cost first (stable, so ties keep index order)
+    // work order of the interactions: groups by descending slice cost (stable, so ties keep
+    // index order), each expanded into its 32-sink slices, so that no single large group
+    // is one warp's work
     HOT_COUNT_LAUNCH();
     k_iota<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, ng);
     int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 32);
     if (rs) return rs;
+    HOT_CK(c->slice_cnt.ensure(ng + 1, s));
+    HOT_CK(c->slice_off.ensure(ng + 1, s));
+    HOT_CK(c->items.ensure(ng + c->N / 32 + 1, s));
+    HOT_COUNT_LAUNCH();
+    k_slice_count<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->gcell.p, c->ccount.p, ng, c->slice_cnt.p);
+    rs = hot_scan_u32_to_u32(c->slice_cnt.p, c->slice_off.p, ng, c->scan_tmp.p, s);
+    if (rs) return rs;
+    HOT_COUNT_LAUNCH();
+    k_slice_fill<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->slice_off.p, ng, c->items.p);
     hot_toc(c, 3);
     if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     c->tol_lists = tol;
