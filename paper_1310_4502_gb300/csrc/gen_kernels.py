@@ -118,35 +118,57 @@ class _Prog:
         return name
 
 
-def _horner_grad(P, X, n, ref):
+def _horner_grad(P, X, n, ref, hess=False):
     """The polynomial X(y) = sum_{|g| <= n} c_g y^g and its gradient from the
     coefficients c_g alone: nested Horner in y_z (inner), y_y, y_x (outer), each chain
     carrying its derivative in its own variable (d <- d y + h before h <- h y + c), and
     the y_z- and y_y-derivatives of the inner chains carried through the outer ones.
-    Returns the names of X, dX/dy_x, dX/dy_y, dX/dy_z (None where identically zero)."""
+    With hess, the second derivatives as well: a second-derivative chain e <- e y + d
+    (before d is updated) gives half the pure second derivative, a derivative chain over
+    an outer variable of a carried first derivative gives the mixed one.
+    Returns the names of X, dX/dy_x, dX/dy_y, dX/dy_z and, with hess, of X_xx/2, X_xy,
+    X_xz, X_yy/2, X_yz, X_zz/2 (None where identically zero)."""
+    f = P.fma
     S = Sx = Sy = Sz = None
+    Sxxh = Sxy = Sxz = Syyh = Syz = Szzh = None
     for i in range(n, -1, -1):
-        t = ty = tz = None
+        t = ty = tz = tyyh = tyz = tzzh = None
         for j in range(n - i, -1, -1):
             m = n - i - j
-            h, hz = ref(i, j, m), None
+            h, hz, hzzh = ref(i, j, m), None, None
             for l in range(m - 1, -1, -1):
-                hz = h if hz is None else P.fma(f"hz{X}_{i}_{j}_{l}", h, "y001", hz)
-                h = P.fma(f"h{X}_{i}_{j}_{l}", ref(i, j, l), "y001", h)
+                if hess:
+                    hzzh = f(f"hzz{X}_{i}_{j}_{l}", hz, "y001", hzzh)
+                hz = h if hz is None else f(f"hz{X}_{i}_{j}_{l}", h, "y001", hz)
+                h = f(f"h{X}_{i}_{j}_{l}", ref(i, j, l), "y001", h)
             if t is None:
-                t, tz = h, hz
+                t, tz, tzzh = h, hz, hzzh
             else:
-                ty = t if ty is None else P.fma(f"ty{X}_{i}_{j}", t, "y010", ty)
-                t = P.fma(f"t{X}_{i}_{j}", h, "y010", t)
-                tz = hz if tz is None else P.fma(f"tz{X}_{i}_{j}", hz, "y010", tz)
+                if hess:
+                    tyyh = f(f"tyy{X}_{i}_{j}", ty, "y010", tyyh)
+                    tyz = f(f"tyz{X}_{i}_{j}", tz, "y010", tyz)
+                    tzzh = f(f"tzz{X}_{i}_{j}", hzzh, "y010", tzzh)
+                ty = t if ty is None else f(f"ty{X}_{i}_{j}", t, "y010", ty)
+                t = f(f"t{X}_{i}_{j}", h, "y010", t)
+                tz = hz if tz is None else f(f"tz{X}_{i}_{j}", hz, "y010", tz)
         if S is None:
-            S, Sy, Sz = t, ty, tz
+            S, Sy, Sz, Syyh, Syz, Szzh = t, ty, tz, tyyh, tyz, tzzh
         else:
-            Sx = S if Sx is None else P.fma(f"sx{X}_{i}", S, "y100", Sx)
-            S = P.fma(f"s{X}_{i}", t, "y100", S)
-            Sy = ty if Sy is None else P.fma(f"sy{X}_{i}", ty, "y100", Sy)
-            Sz = tz if Sz is None else P.fma(f"sz{X}_{i}", tz, "y100", Sz)
-    return S, Sx, Sy, Sz
+            if hess:
+                Sxxh = f(f"sxx{X}_{i}", Sx, "y100", Sxxh)
+                Sxy = f(f"sxy{X}_{i}", Sy, "y100", Sxy)
+                Sxz = f(f"sxz{X}_{i}", Sz, "y100", Sxz)
+                Syyh = f(f"syy{X}_{i}", tyyh, "y100", Syyh)
+                Syz = f(f"syz{X}_{i}", tyz, "y100", Syz)
+                Szzh = f(f"szz{X}_{i}", tzzh, "y100", Szzh)
+            Sx = S if Sx is None else f(f"sx{X}_{i}", S, "y100", Sx)
+            S = f(f"s{X}_{i}", t, "y100", S)
+            Sy = ty if Sy is None else f(f"sy{X}_{i}", ty, "y100", Sy)
+            Sz = tz if Sz is None else f(f"sz{X}_{i}", tz, "y100", Sz)
+    out = [S, Sx, Sy, Sz]
+    if hess:
+        out += [Sxxh, Sxy, Sxz, Syyh, Syz, Szzh]
+    return out
 
 
 def _horner_w(dst, names, tangent):
@@ -195,14 +217,26 @@ def _eval_stmts(p, tangent=False):
     K = p // 2
     for k in range(K + 1):
         n = p - 2 * k
-        P = _Prog(tangent)
-        names = _horner_grad(P, f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@")
+        # with tangent, the Hessian of S_k applied to dy gives the tangents of the gradient
+        # (no forward-mode chains)
+        P = _Prog(False)
+        names = _horner_grad(P, f"S{k}", n, lambda i, j, l, k=k: f"@S,{k},{i},{j},{l}@", hess=tangent)
         L += P.L
-        for nm, v in zip([f"S{k}", f"G{k}_0", f"G{k}_1", f"G{k}_2"], names):
+        for nm, v in zip([f"S{k}", f"G{k}_0", f"G{k}_1", f"G{k}_2"], names[:4]):
             L.append(f"const T {nm} = {v if v is not None else 'T(0)'};")
-            if tangent:
-                dv = P.d(v) if v is not None else None
-                L.append(f"const T d{nm} = {dv if dv else 'T(0)'};")
+        if tangent:
+            dy = ("dy100", "dy010", "dy001")
+
+            def lin(terms):
+                t = [f"{c}{a} * {b}" for c, a, b in terms if a is not None]
+                return " + ".join(t) if t else "T(0)"
+            L.append(f"const T dS{k} = " + lin([("", f"G{k}_{d}", dy[d]) for d in range(3)]) + ";")
+            hxx, hxy, hxz, hyy, hyz, hzz = names[4:]
+            hm = [[(hxx, "T(2) * "), (hxy, ""), (hxz, "")],
+                  [(hxy, ""), (hyy, "T(2) * "), (hyz, "")],
+                  [(hxz, ""), (hyz, ""), (hzz, "T(2) * ")]]
+            for d in range(3):
+                L.append(f"const T dG{k}_{d} = " + lin([(c, a, dy[e]) for e, (a, c) in enumerate(hm[d])]) + ";")
         if n >= 1:
             L.append(f"const T yg{k} = y100 * G{k}_0 + y010 * G{k}_1 + y001 * G{k}_2;")
             if tangent:
