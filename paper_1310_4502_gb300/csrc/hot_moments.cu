@@ -120,13 +120,17 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
 }
 
 // ---------------------------------------------------------------------------
-// M2M for the inner cells of one level: one warp per cell, lanes over components.
-// M_a(z) = sum_children sum_{b <= a} C(a,b) M_b(z_ch) (z_ch - z)^{a-b}.  The binomial
-// translation factorises over the axes, so it is applied as three one-dimensional
-// translations (x, then y, then z):
+// M2M for the inner cells of one level: one block of 8 warps per cell, warp o
+// translating child o (lanes over components), the children's rows summed in child
+// order.  M_a(z) = sum_children sum_{b <= a} C(a,b) M_b(z_ch) (z_ch - z)^{a-b}.  The
+// binomial translation factorises over the axes, so it is applied as three
+// one-dimensional translations (x, then y, then z):
 //   T1(i,j,k) = sum_{i' <= i} C(i,i') dx^{i-i'} M(i',j,k),  then likewise in j and in k,
-// at most p+1 terms per component and pass (float64 throughout).
+// at most p+1 terms per component and pass, each one fused multiply-add with the
+// factor C(e,e') d^{e-e'} taken from a per-child table (float64 throughout).
 // ---------------------------------------------------------------------------
+constexpr int M2M_W = 8;  // warps per block: one per child octant
+
 __device__ __forceinline__ int mom_index(int i, int j, int k)
 {
     const int n = i + j + k;
@@ -134,17 +138,19 @@ __device__ __forceinline__ int mom_index(int i, int j, int k)
 }
 
 template <int P>
-__global__ void __launch_bounds__(MW * 32) k_m2m_level(
+__global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
     const int32_t *__restrict__ cells, int64_t ncells_lvl, const int32_t *__restrict__ child8,
     const int32_t *__restrict__ cnchild, double *__restrict__ cmass, double *__restrict__ ccom,
     double *__restrict__ cmom)
 {
     constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
-    constexpr int NQ = (NC + 31) / 32;
-    __shared__ double sa[MW][NC], sb[MW][NC];  // child moments, then the partial translations
-    __shared__ double sp[MW][3][P + 1];        // powers of the offset z_ch - z
-    __shared__ unsigned char mi[NC][3];
+    constexpr int NF = (P + 1) * (P + 2) / 2;  // factors (e, e') with e' <= e <= P, per axis
+    __shared__ double sa[M2M_W][NC], sb[M2M_W][NC];  // a child's moments and partial translations
+    __shared__ double fac[M2M_W][3][NF];             // C(e,e') d^(e-e'), d = z_ch - z per axis
     __shared__ double binom[P + 1][P + 1];
+    __shared__ unsigned char mi[NC][3];
+    __shared__ int32_t sch[M2M_W];
+    __shared__ double smc[M2M_W][4];  // child mass and centre
     for (int k = threadIdx.x; k < NC; k += blockDim.x) {
         mi[k][0] = hot_midx[k][0];
         mi[k][1] = hot_midx[k][1];
@@ -159,86 +165,85 @@ __global__ void __launch_bounds__(MW * 32) k_m2m_level(
         }
         binom[n][r] = v;
     }
-    __syncthreads();
-    const int w = threadIdx.x >> 5;
+    const int o = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    const int64_t nw = (int64_t)gridDim.x * MW;
-    for (int64_t q0 = (int64_t)blockIdx.x * MW + w; q0 < ncells_lvl; q0 += nw) {
+    for (int64_t q0 = blockIdx.x; q0 < ncells_lvl; q0 += gridDim.x) {
         const int32_t c = cells[q0];
-        if (cnchild[c] == 0) continue;
-        int32_t ch[8];
+        if (cnchild[c] == 0) continue;  // uniform over the block
+        __syncthreads();
+        if (threadIdx.x < M2M_W) {
+            const int32_t k = child8[8 * (int64_t)c + threadIdx.x];
+            sch[threadIdx.x] = k;
+            if (k >= 0) {
+                smc[threadIdx.x][0] = cmass[k];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) smc[threadIdx.x][1 + d] = ccom[3 * (int64_t)k + d];
+            }
+        }
+        __syncthreads();
+        // parent mass and centre of mass, children in octant order (every thread)
         double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            ch[o] = child8[8 * (int64_t)c + o];
-            if (ch[o] >= 0) {
-                double mc = cmass[ch[o]];
+        for (int q = 0; q < M2M_W; ++q) {
+            if (sch[q] >= 0) {
+                const double mc = smc[q][0];
                 m += mc;
-                mx += mc * ccom[3 * (int64_t)ch[o] + 0];
-                my += mc * ccom[3 * (int64_t)ch[o] + 1];
-                mz += mc * ccom[3 * (int64_t)ch[o] + 2];
+                mx += mc * smc[q][1];
+                my += mc * smc[q][2];
+                mz += mc * smc[q][3];
             }
         }
         const double z[3] = {mx / m, my / m, mz / m};
-        double acc[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-        for (int o = 0; o < 8; ++o) {
-            const int32_t k = ch[o];
-            if (k < 0) continue;
-            if (lane < 3) {
-                const double d = ccom[3 * (int64_t)k + lane] - z[lane];
-                double v = 1.0;
-                for (int e = 0; e <= P; ++e) {
-                    sp[w][lane][e] = v;
-                    v *= d;
-                }
+        const int32_t k = sch[o];
+        if (k >= 0) {
+            for (int g = lane; g < 3 * NF; g += 32) {
+                const int d = g / NF, f = g % NF;
+                int e = 0;
+                while ((e + 1) * (e + 2) / 2 <= f) ++e;
+                const int e2 = f - e * (e + 1) / 2;
+                const double dd = smc[o][1 + d] - z[d];
+                double pw = 1.0;
+                for (int t = 0; t < e - e2; ++t) pw *= dd;
+                fac[o][d][f] = binom[e][e2] * pw;
             }
-            for (int g = lane; g < NC; g += 32) sa[w][g] = cmom[(int64_t)k * NC + g];
+            for (int g = lane; g < NC; g += 32) sa[o][g] = cmom[(int64_t)k * NC + g];
             __syncwarp();
             // pass 1 (x): sa -> sb
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int a = lane + 32 * q;
-                if (a < NC) {
-                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
-                    double t = 0.0;
-                    for (int i2 = 0; i2 <= i; ++i2) t += binom[i][i2] * sp[w][0][i - i2] * sa[w][mom_index(i2, j, kk)];
-                    sb[w][a] = t;
-                }
+            for (int a = lane; a < NC; a += 32) {
+                const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
+                const double *F = &fac[o][0][i * (i + 1) / 2];
+                double t = 0.0;
+                for (int i2 = 0; i2 <= i; ++i2) t += F[i2] * sa[o][mom_index(i2, j, kk)];
+                sb[o][a] = t;
             }
             __syncwarp();
             // pass 2 (y): sb -> sa
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int a = lane + 32 * q;
-                if (a < NC) {
-                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
-                    double t = 0.0;
-                    for (int j2 = 0; j2 <= j; ++j2) t += binom[j][j2] * sp[w][1][j - j2] * sb[w][mom_index(i, j2, kk)];
-                    sa[w][a] = t;
-                }
+            for (int a = lane; a < NC; a += 32) {
+                const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
+                const double *F = &fac[o][1][j * (j + 1) / 2];
+                double t = 0.0;
+                for (int j2 = 0; j2 <= j; ++j2) t += F[j2] * sb[o][mom_index(i, j2, kk)];
+                sa[o][a] = t;
             }
             __syncwarp();
-            // pass 3 (z): sa -> accumulated parent moments
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int a = lane + 32 * q;
-                if (a < NC) {
-                    const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
-                    double t = 0.0;
-                    for (int k2 = 0; k2 <= kk; ++k2) t += binom[kk][k2] * sp[w][2][kk - k2] * sa[w][mom_index(i, j, k2)];
-                    acc[q] += t;
-                }
+            // pass 3 (z): sa -> sb, the child's contribution
+            for (int a = lane; a < NC; a += 32) {
+                const int i = mi[a][0], j = mi[a][1], kk = mi[a][2];
+                const double *F = &fac[o][2][kk * (kk + 1) / 2];
+                double t = 0.0;
+                for (int k2 = 0; k2 <= kk; ++k2) t += F[k2] * sa[o][mom_index(i, j, k2)];
+                sb[o][a] = t;
             }
-            __syncwarp();
         }
+        __syncthreads();
+        for (int a = threadIdx.x; a < NC; a += blockDim.x) {
+            double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            int a = lane + 32 * q;
-            if (a < NC) cmom[(int64_t)c * NC + a] = acc[q];
+            for (int q = 0; q < M2M_W; ++q)
+                if (sch[q] >= 0) t += sb[q][a];
+            cmom[(int64_t)c * NC + a] = t;
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             cmass[c] = m;
             ccom[3 * (int64_t)c + 0] = z[0];
             ccom[3 * (int64_t)c + 1] = z[1];
@@ -376,10 +381,10 @@ int moments_p(hot_ctx *c)
     for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
         int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
         if (n <= 0) continue;
-        int blocks = hot_blocks(n, MW, c->nsm * 16);
+        const int blocks = (int)(n < (int64_t)c->nsm * 8 ? n : (int64_t)c->nsm * 8);
         HOT_COUNT_LAUNCH();
-        k_m2m_level<P><<<blocks, MW * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
-                                                  c->cmass.p, c->ccom.p, c->cmom.p);
+        k_m2m_level<P><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                     c->cmass.p, c->ccom.p, c->cmom.p);
     }
     // aggregates of inner cells
     const int64_t max_items = ncell + N * (c->maxlevel + 1) / CHUNK + 1;
