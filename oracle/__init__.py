@@ -54,10 +54,14 @@ def lib():
         L = C.CDLL(build())
         L.orc_nthreads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
-        L.orc_direct.argtypes = [C.c_int64, _d, _d, C.c_double, C.c_double, C.c_int64,
+        L.orc_direct.argtypes = [C.c_int64, _d, _d, C.c_double, C.c_double, C.c_int, C.c_int64,
                                  C.c_void_p, _d, C.c_void_p]
-        L.orc_direct_grad.argtypes = [C.c_int64, _d, _d, C.c_double, C.c_double, _d,
+        L.orc_direct_grad.argtypes = [C.c_int64, _d, _d, C.c_double, C.c_double, C.c_int, _d,
                                       C.c_void_p, _d, _d]
+        L.orc_soft_eval.restype = C.c_int
+        L.orc_soft_eval.argtypes = [C.c_int, C.c_double, C.c_double, _d]
+        L.orc_tree_softening.restype = C.c_int
+        L.orc_tree_softening.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.orc_bbox.argtypes = [C.c_int64, _d, _d, C.POINTER(C.c_double)]
         L.orc_keys.argtypes = [C.c_int64, _d, _d, C.c_double, _u64]
         L.orc_sort.argtypes = [C.c_int64, _u64, _i64]
@@ -126,24 +130,38 @@ def multi_indices(p: int) -> list[tuple[int, int, int]]:
     return out
 
 
-def direct(pos, mass, G=1.0, eps=0.0, sinks=None):
+# Force smoothing kinds (Sec. "Force Smoothing"): Plummer, or the K1 compensating kernel
+# of support eps (its density is a stated reading; see hot_oracle.c).
+SOFT = {"plummer": 0, "k1": 1}
+
+
+def soft_kernel(soft, eps, r):
+    """(f, f2, psi) of one pair at separation r: a = G m f d, phi = -G m psi, f2 = 2 df/d(r^2);
+    None for a skipped pair."""
+    out = np.zeros(3)
+    if not lib().orc_soft_eval(SOFT[soft], float(eps), float(r), out):
+        return None
+    return tuple(out)
+
+
+def direct(pos, mass, G=1.0, eps=0.0, sinks=None, soft="plummer"):
     """O(N^2) softened direct sum; returns (acc [n,3], pot [n]) for the sinks (default all)."""
     pos, mass = _c(pos), _c(mass)
     n = len(mass) if sinks is None else len(sinks)
     sk = None if sinks is None else _c(sinks, np.int64)
     acc = np.zeros((n, 3))
     pot = np.zeros(n)
-    lib().orc_direct(len(mass), pos, mass, G, eps, n, _ptr(sk), acc, _ptr(pot))
+    lib().orc_direct(len(mass), pos, mass, G, eps, SOFT[soft], n, _ptr(sk), acc, _ptr(pot))
     return acc, pot
 
 
-def direct_grad(pos, mass, w, v=None, G=1.0, eps=0.0):
+def direct_grad(pos, mass, w, v=None, G=1.0, eps=0.0, soft="plummer"):
     """Analytic gradient of L = sum w.a + sum v phi of the direct sum: (dL/dx [N,3], dL/dm [N])."""
     pos, mass, w = _c(pos), _c(mass), _c(w)
     vv = None if v is None else _c(v)
     gx = np.zeros_like(pos)
     gm = np.zeros_like(mass)
-    lib().orc_direct_grad(len(mass), pos, mass, G, eps, w, _ptr(vv), gx, gm)
+    lib().orc_direct_grad(len(mass), pos, mass, G, eps, SOFT[soft], w, _ptr(vv), gx, gm)
     return gx, gm
 
 
@@ -256,6 +274,12 @@ class Tree:
                                    out["B1"], out["B2"])
         return out
 
+    def softening(self, soft, eps):
+        """Force smoothing of the lists and forces ("plummer" default, or "k1" with support
+        eps: the lists then accept a cell only if d >= b_max + eps); set before traverse."""
+        if lib().orc_tree_softening(self._h, SOFT[soft], float(eps)) != 0:
+            raise ValueError("bad softening")
+
     def traverse(self, tol, G=1.0, groups=None):
         if groups is None:
             r = lib().orc_tree_traverse(self._h, float(tol), float(G))
@@ -286,6 +310,8 @@ class Tree:
         gs = None if groups is None else _c(groups, np.int64)
         r = lib().orc_tree_force(self._h, G, eps, 0 if gs is None else len(gs), _ptr(gs), acc,
                                  _ptr(pot))
+        if r == -2:
+            raise ValueError("K1 forces need the eps the lists were built with")
         if r != 0:
             raise ValueError("force needs lists")
         return acc, pot
@@ -295,7 +321,10 @@ class Tree:
         n = len(self.mass)
         acc = np.zeros((n, 3))
         pot = np.zeros(n)
-        if lib().orc_frozen_force(self._h, _c(pos), _c(mass), G, eps, acc, _ptr(pot)) != 0:
+        r = lib().orc_frozen_force(self._h, _c(pos), _c(mass), G, eps, acc, _ptr(pot))
+        if r == -2:
+            raise ValueError("K1 forces need the eps the lists were built with")
+        if r != 0:
             raise ValueError("frozen_force needs lists")
         return acc, pot
 
@@ -320,8 +349,9 @@ def frozen_leapfrog(trees, x0, v0, mass, dt, G=1.0, eps=0.0):
     return x, v
 
 
-def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128):
+def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, soft="plummer"):
     t = Tree(pos, mass, leaf_max, group_max)
+    t.softening(soft, eps)
     t.moments(p)
     t.traverse(tol, G)
     return t.force(G, eps)

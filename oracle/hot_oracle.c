@@ -13,7 +13,8 @@
  *
  * What each part follows (section / equation of the paper):
  *   direct sum ............ Eq. (eom) with a = 1 (no expansion), Plummer force
- *                           smoothing (Sec. "Force Smoothing")
+ *                           smoothing or the K1 compensating kernel (Sec. "Force
+ *                           Smoothing"; the K1 density is a stated reading, below)
  *   keys .................. space-filling-curve (Morton) keys, Sec. "Domain
  *                           Decomposition"; 21 bits per dimension, x highest in
  *                           each bit triplet, a leading placeholder bit
@@ -68,17 +69,87 @@ void orc_set_threads(int n)
 }
 
 /* ---------------------------------------------------------------------------
- * Direct sum.  a_i = G sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2}
- *              phi_i = -G sum_{j != i} m_j / sqrt(|x_j - x_i|^2 + eps^2)
+ * Force smoothing (Sec. "Force Smoothing").  A source of mass m at d = x_j - x_i,
+ * r = |d|, gives the sink a = G m f(r^2) d and phi = -G m psi(r); the tidal tensor
+ * of the pair is da/dx_i = -G m [f I + f2 d d^T], f2 = 2 df/d(r^2).
+ *   ORC_SOFT_PLUMMER: s^2 = r^2 + eps^2, f = s^-3, f2 = -3 s^-5, psi = 1/s.
+ *   ORC_SOFT_K1: Dehnen's K1 compensating kernel.  The paper names it (forces above
+ *     the Newtonian ones at the outer edge of the kernel compensate the weaker forces
+ *     inside) without a formula; it is read here as the kernel of unit mass, support
+ *     r < eps and density rho(x) = 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2), x = r/eps:
+ *     the even quartic vanishing at the edge whose second moment is zero (negative
+ *     density for x^2 > 5/9).  Its enclosed mass is M(x) = 175/16 x^3 - 147/8 x^5 +
+ *     135/16 x^7, so for r < eps, with u = x^2,
+ *       f = g(u)/eps^3, g(u) = 175/16 - 147/8 u + 135/16 u^2,
+ *       f2 = 2 g'(u)/eps^5, g'(u) = -147/8 + 135/8 u,
+ *       psi = (105 - 175 u + 147 u^2 - 45 u^3) / (32 eps)
+ *     (psi from integrating M(x)/x^2 inwards from psi(eps) = 1/eps), and exactly
+ *     Newtonian (f = r^-3, f2 = -3 r^-5, psi = 1/r) for r >= eps.  The multipole
+ *     expansion then uses the unsoftened kernel, and a cell is accepted only if every
+ *     sink-source pair is at least eps apart (d >= b_max + eps).
+ * ------------------------------------------------------------------------- */
+enum { ORC_SOFT_PLUMMER = 0, ORC_SOFT_K1 = 1 };
+typedef struct {
+    int kind;
+    double eps;
+} orc_soft;
+
+/* f, f2, psi of one pair at squared separation r2; 0 for a pair that is skipped
+ * (zero separation without softening). */
+static int soft_eval(orc_soft sf, double r2, double *f, double *f2, double *psi)
+{
+    if (sf.kind == ORC_SOFT_K1 && r2 < sf.eps * sf.eps) {
+        double e2 = sf.eps * sf.eps;
+        double e3 = e2 * sf.eps;
+        double u = r2 / e2;
+        *f = (175.0 / 16.0 + u * (-147.0 / 8.0 + u * (135.0 / 16.0))) / e3;
+        *f2 = 2.0 * (-147.0 / 8.0 + u * (135.0 / 8.0)) / (e3 * e2);
+        *psi = (105.0 + u * (-175.0 + u * (147.0 - 45.0 * u))) / (32.0 * sf.eps);
+        return 1;
+    }
+    double s2 = sf.kind == ORC_SOFT_K1 ? r2 : r2 + sf.eps * sf.eps;
+    if (s2 == 0.0) return 0;
+    double sinv = 1.0 / sqrt(s2);
+    *psi = sinv;
+    *f = sinv * sinv * sinv;
+    *f2 = -3.0 * *f * sinv * sinv;
+    return 1;
+}
+
+/* f, f2, psi at separation r (for the parity pins); returns 0 if skipped. */
+int orc_soft_eval(int kind, double eps, double r, double *out)
+{
+    orc_soft sf = {kind, eps};
+    return soft_eval(sf, r * r, out, out + 1, out + 2);
+}
+
+/* The kernel the multipole expansion uses: softened for Plummer, Newtonian for K1. */
+static double m2p_eps2(orc_soft sf) { return sf.kind == ORC_SOFT_K1 ? 0.0 : sf.eps * sf.eps; }
+
+/* ---------------------------------------------------------------------------
+ * Direct sum.  a_i = G sum_{j != i} m_j f(|x_j - x_i|^2) (x_j - x_i),
+ *              phi_i = -G sum_{j != i} m_j psi(|x_j - x_i|); Plummer:
+ *              a_i = G sum m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2},
+ *              phi_i = -G sum m_j / sqrt(|x_j - x_i|^2 + eps^2).
  * A pair whose softened distance is exactly zero is skipped.
  * ------------------------------------------------------------------------- */
 static void pair_acc(const double *xi, const double *xj, double mj, double G,
-                     double eps2, double *a, double *phi)
+                     orc_soft sf, double *a, double *phi)
 {
     double dx = xj[0] - xi[0];
     double dy = xj[1] - xi[1];
     double dz = xj[2] - xi[2];
-    double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    if (sf.kind == ORC_SOFT_K1) {
+        double f, f2, psi;
+        if (!soft_eval(sf, dx * dx + dy * dy + dz * dz, &f, &f2, &psi)) return;
+        double gm = G * mj;
+        a[0] += gm * f * dx;
+        a[1] += gm * f * dy;
+        a[2] += gm * f * dz;
+        *phi -= gm * psi;
+        return;
+    }
+    double r2 = dx * dx + dy * dy + dz * dz + sf.eps * sf.eps;
     if (r2 == 0.0) return;
     double rinv = 1.0 / sqrt(r2);
     double gm = G * mj;
@@ -90,10 +161,10 @@ static void pair_acc(const double *xi, const double *xj, double mj, double G,
 }
 
 /* sinks == NULL means every particle; outputs are indexed like the sink list. */
-void orc_direct(int64_t N, const double *pos, const double *mass, double G, double eps,
+void orc_direct(int64_t N, const double *pos, const double *mass, double G, double eps, int kind,
                 int64_t nsink, const int64_t *sinks, double *acc, double *pot)
 {
-    double eps2 = eps * eps;
+    orc_soft sf = {kind, eps};
     if (sinks == NULL) nsink = N;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t s = 0; s < nsink; s++) {
@@ -101,7 +172,7 @@ void orc_direct(int64_t N, const double *pos, const double *mass, double G, doub
         double a[3] = {0.0, 0.0, 0.0}, phi = 0.0;
         for (int64_t j = 0; j < N; j++) {
             if (j == i) continue;
-            pair_acc(pos + 3 * i, pos + 3 * j, mass[j], G, eps2, a, &phi);
+            pair_acc(pos + 3 * i, pos + 3 * j, mass[j], G, sf, a, &phi);
         }
         acc[3 * s + 0] = a[0];
         acc[3 * s + 1] = a[1];
@@ -111,13 +182,15 @@ void orc_direct(int64_t N, const double *pos, const double *mass, double G, doub
 }
 
 /* Analytic gradient of L = sum_i w_i . a_i + sum_i v_i phi_i of the direct sum.
- * With d = x_j - x_k, s^2 = |d|^2 + eps^2 and K(d) = I/s^3 - 3 d d^T / s^5:
- *   dL/dx_k = G sum_{j != k} [ K(d) (m_k w_j - m_j w_k) + (v_j m_k + v_k m_j)(-d)/s^3 ]
- *   dL/dm_j = G sum_{i != j} [ w_i . (x_j - x_i)/s^3 - v_i / s ]
+ * With d = x_j - x_k and the pair kernel f, f2, psi above, K(d) = f I + f2 d d^T:
+ *   dL/dx_k = G sum_{j != k} [ K(d) (m_k w_j - m_j w_k) - (v_j m_k + v_k m_j) f d ]
+ *   dL/dm_j = G sum_{i != j} [ w_i . (x_j - x_i) f - v_i psi ]
+ * (Plummer: s^2 = |d|^2 + eps^2, K(d) = I/s^3 - 3 d d^T / s^5, f = s^-3, psi = 1/s.)
  * v may be NULL (no potential term). */
-void orc_direct_grad(int64_t N, const double *pos, const double *mass, double G, double eps,
+void orc_direct_grad(int64_t N, const double *pos, const double *mass, double G, double eps, int kind,
                      const double *w, const double *v, double *gpos, double *gmass)
 {
+    orc_soft sf = {kind, eps};
     double eps2 = eps * eps;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t k = 0; k < N; k++) {
@@ -130,6 +203,18 @@ void orc_direct_grad(int64_t N, const double *pos, const double *mass, double G,
             const double *xj = pos + 3 * j;
             const double *wj = w + 3 * j;
             double d[3] = {xj[0] - xk[0], xj[1] - xk[1], xj[2] - xk[2]};
+            if (sf.kind == ORC_SOFT_K1) {
+                double f, f2, psi;
+                if (!soft_eval(sf, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &f, &f2, &psi)) continue;
+                double c[3];
+                for (int e = 0; e < 3; e++) c[e] = mass[k] * wj[e] - mass[j] * wk[e];
+                double dc = d[0] * c[0] + d[1] * c[1] + d[2] * c[2];
+                double vj = v ? v[j] : 0.0;
+                double pv = vj * mass[k] + vk * mass[j];
+                for (int e = 0; e < 3; e++) g[e] += G * (c[e] * f + f2 * d[e] * dc - pv * d[e] * f);
+                gm += G * (-(wj[0] * d[0] + wj[1] * d[1] + wj[2] * d[2]) * f - vj * psi);
+                continue;
+            }
             double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
             if (s2 == 0.0) continue;
             double sinv = 1.0 / sqrt(s2);
@@ -410,6 +495,9 @@ typedef struct orc_tree {
     /* lists per group */
     ivec *lm2p, *lp2p, *lborder;
     double tol, Gmac;
+    /* force smoothing the lists are built for (Plummer unless set) */
+    int soft;
+    double soft_eps;
 } orc_tree;
 
 static int64_t new_cell(orc_tree *t)
@@ -690,9 +778,13 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c)
     double d = dist - t->gdmax[g];
     double b = t->cbmax[c];
     int accept = 0;
+    /* K1: accepted only if no sink comes within eps of a source of the cell */
+    int guard = t->soft != ORC_SOFT_K1 || d >= b + t->soft_eps;
+    if (t->soft == ORC_SOFT_K1 && b + t->soft_eps > 0.0 && fabs(d - (b + t->soft_eps)) <= 1e-9 * (b + t->soft_eps))
+        ivec_push(&t->lborder[g], (int32_t)c);
     if (d > b) {
         double E = orc_mac_bound(d, b, t->cB1[c], t->cB2[c], t->p, t->Gmac);
-        accept = E <= t->tol;
+        accept = guard && E <= t->tol;
         if (fabs(E - t->tol) <= 1e-9 * t->tol) ivec_push(&t->lborder[g], (int32_t)c);
     }
     if (b > 0.0 && fabs(d - b) <= 1e-9 * b) ivec_push(&t->lborder[g], (int32_t)c);
@@ -702,6 +794,25 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c)
         ivec_push(&t->lp2p[g], (int32_t)c);
     else
         for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k]);
+}
+
+/* Force smoothing of the lists and forces: kind ORC_SOFT_PLUMMER (default) or
+ * ORC_SOFT_K1 with support eps.  Set before the traversal. */
+int orc_tree_softening(orc_tree *t, int kind, double eps)
+{
+    if ((kind != ORC_SOFT_PLUMMER && kind != ORC_SOFT_K1) || !(eps >= 0.0)) return -1;
+    t->soft = kind;
+    t->soft_eps = eps;
+    return 0;
+}
+
+/* The smoothing of a force call: the tree's kind with the given eps; K1 needs the eps
+ * its lists were built with (-2 otherwise). */
+static int force_soft(const orc_tree *t, double eps, orc_soft *sf)
+{
+    sf->kind = t->soft;
+    sf->eps = eps;
+    return (t->soft == ORC_SOFT_K1 && eps != t->soft_eps) ? -2 : 0;
 }
 
 int orc_tree_traverse(orc_tree *t, double tol, double G)
@@ -745,10 +856,11 @@ void orc_tree_lists(const orc_tree *t, int32_t *m2p, int32_t *p2p, int32_t *bord
 /* Force on the sinks of one group from its lists, given per-cell moments and
  * (frozen) expansion centres.  Outputs are written at the sinks' original indices. */
 static void group_force(const orc_tree *t, int64_t g, const double *spos, const double *smass,
-                        const double *mom, const int (*tab)[3], double G, double eps2,
+                        const double *mom, const int (*tab)[3], double G, orc_soft sf,
                         double *acc, double *pot)
 {
     int nc = ncomp(t->p);
+    double eps2 = m2p_eps2(sf);
     int64_t gc = t->gcell[g];
     for (int64_t s = t->cbegin[gc]; s < t->cbegin[gc] + t->ccount[gc]; s++) {
         double a[3] = {0.0, 0.0, 0.0}, phi = 0.0;
@@ -763,7 +875,7 @@ static void group_force(const orc_tree *t, int64_t g, const double *spos, const 
             int64_t c = t->lp2p[g].v[e];
             for (int64_t j = t->cbegin[c]; j < t->cbegin[c] + t->ccount[c]; j++) {
                 if (j == s) continue;
-                pair_acc(x, spos + 3 * j, smass[j], G, eps2, a, &phi);
+                pair_acc(x, spos + 3 * j, smass[j], G, sf, a, &phi);
             }
         }
         int64_t i = t->perm[s];
@@ -780,12 +892,13 @@ int orc_tree_force(const orc_tree *t, double G, double eps, int64_t nsel, const 
     if (!t->lm2p) return -1;
     int tab[200][3];
     midx_table(t->p, tab);
-    double eps2 = eps * eps;
+    orc_soft sf;
+    if (force_soft(t, eps, &sf)) return -2;
     if (!gsel) nsel = t->ngroup;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t q = 0; q < nsel; q++) {
         int64_t g = gsel ? gsel[q] : q;
-        group_force(t, g, t->spos, t->smass, t->cmom, (const int(*)[3])tab, G, eps2, acc, pot);
+        group_force(t, g, t->spos, t->smass, t->cmom, (const int(*)[3])tab, G, sf, acc, pot);
     }
     return 0;
 }
@@ -825,7 +938,9 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
     int p = t->p, nc = ncomp(p);
     int tab[200][3];
     midx_table(p, tab);
-    double eps2 = eps * eps;
+    orc_soft sf;
+    if (force_soft(t, eps, &sf)) return NAN;
+    double eps2 = m2p_eps2(sf);
     double *spos = (double *)malloc(sizeof(double) * 3 * (size_t)N);
     double *smass = (double *)malloc(sizeof(double) * (size_t)N);
     for (int64_t s = 0; s < N; s++) {
@@ -852,7 +967,7 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
         double *pot = (double *)malloc(sizeof(double) * (size_t)N);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t g = 0; g < t->ngroup; g++)
-            group_force(t, g, spos, smass, mom, (const int(*)[3])tab, G, eps2, acc, pot);
+            group_force(t, g, spos, smass, mom, (const int(*)[3])tab, G, sf, acc, pot);
         for (int64_t i = 0; i < N; i++) {
             L += w[3 * i] * acc[3 * i] + w[3 * i + 1] * acc[3 * i + 1] + w[3 * i + 2] * acc[3 * i + 2];
             if (v) L += v[i] * pot[i];
@@ -878,7 +993,7 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
             for (int64_t e = 0; e < t->lp2p[gk].n; e++) {
                 int64_t c = t->lp2p[gk].v[e];
                 for (int64_t j = t->cbegin[c]; j < t->cbegin[c] + t->ccount[c]; j++)
-                    if (j != sk) pair_acc(x, spos + 3 * j, smass[j], G, eps2, a, &phi);
+                    if (j != sk) pair_acc(x, spos + 3 * j, smass[j], G, sf, a, &phi);
             }
             L += w[3 * k] * a[0] + w[3 * k + 1] * a[1] + w[3 * k + 2] * a[2];
             if (v) L += v[k] * phi;
@@ -907,7 +1022,7 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
                 for (int64_t s = t->cbegin[gc]; s < t->cbegin[gc] + t->ccount[gc]; s++) {
                     if (s == sk) continue;
                     double a[3] = {0.0, 0.0, 0.0}, phi = 0.0;
-                    pair_acc(spos + 3 * s, spos + 3 * sk, smass[sk], G, eps2, a, &phi);
+                    pair_acc(spos + 3 * s, spos + 3 * sk, smass[sk], G, sf, a, &phi);
                     int64_t i = t->perm[s];
                     Lo += w[3 * i] * a[0] + w[3 * i + 1] * a[1] + w[3 * i + 2] * a[2];
                     if (v) Lo += v[i] * phi;
@@ -934,7 +1049,8 @@ int orc_frozen_force(const orc_tree *t, const double *pos, const double *mass, d
     int p = t->p, nc = ncomp(p);
     int tab[200][3];
     midx_table(p, tab);
-    double eps2 = eps * eps;
+    orc_soft sf;
+    if (force_soft(t, eps, &sf)) return -2;
     double *spos = (double *)malloc(sizeof(double) * 3 * (size_t)N);
     double *smass = (double *)malloc(sizeof(double) * (size_t)N);
     double *ph = (double *)malloc(sizeof(double) * (size_t)N);
@@ -950,7 +1066,7 @@ int orc_frozen_force(const orc_tree *t, const double *pos, const double *mass, d
                       mom + (size_t)nc * c);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t g = 0; g < t->ngroup; g++)
-        group_force(t, g, spos, smass, mom, (const int(*)[3])tab, G, eps2, acc, ph);
+        group_force(t, g, spos, smass, mom, (const int(*)[3])tab, G, sf, acc, ph);
     if (pot) memcpy(pot, ph, sizeof(double) * (size_t)N);
     free(spos);
     free(smass);

@@ -584,3 +584,153 @@ def test_leapfrog_two_body_energy_order_and_reversibility():
     for _ in range(50):
         x, v = _rebuild_step(x, v, m, 0.01)
     assert np.max(np.abs(x - x0)) < 1e-12 and np.max(np.abs(v + v0)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# K1 compensating kernel (Sec. "Force Smoothing").  The paper names Dehnen's K1
+# without a formula; the reading is the unit-mass kernel of support eps with density
+# rho(x) = 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2), x = r/eps.  The pins below derive
+# the pair force and potential from that density by quadrature (shell theorem), so
+# they are independent of the oracle's closed forms.
+# --------------------------------------------------------------------------
+
+def _k1_density(r, eps):
+    x = r / eps
+    return 105.0 / (64.0 * math.pi * eps ** 3) * (1 - x * x) * (5 - 9 * x * x) if x < 1 else 0.0
+
+
+def test_k1_kernel_defining_properties():
+    from scipy.integrate import quad
+    eps = 0.37
+    mass = quad(lambda r: 4 * math.pi * r * r * _k1_density(r, eps), 0, eps)[0]
+    second = quad(lambda r: 4 * math.pi * r ** 4 * _k1_density(r, eps), 0, eps)[0]
+    assert abs(mass - 1.0) < 1e-13
+    assert abs(second) < 1e-14  # the compensation: zero second moment
+
+
+@pytest.mark.parametrize("xr", [0.0, 0.05, 0.3, 0.5, 0.7453, 0.9, 0.999, 1.0, 1.2, 3.0])
+def test_k1_pair_force_and_potential_from_density(xr):
+    from scipy.integrate import quad
+    eps = 0.37
+    r = xr * eps
+    f, f2, psi = oracle.soft_kernel("k1", eps, r)
+    if r > 0:
+        # shell theorem: enclosed mass M(r), a = M(r)/r^2 along d -> f = M(r)/r^3
+        M = quad(lambda t: 4 * math.pi * t * t * _k1_density(t, eps), 0, min(r, eps))[0]
+        assert abs(f - M / r ** 3) <= 1e-12 * abs(M / r ** 3)
+        # potential: psi(r) = int_r^inf M(t)/t^2 dt
+        Mof = lambda t: quad(lambda q: 4 * math.pi * q * q * _k1_density(q, eps), 0, min(t, eps))[0]
+        tail = quad(lambda t: Mof(t) / (t * t), r, eps)[0] if r < eps else 0.0
+        psi_ref = 1.0 / max(r, eps) + tail if r < eps else 1.0 / r
+        assert abs(psi - psi_ref) <= 1e-11 * psi_ref
+        # f2 = 2 df/d(r^2), against a central difference in r^2
+        h = 1e-6 * r * r
+        fp = oracle.soft_kernel("k1", eps, math.sqrt(r * r + h))[0]
+        fm = oracle.soft_kernel("k1", eps, math.sqrt(r * r - h))[0]
+        if abs(xr - 1.0) > 1e-3:  # f is continuous at the edge, f2 is not
+            assert abs(f2 - 2 * (fp - fm) / (2 * h)) <= 1e-6 * abs(f2)
+    else:
+        # the centre: finite force coefficient and potential 105/(32 eps)
+        assert abs(f - 175.0 / 16.0 / eps ** 3) <= 1e-14 * f
+        assert abs(psi - 105.0 / (32.0 * eps)) <= 1e-14 * psi
+    if xr >= 1.0:
+        assert f == pytest.approx(1.0 / r ** 3, rel=1e-15) and psi == pytest.approx(1.0 / r, rel=1e-15)
+        assert f2 == pytest.approx(-3.0 / r ** 5, rel=1e-15)
+
+
+def test_k1_force_is_continuous_and_compensating():
+    eps = 0.37
+    below = oracle.soft_kernel("k1", eps, eps * (1 - 1e-12))
+    above = oracle.soft_kernel("k1", eps, eps * (1 + 1e-12))
+    assert abs(below[0] - above[0]) <= 1e-9 * above[0] and abs(below[2] - above[2]) <= 1e-9 * above[2]
+    # above the Newtonian force near the edge, below it in the interior
+    for x in (0.8, 0.9, 0.97):
+        f = oracle.soft_kernel("k1", eps, x * eps)[0]
+        assert f * (x * eps) ** 3 > 1.0
+    for x in (0.1, 0.3, 0.5):
+        f = oracle.soft_kernel("k1", eps, x * eps)[0]
+        assert f * (x * eps) ** 3 < 1.0
+
+
+def test_k1_direct_sum_third_law_and_newtonian_far_field():
+    rng = np.random.default_rng(31)
+    pos = rng.uniform(-1, 1, (300, 3))
+    mass = rng.uniform(0.5, 1.5, 300)
+    acc, pot = oracle.direct(pos, mass, 1.0, 0.3, soft="k1")
+    assert np.linalg.norm((mass[:, None] * acc).sum(0)) < 1e-12 * np.abs(mass[:, None] * acc).sum()
+    # the softening changes the force, so some pairs are inside the support
+    a0, _ = oracle.direct(pos, mass, 1.0, 0.0)
+    assert np.max(rel_err(acc, a0)) > 1e-3
+    # all pairs farther apart than eps: the unsoftened sum, to rounding
+    grid = np.stack(np.meshgrid(*[np.arange(4.0)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    m = np.ones(len(grid))
+    ak, pk = oracle.direct(grid, m, 1.0, 0.9, soft="k1")
+    an, pn = oracle.direct(grid, m, 1.0, 0.0)
+    assert np.max(rel_err(ak, an)) < 1e-13 and np.max(np.abs(pk - pn) / np.abs(pn)) < 1e-14
+
+
+def test_k1_tree_guard_and_convergence_to_direct_sum():
+    w = W.make("plummer4096")
+    eps = 0.05
+    ref, rphi = oracle.direct(w.pos, w.mass, 1.0, eps, soft="k1")
+    errs = []
+    for tol in (1e-3, 1e-5, 1e-7):
+        t = oracle.Tree(w.pos, w.mass)
+        t.softening("k1", eps)
+        t.moments(6)
+        t.traverse(tol)
+        a, ph = t.force(1.0, eps)
+        errs.append(np.sqrt(np.mean(rel_err(a, ref) ** 2)))
+        # every accepted cell keeps all its sources at least eps from every sink of the group
+        L = t.lists()
+        cl = t.cells()
+        gr = t.groups()
+        mo = t.get_moments()
+        om, cells = L["m2p"]
+        for g in range(len(gr["cell"])):
+            cs = cells[om[g]:om[g + 1]]
+            d = np.linalg.norm(mo["com"][cs] - gr["centre"][g], axis=1) - gr["dmax"][g]
+            assert np.all(d >= mo["bmax"][cs] + eps)
+        with pytest.raises(ValueError):
+            t.force(1.0, 2 * eps)  # K1 lists are built for one eps
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-6  # rms relative, at an absolute tolerance of 1e-7
+
+
+def test_k1_direct_grad_against_finite_differences():
+    rng = np.random.default_rng(8)
+    n, eps = 40, 0.4
+    pos = rng.uniform(-1, 1, (n, 3))
+    mass = rng.uniform(0.5, 1.5, n)
+    w = rng.standard_normal((n, 3))
+    v = rng.standard_normal(n)
+
+    def L(p, m):
+        a, ph = oracle.direct(p, m, 1.0, eps, soft="k1")
+        return float((w * a).sum() + (v * ph).sum())
+
+    gx, gm = oracle.direct_grad(pos, mass, w, v, 1.0, eps, soft="k1")
+    h = 1e-6
+    for k in (0, 7, 19, 33):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[k, d] += h
+            pm[k, d] -= h
+            fd = (L(pp, mass) - L(pm, mass)) / (2 * h)
+            assert abs(gx[k, d] - fd) <= 1e-7 * max(1.0, abs(fd))
+        mp, mm = mass.copy(), mass.copy()
+        mp[k] += h
+        mm[k] -= h
+        fd = (L(pos, mp) - L(pos, mm)) / (2 * h)
+        assert abs(gm[k] - fd) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_k1_frozen_force_is_tree_force():
+    w = W.make("plummer4096")
+    t = oracle.Tree(w.pos, w.mass)
+    t.softening("k1", 0.05)
+    t.moments(4)
+    t.traverse(1e-4)
+    a, ph = t.force(1.0, 0.05)
+    fa, fph = t.frozen_force(w.pos, w.mass, 1.0, 0.05)
+    assert np.max(rel_err(fa, a)) < 1e-12 and np.max(np.abs(fph - ph) / np.abs(ph)) < 1e-12
