@@ -59,16 +59,30 @@ enum {
 
 enum { HOT_FP32_MIXED = 0, HOT_FP64 = 1 };
 
+/* Force smoothing (Sec. "Force Smoothing").  A source of mass m at separation d
+ * (r = |d|) from a sink gives a = G m f(r^2) d and phi = -G m psi(r):
+ *   HOT_SOFT_PLUMMER: f = (r^2 + eps^2)^(-3/2), psi = (r^2 + eps^2)^(-1/2); the
+ *     multipole expansions use the same softened kernel.
+ *   HOT_SOFT_K1: the K1 compensating kernel of support eps, read as the unit-mass
+ *     density 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2), x = r/eps (zero second moment);
+ *     for r < eps, u = r^2/eps^2: f = (175/16 - 147/8 u + 135/16 u^2)/eps^3,
+ *     psi = (105 - 175 u + 147 u^2 - 45 u^3)/(32 eps); Newtonian for r >= eps.  The
+ *     multipole expansions use the unsoftened kernel and a cell is accepted only
+ *     when every source is at least eps from every sink of the group
+ *     (|z - g| - Delta_max >= b_max + eps). */
+enum { HOT_SOFT_PLUMMER = 0, HOT_SOFT_K1 = 1 };
+
 typedef struct hot_ctx hot_ctx;
 
 typedef struct {
     int p;          /* expansion order, 0..6 (potential terms |a| <= p)           */
     double tol;     /* absolute acceleration error bound per accepted cell, > 0  */
-    double eps;     /* Plummer softening length, >= 0                             */
+    double eps;     /* softening length, >= 0 (Plummer length or K1 support)     */
     double G;       /* gravitational constant                                     */
     int leaf_max;   /* a cell with more particles is refined (levels < 21), >= 1  */
     int group_max;  /* sink groups: topmost cells with <= group_max particles     */
     int precision;  /* HOT_FP32_MIXED or HOT_FP64 interaction arithmetic          */
+    int softening;  /* HOT_SOFT_PLUMMER or HOT_SOFT_K1                            */
 } hot_params;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
@@ -77,8 +91,8 @@ typedef struct {
 int hot_create(hot_ctx **out, const hot_params *prm, void *cuda_stream);
 
 /* Replace the parameters (validated as in hot_create).  Changing p, tol, eps,
- * G or precision keeps the tree; changing leaf_max or group_max requires a new
- * hot_build_tree. */
+ * G, precision or softening keeps the tree; changing leaf_max or group_max
+ * requires a new hot_build_tree. */
 int hot_set_params(hot_ctx *ctx, const hot_params *prm);
 
 /* Morton keys, stable radix sort and hashed oct-tree of N particles

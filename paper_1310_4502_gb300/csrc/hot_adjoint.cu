@@ -312,12 +312,13 @@ __global__ void __launch_bounds__(AW * 32) k_adj_l2l(const int32_t *__restrict__
 // a time, all their loads in flight together (a scan of the group sizes, then every lane
 // loads sinks of the batch).  Per item and leaf particle the sums
 //   gx = sum_i [u_i/s^3 - 3 d (d.u_i)/s^5 + v_i d/s^3],  gm = sum_i [u_i.d/s^3 - v_i/s]
-// (d = x_j - x_i, s^2 = |d|^2 + eps^2) go to row roff[leaf] + k n_leaf + j of part (k:
+// (d = x_j - x_i, s^2 = |d|^2 + eps^2; with K1 smoothing f u_i + (f2 (d.u_i) + v_i f) d and
+// (d.u_i) f - v_i psi, the pair functions of k1_pair) go to row roff[leaf] + k n_leaf + j of part (k:
 // the item's rank within its leaf); k_adj_p2p_combine adds the items of each leaf in
 // order: dL/dx_j += G m_j gx, dL/dm_j += G gm.
 constexpr int PS = 128;
 constexpr int LMAX = 64;  // leaf particles per pass (two per lane)
-template <class T>
+template <class T, int SOFT>
 __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
     const uint32_t *__restrict__ nitem_p, const int32_t *__restrict__ icell, const int64_t *__restrict__ ia,
     const int64_t *__restrict__ ib, const uint32_t *__restrict__ tval, const int32_t *__restrict__ gcell,
@@ -335,6 +336,8 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
     const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t nitem = *nitem_p;
+    K1Const<T> kc{};
+    if constexpr (SOFT == HOT_SOFT_K1) kc = k1_const(eps2);
     for (;;) {
         unsigned I0 = 0;
         if (lane == 0) I0 = atomicAdd(work, 1u);
@@ -392,6 +395,24 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                         for (int q = 0; q < 2; ++q) {
                             if (!val[q]) continue;
                             const T dx = xj[q][0] - sx, dy = xj[q][1] - sy, dz = xj[q][2] - sz;
+                            if constexpr (SOFT == HOT_SOFT_K1) {
+                                const T r2 = dx * dx + dy * dy + dz * dz;
+                                T f, f2, psi;
+                                k1_pair(r2, kc, f, f2, psi);
+                                if constexpr (CK) {
+                                    const bool ok = (r2 > T(0) || kc.e2 > T(0)) && (id != (int32_t)slot[q]);
+                                    f = ok ? f : T(0);
+                                    f2 = ok ? f2 : T(0);
+                                    psi = ok ? psi : T(0);
+                                }
+                                const T du = dx * ux + dy * uy + dz * uz;
+                                const T cd = f2 * du + vv * f;
+                                gx[q] += f * ux + cd * dx;
+                                gy[q] += f * uy + cd * dy;
+                                gz[q] += f * uz + cd * dz;
+                                gm[q] += du * f - vv * psi;
+                                continue;
+                            }
                             const T r2 = dx * dx + dy * dy + dz * dz + eps2;
                             T ri;
                             if constexpr (CK) {
@@ -730,11 +751,13 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
             HOT_CK(cudaMemsetAsync(pwork, 0, sizeof(unsigned), s));
             T *pp = (T *)c->adj_pp.p;
             HOT_COUNT_LAUNCH();
-            k_adj_p2p_src<T><<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
-                                                            c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
-                                                            c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
-                                                            (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
-                                                            pwork, pp);
+            auto p2p_src = c->prm.softening == HOT_SOFT_K1 ? k_adj_p2p_src<T, HOT_SOFT_K1>
+                                                           : k_adj_p2p_src<T, HOT_SOFT_PLUMMER>;
+            p2p_src<<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
+                                                   c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
+                                                   c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,
+                                                   (T)(c->prm.eps * c->prm.eps), c->it_off.p, c->adj_roff.p,
+                                                   pwork, pp);
             HOT_COUNT_LAUNCH();
             k_adj_p2p_combine<T><<<hot_blocks(nc, AW, c->nsm * 16), AW * 32, 0, s>>>(
                 nc, c->cnchild.p, c->it_off.p, c->adj_roff.p, c->cbegin.p, c->ccount.p, c->smass.p, pp, c->prm.G,

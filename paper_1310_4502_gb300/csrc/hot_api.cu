@@ -28,6 +28,7 @@ int check_params(const hot_params *p)
     if (!(p->tol > 0.0) || !(p->eps >= 0.0) || !(p->G == p->G)) return HOT_EINVAL;
     if (p->leaf_max < 1 || p->group_max < 1 || p->leaf_max > 4096 || p->group_max > (1 << 20)) return HOT_EINVAL;
     if (p->precision != HOT_FP32_MIXED && p->precision != HOT_FP64) return HOT_EINVAL;
+    if (p->softening != HOT_SOFT_PLUMMER && p->softening != HOT_SOFT_K1) return HOT_EINVAL;
     return HOT_OK;
 }
 
@@ -106,7 +107,7 @@ int hot_set_params(hot_ctx *c, const hot_params *prm)
     if (e) return e;
     bool rebuild = prm->leaf_max != c->prm.leaf_max || prm->group_max != c->prm.group_max;
     bool remoment = prm->p != c->prm.p || prm->eps != c->prm.eps || prm->G != c->prm.G ||
-                    prm->precision != c->prm.precision;
+                    prm->precision != c->prm.precision || prm->softening != c->prm.softening;
     c->prm = *prm;
     if (rebuild) c->stage = 0;
     else if (remoment && c->stage > 1) c->stage = 1;

@@ -291,4 +291,47 @@ __device__ __forceinline__ int key_lcp_levels(uint64_t a, uint64_t b)
 
 __device__ __forceinline__ void hot_flag(unsigned *status, unsigned bit) { atomicOr(status, bit); }
 
+// K1 compensating force smoothing of support eps (Sec. "Force Smoothing"; the kernel is
+// the unit-mass density 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2), x = r/eps).  A source of
+// mass m at d (r^2 = |d|^2) gives a = G m f d and phi = -G m psi, and f2 = 2 df/d(r^2)
+// enters the pair's tidal tensor -G m (f I + f2 d d^T).  For r < eps, u = r^2/eps^2:
+//   f = (175/16 - 147/8 u + 135/16 u^2)/eps^3, f2 = (-147/4 + 135/4 u)/eps^5,
+//   psi = (105 - 175 u + 147 u^2 - 45 u^3)/(32 eps);
+// Newtonian (f = r^-3, f2 = -3 r^-5, psi = 1/r) for r >= eps.  Finite at r = 0 when eps > 0.
+// Evaluated in t = 1 - u, where every coefficient has one sign (the powers of u cancel to
+// a tenth near the edge, which float32 would pay for):
+//   f eps^3 = 1 + 3/2 t + 135/16 t^2,  f2 eps^5 = -(3 + 135/4 t),
+//   psi eps = 1 + t/2 + 3/8 t^2 + 45/32 t^3.
+template <class T>
+struct K1Const {
+    T e2, ie2, ie, ie3, ie5;  // eps^2, 1/eps^2, 1/eps, 1/eps^3, 1/eps^5
+};
+
+template <class T>
+__device__ __forceinline__ K1Const<T> k1_const(T eps2)
+{
+    K1Const<T> k;
+    k.e2 = eps2;
+    k.ie2 = T(1) / eps2;
+    k.ie = T(1) / sqrt(eps2);  // correctly rounded: a common factor of every inside pair
+    k.ie3 = k.ie2 * k.ie;
+    k.ie5 = k.ie3 * k.ie2;
+    return k;
+}
+
+template <class T>
+__device__ __forceinline__ void k1_pair(T r2, const K1Const<T> &k, T &f, T &f2, T &psi)
+{
+    const bool in = r2 < k.e2;
+    const T ri = hot_rsqrt(in ? k.e2 : r2);
+    const T ri2 = ri * ri;
+    const T t = T(1) - r2 * k.ie2;
+    const T fin = (T(1) + t * (T(1.5) + t * T(135.0 / 16.0))) * k.ie3;
+    const T f2in = -(T(3) + t * T(135.0 / 4.0)) * k.ie5;
+    const T pin = (T(1) + t * (T(0.5) + t * (T(0.375) + t * T(45.0 / 32.0)))) * k.ie;
+    f = in ? fin : ri2 * ri;
+    f2 = in ? f2in : T(-3) * ri2 * ri2 * ri;
+    psi = in ? pin : ri;
+}
+
 #endif  // __CUDACC__

@@ -257,7 +257,7 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 // fetched 32 entries at a time, one entry per lane, and broadcast by shuffles; source
 // particles are staged SRC at a time with positions relative to g (float32: the
 // leaf-relative copy plus the leaf offset).
-template <int P, class T, int NS, int MODE>
+template <int P, class T, int NS, int MODE, int SOFT>
 __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, const int32_t *__restrict__ l_p2p,
                                          const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
                                          const T *__restrict__ rec, const float4 *__restrict__ prel,
@@ -268,6 +268,8 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
     constexpr int RL = Cfg<P, T>::RL;
     const unsigned lane = lane_id();
     int fill = 0;
+    K1Const<T> kc{};
+    if constexpr (SOFT == HOT_SOFT_K1) kc = k1_const(eps2);
     // A sink can meet itself, or a source at zero separation, only in a batch holding one
     // of the group's own leaves or when eps = 0; other batches take the loop without the
     // per-pair tests.
@@ -288,6 +290,33 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     const T dx = sx - x[s][0], dy = sy - x[s][1], dz = sz - x[s][2];
+                    if constexpr (SOFT == HOT_SOFT_K1) {
+                        // K1: eps2 is the support squared, not added to the separation
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        T f, f2, psi;
+                        k1_pair(r2, kc, f, f2, psi);
+                        if constexpr (CK) {
+                            const bool ok = (r2 > T(0) || kc.e2 > T(0)) && (id != self[s]);
+                            f = ok ? f : T(0);
+                            f2 = ok ? f2 : T(0);
+                            psi = ok ? psi : T(0);
+                        }
+                        const T mf = m * f;
+                        if constexpr (MODE == 0) {
+                            ax[s] += mf * dx;
+                            ay[s] += mf * dy;
+                            az[s] += mf * dz;
+                            ph[s] -= m * psi;
+                        } else {
+                            // the pair term with the tidal tensor f I + f2 d d^T (Plummer below)
+                            const T du = dx * wt[s][0] + dy * wt[s][1] + dz * wt[s][2];
+                            const T cc = mf * wt[s][3] + m * f2 * du;
+                            ph[s] += mf;
+                            ax[s] += cc * dx;
+                            ay[s] += cc * dy;
+                            az[s] += cc * dz;
+                        }
+                    } else {
                     const T r2 = dx * dx + dy * dy + dz * dz + eps2;
                     T rinv;
                     if constexpr (CK) {
@@ -312,6 +341,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                         ax[s] += cc * dx;
                         ay[s] += cc * dy;
                         az[s] += cc * dz;
+                    }
                     }
                 }
             }
@@ -400,7 +430,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 // tangent evaluation at 4 up to p = 4 and at 2 for p >= 5 (no faster at 3 or 4).
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
 // NS = 2: two sinks per lane (slices of 64 sinks: the items at even 32-sink positions).
-template <int P, class T, int NS, int MODE>
+template <int P, class T, int NS, int MODE, int SOFT>
 __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : 5) k_interact(
     const uint32_t *__restrict__ nitem_p, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const int32_t *__restrict__ cend,
@@ -497,7 +527,7 @@ __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : 5) k_i
             if (!m2p_list<P, T, NS, MODE>(sm, Gr, l_m2p, rec, x, wt, sj, nsplit, active, acc, phase, wait_limit,
                                           probe != 0, status))
                 return;
-            p2p_list<P, T, NS, MODE>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, wt, self, sj, nsplit, active,
+            p2p_list<P, T, NS, MODE, SOFT>(sm, Gr, l_p2p, cbegin, ccount, rec, prel, spos, smass, x, wt, self, sj, nsplit, active,
                                eps2, Gt, acc);
             if (NS == 1) {
                 // combine the list splits of each sink in float64
@@ -546,12 +576,12 @@ __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : 5) k_i
     }
 }
 
-template <int P, class T, int NS, int MODE>
-int launch_interact(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double *acc, double *pot, const T *wsink,
-                    double *gsink)
+template <int P, class T, int NS, int MODE, int SOFT>
+int launch_interact_s(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double *acc, double *pot, const T *wsink,
+                      double *gsink)
 {
     const size_t smem = sizeof(Smem<P, T>) * IW;
-    auto kern = k_interact<P, T, NS, MODE>;
+    auto kern = k_interact<P, T, NS, MODE, SOFT>;
     HOT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HOT_CK(cudaMemsetAsync(work, 0, sizeof(unsigned), s));
     const T *rec = nullptr;
@@ -572,6 +602,16 @@ int launch_interact(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double 
                                        gsink, c->wait_polls ? c->wait_polls : WAIT_LIMIT, c->wait_probe,
                                        c->d_status);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
+}
+
+// The kernel of the context's force smoothing.
+template <int P, class T, int NS, int MODE>
+int launch_interact(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double *acc, double *pot, const T *wsink,
+                    double *gsink)
+{
+    if (c->prm.softening == HOT_SOFT_K1)
+        return launch_interact_s<P, T, NS, MODE, HOT_SOFT_K1>(c, s, cls, work, acc, pot, wsink, gsink);
+    return launch_interact_s<P, T, NS, MODE, HOT_SOFT_PLUMMER>(c, s, cls, work, acc, pot, wsink, gsink);
 }
 
 template <int P>

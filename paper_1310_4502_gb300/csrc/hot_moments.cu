@@ -386,6 +386,9 @@ int moments_p(hot_ctx *c)
         k_m2m_level<P><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
                                                      c->cmass.p, c->ccom.p, c->cmom.p);
     }
+    // the expansion's kernel: Plummer-softened, or Newtonian under K1 smoothing (whose
+    // kernel differs from 1/r only inside eps, which accepted cells keep clear of)
+    const double eps_rec = c->prm.softening == HOT_SOFT_K1 ? 0.0 : c->prm.eps;
     // aggregates of inner cells
     const int64_t max_items = ncell + N * (c->maxlevel + 1) / CHUNK + 1;
     HOT_CK(c->item_off.ensure(ncell + 1, s));
@@ -413,12 +416,12 @@ int moments_p(hot_ctx *c)
         HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
         k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
-                                                                    c->prm.G, c->prm.eps, reclen, c->rec64.p);
+                                                                    c->prm.G, eps_rec, reclen, c->rec64.p);
     } else {
         HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
         k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
-                                                                   c->prm.G, c->prm.eps, reclen, c->rec32.p);
+                                                                   c->prm.G, eps_rec, reclen, c->rec32.p);
     }
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }

@@ -49,9 +49,12 @@ __device__ __forceinline__ void mac_log_newton(double d, double b, double B1, do
 // whenever a step leaves the bracket, until a step or the bracket is below 1e-13
 // relative (r_c = 0 when b_max = 0, where E vanishes).  That accuracy is far inside the
 // 1e-9 band in which the traversal re-takes decisions with the bound itself.
+// guard > 0 (K1 smoothing, guard = eps) also requires d >= b_max + guard, so that every
+// source of an accepted cell is at least eps from every sink: r_c = max(r_c, b_max + guard)
+// (guard = 0 leaves r_c, which is above b_max, unchanged).
 __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
                              const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
-                             double G, double tol, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
+                             double G, double tol, double guard, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -93,6 +96,7 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
             rc = d;
         }
     }
+    rc = fmax(rc, b + guard);
     TCell t;
     t.x = ccom[3 * c + 0];
     t.y = ccom[3 * c + 1];
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     const int32_t *__restrict__ cend,
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
-    const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol,
+    const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, double guard,
     int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                                 __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
                             const double d = __dsub_rn(dist, dmax);
                             const double b = cbmax[c];
-                            acc = d > b && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                            acc = d > b && d >= __dadd_rn(b, guard) && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
                         }
                         }
                         kind = acc ? 1 : (leaf ? 2 : 3);
@@ -342,9 +346,11 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     HOT_CK(c->gkey2.ensure(ng + 1, s));
     HOT_CK(c->gorder.ensure(ng + 1, s));
     HOT_CK(c->gorder2.ensure(ng + 1, s));
+    // acceptance guard of K1 smoothing: no source of an accepted cell within eps of a sink
+    const double guard = c->prm.softening == HOT_SOFT_K1 ? c->prm.eps : 0.0;
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
-                                                            c->p_mom, c->prm.G, tol, c->tcell.p, c->tcellf.p);
+                                                            c->p_mom, c->prm.G, tol, guard, c->tcell.p, c->tcellf.p);
     // One pass into per-group slots when their capacities (the largest counts of the
     // previous traversal plus headroom) fit the budget; otherwise count, scan, fill.
     const int64_t capm = c->slot_capm, capp = c->slot_capp;
@@ -362,13 +368,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         if (slots)
             k_traverse<2><<<blocks, TW * 32, 0, s>>>(
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
                 capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
             k_traverse<0><<<blocks, TW * 32, 0, s>>>(
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
                 slot_over, c->gkey.p, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
@@ -413,7 +419,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_COUNT_LAUNCH();
         k_traverse<1><<<blocks, TW * 32, 0, s>>>(
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, c->trav_scratch.p, c->trav_cap,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }

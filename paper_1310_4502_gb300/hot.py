@@ -16,6 +16,7 @@ from . import build as _build
 HOT_OK, HOT_EINVAL, HOT_ESTATE, HOT_ENOMEM, HOT_EOVERFLOW, HOT_ECUDA, HOT_EINPUT, HOT_ETIMEOUT = (
     0, -1, -2, -3, -4, -5, -6, -7)
 HOT_FP32_MIXED, HOT_FP64 = 0, 1
+HOT_SOFT_PLUMMER, HOT_SOFT_K1 = 0, 1
 HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS, HOT_DBGSET_WAIT_PROBE = 0, 1, 2, 3
 
 DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
@@ -31,7 +32,8 @@ EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moment
 
 class hot_params(C.Structure):
     _fields_ = [("p", C.c_int), ("tol", C.c_double), ("eps", C.c_double), ("G", C.c_double),
-                ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int)]
+                ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int),
+                ("softening", C.c_int)]
 
 
 class HotError(RuntimeError):
@@ -109,9 +111,11 @@ def _need(t, shape_last=None):
     return t
 
 
-def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed"):
+def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
+                softening="plummer"):
     prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
-    return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec)
+    soft = HOT_SOFT_K1 if softening in ("k1", HOT_SOFT_K1) else HOT_SOFT_PLUMMER
+    return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec, soft)
 
 
 class Hot:

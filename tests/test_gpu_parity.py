@@ -208,3 +208,69 @@ def test_call_order_and_bad_arguments():
     with pytest.raises(hot.HotError) as e:
         h.traverse(0.0)
     assert e.value.code == hot.HOT_EINVAL
+
+
+K1_CASES = {
+    # support 0.05 in a unit-scale Plummer sphere: a large share of the P2P pairs inside it
+    "plummer4096_k1": lambda: (W.make("plummer4096").pos, W.make("plummer4096").mass, 0.05),
+    "clustered32k_k1": lambda: (CASES["clustered32k"][0], CASES["clustered32k"][1], 2e-3),
+    "ragged_dup_k1": lambda: (CASES["ragged_dup"][0], CASES["ragged_dup"][1], 0.02),
+}
+
+
+@pytest.mark.parametrize("name", list(K1_CASES))
+@pytest.mark.parametrize("p", [4, 6])
+def test_k1_lists_and_forces(name, p):
+    """K1 compensating smoothing: the lists (with the d >= b_max + eps guard) and the forces
+    against the oracle's K1 tree, at the tolerances of the Plummer parity test."""
+    pos, mass, eps = K1_CASES[name]()
+    tol = 1e-4
+    t = oracle.Tree(pos, mass)
+    t.softening("k1", eps)
+    t.moments(p)
+    t.traverse(tol)
+    ra, rp = t.force(1.0, eps)
+    cl = t.cells()
+    for prec in ("fp64", "mixed"):
+        h, P, M = build(pos, mass, p=p, tol=tol, eps=eps, precision=prec, softening="k1")
+        h.compute_moments(p)
+        h.traverse(tol)
+        assert lists_match(h, t, cl) == 0
+        acc = torch.empty_like(P)
+        pot = torch.empty_like(M)
+        h.evaluate_forces(acc, pot)
+        torch.cuda.synchronize()
+        a = acc.cpu().numpy()
+        ph = pot.cpu().numpy()
+        rel = np.linalg.norm(a - ra, axis=1) / np.linalg.norm(ra, axis=1)
+        prel = np.abs(ph - rp) / np.abs(rp)
+        if prec == "fp64":
+            assert rel.max() < 1e-11, rel.max()
+            assert prel.max() < 1e-11, prel.max()
+        else:
+            assert np.sqrt(np.mean(rel ** 2)) < 1e-5, np.sqrt(np.mean(rel ** 2))
+            assert rel.max() < 1e-3, rel.max()
+            assert prel.max() < 1e-4, prel.max()
+
+
+def test_k1_differs_from_plummer_and_changing_it_recomputes():
+    """The smoothing is part of the parameters: switching it on a built tree recomputes
+    moments and lists, and the two kernels give different forces at short range."""
+    pos, mass, eps = K1_CASES["plummer4096_k1"]()
+    h, P, M = build(pos, mass, p=4, tol=1e-4, eps=eps)
+    h.compute_moments(4)
+    h.traverse(1e-4)
+    acc = torch.empty_like(P)
+    h.evaluate_forces(acc)
+    a_pl = acc.cpu().numpy()
+    h.set_params(p=4, tol=1e-4, eps=eps, softening="k1")
+    with pytest.raises(hot.HotError) as e:
+        h.evaluate_forces(acc)
+    assert e.value.code == hot.HOT_ESTATE
+    h.compute_moments(4)
+    h.traverse(1e-4)
+    h.evaluate_forces(acc)
+    a_k1 = acc.cpu().numpy()
+    ref, _ = oracle.direct(pos, mass, 1.0, eps, soft="k1")
+    assert np.max(np.linalg.norm(a_k1 - a_pl, axis=1) / np.linalg.norm(ref, axis=1)) > 1e-2
+    assert np.sqrt(np.mean((np.linalg.norm(a_k1 - ref, axis=1) / np.linalg.norm(ref, axis=1)) ** 2)) < 1e-4
