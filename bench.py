@@ -425,7 +425,19 @@ def run_ours(args):
                      "stages_ms": st6, "m2p_interactions": s6["n_m2p_int"], "p2p_interactions": s6["n_pairs"],
                      "interact_tflops": (s6["n_m2p_int"] * FLOPS_M2P[6] + s6["n_pairs"] * P2P_FLOPS)
                      / (st6["interact"] * 1e-3) / 1e12}
+        acc_p6 = acc.clone()
         del h64, h6
+        # p = 8, the highest order
+        h8 = hot.Hot(p=8, tol=w.tol, eps=w.eps, precision="mixed")
+        k8 = min(args.steps, 5)
+        t8, st8, _, _ = timed(h8, k8, 1, p=8)
+        s8 = h8.sizes()
+        out["p8"] = {"value": N / (t8 / k8 * 1e-3), "unit": "particles/s", "ms_per_step": t8 / k8,
+                     "stages_ms": st8, "m2p_interactions": s8["n_m2p_int"], "p2p_interactions": s8["n_pairs"],
+                     "interact_tflops": (s8["n_m2p_int"] * FLOPS_M2P[8] + s8["n_pairs"] * P2P_FLOPS)
+                     / (st8["interact"] * 1e-3) / 1e12}
+        acc_p8 = acc.clone()
+        del h8
         # the paper's science tolerance on the same box
         h5 = hot.Hot(p=w.p, tol=1e-5, eps=w.eps, precision="mixed")
         h5.force(P, M, acc)
@@ -462,6 +474,8 @@ def run_ours(args):
             ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps, sinks=sub)
             out["error"].update(sub_err(mixed_acc, ref))
             out["tol1e5"].update(sub_err(acc_tol5, ref))
+            out["p6"].update(sub_err(acc_p6, ref))
+            out["p8"].update(sub_err(acc_p8, ref))
             refk, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps, sinks=sub, soft="k1")
             out["k1"].update(sub_err(acc_k1, refk))
         # the differentiation configuration: clustered recipe at N = 2^18

@@ -75,7 +75,7 @@ enum { HOT_SOFT_PLUMMER = 0, HOT_SOFT_K1 = 1 };
 typedef struct hot_ctx hot_ctx;
 
 typedef struct {
-    int p;          /* expansion order, 0..6 (potential terms |a| <= p)           */
+    int p;          /* expansion order, 0..8 (potential terms |a| <= p)           */
     double tol;     /* absolute acceleration error bound per accepted cell, > 0  */
     double eps;     /* softening length, >= 0 (Plummer length or K1 support)     */
     double G;       /* gravitational constant                                     */
@@ -115,7 +115,7 @@ int hot_build_tree(hot_ctx *ctx, const double *pos, const double *mass, int64_t 
  * M_a = sum m (x - z)^a, |a| <= p): P2M at the leaves, exact binomial
  * translation (M2M) upwards, in float64; plus the acceptance-test aggregates
  * b_max = max |x - z|, B_{p+1}, B_{p+2} (B_n = sum m |x - z|^n), and the
- * interaction coefficient records.  p in [0, 6]; asynchronous. */
+ * interaction coefficient records.  p in [0, 8]; asynchronous. */
 int hot_compute_moments(hot_ctx *ctx, int p);
 
 /* Group-wise traversal (Sec. "Improving instruction-level parallelism": m
@@ -140,7 +140,8 @@ int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
  * lists and frozen expansion centres (moments stay functions of positions and
  * masses).  g_acc device [N][3]; g_pot device [N] or NULL; outputs g_pos
  * device [N][3], g_mass device [N], original order.  Requires a preceding
- * hot_traverse on the same tree. */
+ * hot_traverse on the same tree.  Orders p <= 6 (HOT_EINVAL above: the
+ * coefficient adjoints of one interaction are summed in registers). */
 int hot_adjoint(hot_ctx *ctx, const double *g_acc, const double *g_pot, double *g_pos,
                 double *g_mass);
 

@@ -6,7 +6,7 @@ The paper produces its high-order interaction routines by metaprogramming
 script plays that role for the GPU path.  It writes ``generated.cuh`` with, for
 every order p = 0..6:
 
-* ``m2p_eval<P>(rec, rx, ry, rz, phi, ax, ay, az)`` -- one cell-to-particle
+* ``m2p_eval<P>(rec, rx, ry, rz, phi, ax, ay, az)`` (P <= PMAX) -- one cell-to-particle
   interaction of the Cartesian expansion of the softened kernel
   F(R) = (|R|^2 + eps^2)^{-1/2}, written in a traced form:
       Phi(R) = sum_a (-1)^|a| / a!  d^a F(R) M_a
@@ -37,7 +37,8 @@ import math
 import os
 import sys
 
-PMAX = 6
+PMAX = 8      # largest expansion order of the forces
+ADJ_PMAX = 6  # largest order of the adjoint's routines and tables
 HDR = 8  # record header slots: inv_s, eps^2/s^2, centre hi (3), centre lo (3)
 
 
@@ -86,9 +87,9 @@ def s_terms(p):
 
 # Flops per M2P interaction used as the roofline convention (FMA = 2, rsqrt = 1): the
 # operation count of the traced expansion evaluated with explicit monomials (the first
-# form of this routine).  The Horner form below does the same mathematics with fewer
-# instructions; the convention stays fixed so that rates stay comparable.
-M2P_FLOP_CONVENTION = [32, 40, 82, 164, 307, 534, 874]
+# form of this routine, p = 0..8).  The Horner form below does the same mathematics with
+# fewer instructions; the convention stays fixed so that rates stay comparable.
+M2P_FLOP_CONVENTION = [32, 40, 82, 164, 307, 534, 874, 1358, 2023]
 
 
 class _Prog:
@@ -537,7 +538,7 @@ def main(out_path):
         len(ia), ", ".join("{%d,%d,%d}" % a for a in ia)))
     parts.extend(evals)
     parts.extend(records)
-    ts, ta, tg, tc = m2m_transposed(PMAX)
+    ts, ta, tg, tc = m2m_transposed(ADJ_PMAX)
     parts.append(f"__device__ const unsigned short m2mt_start[{len(ts)}] = {{{', '.join(map(str, ts))}}};")
     parts.append(f"__device__ const unsigned char m2mt_alpha[{len(ta)}] = {{{', '.join(map(str, ta))}}};")
     parts.append(f"__device__ const unsigned char m2mt_gamma[{len(tg)}] = {{{', '.join(map(str, tg))}}};")
@@ -545,7 +546,7 @@ def main(out_path):
     parts.append("static constexpr int HOT_NS[%d] = {%s};" % (PMAX + 1, ", ".join(str(len(s_terms(q))) for q in range(PMAX + 1))))
     # record-adjoint gather tables of every order, concatenated (per-order bases)
     sb, eb, rs, rq, re_, rf = [], [], [], [], [], []
-    for q in range(PMAX + 1):
+    for q in range(ADJ_PMAX + 1):
         st, qq, ee, ff = record_adjoint_table(q)
         sb.append(len(rs))
         eb.append(len(rq))
@@ -553,12 +554,13 @@ def main(out_path):
         rq.extend(qq)
         re_.extend(ee)
         rf.extend(ff)
-    parts.append("static constexpr int RADJ_SBASE[%d] = {%s};" % (PMAX + 1, ", ".join(map(str, sb))))
+    parts.append(f"#define HOT_ADJ_PMAX {ADJ_PMAX}")
+    parts.append("static constexpr int RADJ_SBASE[%d] = {%s};" % (ADJ_PMAX + 1, ", ".join(map(str, sb))))
     parts.append(f"__device__ const unsigned short radj_start[{len(rs)}] = {{{', '.join(map(str, rs))}}};")
     parts.append(f"__device__ const unsigned short radj_q[{len(rq)}] = {{{', '.join(map(str, rq))}}};")
     parts.append(f"__device__ const unsigned char radj_e[{len(re_)}] = {{{', '.join(map(str, re_))}}};")
     parts.append(f"__device__ const double radj_f[{len(rf)}] = {{{', '.join(repr(float(x)) for x in rf)}}};")
-    for q in range(PMAX + 1):
+    for q in range(ADJ_PMAX + 1):
         parts.append(gen_tangent(q))
         parts.append(gen_cbar(q))
         parts.append(gen_record_adjoint(q))
@@ -568,7 +570,7 @@ def main(out_path):
           "T ux, T uy, T uz, T v, T* __restrict__ cb) {"]
     aw = ["template <int P> __device__ __forceinline__ void m2p_record_adjoint(const double* __restrict__ cb, "
           "double inv_s, double G, double* __restrict__ Mbar) {"]
-    for q in range(PMAX + 1):
+    for q in range(ADJ_PMAX + 1):
         kw = "if" if q == 0 else "else if"
         tw.append(f"  {kw} constexpr (P == {q}) {{ if constexpr (sizeof(T) == 4) m2p_tangent_{q}_f32(c, rx, ry, rz, ux, uy, uz, "
                   f"phi, ax, ay, az, dax, day, daz); else m2p_tangent_{q}_f64(c, rx, ry, rz, ux, uy, uz, phi, ax, ay, az, "

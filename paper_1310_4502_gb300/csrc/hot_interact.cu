@@ -426,12 +426,13 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 
 // cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
 // Occupancy (measured on the clustered 2^20 and lattice 128^3 workloads): the forces run
-// at 5 CTAs per SM (102 registers; 4% faster than 4 at p = 4, 3% at p = 6); the adjoint's
-// tangent evaluation at 4 up to p = 4 and at 2 for p >= 5 (no faster at 3 or 4).
+// at 5 CTAs per SM (102 registers; 4% faster than 4 at p = 4, 3% at p = 6), at p = 7, 8 at
+// 2 (their staged records fill the shared memory of 2 CTAs); the adjoint's tangent
+// evaluation at 4 up to p = 4 and at 2 for p >= 5 (no faster at 3 or 4).
 // NS = 1: one sink per lane (slices of 32 sinks, spare lanes split the lists);
 // NS = 2: two sinks per lane (slices of 64 sinks: the items at even 32-sink positions).
 template <int P, class T, int NS, int MODE, int SOFT>
-__global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : 5) k_interact(
+__global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : (P >= 7 ? 2 : 5)) k_interact(
     const uint32_t *__restrict__ nitem_p, int cls, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const int32_t *__restrict__ cend,
     const double *__restrict__ spos, const double *__restrict__ smass, const float4 *__restrict__ prel,
@@ -644,6 +645,8 @@ int hot_impl_forces(hot_ctx *c, double *acc, double *pot)
         case 4: r = forces_p<4>(c, acc, pot); break;
         case 5: r = forces_p<5>(c, acc, pot); break;
         case 6: r = forces_p<6>(c, acc, pot); break;
+        case 7: r = forces_p<7>(c, acc, pot); break;
+        case 8: r = forces_p<8>(c, acc, pot); break;
         default: return HOT_ESTATE;
     }
     hot_toc(c, 4);

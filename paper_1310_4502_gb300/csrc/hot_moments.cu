@@ -440,6 +440,8 @@ int hot_impl_moments(hot_ctx *c, int p)
         case 4: r = moments_p<4>(c); break;
         case 5: r = moments_p<5>(c); break;
         case 6: r = moments_p<6>(c); break;
+        case 7: r = moments_p<7>(c); break;
+        case 8: r = moments_p<8>(c); break;
         default: return HOT_EINVAL;
     }
     hot_toc(c, 2);

@@ -63,6 +63,8 @@ void tg(const double *M, double is, double G, double eps, const double *R, const
 #define DISPATCH(F, ...) switch (p) { case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break; \
     case 2: F<2>(__VA_ARGS__); break; case 3: F<3>(__VA_ARGS__); break; case 4: F<4>(__VA_ARGS__); break; \
     case 5: F<5>(__VA_ARGS__); break; case 6: F<6>(__VA_ARGS__); break; }
+#define DISPATCH8(F, ...) switch (p) { case 7: F<7>(__VA_ARGS__); break; case 8: F<8>(__VA_ARGS__); break; \
+    default: DISPATCH(F, __VA_ARGS__) }
 template <int P> void ev32(const double *M, const double *z, double is, double G, double e, const double *R, double *o)
 { ev<P, float>(M, z, is, G, e, R, o); }
 template <int P> void ev64(const double *M, const double *z, double is, double G, double e, const double *R, double *o)
@@ -71,7 +73,7 @@ extern "C" {
 void g_eval(int p, int dbl, const double *M, const double *z, double is, double G, double eps, const double *R,
             double *out)
 {
-    if (dbl) { DISPATCH(ev64, M, z, is, G, eps, R, out) } else { DISPATCH(ev32, M, z, is, G, eps, R, out) }
+    if (dbl) { DISPATCH8(ev64, M, z, is, G, eps, R, out) } else { DISPATCH8(ev32, M, z, is, G, eps, R, out) }
 }
 void g_tangent(int p, const double *M, double is, double G, double eps, const double *R, const double *u,
                double v, double *out)
@@ -184,7 +186,7 @@ def _sink(rng, com, bmax):
     return (rng.uniform(2.5, 6.0) * bmax) * u / np.linalg.norm(u)
 
 
-@pytest.mark.parametrize("p", range(7))
+@pytest.mark.parametrize("p", range(9))
 def test_record_and_eval_match_oracle_m2p(gen, p):
     rng = np.random.default_rng(100 + p)
     for case in range(6):

@@ -89,7 +89,7 @@ def test_hash_lookup(name):
     assert np.all(h.lookup(absent) == -1)
 
 
-@pytest.mark.parametrize("p", [0, 1, 4, 6])
+@pytest.mark.parametrize("p", [0, 1, 4, 6, 8])
 @pytest.mark.parametrize("prec,mtol", [("fp64", 1e-10), ("mixed", 3e-6)])
 def test_moments(p, prec, mtol):
     """Moments against the oracle's direct sums, relative to m b_max^|a|: float64
@@ -180,6 +180,25 @@ def test_lists_and_forces(name, p):
             assert prel.max() < 1e-4, prel.max()
 
 
+@pytest.mark.parametrize("name", ["plummer4096", "clustered32k", "ragged_dup"])
+def test_lists_and_forces_order8(name):
+    """p = 8, the paper's highest order: lists and forces against the oracle (same
+    tolerances as the lower orders)."""
+    test_lists_and_forces(name, 8)
+
+
+def test_adjoint_refuses_orders_above_6():
+    pos, mass, eps = CASES["plummer4096"]
+    h, P, M = build(pos, mass, p=8, tol=1e-4, eps=eps)
+    h.compute_moments(8)
+    h.traverse(1e-4)
+    acc = torch.empty_like(P)
+    h.evaluate_forces(acc)
+    with pytest.raises(hot.HotError) as e:
+        h.adjoint(torch.ones_like(P), None, torch.empty_like(P), torch.empty_like(M))
+    assert e.value.code == hot.HOT_EINVAL
+
+
 def test_call_order_and_bad_arguments():
     pos, mass, _ = CASES["tiny7"]
     h = hot.Hot()
@@ -202,7 +221,7 @@ def test_call_order_and_bad_arguments():
     assert e.value.code == hot.HOT_EINPUT
     h.build_tree(P, M)
     with pytest.raises(hot.HotError) as e:
-        h.compute_moments(7)
+        h.compute_moments(9)
     assert e.value.code == hot.HOT_EINVAL
     h.compute_moments(4)
     with pytest.raises(hot.HotError) as e:
