@@ -62,6 +62,9 @@ def lib():
         L.orc_soft_eval.argtypes = [C.c_int, C.c_double, C.c_double, _d]
         L.orc_tree_softening.restype = C.c_int
         L.orc_tree_softening.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.orc_tree_order_range.restype = C.c_int
+        L.orc_tree_order_range.argtypes = [C.c_void_p, C.c_int]
+        L.orc_tree_list_orders.argtypes = [C.c_void_p, _i32]
         L.orc_bbox.argtypes = [C.c_int64, _d, _d, C.POINTER(C.c_double)]
         L.orc_keys.argtypes = [C.c_int64, _d, _d, C.c_double, _u64]
         L.orc_sort.argtypes = [C.c_int64, _u64, _i64]
@@ -280,6 +283,13 @@ class Tree:
         if lib().orc_tree_softening(self._h, SOFT[soft], float(eps)) != 0:
             raise ValueError("bad softening")
 
+    def order_range(self, p_lo):
+        """Per-interaction order selection (after moments(p)): every accepted cell is
+        evaluated at the lowest order in [p_lo, p] whose error bound meets the tolerance;
+        p_lo=None restores the fixed order p."""
+        if lib().orc_tree_order_range(self._h, -1 if p_lo is None else int(p_lo)) != 0:
+            raise ValueError("bad order range")
+
     def traverse(self, tol, G=1.0, groups=None):
         if groups is None:
             r = lib().orc_tree_traverse(self._h, float(tol), float(G))
@@ -300,8 +310,10 @@ class Tree:
         p2p = np.zeros(off[-1, 1], dtype=np.int32)
         bor = np.zeros(off[-1, 2], dtype=np.int32)
         lib().orc_tree_lists(self._h, m2p, p2p, bor)
+        order = np.zeros(off[-1, 0], dtype=np.int32)
+        lib().orc_tree_list_orders(self._h, order)
         return dict(m2p=(off[:, 0].copy(), m2p), p2p=(off[:, 1].copy(), p2p),
-                    border=(off[:, 2].copy(), bor))
+                    border=(off[:, 2].copy(), bor), m2p_order=order)
 
     def force(self, G=1.0, eps=0.0, groups=None):
         n = len(self.mass)

@@ -498,6 +498,12 @@ typedef struct orc_tree {
     /* force smoothing the lists are built for (Plummer unless set) */
     int soft;
     double soft_eps;
+    /* per-interaction order selection: with varq, each accepted cell is evaluated at
+     * the lowest order q in [p_lo, p] whose bound meets the tolerance (orders in lm2pq);
+     * cBn[(p+3) c + n] = sum m |x - z|^n, n = 0..p+2 */
+    int varq, p_lo;
+    double *cBn;
+    ivec *lm2pq;
 } orc_tree;
 
 static int64_t new_cell(orc_tree *t)
@@ -620,6 +626,11 @@ static void free_lists(orc_tree *t)
     free(t->lp2p);
     free(t->lborder);
     t->lm2p = t->lp2p = t->lborder = NULL;
+    if (t->lm2pq) {
+        for (int64_t g = 0; g < t->ngroup; g++) free(t->lm2pq[g].v);
+        free(t->lm2pq);
+        t->lm2pq = NULL;
+    }
 }
 
 void orc_tree_free(orc_tree *t)
@@ -630,7 +641,7 @@ void orc_tree_free(orc_tree *t)
     free(t->ckey); free(t->clevel); free(t->cparent); free(t->cnchild); free(t->cchild);
     free(t->cbegin); free(t->ccount);
     free(t->gcell); free(t->gcen); free(t->gdmax);
-    free(t->cmass); free(t->ccom); free(t->cmom); free(t->cbmax); free(t->cB1); free(t->cB2);
+    free(t->cmass); free(t->ccom); free(t->cmom); free(t->cbmax); free(t->cB1); free(t->cB2); free(t->cBn);
     free(t);
 }
 
@@ -694,7 +705,9 @@ int orc_tree_moments(orc_tree *t, int p)
     int tab[200][3];
     midx_table(p, tab);
     t->p = p;
-    free(t->cmass); free(t->ccom); free(t->cmom); free(t->cbmax); free(t->cB1); free(t->cB2);
+    free(t->cmass); free(t->ccom); free(t->cmom); free(t->cbmax); free(t->cB1); free(t->cB2); free(t->cBn);
+    t->varq = 0;
+    t->cBn = (double *)malloc(sizeof(double) * (size_t)(p + 3) * (size_t)t->ncell);
     t->cmass = (double *)malloc(sizeof(double) * (size_t)t->ncell);
     t->ccom = (double *)malloc(sizeof(double) * 3 * (size_t)t->ncell);
     t->cmom = (double *)malloc(sizeof(double) * (size_t)nc * (size_t)t->ncell);
@@ -728,7 +741,32 @@ int orc_tree_moments(orc_tree *t, int p)
         t->cbmax[c] = bmax;
         t->cB1[c] = B1;
         t->cB2[c] = B2;
+        double *Bn = t->cBn + (size_t)(p + 3) * c;
+        for (int q = 0; q < p + 3; q++) Bn[q] = 0.0;
+        for (int64_t s = b; s < b + n; s++) {
+            double dx = t->spos[3 * s + 0] - z[0];
+            double dy = t->spos[3 * s + 1] - z[1];
+            double dz = t->spos[3 * s + 2] - z[2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double rq = 1.0;
+            for (int q = 0; q < p + 3; q++) {
+                Bn[q] += t->smass[s] * rq;
+                rq *= r;
+            }
+        }
     }
+    return 0;
+}
+
+/* Per-interaction order selection (Sec. "Multipole Error Bounds": the bounds decide
+ * between orders of expansion and refinement): after orc_tree_moments(p), orders
+ * p_lo..p; every accepted cell is then evaluated at the lowest order whose bound meets
+ * the tolerance.  p_lo < 0 restores the fixed order p. */
+int orc_tree_order_range(orc_tree *t, int p_lo)
+{
+    if (!t->cmom || p_lo > t->p) return -1;
+    t->varq = p_lo >= 0;
+    t->p_lo = p_lo >= 0 ? p_lo : t->p;
     return 0;
 }
 
@@ -782,6 +820,28 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c)
     int guard = t->soft != ORC_SOFT_K1 || d >= b + t->soft_eps;
     if (t->soft == ORC_SOFT_K1 && b + t->soft_eps > 0.0 && fabs(d - (b + t->soft_eps)) <= 1e-9 * (b + t->soft_eps))
         ivec_push(&t->lborder[g], (int32_t)c);
+    if (t->varq) {
+        /* the lowest order in [p_lo, p] whose bound meets the tolerance */
+        int qa = -1;
+        if (d > b && guard) {
+            const double *Bn = t->cBn + (size_t)(t->p + 3) * c;
+            for (int q = t->p_lo; q <= t->p && qa < 0; q++) {
+                double E = orc_mac_bound(d, b, Bn[q + 1], Bn[q + 2], q, t->Gmac);
+                if (fabs(E - t->tol) <= 1e-9 * t->tol) ivec_push(&t->lborder[g], (int32_t)c);
+                if (E <= t->tol) qa = q;
+            }
+        }
+        if (b > 0.0 && fabs(d - b) <= 1e-9 * b) ivec_push(&t->lborder[g], (int32_t)c);
+        if (qa >= 0) {
+            ivec_push(&t->lm2p[g], (int32_t)c);
+            ivec_push(&t->lm2pq[g], (int32_t)qa);
+        } else if (is_leaf(t, c)) {
+            ivec_push(&t->lp2p[g], (int32_t)c);
+        } else {
+            for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k]);
+        }
+        return;
+    }
     if (d > b) {
         double E = orc_mac_bound(d, b, t->cB1[c], t->cB2[c], t->p, t->Gmac);
         accept = guard && E <= t->tol;
@@ -824,6 +884,7 @@ int orc_tree_traverse(orc_tree *t, double tol, double G)
     t->lm2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
     t->lp2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
     t->lborder = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    if (t->varq) t->lm2pq = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < t->ngroup; g++) trav_rec(t, g, 0);
     return 0;
@@ -839,6 +900,15 @@ void orc_tree_list_sizes(const orc_tree *t, int64_t *sizes)
     }
 }
 
+/* Order of every M2P entry, concatenated like the M2P lists (p everywhere with a fixed
+ * order). */
+void orc_tree_list_orders(const orc_tree *t, int32_t *orders)
+{
+    int64_t a = 0;
+    for (int64_t g = 0; g < t->ngroup; g++)
+        for (int64_t e = 0; e < t->lm2p[g].n; e++) orders[a++] = t->lm2pq ? t->lm2pq[g].v[e] : t->p;
+}
+
 /* Concatenated lists in group order. */
 void orc_tree_lists(const orc_tree *t, int32_t *m2p, int32_t *p2p, int32_t *border)
 {
@@ -852,6 +922,10 @@ void orc_tree_lists(const orc_tree *t, int32_t *m2p, int32_t *p2p, int32_t *bord
         c += t->lborder[g].n;
     }
 }
+
+/* Expansion order of M2P entry e of group g (the moments' order p unless selected per
+ * interaction; lower orders use the leading components, which are ordered by degree). */
+static int m2p_order(const orc_tree *t, int64_t g, int64_t e) { return t->lm2pq ? t->lm2pq[g].v[e] : t->p; }
 
 /* Force on the sinks of one group from its lists, given per-cell moments and
  * (frozen) expansion centres.  Outputs are written at the sinks' original indices. */
@@ -869,7 +943,7 @@ static void group_force(const orc_tree *t, int64_t g, const double *spos, const 
             int64_t c = t->lm2p[g].v[e];
             double R[3];
             for (int d = 0; d < 3; d++) R[d] = x[d] - t->ccom[3 * c + d];
-            m2p_eval(t->p, tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
+            m2p_eval(m2p_order(t, g, e), tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
         }
         for (int64_t e = 0; e < t->lp2p[g].n; e++) {
             int64_t c = t->lp2p[g].v[e];
@@ -914,6 +988,7 @@ int orc_tree_traverse_groups(orc_tree *t, double tol, double G, int64_t nsel, co
     t->lm2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
     t->lp2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
     t->lborder = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    if (t->varq) t->lm2pq = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t q = 0; q < nsel; q++) trav_rec(t, gsel[q], 0);
     return 0;
@@ -988,7 +1063,7 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
                 int64_t c = t->lm2p[gk].v[e];
                 double R[3];
                 for (int d = 0; d < 3; d++) R[d] = x[d] - t->ccom[3 * c + d];
-                m2p_eval(p, (const int(*)[3])tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
+                m2p_eval(m2p_order(t, gk, e), (const int(*)[3])tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
             }
             for (int64_t e = 0; e < t->lp2p[gk].n; e++) {
                 int64_t c = t->lp2p[gk].v[e];
@@ -1010,7 +1085,7 @@ double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass,
                     if (s == sk) continue;
                     double a[3] = {0.0, 0.0, 0.0}, phi = 0.0, R[3];
                     for (int d = 0; d < 3; d++) R[d] = spos[3 * s + d] - t->ccom[3 * c + d];
-                    m2p_eval(p, (const int(*)[3])tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
+                    m2p_eval(m2p_order(t, g, e), (const int(*)[3])tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
                     int64_t i = t->perm[s];
                     Lo += w[3 * i] * a[0] + w[3 * i + 1] * a[1] + w[3 * i + 2] * a[2];
                     if (v) Lo += v[i] * phi;

@@ -734,3 +734,112 @@ def test_k1_frozen_force_is_tree_force():
     a, ph = t.force(1.0, 0.05)
     fa, fph = t.frozen_force(w.pos, w.mass, 1.0, 0.05)
     assert np.max(rel_err(fa, a)) < 1e-12 and np.max(np.abs(fph - ph) / np.abs(ph)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Per-interaction order selection (Sec. "Multipole Error Bounds": the bounds choose
+# between expansion orders and refinement).  Reading: among the orders p_lo..p, an
+# accepted cell is evaluated at the lowest order whose bound meets the tolerance.
+# --------------------------------------------------------------------------
+
+def _ordered_tree(pos, mass, p, p_lo, tol):
+    t = oracle.Tree(pos, mass)
+    t.moments(p)
+    t.order_range(p_lo)
+    t.traverse(tol)
+    return t
+
+
+def test_order_selection_takes_the_lowest_order_meeting_the_bound():
+    """Brute force: B_n recomputed from each cell's particles; every M2P entry's order q
+    meets the bound and order q - 1 (if allowed) does not."""
+    w = W.make("plummer4096")
+    p, p_lo, tol = 8, 1, 1e-5
+    t = _ordered_tree(w.pos, w.mass, p, p_lo, tol)
+    L = t.lists()
+    cl, gr, mo = t.cells(), t.groups(), t.get_moments()
+    _, perm = t.keys()
+    sp = w.pos[perm]
+    sm = w.mass[perm]
+    om, cells = L["m2p"]
+    orders = L["m2p_order"]
+    assert orders.min() >= p_lo and orders.max() <= p and len(set(orders.tolist())) > 2
+    Bcache = {}
+    checked = 0
+    for g in range(0, len(gr["cell"]), 7):
+        for e in range(om[g], om[g + 1]):
+            c, q = cells[e], orders[e]
+            if c not in Bcache:
+                b0, n0 = cl["begin"][c], cl["count"][c]
+                r = np.linalg.norm(sp[b0:b0 + n0] - mo["com"][c], axis=1)
+                Bcache[c] = [float(np.sum(sm[b0:b0 + n0] * r ** k)) for k in range(p + 3)]
+            Bn = Bcache[c]
+            d = np.linalg.norm(mo["com"][c] - gr["centre"][g]) - gr["dmax"][g]
+            b = mo["bmax"][c]
+            assert oracle.mac_bound(d, b, Bn[q + 1], Bn[q + 2], q) <= tol * (1 + 1e-9)
+            if q > p_lo:
+                assert oracle.mac_bound(d, b, Bn[q], Bn[q + 1], q - 1) > tol * (1 - 1e-9)
+            checked += 1
+    assert checked > 1000
+
+
+def test_order_selection_keeps_the_per_interaction_bound():
+    """Unsoftened: every accepted interaction still errs by at most tol at its order."""
+    rng = np.random.default_rng(2)
+    n = 3000
+    pos = np.concatenate([rng.standard_normal((n // 2, 3)) * 0.1, rng.uniform(-1, 1, (n - n // 2, 3))])
+    mass = np.full(n, 1.0 / n)
+    ad, _ = oracle.direct(pos, mass, 1.0, 0.0)
+    for p, p_lo, tol in ((6, 0, 1e-5), (8, 2, 1e-6)):
+        t = _ordered_tree(pos, mass, p, p_lo, tol)
+        at, _ = t.force(1.0, 0.0)
+        L = t.lists()
+        nm = np.diff(L["m2p"][0])
+        g, cl = t.groups(), t.cells()
+        _, perm = t.keys()
+        bound = np.zeros(n)
+        for gi, c in enumerate(g["cell"]):
+            b, cnt = cl["begin"][c], cl["count"][c]
+            bound[perm[b:b + cnt]] = tol * nm[gi]
+        err = np.linalg.norm(at - ad, axis=1)
+        assert np.all(err <= bound * (1 + 1e-9) + 1e-13)
+
+
+def test_order_selection_degenerate_range_is_the_fixed_order():
+    w = W.make("plummer4096")
+    t0 = oracle.Tree(w.pos, w.mass)
+    t0.moments(6)
+    t0.traverse(1e-5)
+    a0, p0 = t0.force(1.0, w.eps)
+    t1 = _ordered_tree(w.pos, w.mass, 6, 6, 1e-5)
+    a1, p1 = t1.force(1.0, w.eps)
+    L0, L1 = t0.lists(), t1.lists()
+    assert np.array_equal(L0["m2p"][1], L1["m2p"][1]) and np.array_equal(L0["p2p"][1], L1["p2p"][1])
+    assert np.all(L1["m2p_order"] == 6)
+    assert np.max(rel_err(a1, a0)) < 1e-15 and np.max(np.abs(p1 - p0) / np.abs(p0)) < 1e-15
+
+
+def test_order_selection_lowers_the_cost_within_the_tolerance():
+    """Each accepted interaction now spends its error budget (E_q just under tol) where
+    the fixed order 8 stays far below it, so the error grows while the cost falls; the
+    per-interaction bound (the previous test) is what the tolerance promises."""
+    w = W.make("plummer4096")
+    ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps)
+    conv = [32, 40, 82, 164, 307, 534, 874, 1358, 2023]  # flops of one M2P per order
+    res = {}
+    for p_lo in (None, 0):
+        t = oracle.Tree(w.pos, w.mass)
+        t.moments(8)
+        t.order_range(p_lo)
+        t.traverse(1e-5)
+        a, _ = t.force(1.0, w.eps)
+        L = t.lists()
+        ns = t.cells()["count"][t.groups()["cell"]]
+        per_group = np.add.reduceat(np.array([conv[q] for q in L["m2p_order"]] + [0]),
+                                    np.minimum(L["m2p"][0][:-1], len(L["m2p_order"])))[:len(ns)]
+        per_group[np.diff(L["m2p"][0]) == 0] = 0
+        res[p_lo] = (float(np.sum(per_group * ns)), np.sqrt(np.mean(rel_err(a, ref) ** 2)))
+    cost_fixed, err_fixed = res[None]
+    cost_var, err_var = res[0]
+    assert cost_var < 0.8 * cost_fixed, (cost_var / cost_fixed)
+    assert err_fixed < err_var < 1e-4, (err_fixed, err_var)
