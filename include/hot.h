@@ -83,6 +83,9 @@ typedef struct {
     int group_max;  /* sink groups: topmost cells with <= group_max particles     */
     int precision;  /* HOT_FP32_MIXED or HOT_FP64 interaction arithmetic          */
     int softening;  /* HOT_SOFT_PLUMMER or HOT_SOFT_K1                            */
+    int p_min;      /* -1: every accepted cell at order p; 0..p: per-interaction  */
+                    /* order selection, the lowest order in [p_min, p] whose      */
+                    /* bound E_q(d) <= tol (B_{q+1}, B_{q+2}) accepts the cell     */
 } hot_params;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
@@ -140,8 +143,9 @@ int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
  * lists and frozen expansion centres (moments stay functions of positions and
  * masses).  g_acc device [N][3]; g_pot device [N] or NULL; outputs g_pos
  * device [N][3], g_mass device [N], original order.  Requires a preceding
- * hot_traverse on the same tree.  Orders p <= 6 (HOT_EINVAL above: the
- * coefficient adjoints of one interaction are summed in registers). */
+ * hot_traverse on the same tree.  Orders p <= 6 and a fixed order (HOT_EINVAL
+ * for p > 6 or under per-interaction order selection: the coefficient adjoints
+ * of one interaction are summed in registers, for one order). */
 int hot_adjoint(hot_ctx *ctx, const double *g_acc, const double *g_pot, double *g_pos,
                 double *g_mass);
 
@@ -181,7 +185,8 @@ enum {
     HOT_DBG_M2P_OFFSETS = 18, /* int64[ngroup + 1]                           */
     HOT_DBG_M2P_CELLS = 19,   /* int32[n_m2p]                                */
     HOT_DBG_P2P_OFFSETS = 20, /* int64[ngroup + 1]                           */
-    HOT_DBG_P2P_CELLS = 21    /* int32[n_p2p]                                */
+    HOT_DBG_P2P_CELLS = 21,   /* int32[n_p2p]                                */
+    HOT_DBG_M2P_ORDERS = 22   /* int32[n_m2p]: expansion order of each M2P entry */
 };
 int hot_debug_get(hot_ctx *ctx, int what, void *host_dst, size_t bytes);
 

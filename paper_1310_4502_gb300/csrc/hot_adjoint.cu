@@ -790,8 +790,9 @@ int adjoint_p(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_po
 
 int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
 {
-    // the adjoint's coefficient sums are register-resident per lane: orders up to 6
-    if (c->p_mom > HOT_ADJ_PMAX) return HOT_EINVAL;
+    // the adjoint's coefficient sums are register-resident per lane: orders up to 6, one
+    // order per call (not under per-interaction order selection)
+    if (c->p_mom > HOT_ADJ_PMAX || c->varq) return HOT_EINVAL;
     hot_tic(c, 5);
     int r;
     switch (c->p_mom) {

@@ -29,6 +29,7 @@ int check_params(const hot_params *p)
     if (p->leaf_max < 1 || p->group_max < 1 || p->leaf_max > 4096 || p->group_max > (1 << 20)) return HOT_EINVAL;
     if (p->precision != HOT_FP32_MIXED && p->precision != HOT_FP64) return HOT_EINVAL;
     if (p->softening != HOT_SOFT_PLUMMER && p->softening != HOT_SOFT_K1) return HOT_EINVAL;
+    if (p->p_min < -1 || p->p_min > p->p) return HOT_EINVAL;
     return HOT_OK;
 }
 
@@ -107,7 +108,8 @@ int hot_set_params(hot_ctx *c, const hot_params *prm)
     if (e) return e;
     bool rebuild = prm->leaf_max != c->prm.leaf_max || prm->group_max != c->prm.group_max;
     bool remoment = prm->p != c->prm.p || prm->eps != c->prm.eps || prm->G != c->prm.G ||
-                    prm->precision != c->prm.precision || prm->softening != c->prm.softening;
+                    prm->precision != c->prm.precision || prm->softening != c->prm.softening ||
+                    prm->p_min != c->prm.p_min;
     c->prm = *prm;
     if (rebuild) c->stage = 0;
     else if (remoment && c->stage > 1) c->stage = 1;
@@ -124,7 +126,7 @@ int hot_build_tree(hot_ctx *c, const double *pos, const double *mass, int64_t N)
 
 int hot_compute_moments(hot_ctx *c, int p)
 {
-    if (!c || p < 0 || p > HOT_PMAX) return HOT_EINVAL;
+    if (!c || p < 0 || p > HOT_PMAX || c->prm.p_min > p) return HOT_EINVAL;
     if (c->stage < 1) return HOT_ESTATE;
     c->prm.p = p;
     c->stage = 1;
@@ -212,6 +214,7 @@ int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
         case HOT_DBG_M2P_CELLS: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
         case HOT_DBG_P2P_OFFSETS: src = c->off_p2p.p; need = (ng + 1) * sizeof(int64_t); min_stage = 3; break;
         case HOT_DBG_P2P_CELLS: src = c->l_p2p.p; need = c->n_p2p * sizeof(int32_t); min_stage = 3; break;
+        case HOT_DBG_M2P_ORDERS: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
         default: return HOT_EINVAL;
     }
     if (c->stage < min_stage) return HOT_ESTATE;
@@ -219,6 +222,15 @@ int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
     if (need == 0) return HOT_OK;
     if (cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, c->st) != cudaSuccess) return HOT_ECUDA;
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
+    // M2P entries carry their order above HOT_ORDER_SHIFT under order selection
+    if (what == HOT_DBG_M2P_CELLS || what == HOT_DBG_M2P_ORDERS) {
+        int32_t *e = (int32_t *)dst;
+        for (int64_t i = 0; i < c->n_m2p; ++i) {
+            const uint32_t v = (uint32_t)e[i];
+            e[i] = what == HOT_DBG_M2P_CELLS ? (int32_t)(v & HOT_CELL_MASK)
+                                             : (c->varq ? (int32_t)(v >> HOT_ORDER_SHIFT) : c->p_mom);
+        }
+    }
     return HOT_OK;
 }
 
@@ -306,6 +318,12 @@ void hot_destroy(hot_ctx *c)
     c->tcell.release(s); c->tcellf.release(s); c->slot_m2p.release(s); c->slot_p2p.release(s);
     c->gkey.release(s); c->gkey2.release(s); c->gorder.release(s); c->gorder2.release(s);
     c->slice_cnt.release(s); c->slice_off.release(s); c->items.release(s);
+    c->cBn.release(s); c->bn_cnt.release(s); c->bn_off.release(s); c->bn_cell.release(s); c->bn_part.release(s);
+    c->rcq.release(s);
+    for (int q = 0; q < HOT_ORDERS; ++q) {
+        c->rec32q[q].release(s);
+        c->rec64q[q].release(s);
+    }
     c->adj_w.release(s); c->adj_xhl.release(s); c->adj_gsink.release(s); c->adj_gp2p.release(s);
     c->adj_mbar.release(s); c->adj_cbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);
     c->tp_val.release(s); c->tp_val2.release(s); c->tp_start.release(s); c->tp_end.release(s);

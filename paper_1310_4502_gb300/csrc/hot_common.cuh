@@ -23,6 +23,11 @@
 
 #define HOT_MAXLEVEL 21
 
+// Per-interaction order selection: an M2P list entry is cell | order << HOT_ORDER_SHIFT.
+#define HOT_ORDER_SHIFT 27
+#define HOT_CELL_MASK ((1u << HOT_ORDER_SHIFT) - 1u)
+#define HOT_ORDERS 9  // orders 0..8
+
 // Device memory the one-pass traversal may hold in per-group list slots (bytes).
 #define HOT_SLOT_BUDGET (16.0 * 1024 * 1024 * 1024)
 
@@ -130,6 +135,15 @@ struct hot_ctx {
     DBuf<float> rec32;
     DBuf<double> rec64;
     DBuf<float4> prel;
+    // per-interaction order selection (0 <= p_min < p): orders q_lo..p_mom
+    int varq = 0, q_lo = 0;
+    DBuf<double> cBn;                  // [ncell][p+3]: B_n = sum m |x - z|^n, n = 0..p+2
+    DBuf<uint32_t> bn_cnt, bn_off;     // aggregate work items of every cell
+    DBuf<int32_t> bn_cell;
+    DBuf<double> bn_part;
+    DBuf<float> rec32q[HOT_ORDERS];    // records of the orders below p (order p: rec32 / rec64)
+    DBuf<double> rec64q[HOT_ORDERS];
+    DBuf<double> rcq;                  // [ncell][p - q_lo + 1]: acceptance radius of each order
 
     // lists
     double tol_lists = 0;
@@ -223,6 +237,7 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
 int hot_impl_moments(hot_ctx *c, int p);
 int hot_impl_traverse(hot_ctx *c, double tol);
 int hot_impl_forces(hot_ctx *c, double *acc, double *pot);
+int hot_impl_forces_vq(hot_ctx *c, double *acc, double *pot);
 int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos,
                      double *g_mass);
 int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink, cudaStream_t s);

@@ -336,9 +336,8 @@ template <int P, class T>
 __global__ void k_records(const double *__restrict__ cmom, const double *__restrict__ ccom,
                           const double *__restrict__ cbmax,
                           const int32_t *__restrict__ clevel, int64_t ncell, const double *__restrict__ frame,
-                          double G, double eps, int reclen, T *__restrict__ rec)
+                          double G, double eps, int reclen, int mom_stride, T *__restrict__ rec)
 {
-    constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const double L = frame[3];
@@ -352,7 +351,97 @@ __global__ void k_records(const double *__restrict__ cmom, const double *__restr
         frexp(L, &e);
         inv_s = ldexp(1.0, clevel[c] - e);
     }
-    m2p_record<P, T>(cmom + c * NC, ccom + 3 * c, inv_s, G, eps, rec + c * (int64_t)reclen);
+    m2p_record<P, T>(cmom + c * mom_stride, ccom + 3 * c, inv_s, G, eps, rec + c * (int64_t)reclen);
+}
+
+// ---------------------------------------------------------------------------
+// Per-interaction order selection: B_n = sum m |x - z|^n for n = 0..p+2 of every cell
+// (the acceptance bound of each order q needs B_{q+1}, B_{q+2}), from the particles in
+// work items of CHUNK, summed per cell in item order; and the records of the lower
+// orders, from the leading components of the order-p moments.
+// ---------------------------------------------------------------------------
+__global__ void k_bn_count(const int32_t *__restrict__ ccount, int64_t ncell, uint32_t *__restrict__ nitem)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) nitem[c] = (uint32_t)((ccount[c] + CHUNK - 1) / CHUNK);
+}
+
+template <int P>
+__global__ void __launch_bounds__(MW * 32) k_bn_part(
+    const int32_t *__restrict__ item_cell, const uint32_t *__restrict__ off, const uint32_t *__restrict__ nitem_p,
+    const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount, const double *__restrict__ ccom,
+    const double *__restrict__ spos, const double *__restrict__ smass, double *__restrict__ part)
+{
+    constexpr int NB = P + 3;
+    const int64_t nitem = *nitem_p;
+    const unsigned lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * MW;
+    for (int64_t it = (int64_t)blockIdx.x * MW + (threadIdx.x >> 5); it < nitem; it += nw) {
+        const int32_t c = item_cell[it];
+        const int64_t b = cbegin[c] + (it - off[c]) * CHUNK;
+        const int64_t e0 = cbegin[c] + (int64_t)ccount[c];
+        const int64_t e = b + CHUNK < e0 ? b + CHUNK : e0;
+        const double z0 = ccom[3 * (int64_t)c + 0], z1 = ccom[3 * (int64_t)c + 1], z2 = ccom[3 * (int64_t)c + 2];
+        double B[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) B[q] = 0.0;
+        for (int64_t s = b + lane; s < e; s += 32) {
+            const double dx = spos[3 * s + 0] - z0, dy = spos[3 * s + 1] - z1, dz = spos[3 * s + 2] - z2;
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const double ms = smass[s];
+            double rq = 1.0;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                B[q] += ms * rq;
+                rq *= r;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const double v = warp_sum(B[q]);
+            if (lane == 0) part[NB * it + q] = v;
+        }
+    }
+}
+
+__global__ void k_bn_combine(const uint32_t *__restrict__ off, int64_t ncell, int nb, const double *__restrict__ part,
+                             double *__restrict__ cBn)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    for (int q = 0; q < nb; ++q) {
+        double t = 0.0;
+        for (uint32_t k = off[c]; k < off[c + 1]; ++k) t += part[(int64_t)nb * k + q];
+        cBn[(int64_t)nb * c + q] = t;
+    }
+}
+
+// Records of order q from moments of stride mom_stride (the order-p moments).
+template <class T>
+int records_of_order(hot_ctx *c, int q, int mom_stride, double eps_rec, T *dst)
+{
+    const int64_t nc = c->ncell;
+    HOT_COUNT_LAUNCH();
+#define HOT_REC_Q(QQ)                                                                                         \
+    case QQ:                                                                                                  \
+        k_records<QQ, T><<<hot_blocks(nc, 128), 128, 0, c->st>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, \
+                                                                 nc, c->frame.p, c->prm.G, eps_rec,          \
+                                                                 HOT_REC_LEN[QQ], mom_stride, dst);           \
+        break;
+    switch (q) {
+        HOT_REC_Q(0)
+        HOT_REC_Q(1)
+        HOT_REC_Q(2)
+        HOT_REC_Q(3)
+        HOT_REC_Q(4)
+        HOT_REC_Q(5)
+        HOT_REC_Q(6)
+        HOT_REC_Q(7)
+        HOT_REC_Q(8)
+        default: return HOT_EINVAL;
+    }
+#undef HOT_REC_Q
+    return HOT_OK;
 }
 
 template <int P>
@@ -416,12 +505,44 @@ int moments_p(hot_ctx *c)
         HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
         k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
-                                                                    c->prm.G, eps_rec, reclen, c->rec64.p);
+                                                                    c->prm.G, eps_rec, reclen, NC, c->rec64.p);
     } else {
         HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
         HOT_COUNT_LAUNCH();
         k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
-                                                                   c->prm.G, eps_rec, reclen, c->rec32.p);
+                                                                   c->prm.G, eps_rec, reclen, NC, c->rec32.p);
+    }
+    // per-interaction order selection: B_n of every cell and the records of orders p_min..p-1
+    c->varq = c->prm.p_min >= 0 && c->prm.p_min < P;
+    c->q_lo = c->varq ? c->prm.p_min : P;
+    if (c->varq) {
+        constexpr int NB = P + 3;
+        HOT_CK(c->bn_cnt.ensure(ncell + 1, s));
+        HOT_CK(c->bn_off.ensure(ncell + 1, s));
+        HOT_CK(c->bn_cell.ensure(max_items, s));
+        HOT_CK(c->bn_part.ensure((size_t)NB * max_items, s));
+        HOT_CK(c->cBn.ensure((size_t)NB * ncell, s));
+        HOT_COUNT_LAUNCH();
+        k_bn_count<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->ccount.p, ncell, c->bn_cnt.p);
+        r = hot_scan_u32_to_u32(c->bn_cnt.p, c->bn_off.p, ncell, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_COUNT_LAUNCH();
+        k_item_cells<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->bn_off.p, ncell, c->bn_cell.p);
+        HOT_COUNT_LAUNCH();
+        k_bn_part<P><<<c->nsm * 16, MW * 32, 0, s>>>(c->bn_cell.p, c->bn_off.p, c->bn_off.p + ncell, c->cbegin.p,
+                                                     c->ccount.p, c->ccom.p, c->spos.p, c->smass.p, c->bn_part.p);
+        HOT_COUNT_LAUNCH();
+        k_bn_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->bn_off.p, ncell, NB, c->bn_part.p, c->cBn.p);
+        for (int q = c->q_lo; q < P; ++q) {
+            if (c->prm.precision == HOT_FP64) {
+                HOT_CK(c->rec64q[q].ensure((size_t)HOT_REC_LEN[q] * ncell, s));
+                r = records_of_order<double>(c, q, NC, eps_rec, c->rec64q[q].p);
+            } else {
+                HOT_CK(c->rec32q[q].ensure((size_t)HOT_REC_LEN[q] * ncell, s));
+                r = records_of_order<float>(c, q, NC, eps_rec, c->rec32q[q].p);
+            }
+            if (r) return r;
+        }
     }
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }

@@ -52,13 +52,8 @@ __device__ __forceinline__ void mac_log_newton(double d, double b, double B1, do
 // guard > 0 (K1 smoothing, guard = eps) also requires d >= b_max + guard, so that every
 // source of an accepted cell is at least eps from every sink: r_c = max(r_c, b_max + guard)
 // (guard = 0 leaves r_c, which is above b_max, unchanged).
-__global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
-                             const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
-                             double G, double tol, double guard, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
+__device__ double mac_radius_solve(double b, double B1, double B2, int p, double G, double tol)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const double b = cbmax[c], B1 = cB1[c], B2 = cB2[c];
     double rc = 0.0;
     if (b > 0.0) {
         double lo = b, hi = 2.0 * b;
@@ -96,6 +91,33 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
             rc = d;
         }
     }
+    return rc;
+}
+
+// With per-interaction order selection (cBn != nullptr: B_n of every cell, n = 0..p+2) the
+// radius of every order q_lo..p goes to rcq and a cell is accepted at the smallest one
+// (some order meets the tolerance).
+__global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
+                             const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
+                             double G, double tol, double guard, const double *__restrict__ cBn, int q_lo,
+                             double *__restrict__ rcq, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double b = cbmax[c];
+    double rc;
+    if (cBn) {
+        const double *Bn = cBn + (int64_t)(p + 3) * c;
+        const int nq = p - q_lo + 1;
+        rc = INFINITY;
+        for (int q = q_lo; q <= p; ++q) {
+            const double r = mac_radius_solve(b, Bn[q + 1], Bn[q + 2], q, G, tol);
+            rcq[(int64_t)nq * c + (q - q_lo)] = r;
+            rc = fmin(rc, r);
+        }
+    } else {
+        rc = mac_radius_solve(b, cB1[c], cB2[c], p, G, tol);
+    }
     rc = fmax(rc, b + guard);
     TCell t;
     t.x = ccom[3 * c + 0];
@@ -130,6 +152,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, double guard,
+    const double *__restrict__ cBn, int q_lo, const double *__restrict__ rcq,
     int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
@@ -173,6 +196,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
             for (int base = 0; base < na; base += 32) {
                 const int i = base + (int)lane;
                 const int32_t c = i < na ? A[i] : -1;
+                int32_t ent = c;  // the M2P entry: the cell, with its order under order selection
                 int kind = 0;  // 1 M2P, 2 P2P, 3 open
                 if (c >= 0) {
                     const bool leaf = cnchild[c] == 0;
@@ -212,21 +236,60 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                                 __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
                             const double d = __dsub_rn(dist, dmax);
                             const double b = cbmax[c];
-                            acc = d > b && d >= __dadd_rn(b, guard) && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                            if (cBn) {
+                                // some order of the range meets the tolerance
+                                const double *Bn = cBn + (int64_t)(p + 3) * c;
+                                acc = false;
+                                if (d > b && d >= __dadd_rn(b, guard))
+                                    for (int q = q_lo; q <= p && !acc; ++q)
+                                        acc = mac_bound(d, b, Bn[q + 1], Bn[q + 2], q, G) <= tol;
+                            } else {
+                                acc = d > b && d >= __dadd_rn(b, guard) && mac_bound(d, b, cB1[c], cB2[c], p, G) <= tol;
+                            }
                         }
                         }
                         kind = acc ? 1 : (leaf ? 2 : 3);
+                        if (cBn && acc) {
+                            // the lowest order whose radius the distance reaches; within 1e-9 of a
+                            // radius, that order's bound as stated (d rounded as the oracle does)
+                            const TCell t = tcell[c];
+                            const double ex = __dsub_rn(t.x, gx), ey = __dsub_rn(t.y, gy), ez = __dsub_rn(t.z, gz);
+                            const double dist = __dsqrt_rn(
+                                __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+                            const double d = __dsub_rn(dist, dmax);
+                            const double b = cbmax[c];
+                            const double *Bn = cBn + (int64_t)(p + 3) * c;
+                            const int nq = p - q_lo + 1;
+                            int qa = p;
+                            for (int q = q_lo; q <= p; ++q) {
+                                const double rq = rcq[(int64_t)nq * c + (q - q_lo)];
+                                bool ok;
+                                if (!(rq < INFINITY))
+                                    ok = false;
+                                else if (d > rq * (1.0 + 1e-9))
+                                    ok = true;
+                                else if (d < rq * (1.0 - 1e-9))
+                                    ok = false;
+                                else
+                                    ok = d > b && mac_bound(d, b, Bn[q + 1], Bn[q + 2], q, G) <= tol;
+                                if (ok) {
+                                    qa = q;
+                                    break;
+                                }
+                            }
+                            ent = (int32_t)((uint32_t)c | ((uint32_t)qa << HOT_ORDER_SHIFT));
+                        }
                     }
                 }
                 const unsigned mm = __ballot_sync(0xffffffffu, kind == 1);
                 const unsigned pm = __ballot_sync(0xffffffffu, kind == 2);
                 if (FILL) {
-                    if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = c;
+                    if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = ent;
                     if (kind == 2) l_p2p[op + np + __popc(pm & lt)] = c;
                 } else {
                     if (SLOTS) {
                         const int64_t im = nm + __popc(mm & lt), ip = np + __popc(pm & lt);
-                        if (kind == 1 && im < capm) l_m2p[om + im] = c;
+                        if (kind == 1 && im < capm) l_m2p[om + im] = ent;
                         if (kind == 2 && ip < capp) l_p2p[op + ip] = c;
                     }
                     if (kind == 2) p2p_parts += (uint64_t)ccount[c];
@@ -348,9 +411,16 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     HOT_CK(c->gorder2.ensure(ng + 1, s));
     // acceptance guard of K1 smoothing: no source of an accepted cell within eps of a sink
     const double guard = c->prm.softening == HOT_SOFT_K1 ? c->prm.eps : 0.0;
+    // per-interaction order selection: radii of every order, orders in the M2P entries
+    const double *cBn = c->varq ? c->cBn.p : nullptr;
+    if (c->varq) {
+        if (c->ncell > (int64_t)HOT_CELL_MASK) return HOT_EINVAL;
+        HOT_CK(c->rcq.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
+    }
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
-                                                            c->p_mom, c->prm.G, tol, guard, c->tcell.p, c->tcellf.p);
+                                                            c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p,
+                                                            c->tcell.p, c->tcellf.p);
     // One pass into per-group slots when their capacities (the largest counts of the
     // previous traversal plus headroom) fit the budget; otherwise count, scan, fill.
     const int64_t capm = c->slot_capm, capp = c->slot_capp;
@@ -368,13 +438,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         if (slots)
             k_traverse<2><<<blocks, TW * 32, 0, s>>>(
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
                 capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
             k_traverse<0><<<blocks, TW * 32, 0, s>>>(
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
                 slot_over, c->gkey.p, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
@@ -419,7 +489,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_COUNT_LAUNCH();
         k_traverse<1><<<blocks, TW * 32, 0, s>>>(
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, c->trav_scratch.p, c->trav_cap,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }

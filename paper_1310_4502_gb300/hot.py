@@ -22,7 +22,7 @@ HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS, HOT_DBGSET_
 DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
            CELL_PARENT=7, CELL_NCHILD=8, GROUP_CELL=9, GROUP_CENTRE=10, GROUP_DMAX=11, CELL_MASS=12,
            CELL_COM=13, MOMENTS=14, CELL_BMAX=15, CELL_B1=16, CELL_B2=17, M2P_OFFSETS=18, M2P_CELLS=19,
-           P2P_OFFSETS=20, P2P_CELLS=21)
+           P2P_OFFSETS=20, P2P_CELLS=21, M2P_ORDERS=22)
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
@@ -33,7 +33,7 @@ EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moment
 class hot_params(C.Structure):
     _fields_ = [("p", C.c_int), ("tol", C.c_double), ("eps", C.c_double), ("G", C.c_double),
                 ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int),
-                ("softening", C.c_int)]
+                ("softening", C.c_int), ("p_min", C.c_int)]
 
 
 class HotError(RuntimeError):
@@ -112,10 +112,11 @@ def _need(t, shape_last=None):
 
 
 def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
-                softening="plummer"):
+                softening="plummer", p_min=None):
     prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
     soft = HOT_SOFT_K1 if softening in ("k1", HOT_SOFT_K1) else HOT_SOFT_PLUMMER
-    return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec, soft)
+    return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec, soft,
+                      -1 if p_min is None else int(p_min))
 
 
 class Hot:
@@ -206,6 +207,7 @@ class Hot:
             "MOMENTS": (np.float64, (nc, ncomp)), "CELL_BMAX": (np.float64, (nc,)), "CELL_B1": (np.float64, (nc,)),
             "CELL_B2": (np.float64, (nc,)), "M2P_OFFSETS": (np.int64, (ng + 1,)), "M2P_CELLS": (np.int32, (s["n_m2p"],)),
             "P2P_OFFSETS": (np.int64, (ng + 1,)), "P2P_CELLS": (np.int32, (s["n_p2p"],)),
+            "M2P_ORDERS": (np.int32, (s["n_m2p"],)),
         }[what]
         out = np.zeros(spec[1], dtype=spec[0])
         _ck(load().hot_debug_get(self._h, DBG[what], out.ctypes.data_as(C.c_void_p), out.nbytes),

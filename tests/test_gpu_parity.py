@@ -293,3 +293,67 @@ def test_k1_differs_from_plummer_and_changing_it_recomputes():
     ref, _ = oracle.direct(pos, mass, 1.0, eps, soft="k1")
     assert np.max(np.linalg.norm(a_k1 - a_pl, axis=1) / np.linalg.norm(ref, axis=1)) > 1e-2
     assert np.sqrt(np.mean((np.linalg.norm(a_k1 - ref, axis=1) / np.linalg.norm(ref, axis=1)) ** 2)) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["plummer4096", "clustered32k", "ragged_dup"])
+@pytest.mark.parametrize("p,p_min", [(8, 0), (6, 2)])
+def test_order_selection_lists_orders_and_forces(name, p, p_min):
+    """Per-interaction order selection: the lists, the order of every M2P entry (the
+    lowest order in [p_min, p] meeting the bound) and the forces against the oracle."""
+    pos, mass, eps = CASES[name]
+    tol = 1e-4 if name != "ragged_dup" else 1e-5
+    t = oracle.Tree(pos, mass)
+    t.moments(p)
+    t.order_range(p_min)
+    t.traverse(tol)
+    ra, rp = t.force(1.0, eps)
+    cl = t.cells()
+    L = t.lists()
+    om, cm = L["m2p"]
+    qo = L["m2p_order"]
+    ob, cb = L["border"]
+    assert len(set(qo.tolist())) > 1
+    for prec in ("fp64", "mixed"):
+        h, P, M = build(pos, mass, p=p, tol=tol, eps=eps, precision=prec, p_min=p_min)
+        h.compute_moments(p)
+        h.traverse(tol)
+        assert lists_match(h, t, cl) == 0
+        goff = h.debug_get("M2P_OFFSETS")
+        gcells = h.debug_get("M2P_CELLS")
+        gq = h.debug_get("M2P_ORDERS")
+        for g in range(len(om) - 1):
+            border = set(cb[ob[g]:ob[g + 1]].tolist())
+            ref = dict(zip(cm[om[g]:om[g + 1]].tolist(), qo[om[g]:om[g + 1]].tolist()))
+            got = dict(zip(gcells[goff[g]:goff[g + 1]].tolist(), gq[goff[g]:goff[g + 1]].tolist()))
+            for c in ref.keys() & got.keys():
+                assert ref[c] == got[c] or c in border, (g, c, ref[c], got[c])
+        acc = torch.empty_like(P)
+        pot = torch.empty_like(M)
+        h.evaluate_forces(acc, pot)
+        torch.cuda.synchronize()
+        a = acc.cpu().numpy()
+        ph = pot.cpu().numpy()
+        rel = np.linalg.norm(a - ra, axis=1) / np.linalg.norm(ra, axis=1)
+        prel = np.abs(ph - rp) / np.abs(rp)
+        if prec == "fp64":
+            assert rel.max() < 1e-11, rel.max()
+            assert prel.max() < 1e-11, prel.max()
+        else:
+            assert np.sqrt(np.mean(rel ** 2)) < 1e-5, np.sqrt(np.mean(rel ** 2))
+            assert rel.max() < 1e-3, rel.max()
+            assert prel.max() < 1e-4, prel.max()
+        if prec == "mixed":
+            with pytest.raises(hot.HotError) as e:
+                h.adjoint(torch.ones_like(P), None, torch.empty_like(P), torch.empty_like(M))
+            assert e.value.code == hot.HOT_EINVAL
+
+
+def test_order_range_is_validated():
+    with pytest.raises(hot.HotError) as e:
+        hot.Hot(p=4, p_min=5)
+    assert e.value.code == hot.HOT_EINVAL
+    pos, mass, _ = CASES["plummer4096"]
+    h, _, _ = build(pos, mass, p=6, p_min=3)
+    with pytest.raises(hot.HotError) as e:
+        h.compute_moments(2)
+    assert e.value.code == hot.HOT_EINVAL
