@@ -22,10 +22,17 @@ int forces_p(hot_ctx *c, double *acc, double *pot)
         return launch_interact<P, double, 1, 0>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
     if constexpr (P >= 5) {
         // large expansions: groups of more than 32 sinks run two sinks per lane, so that
-        // every coefficient read from shared memory feeds two independent evaluations
-        int r = launch_interact<P, float, 1, 0>(c, c->st, 1, work, acc, pot, nullptr, nullptr);
-        if (r) return r;
-        return launch_interact<P, float, 2, 0>(c, c->st, 2, work, acc, pot, nullptr, nullptr);
+        // every coefficient read from shared memory feeds two independent evaluations.  The
+        // two classes run concurrently (the second on the second stream, with its own work
+        // counter), so that each fills the other's tail of idle SMs.
+        unsigned *work2 = (unsigned *)(c->sizes.p + 57);
+        HOT_CK(cudaEventRecord(c->ev_fork, c->st));
+        HOT_CK(cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        int r = launch_interact<P, float, 2, 0>(c, c->st2, 2, work2, acc, pot, nullptr, nullptr);
+        const int r1 = launch_interact<P, float, 1, 0>(c, c->st, 1, work, acc, pot, nullptr, nullptr);
+        HOT_CK(cudaEventRecord(c->ev_join, c->st2));
+        HOT_CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+        return r ? r : r1;
     }
     return launch_interact<P, float, 1, 0>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
 }

@@ -468,7 +468,14 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
     }
 }
 
-// cls: 0 = every group, 1 = groups of at most 32 sinks, 2 = groups of more than 32.
+// Groups whose slices run two sinks per lane (p >= 5): more than 32 sinks, and a last
+// 64-sink slice at least three quarters full.  A ragged remainder of up to 48 sinks costs
+// less as 32-sink slices, whose small last slice splits its lists across spare lanes
+// (clustered 2^20, p = 6: 16.5 ms against 18.2 ms with every group of more than 32; the
+// lattice 128^3, whose groups hold about 64 sinks, unchanged at 18.9 ms).
+__device__ __forceinline__ bool two_sinks_per_lane(int n) { return n > 32 && (n % 64 == 0 || n % 64 > 48); }
+
+// cls: 0 = every group, 1 = groups of one sink per lane, 2 = groups of two sinks per lane.
 // Occupancy (measured on the clustered 2^20 and lattice 128^3 workloads): the forces run
 // at 5 CTAs per SM (102 registers; 4% faster than 4 at p = 4, 3% at p = 6), at p = 7, 8 at
 // 2 (their staged records fill the shared memory of 2 CTAs); the adjoint's tangent
@@ -515,7 +522,7 @@ __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : (P >= 
         const int32_t gc = gcell[g];
         Group<T> Gr;
         Gr.n = ccount[gc];
-        if ((cls == 1 && Gr.n > 32) || (cls == 2 && Gr.n <= 32)) continue;
+        if ((cls == 1 && two_sinks_per_lane(Gr.n)) || (cls == 2 && !two_sinks_per_lane(Gr.n))) continue;
         Gr.gb = cbegin[gc];
         Gr.gx = gcen[3 * g + 0];
         Gr.gy = gcen[3 * g + 1];
