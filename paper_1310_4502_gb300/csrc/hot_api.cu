@@ -314,7 +314,7 @@ void hot_destroy(hot_ctx *c)
     c->cmom.release(s); c->cbmax.release(s); c->cB1.release(s); c->cB2.release(s); c->item_off.release(s);
     c->item_cell.release(s); c->item_part.release(s); c->rec32.release(s); c->rec64.release(s); c->prel.release(s);
     c->cnt_m2p.release(s); c->cnt_p2p.release(s); c->off_m2p.release(s); c->off_p2p.release(s);
-    c->l_m2p.release(s); c->l_p2p.release(s); c->trav_scratch.release(s); c->pairs_per_group.release(s);
+    c->l_m2p.release(s); c->l_p2p.release(s); c->trav_scratch.release(s);
     c->tcell.release(s); c->tcellf.release(s); c->slot_m2p.release(s); c->slot_p2p.release(s);
     c->gkey.release(s); c->gkey2.release(s); c->gorder.release(s); c->gorder2.release(s);
     c->slice_cnt.release(s); c->slice_off.release(s); c->items.release(s);
@@ -325,7 +325,7 @@ void hot_destroy(hot_ctx *c)
         c->rec64q[q].release(s);
     }
     c->adj_w.release(s); c->adj_xhl.release(s); c->adj_gsink.release(s); c->adj_gp2p.release(s);
-    c->adj_mbar.release(s); c->adj_cbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);
+    c->adj_mbar.release(s); c->tp_key.release(s); c->tp_key2.release(s);
     c->tp_val.release(s); c->tp_val2.release(s); c->tp_start.release(s); c->tp_end.release(s);
     c->it_cnt.release(s); c->it_off.release(s); c->it_cell.release(s); c->it_a.release(s); c->it_b.release(s);
     c->it_part.release(s); c->adj_pp.release(s); c->adj_roff.release(s);

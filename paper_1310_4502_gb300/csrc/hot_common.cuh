@@ -159,7 +159,7 @@ struct hot_ctx {
     // adjoint
     DBuf<unsigned char> adj_w;   // sink weights (u, v) per sorted slot, T4
     DBuf<float> adj_xhl;         // sorted positions as float hi/lo pairs [N][8]
-    DBuf<double> adj_gsink, adj_gp2p, adj_mbar, adj_cbar;
+    DBuf<double> adj_gsink, adj_gp2p, adj_mbar;
     DBuf<uint64_t> tp_key, tp_key2;
     DBuf<uint32_t> tp_val, tp_val2;
     DBuf<int64_t> tp_start, tp_end;
@@ -180,7 +180,6 @@ struct hot_ctx {
     DBuf<uint32_t> gorder, gorder2;  // groups in descending slice cost
     DBuf<uint32_t> slice_cnt, slice_off;  // 32-sink slices per group (sorted order), offsets
     DBuf<uint64_t> items;            // work items of the interaction kernels: group << 32 | first sink
-    DBuf<int64_t> pairs_per_group;
 
     // status
     unsigned *d_status = nullptr;
