@@ -118,7 +118,9 @@ int hot_build_tree(hot_ctx *ctx, const double *pos, const double *mass, int64_t 
  * M_a = sum m (x - z)^a, |a| <= p): P2M at the leaves, exact binomial
  * translation (M2M) upwards, in float64; plus the acceptance-test aggregates
  * b_max = max |x - z|, B_{p+1}, B_{p+2} (B_n = sum m |x - z|^n), and the
- * interaction coefficient records.  p in [0, 8]; asynchronous. */
+ * interaction coefficient records.  Under per-interaction order selection
+ * (p_min >= 0) also B_n for every n <= p+2 and the records of the orders p_min..p-1.
+ * p in [0, 8], p >= p_min; asynchronous. */
 int hot_compute_moments(hot_ctx *ctx, int p);
 
 /* Group-wise traversal (Sec. "Improving instruction-level parallelism": m
@@ -127,14 +129,19 @@ int hot_compute_moments(hot_ctx *ctx, int p);
  *   d = |z_c - g| - Delta_max   (g: centre of the group's bounding box,
  *                                Delta_max: largest distance of a sink from g)
  *   accept cell c for group g  iff  d > b_max and
- *   E(d) = G/d^2 (1 - b_max/d)^-2 [(p+2) B_{p+1}/d^{p+1} - (p+1) B_{p+2}/d^{p+2}] <= tol.
+ *   E(d) = G/d^2 (1 - b_max/d)^-2 [(p+2) B_{p+1}/d^{p+1} - (p+1) B_{p+2}/d^{p+2}] <= tol
+ *   (with K1 smoothing also d >= b_max + eps).
+ * Under per-interaction order selection a cell is accepted if the bound E_q of some
+ * order q in [p_min, p] (B_{q+1}, B_{q+2} in place of B_{p+1}, B_{p+2}) meets tol,
+ * and is evaluated at the lowest such order; the order is kept with the list entry.
  * Rejected leaves go to the particle-particle list, rejected inner cells are
  * opened.  tol > 0.  Synchronises the stream once (list sizes). */
 int hot_traverse(hot_ctx *ctx, double tol);
 
-/* Interactions on the lists: M2P (expansion of the softened kernel) and
- * softened P2P; sums are kept per sink in float32 with compensated (Kahan)
- * accumulation in the mixed mode, float64 otherwise.
+/* Interactions on the lists: M2P (expansion of the Plummer-softened kernel, or of
+ * 1/r under K1 smoothing; at each entry's order under order selection) and
+ * softened P2P (Plummer or K1); sums are kept per sink in float32 with
+ * compensated (Kahan) accumulation in the mixed mode, float64 otherwise.
  *   acc device, [N][3] float64, written in the caller's original order
  *   pot device, [N] float64 or NULL                                      */
 int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
