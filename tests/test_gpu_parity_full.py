@@ -8,8 +8,9 @@ group at a time.  Compared on those sinks: the FP64 path to 1e-11 relative, the 
 path to 1e-5 rms / 1e-3 max relative (acceleration) and 1e-4 max relative (potential),
 the tolerances of the small-size parity tests.
 
-Workloads: the clustered box at N = 2^20 (p = 4 and p = 6), the Zel'dovich lattice at
-128^3 (p = 6) and, as the largest size, 256^3 (p = 6, mixed only).
+Workloads: the clustered box at N = 2^20 (p = 4 and p = 6; p = 4 with K1 smoothing; p = 8
+with per-interaction order selection over 0..8), the Zel'dovich lattice at 128^3 (p = 6)
+and, as the largest size, 256^3 (p = 6, mixed only).
 """
 import numpy as np
 import pytest
@@ -57,15 +58,19 @@ def sinks_of(t, gs):
     return np.concatenate(idx)
 
 
-@pytest.mark.parametrize("name,p,precisions", [
-    ("clustered20", 4, ("mixed", "fp64")),
-    ("clustered20", 6, ("mixed", "fp64")),
-    ("zeldovich128", 6, ("mixed", "fp64")),
-    ("zeldovich256", 6, ("mixed",)),
+@pytest.mark.parametrize("name,p,precisions,opts", [
+    ("clustered20", 4, ("mixed", "fp64"), {}),
+    ("clustered20", 6, ("mixed", "fp64"), {}),
+    ("clustered20", 4, ("mixed", "fp64"), {"softening": "k1"}),
+    ("clustered20", 8, ("mixed", "fp64"), {"p_min": 0}),
+    ("zeldovich128", 6, ("mixed", "fp64"), {}),
+    ("zeldovich256", 6, ("mixed",), {}),
 ])
-def test_full_size_sampled_forces(name, p, precisions):
+def test_full_size_sampled_forces(name, p, precisions, opts):
     w, t = workload(name)
+    t.softening(opts.get("softening", "plummer"), w.eps)
     t.moments(p)
+    t.order_range(opts.get("p_min"))
     gs = sample_groups(t, seed=100 + p)
     t.traverse(w.tol, groups=gs)
     ra, rp = t.force(1.0, w.eps, groups=gs)
@@ -77,7 +82,7 @@ def test_full_size_sampled_forces(name, p, precisions):
     P = torch.tensor(w.pos, device=dev)
     M = torch.tensor(w.mass, device=dev)
     for prec in precisions:
-        h = hot.Hot(p=p, tol=w.tol, eps=w.eps, precision=prec)
+        h = hot.Hot(p=p, tol=w.tol, eps=w.eps, precision=prec, **opts)
         h.build_tree(P, M)
         # the group cells the oracle sampled are the GPU's groups too
         gcell = h.debug_get("GROUP_CELL")
