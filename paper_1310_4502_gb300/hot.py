@@ -266,10 +266,11 @@ def key_frame_noalloc(pos, mass, frame, stream=None):
 
 
 def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
-               ctx: Hot | None = None, want_pot=True):
+               ctx: Hot | None = None, want_pot=True, softening="plummer", p_min=None):
     """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N]."""
     import torch
-    h = ctx or Hot(p=p, tol=tol, eps=eps, G=G, leaf_max=leaf_max, group_max=group_max, precision=precision)
+    h = ctx or Hot(p=p, tol=tol, eps=eps, G=G, leaf_max=leaf_max, group_max=group_max, precision=precision,
+                   softening=softening, p_min=p_min)
     h.build_tree(pos, mass)
     h.compute_moments(p)
     h.traverse(tol)
