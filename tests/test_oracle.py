@@ -843,3 +843,88 @@ def test_order_selection_lowers_the_cost_within_the_tolerance():
     cost_var, err_var = res[0]
     assert cost_var < 0.8 * cost_fixed, (cost_var / cost_fixed)
     assert err_fixed < err_var < 1e-4, (err_fixed, err_var)
+
+
+# --------------------------------------------------------------------------
+# Periodic boundaries (Sec. "Boundary Conditions"): the lattice-sum method -- images
+# within ws = 2 directly, all farther ones through a local expansion with lattice-summed
+# coefficients -- against Ewald summation (neutralising background, tin-foil boundary).
+# --------------------------------------------------------------------------
+
+def test_ewald_wigner_constant_and_invariances():
+    from oracle import periodic as PR
+    L = 1.7
+    # one particle: psi_self L is the simple-cubic Wigner constant -2.837297479...
+    _, p = PR.ewald(np.array([[0.3, 0.2, 1.1]]), np.array([1.0]), L)
+    assert abs(-p[0] * L - (-2.837297479480620)) < 1e-9
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, L, (48, 3))
+    m = rng.uniform(0.5, 1.5, 48)
+    a1, p1 = PR.ewald(x, m, L)
+    a2, p2 = PR.ewald(x, m, L, alpha=4.5 / L, kmax=16)        # the splitting does not matter
+    assert np.max(np.abs(a1 - a2)) < 1e-12 * np.max(np.abs(a1))
+    assert np.max(np.abs(p1 - p2)) < 1e-12 * np.max(np.abs(p1))
+    assert np.max(np.abs((m[:, None] * a1).sum(0))) < 1e-12 * np.abs(m[:, None] * a1).sum()
+    a3, p3 = PR.ewald(np.mod(x + np.array([0.4, -1.3, 0.77]), L), m, L)   # translation
+    assert np.max(np.abs(a3 - a1)) < 1e-11 * np.max(np.abs(a1))
+    assert np.max(np.abs(p3 - p1)) < 1e-11 * np.max(np.abs(p1))
+
+
+def test_lattice_coefficients_laplace_symmetry_and_direct_sums():
+    from oracle import periodic as PR
+    L = 1.3
+    V = L ** 3
+    D = PR.lattice_coefficients(L, 17, ws=2)
+    even = {n: max(abs(D[g]) for g in D if sum(g) == n) for n in range(0, 18, 2)}
+    # odd orders vanish by symmetry: their scale is that of the neighbouring even orders
+    scale = {n: even[n] if n % 2 == 0 else max(even[n - 1], even.get(n + 1, 0.0)) for n in range(18)}
+    # the far part is harmonic apart from the background: lap psi_far(0) = 4 pi / V, and
+    # every derivative of it is harmonic
+    for g in D:
+        if sum(g) > 15:
+            continue
+        lap = D[(g[0] + 2, g[1], g[2])] + D[(g[0], g[1] + 2, g[2])] + D[(g[0], g[1], g[2] + 2)]
+        ref = 4 * math.pi / V if sum(g) == 0 else 0.0
+        assert abs(lap - ref) <= 1e-8 * scale[sum(g) + 2], g
+    # cubic symmetry: odd orders vanish, permutations agree
+    for g in D:
+        n = sum(g)
+        if n % 2 == 1:
+            assert abs(D[g]) <= 1e-9 * scale[n]
+        else:
+            for h in ((g[1], g[0], g[2]), (g[2], g[1], g[0]), (g[0], g[2], g[1])):
+                assert abs(D[g] - D[h]) <= 1e-9 * scale[n]
+    assert abs(D[(2, 0, 0)] - 4 * math.pi / (3 * V)) < 1e-13 * D[(2, 0, 0)]
+    # from order 10 on the lattice sum of derivatives of 1/r converges absolutely and fast:
+    # the direct sum over the images beyond ws agrees
+    n = PR._images(24)
+    n = n[np.max(np.abs(n), axis=1) > 2]
+    R = n * L
+    u = np.sum(R * R, axis=1)
+    F = np.array([(-0.5) ** k * PR._dfact(2 * k - 1) * u ** (-(2 * k + 1) / 2) for k in range(17)])
+    Dd = PR._radial_derivs(F, R, 16)
+    for g in Dd:
+        if sum(g) in (12, 16) and sum(g) % 2 == 0:
+            assert abs(D[g] - Dd[g]) <= 1e-8 * scale[sum(g)], g
+
+
+def test_lattice_method_matches_ewald_and_converges_with_order():
+    """Images within ws = 2 by direct summation plus the far images through the local
+    expansion of order p: the Ewald result to single-precision accuracy at p = 8 (the
+    paper's "one part in 1e7"), the error falling with p."""
+    from oracle import periodic as PR
+    L = 1.0
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, L, (64, 3))
+    m = rng.uniform(0.5, 1.5, 64)
+    ra, rp = PR.ewald(x, m, L)
+    an, pn = PR.near_images_direct(x, m, L)
+    D = PR.lattice_coefficients(L, 17)
+    errs = []
+    for p in (2, 4, 6, 8):
+        af, pf = PR.far_field(x, m, L, (0.0, 0.0, 0.0), p=p, D=D)
+        errs.append(np.max(rel_err(an + af, ra)))
+        if p == 8:
+            assert np.max(np.abs(pn + pf - rp) / np.abs(rp)) < 1e-5
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] < 5e-7
