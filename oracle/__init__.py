@@ -65,6 +65,9 @@ def lib():
         L.orc_tree_order_range.restype = C.c_int
         L.orc_tree_order_range.argtypes = [C.c_void_p, C.c_int]
         L.orc_tree_list_orders.argtypes = [C.c_void_p, _i32]
+        L.orc_tree_periodic.restype = C.c_int
+        L.orc_tree_periodic.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.orc_tree_list_images.argtypes = [C.c_void_p, _i32, _i32]
         L.orc_bbox.argtypes = [C.c_int64, _d, _d, C.POINTER(C.c_double)]
         L.orc_keys.argtypes = [C.c_int64, _d, _d, C.c_double, _u64]
         L.orc_sort.argtypes = [C.c_int64, _u64, _i64]
@@ -290,6 +293,13 @@ class Tree:
         if lib().orc_tree_order_range(self._h, -1 if p_lo is None else int(p_lo)) != 0:
             raise ValueError("bad order range")
 
+    def periodic(self, L, ws=2):
+        """Periodic images (Sec. "Boundary Conditions"): every group also traverses the tree
+        shifted by n L, |n|_inf <= ws; the forces are then the near field of the periodic
+        problem (oracle.periodic adds the far field).  L = 0 restores open boundaries."""
+        if lib().orc_tree_periodic(self._h, float(L), int(ws)) != 0:
+            raise ValueError("bad periodic box")
+
     def traverse(self, tol, G=1.0, groups=None):
         if groups is None:
             r = lib().orc_tree_traverse(self._h, float(tol), float(G))
@@ -312,8 +322,11 @@ class Tree:
         lib().orc_tree_lists(self._h, m2p, p2p, bor)
         order = np.zeros(off[-1, 0], dtype=np.int32)
         lib().orc_tree_list_orders(self._h, order)
+        mimg = np.zeros(off[-1, 0], dtype=np.int32)
+        pimg = np.zeros(off[-1, 1], dtype=np.int32)
+        lib().orc_tree_list_images(self._h, mimg, pimg)
         return dict(m2p=(off[:, 0].copy(), m2p), p2p=(off[:, 1].copy(), p2p),
-                    border=(off[:, 2].copy(), bor), m2p_order=order)
+                    border=(off[:, 2].copy(), bor), m2p_order=order, m2p_image=mimg, p2p_image=pimg)
 
     def force(self, G=1.0, eps=0.0, groups=None):
         n = len(self.mass)

@@ -33,6 +33,9 @@
  *   P2P ................... pairwise softened sum, Eq. (eom)
  *   sink groups / lists ... dual-tree traversal with m x n blocking, Sec.
  *                           "Improving instruction-level parallelism"
+ *   periodic images ....... Sec. "Boundary Conditions": the tree's images within ws
+ *                           cubes as further sources (the far field and the Ewald
+ *                           reference are in periodic.py)
  *   gradient .............. analytic derivative of the direct sum (pair sum
  *                           weighted by the tidal tensor); frozen-structure tree
  *                           function for finite differences
@@ -504,6 +507,12 @@ typedef struct orc_tree {
     int varq, p_lo;
     double *cBn;
     ivec *lm2pq;
+    /* periodic images (Sec. "Boundary Conditions"): with per_L > 0 every group also
+     * traverses the tree shifted by n per_L, |n|_inf <= per_ws; the image of every list
+     * entry in lm2pi / lp2pi (index ((nx+ws) w + ny+ws) w + nz+ws, w = 2 ws + 1) */
+    double per_L;
+    int per_ws;
+    ivec *lm2pi, *lp2pi;
 } orc_tree;
 
 static int64_t new_cell(orc_tree *t)
@@ -631,6 +640,45 @@ static void free_lists(orc_tree *t)
         free(t->lm2pq);
         t->lm2pq = NULL;
     }
+    if (t->lm2pi) {
+        for (int64_t g = 0; g < t->ngroup; g++) {
+            free(t->lm2pi[g].v);
+            free(t->lp2pi[g].v);
+        }
+        free(t->lm2pi);
+        free(t->lp2pi);
+        t->lm2pi = t->lp2pi = NULL;
+    }
+}
+
+/* Images of the periodic tree: their number, the central one, and the shift of one. */
+static int per_nimg(const orc_tree *t)
+{
+    int w = 2 * t->per_ws + 1;
+    return t->per_L > 0.0 ? w * w * w : 1;
+}
+static int per_central(const orc_tree *t) { return (per_nimg(t) - 1) / 2; }
+static void per_shift(const orc_tree *t, int img, double sh[3])
+{
+    if (!(t->per_L > 0.0)) {
+        sh[0] = sh[1] = sh[2] = 0.0;
+        return;
+    }
+    int w = 2 * t->per_ws + 1;
+    sh[0] = (double)(img / (w * w) - t->per_ws) * t->per_L;
+    sh[1] = (double)((img / w) % w - t->per_ws) * t->per_L;
+    sh[2] = (double)(img % w - t->per_ws) * t->per_L;
+}
+
+/* Periodic images for the lists and forces: side L > 0 of the periodic cube and the
+ * number ws of neighbouring cubes on every side whose images the tree serves (the rest
+ * is the far field's); L = 0 restores open boundaries.  Set before the traversal. */
+int orc_tree_periodic(orc_tree *t, double L, int ws)
+{
+    if (!(L >= 0.0) || ws < 0 || ws > 4) return -1;
+    t->per_L = L;
+    t->per_ws = ws;
+    return 0;
 }
 
 void orc_tree_free(orc_tree *t)
@@ -798,17 +846,34 @@ static int ancestor_or_self(const orc_tree *t, int64_t c, int64_t gc)
  *     else leaf                 -> P2P
  *     else                      -> descend
  * Decisions within 1e-9 (relative) of a threshold are recorded as borderline. */
-static void trav_rec(orc_tree *t, int64_t g, int64_t c)
+static void push_m2p(orc_tree *t, int64_t g, int64_t c, int img)
+{
+    ivec_push(&t->lm2p[g], (int32_t)c);
+    if (t->lm2pi) ivec_push(&t->lm2pi[g], img);
+}
+static void push_p2p(orc_tree *t, int64_t g, int64_t c, int img)
+{
+    ivec_push(&t->lp2p[g], (int32_t)c);
+    if (t->lp2pi) ivec_push(&t->lp2pi[g], img);
+}
+
+static void trav_rec(orc_tree *t, int64_t g, int64_t c, int img)
 {
     int64_t gc = t->gcell[g];
-    if (ancestor_or_self(t, c, gc)) {
+    if (img == per_central(t) && ancestor_or_self(t, c, gc)) {
         if (is_leaf(t, c))
-            ivec_push(&t->lp2p[g], (int32_t)c);
+            push_p2p(t, g, c, img);
         else
-            for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k]);
+            for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k], img);
         return;
     }
-    const double *z = t->ccom + 3 * c;
+    const double *z0 = t->ccom + 3 * c;
+    double z[3] = {z0[0], z0[1], z0[2]};
+    if (t->per_L > 0.0) {
+        double sh[3];
+        per_shift(t, img, sh);
+        for (int d = 0; d < 3; d++) z[d] += sh[d];
+    }
     double dx = z[0] - t->gcen[3 * g + 0];
     double dy = z[1] - t->gcen[3 * g + 1];
     double dz = z[2] - t->gcen[3 * g + 2];
@@ -833,12 +898,12 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c)
         }
         if (b > 0.0 && fabs(d - b) <= 1e-9 * b) ivec_push(&t->lborder[g], (int32_t)c);
         if (qa >= 0) {
-            ivec_push(&t->lm2p[g], (int32_t)c);
+            push_m2p(t, g, c, img);
             ivec_push(&t->lm2pq[g], (int32_t)qa);
         } else if (is_leaf(t, c)) {
-            ivec_push(&t->lp2p[g], (int32_t)c);
+            push_p2p(t, g, c, img);
         } else {
-            for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k]);
+            for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k], img);
         }
         return;
     }
@@ -849,11 +914,29 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c)
     }
     if (b > 0.0 && fabs(d - b) <= 1e-9 * b) ivec_push(&t->lborder[g], (int32_t)c);
     if (accept)
-        ivec_push(&t->lm2p[g], (int32_t)c);
+        push_m2p(t, g, c, img);
     else if (is_leaf(t, c))
-        ivec_push(&t->lp2p[g], (int32_t)c);
+        push_p2p(t, g, c, img);
     else
-        for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k]);
+        for (int k = 0; k < t->cnchild[c]; k++) trav_rec(t, g, t->cchild[c][k], img);
+}
+
+/* All lists of group g: the central tree and, when periodic, every image. */
+static void trav_group(orc_tree *t, int64_t g)
+{
+    for (int img = 0; img < per_nimg(t); img++) trav_rec(t, g, 0, img);
+}
+
+static void alloc_lists(orc_tree *t)
+{
+    t->lm2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    t->lp2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    t->lborder = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    if (t->varq) t->lm2pq = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    if (t->per_L > 0.0) {
+        t->lm2pi = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+        t->lp2pi = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    }
 }
 
 /* Force smoothing of the lists and forces: kind ORC_SOFT_PLUMMER (default) or
@@ -881,12 +964,9 @@ int orc_tree_traverse(orc_tree *t, double tol, double G)
     free_lists(t);
     t->tol = tol;
     t->Gmac = G;
-    t->lm2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    t->lp2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    t->lborder = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    if (t->varq) t->lm2pq = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    alloc_lists(t);
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t g = 0; g < t->ngroup; g++) trav_rec(t, g, 0);
+    for (int64_t g = 0; g < t->ngroup; g++) trav_group(t, g);
     return 0;
 }
 
@@ -907,6 +987,16 @@ void orc_tree_list_orders(const orc_tree *t, int32_t *orders)
     int64_t a = 0;
     for (int64_t g = 0; g < t->ngroup; g++)
         for (int64_t e = 0; e < t->lm2p[g].n; e++) orders[a++] = t->lm2pq ? t->lm2pq[g].v[e] : t->p;
+}
+
+/* Image of every M2P and P2P entry, concatenated like the lists (0 without periodicity). */
+void orc_tree_list_images(const orc_tree *t, int32_t *m2p_img, int32_t *p2p_img)
+{
+    int64_t a = 0, b = 0;
+    for (int64_t g = 0; g < t->ngroup; g++) {
+        for (int64_t e = 0; e < t->lm2p[g].n; e++) m2p_img[a++] = t->lm2pi ? t->lm2pi[g].v[e] : 0;
+        for (int64_t e = 0; e < t->lp2p[g].n; e++) p2p_img[b++] = t->lp2pi ? t->lp2pi[g].v[e] : 0;
+    }
 }
 
 /* Concatenated lists in group order. */
@@ -941,15 +1031,24 @@ static void group_force(const orc_tree *t, int64_t g, const double *spos, const 
         const double *x = spos + 3 * s;
         for (int64_t e = 0; e < t->lm2p[g].n; e++) {
             int64_t c = t->lm2p[g].v[e];
-            double R[3];
-            for (int d = 0; d < 3; d++) R[d] = x[d] - t->ccom[3 * c + d];
+            double R[3], sh[3];
+            per_shift(t, t->lm2pi ? t->lm2pi[g].v[e] : 0, sh);
+            for (int d = 0; d < 3; d++) R[d] = x[d] - (t->ccom[3 * c + d] + sh[d]);
             m2p_eval(m2p_order(t, g, e), tab, mom + (size_t)nc * c, R, G, eps2, a, &phi);
         }
         for (int64_t e = 0; e < t->lp2p[g].n; e++) {
             int64_t c = t->lp2p[g].v[e];
+            const int img = t->lp2pi ? t->lp2pi[g].v[e] : per_central(t);
+            double sh[3];
+            per_shift(t, img, sh);
             for (int64_t j = t->cbegin[c]; j < t->cbegin[c] + t->ccount[c]; j++) {
-                if (j == s) continue;
-                pair_acc(x, spos + 3 * j, smass[j], G, sf, a, &phi);
+                if (j == s && img == per_central(t)) continue;
+                if (t->per_L > 0.0) {
+                    const double xj[3] = {spos[3 * j] + sh[0], spos[3 * j + 1] + sh[1], spos[3 * j + 2] + sh[2]};
+                    pair_acc(x, xj, smass[j], G, sf, a, &phi);
+                } else {
+                    pair_acc(x, spos + 3 * j, smass[j], G, sf, a, &phi);
+                }
             }
         }
         int64_t i = t->perm[s];
@@ -985,12 +1084,9 @@ int orc_tree_traverse_groups(orc_tree *t, double tol, double G, int64_t nsel, co
     free_lists(t);
     t->tol = tol;
     t->Gmac = G;
-    t->lm2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    t->lp2p = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    t->lborder = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
-    if (t->varq) t->lm2pq = (ivec *)calloc((size_t)t->ngroup, sizeof(ivec));
+    alloc_lists(t);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t q = 0; q < nsel; q++) trav_rec(t, gsel[q], 0);
+    for (int64_t q = 0; q < nsel; q++) trav_group(t, gsel[q]);
     return 0;
 }
 
@@ -1008,7 +1104,7 @@ int orc_tree_traverse_groups(orc_tree *t, double tol, double G, int64_t nsel, co
 double orc_frozen_loss(const orc_tree *t, const double *pos, const double *mass, double G,
                        double eps, const double *w, const double *v, int64_t k)
 {
-    if (!t->lm2p) return NAN;
+    if (!t->lm2p || t->per_L > 0.0) return NAN;  /* open boundaries only */
     int64_t N = t->N;
     int p = t->p, nc = ncomp(p);
     int tab[200][3];

@@ -232,3 +232,18 @@ def far_field(pos, mass, L, lo, p=8, ws=2, G=1.0, D=None):
             ef = fac(e[0]) * fac(e[1]) * fac(e[2])
             acc[:, d] += G * v * y[:, 0] ** e[0] * y[:, 1] ** e[1] * y[:, 2] ** e[2] / ef
     return acc, pot
+
+
+def tree_force(pos, mass, L, lo, p=8, tol=1e-6, ws=2, p_far=8, G=1.0, eps=0.0, D=None,
+               leaf_max=64, group_max=128):
+    """The paper's periodic force: the tree over the central cube and its images within ws
+    (open-boundary tree code with the images as further sources), plus the far images
+    through the local expansion of order p_far.  Positions inside [lo, lo + L)^3."""
+    from . import Tree
+    t = Tree(pos, mass, leaf_max, group_max)
+    t.periodic(L, ws)
+    t.moments(p)
+    t.traverse(tol, G)
+    an, pn = t.force(G, eps)
+    af, pf = far_field(pos, mass, L, lo, p=p_far, ws=ws, G=G, D=D)
+    return an + af, pn + pf

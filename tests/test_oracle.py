@@ -928,3 +928,38 @@ def test_lattice_method_matches_ewald_and_converges_with_order():
             assert np.max(np.abs(pn + pf - rp) / np.abs(rp)) < 1e-5
     assert errs[0] > errs[1] > errs[2] > errs[3]
     assert errs[3] < 5e-7
+
+
+def _periodic_case(n=600, L=1.0, seed=9):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0, L, (n, 3)), rng.uniform(0.5, 1.5, n) / n, L
+
+
+def test_periodic_tree_near_field_is_the_image_sum():
+    """With every interaction P2P, the periodic tree (central cube and its images within
+    ws = 2) is the plain sum over those images; image indices name real shifts."""
+    from oracle import periodic as PR
+    x, m, L = _periodic_case()
+    an, pn = PR.near_images_direct(x, m, L)
+    t = oracle.Tree(x, m, 16, 32)
+    t.periodic(L, 2)
+    t.moments(4)
+    t.traverse(1e-300)
+    a, p = t.force(1.0, 0.0)
+    assert np.max(rel_err(a, an)) < 1e-12 and np.max(np.abs(p - pn) / np.abs(pn)) < 1e-12
+    Ls = t.lists()
+    assert Ls["p2p_image"].min() >= 0 and Ls["p2p_image"].max() <= 124
+    assert len(set(Ls["p2p_image"].tolist())) == 125
+
+
+def test_periodic_tree_converges_to_ewald():
+    from oracle import periodic as PR
+    x, m, L = _periodic_case()
+    ra, _ = PR.ewald(x, m, L)
+    D = PR.lattice_coefficients(L, 17)
+    errs = []
+    for tol in (1e-4, 1e-6, 1e-8):
+        a, _ = PR.tree_force(x, m, L, (0.0, 0.0, 0.0), p=8, tol=tol, D=D, leaf_max=16, group_max=32)
+        errs.append(np.sqrt(np.mean(rel_err(a, ra) ** 2)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-7
