@@ -86,6 +86,17 @@ typedef struct {
     int p_min;      /* -1: every accepted cell at order p; 0..p: per-interaction  */
                     /* order selection, the lowest order in [p_min, p] whose      */
                     /* bound E_q(d) <= tol (B_{q+1}, B_{q+2}) accepts the cell     */
+    double box;     /* 0: open boundaries; > 0: periodic cube of this side holding */
+                    /* every particle (Sec. "Boundary Conditions"): the tree      */
+                    /* serves the cube and its images within ws, a local          */
+                    /* expansion of order 8 (lattice sums) every farther image;   */
+                    /* neutralising background, conducting boundary.  Excludes    */
+                    /* p_min >= 0 and the adjoint                                 */
+    int ws;         /* periodic: neighbouring cubes on every side served by the   */
+                    /* tree, 1..2 (2: the central cube and its 124 neighbours)    */
+    double box_lo[3]; /* periodic: lower corner of the cube; every position in   */
+                    /* [box_lo, box_lo + box) (not checked: a particle outside    */
+                    /* gives forces of no defined meaning, never a fault)         */
 } hot_params;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
@@ -135,13 +146,21 @@ int hot_compute_moments(hot_ctx *ctx, int p);
  * order q in [p_min, p] (B_{q+1}, B_{q+2} in place of B_{p+1}, B_{p+2}) meets tol,
  * and is evaluated at the lowest such order; the order is kept with the list entry.
  * Rejected leaves go to the particle-particle list, rejected inner cells are
- * opened.  tol > 0.  Synchronises the stream once (list sizes). */
+ * opened.  Under periodic boundaries every group also traverses the images of the
+ * tree within ws cubes (the tree moved by nL, |n|_inf <= ws; in the central one the
+ * group's ancestors are opened as above, in the others every cell is tested), each
+ * list entry tagged with its image.  tol > 0.  Synchronises the stream once (list
+ * sizes); HOT_EINVAL under periodic boundaries with 2^24 cells or more. */
 int hot_traverse(hot_ctx *ctx, double tol);
 
 /* Interactions on the lists: M2P (expansion of the Plummer-softened kernel, or of
  * 1/r under K1 smoothing; at each entry's order under order selection) and
  * softened P2P (Plummer or K1); sums are kept per sink in float32 with
- * compensated (Kahan) accumulation in the mixed mode, float64 otherwise.
+ * compensated (Kahan) accumulation in the mixed mode, float64 otherwise.  Under
+ * periodic boundaries the sources of an image entry are moved by its nL, no sink
+ * meets itself outside the central cube, and the far images' local expansion of
+ * order 8 (moments of all particles about the cube's centre, the lattice sums of
+ * hot_lattice_sums, float32 in the mixed mode) is added.
  *   acc device, [N][3] float64, written in the caller's original order
  *   pot device, [N] float64 or NULL                                      */
 int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
@@ -193,7 +212,9 @@ enum {
     HOT_DBG_M2P_CELLS = 19,   /* int32[n_m2p]                                */
     HOT_DBG_P2P_OFFSETS = 20, /* int64[ngroup + 1]                           */
     HOT_DBG_P2P_CELLS = 21,   /* int32[n_p2p]                                */
-    HOT_DBG_M2P_ORDERS = 22   /* int32[n_m2p]: expansion order of each M2P entry */
+    HOT_DBG_M2P_ORDERS = 22,  /* int32[n_m2p]: expansion order of each M2P entry */
+    HOT_DBG_M2P_IMAGES = 23,  /* int32[n_m2p]: periodic image of each M2P entry  */
+    HOT_DBG_P2P_IMAGES = 24   /* int32[n_p2p]: periodic image of each P2P entry  */
 };
 int hot_debug_get(hot_ctx *ctx, int what, void *host_dst, size_t bytes);
 
@@ -270,6 +291,17 @@ int hot_axpy(hot_ctx *ctx, double *y, const double *x, double alpha, int64_t n);
  * peak to the current value.  Host-side bookkeeping only (no device call).  The
  * paper has no counterpart: it serves the memory report of multi-step runs. */
 int hot_memory_stats(int64_t out[2], int reset_peak);
+
+/* Lattice sums of periodic boundaries (Sec. "Boundary Conditions"): D^g psi_far(0) for
+ * every multi-index |g| <= order, psi_far the periodic Green's function of a cube of side
+ * L (Ewald conventions: neutralising background, conducting boundary) less the images
+ * within ws cubes, 1/|r + nL| for |n|_inf <= ws.  These are the coefficients of the far
+ * images' local expansion, computed on the host (no device call).
+ *   out  host, far_nc(order) = (order+1)(order+2)(order+3)/6 doubles, graded order: by
+ *        |g|, then by descending g_x, then by descending g_y (index n(n+1)(n+2)/6 +
+ *        j(j+1)/2 + g_z, n = |g|, j = g_y + g_z)
+ * L > 0 finite, ws in 1..2, order in 0..17.  Returns HOT_OK or HOT_EINVAL. */
+int hot_lattice_sums(double L, int ws, int order, double *out);
 
 /* Fused-multiply-add throughput microbenchmark (for roofline denominators):
  * runs a register-resident FMA loop on every SM and writes the achieved

@@ -792,7 +792,7 @@ int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, doubl
 {
     // the adjoint's coefficient sums are register-resident per lane: orders up to 6, one
     // order per call (not under per-interaction order selection)
-    if (c->p_mom > HOT_ADJ_PMAX || c->varq) return HOT_EINVAL;
+    if (c->p_mom > HOT_ADJ_PMAX || c->varq || c->prm.box > 0.0) return HOT_EINVAL;
     hot_tic(c, 5);
     int r;
     switch (c->p_mom) {

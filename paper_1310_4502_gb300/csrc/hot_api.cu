@@ -1,5 +1,6 @@
 // hot_api.cu -- the C ABI declared in include/hot.h: context lifetime, argument checks,
 // stage ordering, status word, debug copies, hash lookups and the FMA microbenchmark.
+#include <cmath>
 #include <new>
 
 #include "hot_common.cuh"
@@ -30,6 +31,11 @@ int check_params(const hot_params *p)
     if (p->precision != HOT_FP32_MIXED && p->precision != HOT_FP64) return HOT_EINVAL;
     if (p->softening != HOT_SOFT_PLUMMER && p->softening != HOT_SOFT_K1) return HOT_EINVAL;
     if (p->p_min < -1 || p->p_min > p->p) return HOT_EINVAL;
+    if (!(p->box >= 0.0) || !std::isfinite(p->box) || (p->box > 0.0 && (p->ws < 1 || p->ws > HOT_WS_MAX)))
+        return HOT_EINVAL;
+    if (p->box > 0.0 && !(std::isfinite(p->box_lo[0]) && std::isfinite(p->box_lo[1]) && std::isfinite(p->box_lo[2])))
+        return HOT_EINVAL;
+    if (p->box > 0.0 && p->p_min >= 0) return HOT_EINVAL;  // one or the other
     return HOT_OK;
 }
 
@@ -109,7 +115,7 @@ int hot_set_params(hot_ctx *c, const hot_params *prm)
     bool rebuild = prm->leaf_max != c->prm.leaf_max || prm->group_max != c->prm.group_max;
     bool remoment = prm->p != c->prm.p || prm->eps != c->prm.eps || prm->G != c->prm.G ||
                     prm->precision != c->prm.precision || prm->softening != c->prm.softening ||
-                    prm->p_min != c->prm.p_min;
+                    prm->p_min != c->prm.p_min || prm->box != c->prm.box || prm->ws != c->prm.ws;
     c->prm = *prm;
     if (rebuild) c->stage = 0;
     else if (remoment && c->stage > 1) c->stage = 1;
@@ -215,6 +221,8 @@ int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
         case HOT_DBG_P2P_OFFSETS: src = c->off_p2p.p; need = (ng + 1) * sizeof(int64_t); min_stage = 3; break;
         case HOT_DBG_P2P_CELLS: src = c->l_p2p.p; need = c->n_p2p * sizeof(int32_t); min_stage = 3; break;
         case HOT_DBG_M2P_ORDERS: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
+        case HOT_DBG_M2P_IMAGES: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
+        case HOT_DBG_P2P_IMAGES: src = c->l_p2p.p; need = c->n_p2p * sizeof(int32_t); min_stage = 3; break;
         default: return HOT_EINVAL;
     }
     if (c->stage < min_stage) return HOT_ESTATE;
@@ -222,13 +230,22 @@ int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
     if (need == 0) return HOT_OK;
     if (cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, c->st) != cudaSuccess) return HOT_ECUDA;
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
-    // M2P entries carry their order above HOT_ORDER_SHIFT under order selection
-    if (what == HOT_DBG_M2P_CELLS || what == HOT_DBG_M2P_ORDERS) {
+    // M2P entries carry their order above HOT_ORDER_SHIFT under order selection; M2P and
+    // P2P entries their image above HOT_IMG_SHIFT under periodic boundaries
+    const bool per = c->prm.box > 0.0;
+    const bool m2p = what == HOT_DBG_M2P_CELLS || what == HOT_DBG_M2P_ORDERS || what == HOT_DBG_M2P_IMAGES;
+    const bool p2p = what == HOT_DBG_P2P_CELLS || what == HOT_DBG_P2P_IMAGES;
+    if (m2p || p2p) {
         int32_t *e = (int32_t *)dst;
-        for (int64_t i = 0; i < c->n_m2p; ++i) {
+        const int64_t n = m2p ? c->n_m2p : c->n_p2p;
+        for (int64_t i = 0; i < n; ++i) {
             const uint32_t v = (uint32_t)e[i];
-            e[i] = what == HOT_DBG_M2P_CELLS ? (int32_t)(v & HOT_CELL_MASK)
-                                             : (c->varq ? (int32_t)(v >> HOT_ORDER_SHIFT) : c->p_mom);
+            if (what == HOT_DBG_M2P_CELLS || what == HOT_DBG_P2P_CELLS)
+                e[i] = (int32_t)(per ? (v & HOT_IMG_CELL_MASK) : (c->varq ? (v & HOT_CELL_MASK) : v));
+            else if (what == HOT_DBG_M2P_ORDERS)
+                e[i] = c->varq ? (int32_t)(v >> HOT_ORDER_SHIFT) : c->p_mom;
+            else
+                e[i] = per ? (int32_t)(v >> HOT_IMG_SHIFT) : 0;
         }
     }
     return HOT_OK;
@@ -320,6 +337,7 @@ void hot_destroy(hot_ctx *c)
     c->slice_cnt.release(s); c->slice_off.release(s); c->items.release(s);
     c->cBn.release(s); c->bn_cnt.release(s); c->bn_off.release(s); c->bn_cell.release(s); c->bn_part.release(s);
     c->rcq.release(s);
+    c->per_D.release(s); c->per_part.release(s); c->per_coef.release(s);
     for (int q = 0; q < HOT_ORDERS; ++q) {
         c->rec32q[q].release(s);
         c->rec64q[q].release(s);

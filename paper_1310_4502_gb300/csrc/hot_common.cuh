@@ -27,6 +27,12 @@
 #define HOT_ORDER_SHIFT 27
 #define HOT_CELL_MASK ((1u << HOT_ORDER_SHIFT) - 1u)
 #define HOT_ORDERS 9  // orders 0..8
+// Periodic boundaries: a list entry is cell | image << HOT_IMG_SHIFT, image index
+// ((nx + ws) w + ny + ws) w + nz + ws, w = 2 ws + 1.
+#define HOT_IMG_SHIFT 24
+#define HOT_IMG_CELL_MASK ((1u << HOT_IMG_SHIFT) - 1u)
+#define HOT_WS_MAX 2  // (2 ws + 1)^3 images in the 8 bits above HOT_IMG_SHIFT
+#define HOT_PFAR 8    // order of the far images' local expansion
 
 // Device memory the one-pass traversal may hold in per-group list slots (bytes).
 #define HOT_SLOT_BUDGET (16.0 * 1024 * 1024 * 1024)
@@ -144,6 +150,12 @@ struct hot_ctx {
     DBuf<float> rec32q[HOT_ORDERS];    // records of the orders below p (order p: rec32 / rec64)
     DBuf<double> rec64q[HOT_ORDERS];
     DBuf<double> rcq;                  // [ncell][p - q_lo + 1]: acceptance radius of each order
+    // periodic boundaries: lattice sums D^g psi_far(0) (host copy and device, for the side
+    // per_D_L and ws per_D_ws), moment partials and L2P coefficients of the far images
+    std::vector<double> per_Dh;
+    double per_D_L = 0.0;
+    int per_D_ws = 0;
+    DBuf<double> per_D, per_part, per_coef;
 
     // lists
     double tol_lists = 0;
@@ -237,6 +249,7 @@ int hot_impl_moments(hot_ctx *c, int p);
 int hot_impl_traverse(hot_ctx *c, double tol);
 int hot_impl_forces(hot_ctx *c, double *acc, double *pot);
 int hot_impl_forces_vq(hot_ctx *c, double *acc, double *pot);
+int hot_impl_far_field(hot_ctx *c, double *acc, double *pot);
 int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos,
                      double *g_mass);
 int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink, cudaStream_t s);

@@ -60,6 +60,8 @@ int hot_impl_forces(hot_ctx *c, double *acc, double *pot)
         case 8: r = forces_p<8>(c, acc, pot); break;
         default: return HOT_ESTATE;
     }
+    // periodic boundaries: the far images' local expansion, added to the tree's forces
+    if (!r) r = hot_impl_far_field(c, acc, pot);
     hot_toc(c, 4);
     return r;
 }

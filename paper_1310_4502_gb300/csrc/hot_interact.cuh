@@ -57,7 +57,7 @@ struct alignas(16) Smem {
     T loff[32][3];              // P2P batch: leaf centre offsets
     unsigned long long bar[2];
     unsigned long long probe;   // test setting: a barrier nothing ever arrives on
-    unsigned char qo[2][CH];    // order of each staged record (per-interaction order selection)
+    unsigned char qo[2][CH];    // order (per-interaction order selection) or periodic image of each staged record
 };
 
 // Records of every order (per-interaction order selection): base pointer and length.
@@ -170,7 +170,22 @@ struct Group {
     int64_t m0, m1;  // M2P list range
     int64_t p0, p1;  // P2P list range
     int32_t own0, own1;  // pre-order range of the group's cell: its own leaves
+    double pL;           // periodic boundaries: side of the cube (0: open)
+    int pws;             // periodic boundaries: images within pws cubes on every side
 };
+
+// Periodic boundaries: the shift n L of image img (index ((nx + ws) w + ny + ws) w + nz + ws,
+// w = 2 ws + 1), the sources of the image being the central ones moved by n L.
+template <class T>
+__device__ __forceinline__ void image_shift(const Group<T> &G, unsigned img, T &sx, T &sy, T &sz)
+{
+    const int w = 2 * G.pws + 1;
+    sx = (T)((double)((int)(img / (unsigned)(w * w)) - G.pws) * G.pL);
+    sy = (T)((double)((int)((img / (unsigned)w) % (unsigned)w) - G.pws) * G.pL);
+    sz = (T)((double)((int)(img % (unsigned)w) - G.pws) * G.pL);
+}
+// Bit of a staged leaf's first slot marking a leaf of a non-central image (slots are below 2^30).
+constexpr int32_t IMG_LEAF = 0x40000000;
 
 // Offset z_c - g in T from the hi/lo pairs of the cell (record header slots 2..7) and of
 // the group centre: (z_hi - g_hi) + (z_lo - g_lo).
@@ -228,11 +243,15 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 bulk_g2s(&sm.rec[b][lane][0], rq.rec[q] + ci * rq.rl[q], bytes, &sm.bar[b]);
             }
         } else {
+            // periodic boundaries: an entry is cell | image << HOT_IMG_SHIFT
+            const bool per = G.pws > 0;
+            const uint32_t ci = per ? ((uint32_t)cell & HOT_IMG_CELL_MASK) : (uint32_t)cell;
             if (lane == 0) mbar_expect_tx(&sm.bar[b], (uint32_t)ne * RB);
             __syncwarp();
             if ((int)lane < ne) {
+                if (per) sm.qo[b][lane] = (unsigned char)((uint32_t)cell >> HOT_IMG_SHIFT);
                 fence_async_smem();
-                bulk_g2s(&sm.rec[b][lane][0], rec + (int64_t)cell * RL, RB, &sm.bar[b]);
+                bulk_g2s(&sm.rec[b][lane][0], rec + (int64_t)ci * RL, RB, &sm.bar[b]);
             }
         }
     };
@@ -258,6 +277,13 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         if ((int)lane < ne) {
             T ox, oy, oz;
             centre_offset(&sm.rec[b][lane][0], G, ox, oy, oz);
+            if (!VQ && G.pws > 0) {
+                T sx, sy, sz;
+                image_shift(G, sm.qo[b][lane], sx, sy, sz);
+                ox += sx;
+                oy += sy;
+                oz += sz;
+            }
             if constexpr (sizeof(T) == 4) {
                 *reinterpret_cast<float4 *>(&sm.off[b][lane][0]) = make_float4(ox, oy, oz, 0.f);
             } else {
@@ -418,14 +444,37 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
         T ox = T(0), oy = T(0), oz = T(0);
         bool own = false;
         if ((int)lane < ne) {
-            const int32_t leaf = l_p2p[e0 + lane];
-            own = leaf >= G.own0 && leaf < G.own1;
-            lb = cbegin[leaf];
+            // periodic boundaries: an entry is leaf | image << HOT_IMG_SHIFT; the sources of
+            // a leaf of a non-central image are marked (IMG_LEAF) so that no sink meets
+            // itself there, and carry the image's shift: in the leaf offset (float32), or
+            // alone in its place (float64, whose sources are taken relative to g directly)
+            const int32_t ent = l_p2p[e0 + lane];
+            int32_t leaf = ent;
+            T sx = T(0), sy = T(0), sz = T(0);
+            bool central = true;
+            if (G.pws > 0) {
+                const unsigned img = (uint32_t)ent >> HOT_IMG_SHIFT;
+                const int w = 2 * G.pws + 1;
+                leaf = (int32_t)((uint32_t)ent & HOT_IMG_CELL_MASK);
+                central = 2 * (int)img == w * w * w - 1;
+                image_shift(G, img, sx, sy, sz);
+            }
+            own = central && leaf >= G.own0 && leaf < G.own1;
+            lb = cbegin[leaf] | (central ? 0 : IMG_LEAF);
             lc = ccount[leaf];
-            T h[8];
+            if constexpr (sizeof(T) == 4) {
+                T h[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) h[q] = rec[(int64_t)leaf * RL + q];
-            centre_offset(h, G, ox, oy, oz);
+                for (int q = 0; q < 8; ++q) h[q] = rec[(int64_t)leaf * RL + q];
+                centre_offset(h, G, ox, oy, oz);
+                ox += sx;
+                oy += sy;
+                oz += sz;
+            } else {
+                ox = sx;
+                oy = sy;
+                oz = sz;
+            }
         }
         const bool checked = __any_sync(0xffffffffu, own) || !(eps2 > T(0));
         const int incl = warp_incl_scan(lc);
@@ -449,7 +498,8 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     else
                         hi = mid;
                 }
-                const int64_t s = (int64_t)sm.lbeg[lo] + (t - sm.lex[lo]);
+                const int32_t lbv = sm.lbeg[lo];
+                const int64_t s = (int64_t)(lbv & ~IMG_LEAF) + (t - sm.lex[lo]);
                 if constexpr (sizeof(T) == 4) {
                     const float4 v = prel[s];
                     // one 16-byte store per source (scalar stores at a 16-byte lane stride
@@ -457,12 +507,12 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     *reinterpret_cast<float4 *>(&sm.src[u][0]) =
                         make_float4(v.x + sm.loff[lo][0], v.y + sm.loff[lo][1], v.z + sm.loff[lo][2], v.w);
                 } else {
-                    sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx);
-                    sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy);
-                    sm.src[u][2] = (T)(spos[3 * s + 2] - G.gz);
+                    sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx) + sm.loff[lo][0];
+                    sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy) + sm.loff[lo][1];
+                    sm.src[u][2] = (T)(spos[3 * s + 2] - G.gz) + sm.loff[lo][2];
                     sm.src[u][3] = (T)smass[s];
                 }
-                sm.sidx[u] = (int32_t)s;
+                sm.sidx[u] = (lbv & IMG_LEAF) ? -1 : (int32_t)s;
             }
             fill = take;
             flush(checked);
@@ -493,7 +543,7 @@ __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : (P >= 
     const int64_t *__restrict__ off_p2p, const int32_t *__restrict__ l_p2p, const uint32_t *__restrict__ perm,
     const uint64_t *__restrict__ items, T eps2, double G, unsigned *__restrict__ work, double *__restrict__ acc_out, double *__restrict__ pot_out,
     const T *__restrict__ wsink, double *__restrict__ gsink, uint32_t wait_limit, int probe,
-    unsigned *__restrict__ status, const RecTab<T> rq)
+    unsigned *__restrict__ status, const RecTab<T> rq, double per_L, int per_ws)
 {
     using S = Smem<P, T>;
     constexpr int CH = Cfg<P, T>::CH;
@@ -543,6 +593,8 @@ __global__ void __launch_bounds__(IW * 32, MODE == 1 ? (P >= 5 ? 2 : 4) : (P >= 
         Gr.p1 = off_p2p[g + 1];
         Gr.own0 = gc;
         Gr.own1 = cend[gc];
+        Gr.pL = per_L;
+        Gr.pws = per_L > 0.0 ? per_ws : 0;
         {
             const int rem = Gr.n - s0;
             int ns, nsplit, si, sj;
@@ -664,7 +716,7 @@ int launch_interact_s(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, doubl
                                        c->smass.p, c->prel.p, c->ccom.p, rec, c->off_m2p.p, c->l_m2p.p, c->off_p2p.p,
                                        c->l_p2p.p, c->idx.p, c->items.p, eps2, c->prm.G, work, acc, pot, wsink,
                                        gsink, c->wait_polls ? c->wait_polls : WAIT_LIMIT, c->wait_probe,
-                                       c->d_status, rq);
+                                       c->d_status, rq, c->prm.box > 0.0 ? c->prm.box : 0.0, c->prm.ws);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
 }
 

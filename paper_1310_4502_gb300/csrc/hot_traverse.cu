@@ -144,7 +144,9 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
 // a group whose lists do not fit sets *slot_over and keeps counting.  MODE 0 also
 // records the largest counts.  Both add the P2P source-particle visits (the particles
 // of every listed leaf, summed over groups) to maxc[3] and write each group's cost key.
-template <int MODE>
+// PER: periodic boundaries (per_L > 0), the open-boundary instantiation carrying none of
+// the image loop's state.
+template <int MODE, bool PER>
 __global__ void __launch_bounds__(TW * 32) k_traverse(
     int64_t ngroup, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const double *__restrict__ gdmax, const TCell *__restrict__ tcell, const TCellF *__restrict__ tcf,
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, double guard,
-    const double *__restrict__ cBn, int q_lo, const double *__restrict__ rcq,
+    const double *__restrict__ cBn, int q_lo, const double *__restrict__ rcq, double per_L, int per_ws,
     int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
@@ -171,10 +173,8 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
-        const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+        const double gx0 = gcen[3 * g + 0], gy0 = gcen[3 * g + 1], gz0 = gcen[3 * g + 2];
         const double dmax = gdmax[g];
-        const float ghx = (float)gx, ghy = (float)gy, ghz = (float)gz;
-        const float glx = (float)(gx - (double)ghx), gly = (float)(gy - (double)ghy), glz = (float)(gz - (double)ghz);
         const float dmaxf = (float)dmax;
         int64_t om = 0, op = 0;
         if (FILL) {
@@ -184,13 +184,27 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
             om = g * capm;
             op = g * capp;
         }
+        uint32_t nm = 0, np = 0;
+        uint64_t p2p_parts = 0;
+        bool overflow = false;
+        // periodic boundaries: the central tree and its images within per_ws, the image's
+        // sources being the tree shifted by s, i.e. the group centre moved by -s; every
+        // entry is tagged with its image
+        const bool per = PER && per_L > 0.0;
+        const int pw = 2 * per_ws + 1;
+        const int nimg = per ? pw * pw * pw : 1;
+        for (int img = 0; img < nimg && !overflow; ++img) {
+        const bool central = 2 * img == nimg - 1;
+        const uint32_t tag = per ? (uint32_t)img << HOT_IMG_SHIFT : 0u;
+        const double gx = per ? gx0 - (double)(img / (pw * pw) - per_ws) * per_L : gx0;
+        const double gy = per ? gy0 - (double)((img / pw) % pw - per_ws) * per_L : gy0;
+        const double gz = per ? gz0 - (double)(img % pw - per_ws) * per_L : gz0;
+        const float ghx = (float)gx, ghy = (float)gy, ghz = (float)gz;
+        const float glx = (float)(gx - (double)ghx), gly = (float)(gy - (double)ghy), glz = (float)(gz - (double)ghz);
         int32_t *A = bufA, *B = bufB;
         if (lane == 0) A[0] = 0;
         __syncwarp();
         int na = 1;
-        uint32_t nm = 0, np = 0;
-        uint64_t p2p_parts = 0;
-        bool overflow = false;
         while (na > 0 && !overflow) {
             int nb = 0;
             for (int base = 0; base < na; base += 32) {
@@ -201,7 +215,8 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 if (c >= 0) {
                     const bool leaf = cnchild[c] == 0;
                     // pre-order: c is the group's cell or an ancestor iff gc lies in c's subtree
-                    const bool anc = c <= gc && gc < cend[c];
+                    // (in the central tree; in an image every cell is a source)
+                    const bool anc = central && c <= gc && gc < cend[c];
                     if (anc) {
                         kind = leaf ? 2 : 3;
                     } else {
@@ -284,13 +299,13 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 const unsigned mm = __ballot_sync(0xffffffffu, kind == 1);
                 const unsigned pm = __ballot_sync(0xffffffffu, kind == 2);
                 if (FILL) {
-                    if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = ent;
-                    if (kind == 2) l_p2p[op + np + __popc(pm & lt)] = c;
+                    if (kind == 1) l_m2p[om + nm + __popc(mm & lt)] = (int32_t)((uint32_t)ent | tag);
+                    if (kind == 2) l_p2p[op + np + __popc(pm & lt)] = (int32_t)((uint32_t)c | tag);
                 } else {
                     if (SLOTS) {
                         const int64_t im = nm + __popc(mm & lt), ip = np + __popc(pm & lt);
-                        if (kind == 1 && im < capm) l_m2p[om + im] = ent;
-                        if (kind == 2 && ip < capp) l_p2p[op + ip] = c;
+                        if (kind == 1 && im < capm) l_m2p[om + im] = (int32_t)((uint32_t)ent | tag);
+                        if (kind == 2 && ip < capp) l_p2p[op + ip] = (int32_t)((uint32_t)c | tag);
                     }
                     if (kind == 2) p2p_parts += (uint64_t)ccount[c];
                 }
@@ -319,6 +334,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
             B = t;
             na = nb;
         }
+        }  // images
         if (overflow) {
             if (lane == 0) hot_flag(status, HOT_ST_FRONTIER);
             nm = np = 0;
@@ -413,6 +429,9 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     const double guard = c->prm.softening == HOT_SOFT_K1 ? c->prm.eps : 0.0;
     // per-interaction order selection: radii of every order, orders in the M2P entries
     const double *cBn = c->varq ? c->cBn.p : nullptr;
+    // periodic boundaries: images of the tree, tagged in the entries
+    const double per_L = c->prm.box > 0.0 ? c->prm.box : 0.0;
+    if (per_L > 0.0 && c->ncell > (int64_t)HOT_IMG_CELL_MASK) return HOT_EINVAL;
     if (c->varq) {
         if (c->ncell > (int64_t)HOT_CELL_MASK) return HOT_EINVAL;
         HOT_CK(c->rcq.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
@@ -430,21 +449,28 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_CK(c->slot_p2p.ensure((size_t)ng * capp, s));
     }
     int64_t host[8];
+#define HOT_TRAV_LAUNCH(M, ...)                                            \
+    do {                                                                   \
+        if (per_L > 0.0)                                                   \
+            k_traverse<M, true><<<blocks, TW * 32, 0, s>>>(__VA_ARGS__);   \
+        else                                                               \
+            k_traverse<M, false><<<blocks, TW * 32, 0, s>>>(__VA_ARGS__);  \
+    } while (0)
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 6 * sizeof(int64_t), s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 58, 0, 4 * sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
         if (slots)
-            k_traverse<2><<<blocks, TW * 32, 0, s>>>(
+            HOT_TRAV_LAUNCH(2,
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
                 capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
-            k_traverse<0><<<blocks, TW * 32, 0, s>>>(
+            HOT_TRAV_LAUNCH(0,
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
                 slot_over, c->gkey.p, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
@@ -487,9 +513,9 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     } else {
         HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
-        k_traverse<1><<<blocks, TW * 32, 0, s>>>(
+        HOT_TRAV_LAUNCH(1,
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->trav_scratch.p, c->trav_cap,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }

@@ -22,18 +22,19 @@ HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS, HOT_DBGSET_
 DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
            CELL_PARENT=7, CELL_NCHILD=8, GROUP_CELL=9, GROUP_CENTRE=10, GROUP_DMAX=11, CELL_MASS=12,
            CELL_COM=13, MOMENTS=14, CELL_BMAX=15, CELL_B1=16, CELL_B2=17, M2P_OFFSETS=18, M2P_CELLS=19,
-           P2P_OFFSETS=20, P2P_CELLS=21, M2P_ORDERS=22)
+           P2P_OFFSETS=20, P2P_CELLS=21, M2P_ORDERS=22, M2P_IMAGES=23, P2P_IMAGES=24)
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
            "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats", "hot_synchronize", "hot_debug_set")
+           "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums")
 
 
 class hot_params(C.Structure):
     _fields_ = [("p", C.c_int), ("tol", C.c_double), ("eps", C.c_double), ("G", C.c_double),
                 ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int),
-                ("softening", C.c_int), ("p_min", C.c_int)]
+                ("softening", C.c_int), ("p_min", C.c_int), ("box", C.c_double), ("ws", C.c_int),
+                ("box_lo", C.c_double * 3)]
 
 
 class HotError(RuntimeError):
@@ -80,10 +81,11 @@ def load():
     L.hot_memory_stats.argtypes = [C.POINTER(C.c_int64), C.c_int]
     L.hot_synchronize.argtypes = [vp]
     L.hot_debug_set.argtypes = [vp, C.c_int, C.c_int64]
+    L.hot_lattice_sums.argtypes = [C.c_double, C.c_int, C.c_int, vp]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
                  "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats", "hot_synchronize", "hot_debug_set"):
+           "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -112,11 +114,12 @@ def _need(t, shape_last=None):
 
 
 def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
-                softening="plummer", p_min=None):
+                softening="plummer", p_min=None, box=0.0, ws=2, box_lo=(0.0, 0.0, 0.0)):
     prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
     soft = HOT_SOFT_K1 if softening in ("k1", HOT_SOFT_K1) else HOT_SOFT_PLUMMER
     return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec, soft,
-                      -1 if p_min is None else int(p_min))
+                      -1 if p_min is None else int(p_min), float(box), int(ws),
+                      (C.c_double * 3)(*[float(v) for v in box_lo]))
 
 
 class Hot:
@@ -207,7 +210,8 @@ class Hot:
             "MOMENTS": (np.float64, (nc, ncomp)), "CELL_BMAX": (np.float64, (nc,)), "CELL_B1": (np.float64, (nc,)),
             "CELL_B2": (np.float64, (nc,)), "M2P_OFFSETS": (np.int64, (ng + 1,)), "M2P_CELLS": (np.int32, (s["n_m2p"],)),
             "P2P_OFFSETS": (np.int64, (ng + 1,)), "P2P_CELLS": (np.int32, (s["n_p2p"],)),
-            "M2P_ORDERS": (np.int32, (s["n_m2p"],)),
+            "M2P_ORDERS": (np.int32, (s["n_m2p"],)), "M2P_IMAGES": (np.int32, (s["n_m2p"],)),
+            "P2P_IMAGES": (np.int32, (s["n_p2p"],)),
         }[what]
         out = np.zeros(spec[1], dtype=spec[0])
         _ck(load().hot_debug_get(self._h, DBG[what], out.ctypes.data_as(C.c_void_p), out.nbytes),
@@ -245,6 +249,17 @@ class Hot:
         return v.value
 
 
+def lattice_sums(L, ws=2, order=17):
+    """D^g psi_far(0), |g| <= order, of a periodic cube of side L less the images within ws
+    (host computation): a numpy array in graded order (by |g|, then descending g_x, then
+    descending g_y)."""
+    import numpy as np
+    n = (order + 1) * (order + 2) * (order + 3) // 6 if order >= 0 else 0
+    out = np.zeros(max(n, 1))
+    _ck(load().hot_lattice_sums(float(L), int(ws), int(order), out.ctypes.data_as(C.c_void_p)), "hot_lattice_sums")
+    return out[:n]
+
+
 def memory_stats(reset_peak=False):
     """(bytes the library holds on the device now, peak bytes since load or last reset)."""
     out = (C.c_int64 * 2)()
@@ -266,11 +281,13 @@ def key_frame_noalloc(pos, mass, frame, stream=None):
 
 
 def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
-               ctx: Hot | None = None, want_pot=True, softening="plummer", p_min=None):
-    """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N]."""
+               ctx: Hot | None = None, want_pot=True, softening="plummer", p_min=None, box=0.0, ws=2,
+               box_lo=(0.0, 0.0, 0.0)):
+    """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N];
+    box > 0: periodic cube [box_lo, box_lo + box) with the images within ws served by the tree."""
     import torch
     h = ctx or Hot(p=p, tol=tol, eps=eps, G=G, leaf_max=leaf_max, group_max=group_max, precision=precision,
-                   softening=softening, p_min=p_min)
+                   softening=softening, p_min=p_min, box=box, ws=ws, box_lo=box_lo)
     h.build_tree(pos, mass)
     h.compute_moments(p)
     h.traverse(tol)
