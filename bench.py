@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / p=6 / error legs")
     ap.add_argument("--no-leapfrog", action="store_true", help="skip the 8-step leapfrog forward+backward leg")
     ap.add_argument("--leapfrog-workload", default="zeldovich256")
+    ap.add_argument("--boundary", default="open", choices=["open", "periodic"],
+                    help="periodic: the workload wrapped into the unit cube, images within ws = 2 "
+                         "through the tree, the farther ones through the lattice sums (no adjoint)")
     return ap.parse_args()
 
 
@@ -291,13 +294,17 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     w = W.make(args.workload)
     N = w.n
+    periodic = args.boundary == "periodic"
+    if periodic:
+        w.pos = np.mod(w.pos, 1.0)
     P = torch.tensor(w.pos, device=dev)
     M = torch.tensor(w.mass, device=dev)
     acc = torch.empty_like(P)
     pot = torch.empty_like(M)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    bkw = dict(box=1.0, ws=2) if periodic else {}
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed", **bkw)
 
     def step(ctx, p):
         ctx.build_tree(P, M)
@@ -349,7 +356,7 @@ def run_ours(args):
     fma32 = h.fma_peak(False) / 1e12
     fma64 = h.fma_peak(True) / 1e12
     roof = {"kernel": f"k_interact<p={w.p},float>", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for(w.p),
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None if periodic else traffic_for(w.p),
             "peak_note": (f"FP32 non-tensor: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max clock); "
                           f"FMA microbenchmark measured {fma32:.1f} TFLOP/s"),
             "flop_convention": f"M2P {FLOPS_M2P[w.p]} flop (generated p={w.p} routine, FMA=2), P2P 28 flop",
@@ -372,13 +379,16 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": describe(w), "N": N, "p": w.p, "tol": w.tol, "eps": w.eps, "leaf_max": h.params.leaf_max,
                       "group_max": h.params.group_max, "l2": "flushed between steps (256 MiB write, untimed)",
-                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+                      "parallelism": "replicas" if ws > 1 else "single GPU",
+                      "boundary": "periodic unit cube (positions wrapped), ws = 2, far images order 8"
+                      if periodic else "open"},
            "stages_ms": stages, "sizes": {k: v for k, v in sz.items() if k != "launches"},
            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "hbm_stages": hbm_stages,
            "fp64_peak_tflops_measured": fma64}
 
-    out["adjoint"] = adjoint_leg(h, lambda: step(h, w.p), N, dev, args.steps, flush, stream)
-    out["adjoint"]["workload"] = describe(w)
+    if not periodic:
+        out["adjoint"] = adjoint_leg(h, lambda: step(h, w.p), N, dev, args.steps, flush, stream)
+        out["adjoint"]["workload"] = describe(w)
 
     # end to end through the public API with host buffers
     pos_h = torch.tensor(w.pos).pin_memory()
@@ -403,7 +413,7 @@ def run_ours(args):
                   "h2d_bytes_per_step": pos_h.nbytes + mass_h.nbytes,
                   "d2h_bytes_per_step": acc_h.nbytes + pot_h.nbytes}
 
-    if not args.no_extras:
+    if not args.no_extras and not periodic:
         mixed_acc = acc.clone()
         # FP64 path, same lists
         h64 = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="fp64")

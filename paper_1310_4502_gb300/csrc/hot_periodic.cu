@@ -169,7 +169,9 @@ void lattice_sums_unit(int ws, int K, double *D)
 
 // Moments about c of the particles of tiles blockIdx.x, blockIdx.x + gridDim.x, ...:
 // part[block][a] = sum m (x - c)^a, |a| <= PF.  T: arithmetic of a tile's sum (float32:
-// the tile sums are added in float64, and the moments of order <= 2 are float64 throughout).
+// the tile sums are added in float64).  The moments of order <= 2 are float64 throughout:
+// each loading thread accumulates those of its own particles (1, x, y, z, x^2, xy, xz,
+// y^2, yz, z^2 in the graded order), reduced over the block at the end.
 template <class T>
 __global__ void __launch_bounds__(FB) k_far_moments(const double *__restrict__ spos, const double *__restrict__ smass,
                                                     int64_t N, double cx, double cy, double cz,
@@ -177,11 +179,14 @@ __global__ void __launch_bounds__(FB) k_far_moments(const double *__restrict__ s
 {
     __shared__ T pw[FT][3][PF + 1];
     __shared__ T ms[FT];
-    __shared__ double yd[FT][4];  // float64 offsets and mass (moments of order <= 2)
+    __shared__ double red[FT / 32][NLO];
     const int t = threadIdx.x;
     int a0 = 0, a1 = 0, a2 = 0;
     if (t < NM) far_decode(t, a0, a1, a2);
     double tot = 0.0;
+    double lo[NLO];
+#pragma unroll
+    for (int k = 0; k < NLO; ++k) lo[k] = 0.0;
     const int64_t ntile = (N + FT - 1) / FT;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         __syncthreads();
@@ -189,35 +194,58 @@ __global__ void __launch_bounds__(FB) k_far_moments(const double *__restrict__ s
             const int64_t i = tile * FT + t;
             const bool ok = i < N;
             const double c3[3] = {cx, cy, cz};
+            double y[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const T y = ok ? (T)(spos[3 * i + d] - c3[d]) : T(0);
+                y[d] = ok ? spos[3 * i + d] - c3[d] : 0.0;
+                const T yt = (T)y[d];
                 T p = T(1);
 #pragma unroll
                 for (int k = 0; k <= PF; ++k) {
                     pw[t][d][k] = p;
-                    p *= y;
+                    p *= yt;
                 }
             }
-            ms[t] = ok ? (T)smass[i] : T(0);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) yd[t][d] = ok ? spos[3 * i + d] - c3[d] : 0.0;
-            yd[t][3] = ok ? smass[i] : 0.0;
+            const double m = ok ? smass[i] : 0.0;
+            ms[t] = (T)m;
+            if (sizeof(T) == 4) {
+                const double mx = m * y[0], my = m * y[1], mz = m * y[2];
+                lo[0] += m;
+                lo[1] += mx;
+                lo[2] += my;
+                lo[3] += mz;
+                lo[4] += mx * y[0];
+                lo[5] += mx * y[1];
+                lo[6] += mx * y[2];
+                lo[7] += my * y[1];
+                lo[8] += my * y[2];
+                lo[9] += mz * y[2];
+            }
         }
         __syncthreads();
-        if (sizeof(T) == 4 && t < NLO) {
-            for (int i = 0; i < FT; ++i) {
-                double v = yd[i][3];
-                for (int k = 0; k < a0; ++k) v *= yd[i][0];
-                for (int k = 0; k < a1; ++k) v *= yd[i][1];
-                for (int k = 0; k < a2; ++k) v *= yd[i][2];
-                tot += v;
-            }
-        } else if (t < NM) {
+        if (t < NM && (sizeof(T) == 8 || t >= NLO)) {
             T s = T(0);
 #pragma unroll 4
             for (int i = 0; i < FT; ++i) s += ms[i] * pw[i][0][a0] * pw[i][1][a1] * pw[i][2][a2];
             tot += (double)s;
+        }
+    }
+    if (sizeof(T) == 4) {
+        // the float64 low orders: warp sums of the loading threads, then across their warps
+        if (t < FT) {
+#pragma unroll
+            for (int k = 0; k < NLO; ++k) {
+                double v = lo[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if ((t & 31) == 0) red[t >> 5][k] = v;
+            }
+        }
+        __syncthreads();
+        if (t < NLO) {
+            tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < FT / 32; ++w) tot += red[w][t];
         }
     }
     if (t < NM) part[(int64_t)blockIdx.x * NM + t] = tot;
