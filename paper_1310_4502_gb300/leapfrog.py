@@ -42,6 +42,10 @@ class KDK:
     def __init__(self, ctx: "_hot.Hot", dt: float, steps: int, every: int = 1):
         if steps < 1 or every < 1:
             raise ValueError("steps and every must be >= 1")
+        if getattr(ctx.params, "box", 0.0) > 0.0:
+            # the backward is hot_adjoint, which periodic boundaries do not have, and the
+            # drifts would carry particles out of the cube the forces assume
+            raise ValueError("the leapfrog runs on open boundaries only")
         self.h = ctx
         self.dt = float(dt)
         self.S = int(steps)

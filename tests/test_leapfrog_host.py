@@ -141,3 +141,14 @@ def test_backward_needs_forward_and_rejects_bad_sizes():
         KDK(DirectCtx(0.1), 0.1, 0)
     with pytest.raises(RuntimeError):
         KDK(DirectCtx(0.1), 0.1, 2).backward(None, None)
+
+
+def test_periodic_contexts_are_refused():
+    """The reverse sweep is hot_adjoint, which periodic boundaries do not have."""
+    ctx = DirectCtx(0.1)
+
+    class _Per(_P):
+        box = 1.0
+    ctx.params = _Per()
+    with pytest.raises(ValueError):
+        KDK(ctx, 0.1, 2)
