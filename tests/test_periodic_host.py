@@ -76,3 +76,44 @@ def test_lattice_sums_reject_bad_arguments(L, ws, order):
     with pytest.raises(hot.HotError) as e:
         hot.lattice_sums(L, ws, order)
     assert e.value.code == hot.HOT_EINVAL
+
+
+def test_lattice_sums_ws1_minus_ws2_is_the_shell_sum():
+    """psi_far(ws = 1) - psi_far(ws = 2) is the plain sum of 1/|r + nL| over the 98 images
+    with |n|_inf = 2: its derivatives at 0 (a finite sum, no Ewald splitting) pin the
+    library's split of near and far images."""
+    L, K = 1.3, 9
+    d = hot.lattice_sums(L, 1, K) - hot.lattice_sums(L, 2, K)
+    r = np.arange(-2, 3)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    n = n[np.max(np.abs(n), axis=1) == 2]
+    R = n * L
+    u = np.sum(R * R, axis=1)
+
+    def dfact(k):
+        out = 1
+        while k > 1:
+            out *= k
+            k -= 2
+        return out
+    # F(u) = u^(-1/2): F^(m)(u) = (-1/2)^m (2m - 1)!! u^(-(m + 1/2))
+    F = np.array([(-0.5) ** m * dfact(2 * m - 1) * u ** (-(m + 0.5)) for m in range(K + 1)])
+    ref = PR._radial_derivs(F, R, K)
+    sc = order_scale(ref)
+    for g, v in ref.items():
+        assert abs(d[gidx(g)] - v) <= 1e-11 * max(sc[sum(g)], 1e-300) + 1e-14, (g, d[gidx(g)], v)
+
+
+def test_far_field_with_the_library_sums_matches_the_oracle():
+    """The oracle's far-field expansion fed with the library's lattice sums instead of its
+    own: forces agree to 1e-11 of their rms (the sums differ only at high orders, where
+    the weights (L/2)^n / n! are small)."""
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, 1, (300, 3))
+    m = rng.uniform(0.5, 1.5, 300) / 300
+    D = hot.lattice_sums(1.0, 2, 17)
+    Do = PR.lattice_coefficients(1.0, 17, 2)
+    a1, p1 = PR.far_field(x, m, 1.0, (0.0, 0.0, 0.0), D=Do)
+    a2, p2 = PR.far_field(x, m, 1.0, (0.0, 0.0, 0.0), D={g: D[gidx(g)] for g in Do})
+    assert np.max(np.abs(a1 - a2)) < 1e-11 * np.sqrt(np.mean(a1 ** 2))
+    assert np.max(np.abs(p1 - p2)) < 1e-11 * np.sqrt(np.mean(p1 ** 2))
