@@ -138,7 +138,7 @@ def multi_indices(p: int) -> list[tuple[int, int, int]]:
 
 # Force smoothing kinds (Sec. "Force Smoothing"): Plummer, or the K1 compensating kernel
 # of support eps (its density is a stated reading; see hot_oracle.c).
-SOFT = {"plummer": 0, "k1": 1}
+SOFT = {"plummer": 0, "k1": 1, "spline": 2}
 
 
 def soft_kernel(soft, eps, r):
@@ -281,8 +281,9 @@ class Tree:
         return out
 
     def softening(self, soft, eps):
-        """Force smoothing of the lists and forces ("plummer" default, or "k1" with support
-        eps: the lists then accept a cell only if d >= b_max + eps); set before traverse."""
+        """Force smoothing of the lists and forces ("plummer" default, or "k1" / "spline" with
+        support eps: the lists then accept a cell only if d >= b_max + eps); set before
+        traverse."""
         if lib().orc_tree_softening(self._h, SOFT[soft], float(eps)) != 0:
             raise ValueError("bad softening")
 

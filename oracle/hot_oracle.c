@@ -90,8 +90,25 @@ void orc_set_threads(int n)
  *     Newtonian (f = r^-3, f2 = -3 r^-5, psi = 1/r) for r >= eps.  The multipole
  *     expansion then uses the unsoftened kernel, and a cell is accepted only if every
  *     sink-source pair is at least eps apart (d >= b_max + eps).
+ *   ORC_SOFT_SPLINE: the cubic spline kernel the paper cites (Springel 2005), read as the
+ *     kernel of unit mass, support r < eps and density 8/(pi eps^3) w(x), x = r/eps,
+ *     w = 1 - 6x^2 + 6x^3 (x < 1/2), 2(1 - x)^3 (1/2 <= x < 1).  Its enclosed mass
+ *     M(x) = 32/3 x^3 - 192/5 x^5 + 32 x^6 (x < 1/2),
+ *            -1/15 + 64/3 x^3 - 48 x^4 + 192/5 x^5 - 32/3 x^6 (x >= 1/2), so with
+ *     f = g(x)/eps^3, g = M/x^3, f2 = g'(x)/(x eps^5) and psi (integrating M/x^2 inwards
+ *     from psi(eps) = 1/eps):
+ *       x < 1/2:  g = 32/3 - 192/5 x^2 + 32 x^3,  g'/x = -384/5 + 96 x,
+ *                 psi eps = 14/5 - 16/3 x^2 + 48/5 x^4 - 32/5 x^5;
+ *       x >= 1/2: g = 64/3 - 48 x + 192/5 x^2 - 32/3 x^3 - 1/(15 x^3),
+ *                 g'/x = 384/5 - 48/x - 32 x + 1/(5 x^5),
+ *                 psi eps = 16/5 - 1/(15 x) - 32/3 x^2 + 16 x^3 - 48/5 x^4 + 32/15 x^5;
+ *     Newtonian for r >= eps; like K1 (a kernel of compact support), unsoftened
+ *     expansions and the guard d >= b_max + eps.
  * ------------------------------------------------------------------------- */
-enum { ORC_SOFT_PLUMMER = 0, ORC_SOFT_K1 = 1 };
+enum { ORC_SOFT_PLUMMER = 0, ORC_SOFT_K1 = 1, ORC_SOFT_SPLINE = 2 };
+
+/* Kernels of compact support (Newtonian beyond eps). */
+static int soft_compact(int kind) { return kind == ORC_SOFT_K1 || kind == ORC_SOFT_SPLINE; }
 typedef struct {
     int kind;
     double eps;
@@ -101,6 +118,25 @@ typedef struct {
  * (zero separation without softening). */
 static int soft_eval(orc_soft sf, double r2, double *f, double *f2, double *psi)
 {
+    if (sf.kind == ORC_SOFT_SPLINE && r2 < sf.eps * sf.eps) {
+        double e = sf.eps, e3 = e * e * e;
+        double x = sqrt(r2) / e;
+        double g, gx, pe;
+        if (x < 0.5) {
+            g = 32.0 / 3.0 + x * x * (-192.0 / 5.0 + 32.0 * x);
+            gx = -384.0 / 5.0 + 96.0 * x;
+            pe = 14.0 / 5.0 + x * x * (-16.0 / 3.0 + x * x * (48.0 / 5.0 - 32.0 / 5.0 * x));
+        } else {
+            double x3 = x * x * x;
+            g = 64.0 / 3.0 + x * (-48.0 + x * (192.0 / 5.0 - 32.0 / 3.0 * x)) - 1.0 / (15.0 * x3);
+            gx = 384.0 / 5.0 - 48.0 / x - 32.0 * x + 1.0 / (5.0 * x3 * x * x);
+            pe = 16.0 / 5.0 - 1.0 / (15.0 * x) + x * x * (-32.0 / 3.0 + x * (16.0 + x * (-48.0 / 5.0 + 32.0 / 15.0 * x)));
+        }
+        *f = g / e3;
+        *f2 = gx / (e3 * e * e);
+        *psi = pe / e;
+        return 1;
+    }
     if (sf.kind == ORC_SOFT_K1 && r2 < sf.eps * sf.eps) {
         double e2 = sf.eps * sf.eps;
         double e3 = e2 * sf.eps;
@@ -110,7 +146,7 @@ static int soft_eval(orc_soft sf, double r2, double *f, double *f2, double *psi)
         *psi = (105.0 + u * (-175.0 + u * (147.0 - 45.0 * u))) / (32.0 * sf.eps);
         return 1;
     }
-    double s2 = sf.kind == ORC_SOFT_K1 ? r2 : r2 + sf.eps * sf.eps;
+    double s2 = soft_compact(sf.kind) ? r2 : r2 + sf.eps * sf.eps;
     if (s2 == 0.0) return 0;
     double sinv = 1.0 / sqrt(s2);
     *psi = sinv;
@@ -127,7 +163,7 @@ int orc_soft_eval(int kind, double eps, double r, double *out)
 }
 
 /* The kernel the multipole expansion uses: softened for Plummer, Newtonian for K1. */
-static double m2p_eps2(orc_soft sf) { return sf.kind == ORC_SOFT_K1 ? 0.0 : sf.eps * sf.eps; }
+static double m2p_eps2(orc_soft sf) { return soft_compact(sf.kind) ? 0.0 : sf.eps * sf.eps; }
 
 /* ---------------------------------------------------------------------------
  * Direct sum.  a_i = G sum_{j != i} m_j f(|x_j - x_i|^2) (x_j - x_i),
@@ -142,7 +178,7 @@ static void pair_acc(const double *xi, const double *xj, double mj, double G,
     double dx = xj[0] - xi[0];
     double dy = xj[1] - xi[1];
     double dz = xj[2] - xi[2];
-    if (sf.kind == ORC_SOFT_K1) {
+    if (soft_compact(sf.kind)) {
         double f, f2, psi;
         if (!soft_eval(sf, dx * dx + dy * dy + dz * dz, &f, &f2, &psi)) return;
         double gm = G * mj;
@@ -206,7 +242,7 @@ void orc_direct_grad(int64_t N, const double *pos, const double *mass, double G,
             const double *xj = pos + 3 * j;
             const double *wj = w + 3 * j;
             double d[3] = {xj[0] - xk[0], xj[1] - xk[1], xj[2] - xk[2]};
-            if (sf.kind == ORC_SOFT_K1) {
+            if (soft_compact(sf.kind)) {
                 double f, f2, psi;
                 if (!soft_eval(sf, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], &f, &f2, &psi)) continue;
                 double c[3];
@@ -882,8 +918,8 @@ static void trav_rec(orc_tree *t, int64_t g, int64_t c, int img)
     double b = t->cbmax[c];
     int accept = 0;
     /* K1: accepted only if no sink comes within eps of a source of the cell */
-    int guard = t->soft != ORC_SOFT_K1 || d >= b + t->soft_eps;
-    if (t->soft == ORC_SOFT_K1 && b + t->soft_eps > 0.0 && fabs(d - (b + t->soft_eps)) <= 1e-9 * (b + t->soft_eps))
+    int guard = !soft_compact(t->soft) || d >= b + t->soft_eps;
+    if (soft_compact(t->soft) && b + t->soft_eps > 0.0 && fabs(d - (b + t->soft_eps)) <= 1e-9 * (b + t->soft_eps))
         ivec_push(&t->lborder[g], (int32_t)c);
     if (t->varq) {
         /* the lowest order in [p_lo, p] whose bound meets the tolerance */
@@ -940,10 +976,10 @@ static void alloc_lists(orc_tree *t)
 }
 
 /* Force smoothing of the lists and forces: kind ORC_SOFT_PLUMMER (default) or
- * ORC_SOFT_K1 with support eps.  Set before the traversal. */
+ * ORC_SOFT_K1 or ORC_SOFT_SPLINE with support eps.  Set before the traversal. */
 int orc_tree_softening(orc_tree *t, int kind, double eps)
 {
-    if ((kind != ORC_SOFT_PLUMMER && kind != ORC_SOFT_K1) || !(eps >= 0.0)) return -1;
+    if ((kind != ORC_SOFT_PLUMMER && !soft_compact(kind)) || !(eps >= 0.0)) return -1;
     t->soft = kind;
     t->soft_eps = eps;
     return 0;
@@ -955,7 +991,7 @@ static int force_soft(const orc_tree *t, double eps, orc_soft *sf)
 {
     sf->kind = t->soft;
     sf->eps = eps;
-    return (t->soft == ORC_SOFT_K1 && eps != t->soft_eps) ? -2 : 0;
+    return (soft_compact(t->soft) && eps != t->soft_eps) ? -2 : 0;
 }
 
 int orc_tree_traverse(orc_tree *t, double tol, double G)

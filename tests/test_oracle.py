@@ -737,6 +737,115 @@ def test_k1_frozen_force_is_tree_force():
 
 
 # --------------------------------------------------------------------------
+# Cubic spline kernel (Sec. "Force Smoothing" cites it, Springel 2005, without a formula):
+# the unit-mass kernel of support eps with density 8/(pi eps^3) w(x), w = 1 - 6x^2 + 6x^3
+# for x < 1/2 and 2(1 - x)^3 for 1/2 <= x < 1.  As for K1, the pins derive the pair terms
+# from that density by quadrature, independent of the oracle's closed forms.
+# --------------------------------------------------------------------------
+
+def _spline_density(r, eps):
+    x = r / eps
+    if x < 0.5:
+        return 8.0 / (math.pi * eps ** 3) * (1 - 6 * x * x + 6 * x ** 3)
+    return 8.0 / (math.pi * eps ** 3) * 2 * (1 - x) ** 3 if x < 1 else 0.0
+
+
+@pytest.mark.parametrize("xr", [0.0, 0.05, 0.3, 0.4999, 0.5, 0.5001, 0.7453, 0.9, 0.999, 1.0, 1.2, 3.0])
+def test_spline_pair_force_and_potential_from_density(xr):
+    from scipy.integrate import quad
+    eps = 0.37
+    assert abs(quad(lambda r: 4 * math.pi * r * r * _spline_density(r, eps), 0, eps, points=[eps / 2])[0] - 1) < 1e-13
+    r = xr * eps
+    f, f2, psi = oracle.soft_kernel("spline", eps, r)
+
+    def Mof(t):
+        return quad(lambda q: 4 * math.pi * q * q * _spline_density(q, eps), 0, min(t, eps), points=[eps / 2])[0]
+    if r > 0:
+        assert abs(f - Mof(r) / r ** 3) <= 1e-12 * abs(f)
+        tail = quad(lambda t: Mof(t) / (t * t), r, eps, points=[eps / 2])[0] if r < eps else 0.0
+        psi_ref = 1.0 / eps + tail if r < eps else 1.0 / r
+        assert abs(psi - psi_ref) <= 1e-11 * psi_ref
+        h = 1e-6 * r * r
+        fp = oracle.soft_kernel("spline", eps, math.sqrt(r * r + h))[0]
+        fm = oracle.soft_kernel("spline", eps, math.sqrt(r * r - h))[0]
+        assert abs(f2 - 2 * (fp - fm) / (2 * h)) <= 1e-6 * abs(f2)
+    else:
+        # the centre: f = (4/3) pi rho(0) / (unit mass) = 32/3 eps^-3, psi = 14/(5 eps)
+        assert abs(f - 32.0 / 3.0 / eps ** 3) <= 1e-14 * f
+        assert abs(psi - 14.0 / (5.0 * eps)) <= 1e-14 * psi
+    if xr >= 1.0:
+        assert f == pytest.approx(1.0 / r ** 3, rel=1e-15) and psi == pytest.approx(1.0 / r, rel=1e-15)
+
+
+def test_spline_force_never_exceeds_newtonian_and_is_continuous():
+    """A positive density: the force is below the Newtonian one inside the support (no
+    compensation, unlike K1) and the force, its slope and the potential are continuous at
+    x = 1/2 and at the edge."""
+    eps = 0.37
+    for x in (0.1, 0.3, 0.5, 0.8, 0.97):
+        f = oracle.soft_kernel("spline", eps, x * eps)[0]
+        assert f * (x * eps) ** 3 < 1.0
+    for x0 in (0.5, 1.0):
+        lo = oracle.soft_kernel("spline", eps, eps * x0 * (1 - 1e-12))
+        hi = oracle.soft_kernel("spline", eps, eps * x0 * (1 + 1e-12))
+        for k in range(3):
+            assert abs(lo[k] - hi[k]) <= 1e-8 * abs(hi[k])
+
+
+def test_spline_direct_sum_tree_and_gradient():
+    """Third law; the unsoftened sum when every pair is farther than eps; the tree with the
+    compact-support guard converging to the spline direct sum; the analytic gradient
+    against central differences."""
+    rng = np.random.default_rng(32)
+    pos = rng.uniform(-1, 1, (300, 3))
+    mass = rng.uniform(0.5, 1.5, 300)
+    acc, _ = oracle.direct(pos, mass, 1.0, 0.3, soft="spline")
+    assert np.linalg.norm((mass[:, None] * acc).sum(0)) < 1e-12 * np.abs(mass[:, None] * acc).sum()
+    grid = np.stack(np.meshgrid(*[np.arange(4.0)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    ak, _ = oracle.direct(grid, np.ones(len(grid)), 1.0, 0.9, soft="spline")
+    an, _ = oracle.direct(grid, np.ones(len(grid)), 1.0, 0.0)
+    assert np.max(rel_err(ak, an)) < 1e-13
+    w = W.make("plummer4096")
+    eps = 0.05
+    ref, _ = oracle.direct(w.pos, w.mass, 1.0, eps, soft="spline")
+    errs = []
+    for tol in (1e-3, 1e-5, 1e-7):
+        t = oracle.Tree(w.pos, w.mass)
+        t.softening("spline", eps)
+        t.moments(6)
+        t.traverse(tol)
+        a, _ = t.force(1.0, eps)
+        errs.append(np.sqrt(np.mean(rel_err(a, ref) ** 2)))
+        L = t.lists()
+        gr, mo = t.groups(), t.get_moments()
+        om, cells = L["m2p"]
+        for g in range(len(gr["cell"])):
+            cs = cells[om[g]:om[g + 1]]
+            d = np.linalg.norm(mo["com"][cs] - gr["centre"][g], axis=1) - gr["dmax"][g]
+            assert np.all(d >= mo["bmax"][cs] + eps)
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6
+    n = 40
+    p0, m0 = rng.uniform(-1, 1, (n, 3)), rng.uniform(0.5, 1.5, n)
+    wt, v = rng.standard_normal((n, 3)), rng.standard_normal(n)
+
+    def loss(p, m):
+        a, ph = oracle.direct(p, m, 1.0, 0.4, soft="spline")
+        return float((wt * a).sum() + (v * ph).sum())
+    gx, gm = oracle.direct_grad(p0, m0, wt, v, 1.0, 0.4, soft="spline")
+    h = 1e-6
+    for k in (0, 7, 19, 33):
+        for d in range(3):
+            pp, pm = p0.copy(), p0.copy()
+            pp[k, d] += h
+            pm[k, d] -= h
+            assert abs(gx[k, d] - (loss(pp, m0) - loss(pm, m0)) / (2 * h)) <= 1e-7 * max(1.0, abs(gx[k, d]))
+        mp, mm = m0.copy(), m0.copy()
+        mp[k] += h
+        mm[k] -= h
+        assert abs(gm[k] - (loss(p0, mp) - loss(p0, mm)) / (2 * h)) <= 1e-7 * max(1.0, abs(gm[k]))
+
+
+# --------------------------------------------------------------------------
 # Per-interaction order selection (Sec. "Multipole Error Bounds": the bounds choose
 # between expansion orders and refinement).  Reading: among the orders p_lo..p, an
 # accepted cell is evaluated at the lowest order whose bound meets the tolerance.
