@@ -1072,3 +1072,26 @@ def test_periodic_tree_converges_to_ewald():
         errs.append(np.sqrt(np.mean(rel_err(a, ra) ** 2)))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 1e-7
+
+
+def test_periodic_tree_force_is_lattice_translation_invariant():
+    """Moving every particle and the cube by a lattice vector changes nothing; a shift
+    with wrap-around changes the tree but not the periodic force beyond the method's
+    accuracy (p = 8, tol 1e-8: each within 2e-7 rms of Ewald, which the shift leaves
+    unchanged)."""
+    from oracle import periodic as PR
+    rng = np.random.default_rng(19)
+    n, L = 200, 1.0
+    x = rng.uniform(0, L, (n, 3))
+    m = rng.uniform(0.5, 1.5, n) / n
+    D = PR.lattice_coefficients(L, 17)
+    a0, p0 = PR.tree_force(x, m, L, (0.0, 0.0, 0.0), p=8, tol=1e-8, D=D, leaf_max=16, group_max=32)
+    a1, p1 = PR.tree_force(x + [L, -L, 2 * L], m, L, (L, -L, 2 * L), p=8, tol=1e-8, D=D, leaf_max=16,
+                           group_max=32)
+    assert np.max(rel_err(a1, a0)) < 1e-9 and np.max(np.abs(p1 - p0)) < 1e-9 * np.sqrt(np.mean(p0 ** 2))
+    s = np.array([0.37, 0.81, 0.05])
+    a2, _ = PR.tree_force(np.mod(x + s, L), m, L, (0.0, 0.0, 0.0), p=8, tol=1e-8, D=D, leaf_max=16, group_max=32)
+    ra, _ = PR.ewald(x, m, L)
+    rs, _ = PR.ewald(np.mod(x + s, L), m, L)
+    assert np.max(rel_err(rs, ra)) < 1e-10
+    assert np.sqrt(np.mean(rel_err(a0, ra) ** 2)) < 2e-7 and np.sqrt(np.mean(rel_err(a2, ra) ** 2)) < 2e-7
