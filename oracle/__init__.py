@@ -73,6 +73,7 @@ def lib():
         L.orc_sort.argtypes = [C.c_int64, _u64, _i64]
         L.orc_m2p.argtypes = [C.c_int, _d, _d, C.c_double, C.c_double, _d,
                               C.POINTER(C.c_double)]
+        L.orc_m2p_points.argtypes = [C.c_int, _d, _d, C.c_int64, _d, C.c_double, C.c_double, _d, _d]
         L.orc_moments.argtypes = [C.c_int64, _d, _d, _d, C.c_int, _d]
         L.orc_mac_bound.restype = C.c_double
         L.orc_mac_bound.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double]
@@ -198,6 +199,15 @@ def m2p(p, M, R, G=1.0, eps=0.0):
     pot = C.c_double()
     lib().orc_m2p(int(p), _c(M), _c(R), G, eps, acc, C.byref(pot))
     return acc, pot.value
+
+
+def m2p_points(p, M, z, x, G=1.0, eps=0.0):
+    """m2p at every point of x [n,3] (R = x - z): (acc [n,3], pot [n])."""
+    x = _c(x)
+    acc = np.zeros((len(x), 3))
+    pot = np.zeros(len(x))
+    lib().orc_m2p_points(int(p), _c(M), _c(z), len(x), x, G, eps, acc, pot)
+    return acc, pot
 
 
 def moments(pos, mass, z, p):

@@ -44,7 +44,7 @@ import math
 
 import numpy as np
 
-from . import Tree, direct, m2p, mac_bound, moments, multi_indices
+from . import Tree, direct, m2p_points, mac_bound, moments, multi_indices
 
 
 # ---- the uniform cube ----
@@ -238,10 +238,9 @@ class BackgroundTree:
                 return fa, fp
 
             def expand(M, z):
-                for i in range(len(sinks)):
-                    ai, pi = m2p(p, M, xs[i] - z, G, eps)
-                    a[i] += ai
-                    ph[i] += pi
+                ai, pi = m2p_points(p, M, z, xs, G, eps)
+                a[:] += ai
+                ph[:] += pi
 
             def p2p(c):
                 src = self.particles(c)

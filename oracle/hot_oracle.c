@@ -471,6 +471,21 @@ void orc_m2p(int p, const double *M, const double *R, double G, double eps, doub
     m2p_eval(p, (const int(*)[3])tab, M, R, G, eps * eps, acc, pot);
 }
 
+/* The same expansion (moments M about z) at n points x: acc [n][3], pot [n] added to. */
+void orc_m2p_points(int p, const double *M, const double *z, int64_t n, const double *x, double G,
+                    double eps, double *acc, double *pot)
+{
+    int tab[200][3];
+    midx_table(p, tab);
+    for (int64_t i = 0; i < n; i++) {
+        double R[3] = {x[3 * i] - z[0], x[3 * i + 1] - z[1], x[3 * i + 2] - z[2]};
+        double a[3] = {0.0, 0.0, 0.0}, ph = 0.0;
+        m2p_eval(p, (const int(*)[3])tab, M, R, G, eps * eps, a, &ph);
+        for (int d = 0; d < 3; d++) acc[3 * i + d] += a[d];
+        pot[i] += ph;
+    }
+}
+
 /* Exported for unit tests: raw moments of a particle set about z. */
 void orc_moments(int64_t n, const double *pos, const double *mass, const double *z, int p,
                  double *M)
