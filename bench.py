@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / p=6 / error legs")
     ap.add_argument("--no-leapfrog", action="store_true", help="skip the 8-step leapfrog forward+backward leg")
     ap.add_argument("--leapfrog-workload", default="zeldovich256")
+    ap.add_argument("--build-only", action="store_true",
+                    help="time only the tree build (bounding cube, keys, sort, gather, tree) on --workload "
+                         "and print one JSON line (the command the sort kernels' ncu captures run)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the forward step and the adjoint on --workload (the sequence the "
+                         "adjoint kernels' profiles capture) and print one JSON line")
     ap.add_argument("--boundary", default="open", choices=["open", "periodic"],
                     help="periodic: the workload wrapped into the unit cube, images within ws = 2 "
                          "through the tree, the farther ones through the lattice sums (no adjoint)")
@@ -284,6 +290,152 @@ def leapfrog_leg(wname, dev, stream, steps=8, dt=1e-3):
             "peak_torch_bytes": torch_peak}
 
 
+# Algorithmic bytes per particle of the keys and sort stage: bounding cube (read position
+# and mass, 32 B), keys with the digit histograms (read position, write key and index, 36 B),
+# eight radix passes (read and write key and index, 8 x 24 B), gather into key order (read
+# index, position and mass, write them sorted, 68 B).
+SORT_BYTES = 32 + 36 + 8 * 24 + 68
+
+
+def build_leg(wname, dev, stream, flush, K):
+    """hot_build_tree alone on a workload, CUDA-event timed per stage with an L2 flush
+    between calls: keys + sort against the measured HBM bandwidth."""
+    import torch
+    from paper_1310_4502_gb300 import hot
+    w = W.make(wname)
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    for _ in range(3):
+        h.build_tree(P, M)
+    st = {"sort": 0.0, "build": 0.0}
+    tot = 0.0
+    for _ in range(K):
+        tot += _ev_ms(stream, lambda: h.build_tree(P, M), flush)[0]
+        t = h.stage_times()
+        st["sort"] += t["sort"] / K
+        st["build"] += t["build"] / K
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    gbs = w.n * SORT_BYTES / (st["sort"] * 1e-3) / 1e9
+    out = {"workload": describe(w), "N": w.n, "steps": K, "ms_per_call": tot / K, "stages_ms": st,
+           "keys_sort": {"bytes_per_particle": SORT_BYTES, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm},
+           "build_particles_per_s": w.n / (st["build"] * 1e-3)}
+    del h
+    return out
+
+
+def run_build_only(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    print(json.dumps({"build_only": build_leg(args.workload, dev, torch.cuda.current_stream(), flush,
+                                              args.steps)}), flush=True)
+
+
+def lattice_leg(dev, stream, flush, K, with_cpu, wname="zeldovich128"):
+    """The lattice configuration: Zel'dovich lattice 128^3, p = 6, mixed precision; step time,
+    the per-stage split (keys + sort, build, moments, traversal, interactions) and the
+    interaction rates, plus the truncation error against the FP64 direct sum on a seeded
+    4096-particle subsample."""
+    import torch
+    from paper_1310_4502_gb300 import hot
+    w = W.make(wname)
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    acc = torch.empty_like(P)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    for _ in range(3):
+        h.force(P, M, acc)
+    tot, stages = 0.0, {}
+    for _ in range(K):
+        tot += _ev_ms(stream, lambda: h.force(P, M, acc), flush)[0]
+        for k, v in h.stage_times().items():
+            stages[k] = stages.get(k, 0.0) + v / K
+    stages.pop("adjoint", None)
+    sz = h.sizes()
+    ms = tot / K
+    t_int = stages["interact"] * 1e-3
+    out = {"workload": describe(w), "N": w.n, "p": w.p, "steps": K, "ms_per_step": ms,
+           "value": w.n / (ms * 1e-3), "unit": "particles/s", "stages_ms": stages,
+           "m2p_interactions": sz["n_m2p_int"], "p2p_interactions": sz["n_pairs"],
+           "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int,
+           "interact_tflops_convention": (sz["n_m2p_int"] * FLOPS_M2P[w.p] + sz["n_pairs"] * P2P_FLOPS) / t_int / 1e12,
+           "interact_tflops_source_form": (sz["n_m2p_int"] * FLOPS_M2P_SRC[w.p] + sz["n_pairs"] * P2P_FLOPS)
+           / t_int / 1e12}
+    if with_cpu:
+        import oracle
+        sub = np.sort(np.random.default_rng(3).choice(w.n, 4096, replace=False))
+        ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps, sinks=sub)
+        e = np.linalg.norm(acc.cpu().numpy()[sub] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        out["tree_vs_direct_rms_rel_4096"] = float(np.sqrt(np.mean(e ** 2)))
+        out["tree_vs_direct_max_rel_4096"] = float(e.max())
+    del h
+    return out
+
+
+def plummer_leg(dev, stream, K):
+    """The small configuration: Plummer sphere N = 4096 (eps = 0.01, p = 4, tol = 1e-4), FP64
+    throughout; step time, the error against the FP64 direct sum, and the radial
+    acceleration against the truncated Plummer profile -G M(<r)/r^2 (M(<r) = r^3 (r^2+1)^-3/2
+    / X(20)) in radial bins of at least 128 particles (sampling noise and softening bias
+    included: context, not a bound)."""
+    import torch
+    import oracle
+    from paper_1310_4502_gb300 import hot
+    w = W.make("plummer4096")
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    acc = torch.empty_like(P)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="fp64")
+    for _ in range(3):
+        h.force(P, M, acc)
+    tot = 0.0
+    for _ in range(K):
+        tot += _ev_ms(stream, lambda: h.force(P, M, acc), None)[0]
+    a = acc.cpu().numpy()
+    ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps)
+    e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    r = np.linalg.norm(w.pos, axis=1)
+    ar = -np.sum(a * w.pos, axis=1) / r
+    xmax = 20.0 ** 3 / (20.0 ** 2 + 1.0) ** 1.5
+    menc = r ** 3 / (r * r + 1.0) ** 1.5 / xmax
+    q = ar * r * r / menc
+    order = np.argsort(r)
+    bins = []
+    for b in np.array_split(order, len(order) // 256):
+        bins.append({"r_median": float(np.median(r[b])), "mean_ratio": float(np.mean(q[b])), "n": len(b)})
+    dev_max = max(abs(b["mean_ratio"] - 1.0) for b in bins)
+    out = {"workload": describe(w) + "; FP64 throughout", "N": w.n, "steps": K, "ms_per_step": tot / K,
+           "value": w.n / (tot / K * 1e-3), "unit": "particles/s",
+           "tree_vs_direct_rms_rel": float(np.sqrt(np.mean(e ** 2))), "tree_vs_direct_max_rel": float(e.max()),
+           "profile_bins": len(bins), "profile_max_bin_deviation": dev_max,
+           "profile_note": "bin mean of -a_r r^2 / M(<r) over 256-particle radial bins (1 = the analytic profile)"}
+    del h
+    return out
+
+
+def run_adjoint_only(args):
+    """Forward step and adjoint on one workload, CUDA-event timed: the command the adjoint
+    kernels' ncu captures run."""
+    import torch
+    from paper_1310_4502_gb300 import hot
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = W.make(args.workload)
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    acc = torch.empty_like(P)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    for _ in range(args.warmup):
+        h.force(P, M, acc)
+    r = adjoint_leg(h, lambda: h.force(P, M, acc), w.n, dev, args.steps, flush, stream)
+    r["workload"] = describe(w)
+    print(json.dumps({"adjoint_only": r}), flush=True)
+
+
 def run_ours(args):
     import torch
 
@@ -359,18 +511,31 @@ def run_ours(args):
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None if periodic else traffic_for(w.p),
             "peak_note": (f"FP32 non-tensor: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max clock); "
                           f"FMA microbenchmark measured {fma32:.1f} TFLOP/s"),
-            "flop_convention": f"M2P {FLOPS_M2P[w.p]} flop (generated p={w.p} routine, FMA=2), P2P 28 flop",
+            "flop_convention": (f"M2P {FLOPS_M2P[w.p]} flop per interaction (the explicit-monomial form of the "
+                                f"generated p={w.p} routine, FMA=2; a fixed convention), P2P 28 flop (the paper's)"),
+            "m2p_flops_source_form": FLOPS_M2P_SRC[w.p],
+            "achieved_source_form": (sz["n_m2p_int"] * FLOPS_M2P_SRC[w.p] + flops_p2p) / t_int / 1e12,
             "m2p_interactions": sz["n_m2p_int"], "p2p_interactions": sz["n_pairs"],
             "ms_per_launch": stages["interact"],
             "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int,
             "m2p_interactions_per_s": sz["n_m2p_int"] / t_int, "p2p_pairs_per_s": sz["n_pairs"] / t_int}
+    roof["frac_source_form"] = roof["achieved_source_form"] / peak
+    ex = None if periodic else executed_for(w.p)
+    if ex is not None:
+        # FP32 operations the captured launch executed (ncu thread-instruction counters:
+        # FFMA 2, FADD 1, FMUL 1, the paired forms twice that), over the live launch time
+        exf = 2 * ex["ffma"] + ex["fadd"] + ex["fmul"] + 4 * ex.get("ffma2", 0) + 2 * ex.get("fadd2", 0) \
+            + 2 * ex.get("fmul2", 0)
+        roof["executed"] = {"fp32_flops_per_launch": exf, "achieved": exf / t_int / 1e12,
+                            "frac": exf / t_int / 1e12 / peak, "mufu_warp_inst": ex.get("mufu"),
+                            "source": ex["source"]}
     # the HBM-bound integer stages against the measured copy bandwidth, with algorithmic
-    # bytes per particle: bounding cube + keys (read positions twice and masses, write key
-    # and index: 68 B), eight 8-bit LSD passes over (key, index) (192 B), gather of
-    # positions and masses into key order (64 B); tree build from the sorted keys (12 B)
+    # bytes per particle: keys and sort (SORT_BYTES); tree build from the sorted keys
+    # (12 B).  At this size (2^20) the sort's arrays fit in L2; the 256^3 leg below is the
+    # HBM-bound case.
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_stages = {}
-    for name, stage, bpp in (("keys_sort", "sort", 68 + 192 + 64), ("build", "build", 12)):
+    for name, stage, bpp in (("keys_sort", "sort", SORT_BYTES), ("build", "build", 12)):
         gbs = N * bpp / (stages[stage] * 1e-3) / 1e9
         hbm_stages[name] = {"bytes_per_particle": bpp, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
 
@@ -528,10 +693,20 @@ def run_ours(args):
         out["adjoint_2e18"] = adjoint_leg(hd, lambda: hd.force(Pd, Md, ad), wd.n, dev, args.steps, flush, stream)
         out["adjoint_2e18"]["workload"] = describe(wd)
         del hd
+        out["lattice128"] = lattice_leg(dev, stream, flush, min(args.steps, 10), rank == 0 and not args.no_cpu)
+        out["sort256"] = build_leg("zeldovich256", dev, stream, flush, min(args.steps, 10))
+        out["plummer4096_fp64"] = plummer_leg(dev, stream, min(args.steps, 10))
     if not args.no_leapfrog:
         out["leapfrog"] = leapfrog_leg(args.leapfrog_workload, dev, stream)
     if rank == 0 and not args.no_cpu:
+        import oracle
         out["cpu_baseline"] = {k: v for k, v in oracle_sample(w).items() if k != "seconds"}
+        nt = oracle.nthreads()
+        oracle.set_threads(1)
+        one = oracle_sample(w, frac_inv=2048)
+        oracle.set_threads(nt)
+        out["cpu_baseline"]["single_core"] = {"value": one["value"], "unit": "particles/s", "cores": 1,
+                                              "sample": one["sample"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -545,6 +720,22 @@ def _flops_table():
 
 
 FLOPS_M2P = _flops_table()
+
+
+def _flops_source_table():
+    from paper_1310_4502_gb300.csrc.gen_kernels import m2p_source_flops, PMAX
+    return [m2p_source_flops(q) for q in range(PMAX + 1)]
+
+
+FLOPS_M2P_SRC = _flops_source_table()
+
+# ncu thread-instruction counts of one interaction-kernel launch on the headline workload,
+# with the hash of the kernel sources they were taken on (reported only while unchanged).
+EXECUTED = {}
+
+
+def executed_for(p):
+    return EXECUTED.get((p, _kernel_hash()))
 
 # ncu-measured DRAM traffic of the interaction kernel, per launch, on the workload above,
 # with the source hash it was taken on; reported only while the kernel is unchanged.
@@ -571,5 +762,9 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.adjoint_only:
+        run_adjoint_only(a)
+    elif a.build_only:
+        run_build_only(a)
     else:
         run_ours(a)

@@ -48,7 +48,7 @@ extern "C" {
 
 enum {
     HOT_OK = 0,
-    HOT_EINVAL = -1,     /* bad argument (N < 1, p outside [0,6], tol <= 0, eps < 0, ...) */
+    HOT_EINVAL = -1,     /* bad argument (N < 1, p outside [0,8], tol <= 0, eps < 0, ...) */
     HOT_ESTATE = -2,     /* call out of order (e.g. forces before traverse) */
     HOT_ENOMEM = -3,     /* device allocation failed */
     HOT_EOVERFLOW = -4,  /* a capacity limit was still exceeded after the internal retry */
@@ -69,20 +69,28 @@ enum { HOT_FP32_MIXED = 0, HOT_FP64 = 1 };
  *     psi = (105 - 175 u + 147 u^2 - 45 u^3)/(32 eps); Newtonian for r >= eps.  The
  *     multipole expansions use the unsoftened kernel and a cell is accepted only
  *     when every source is at least eps from every sink of the group
- *     (|z - g| - Delta_max >= b_max + eps). */
-enum { HOT_SOFT_PLUMMER = 0, HOT_SOFT_K1 = 1 };
+ *     (|z - g| - Delta_max >= b_max + eps).
+ *   HOT_SOFT_SPLINE: the cubic spline kernel of support eps (the kernel of the SPH code
+ *     the section cites), the unit-mass density 8/(pi eps^3) w(x), x = r/eps,
+ *     w = 1 - 6 x^2 + 6 x^3 (x < 1/2), 2 (1 - x)^3 (1/2 <= x < 1).  For r < eps:
+ *     x < 1/2: f = (32/3 - 192/5 x^2 + 32 x^3)/eps^3,
+ *              psi = (14/5 - 16/3 x^2 + 48/5 x^4 - 32/5 x^5)/eps;
+ *     x >= 1/2, t = 1 - x, M = 1 - 16 t^4 + 128/5 t^5 - 32/3 t^6 (enclosed mass):
+ *              f = M/r^3, psi = M/r + (16 t^4 - 64/5 t^5)/eps;
+ *     Newtonian for r >= eps; expansions and acceptance as for K1. */
+enum { HOT_SOFT_PLUMMER = 0, HOT_SOFT_K1 = 1, HOT_SOFT_SPLINE = 2 };
 
 typedef struct hot_ctx hot_ctx;
 
 typedef struct {
     int p;          /* expansion order, 0..8 (potential terms |a| <= p)           */
     double tol;     /* absolute acceleration error bound per accepted cell, > 0  */
-    double eps;     /* softening length, >= 0 (Plummer length or K1 support)     */
+    double eps;     /* softening length, >= 0 (Plummer length, K1 or spline support) */
     double G;       /* gravitational constant                                     */
     int leaf_max;   /* a cell with more particles is refined (levels < 21), >= 1  */
     int group_max;  /* sink groups: topmost cells with <= group_max particles     */
     int precision;  /* HOT_FP32_MIXED or HOT_FP64 interaction arithmetic          */
-    int softening;  /* HOT_SOFT_PLUMMER or HOT_SOFT_K1                            */
+    int softening;  /* HOT_SOFT_PLUMMER, HOT_SOFT_K1 or HOT_SOFT_SPLINE           */
     int p_min;      /* -1: every accepted cell at order p; 0..p: per-interaction  */
                     /* order selection, the lowest order in [p_min, p] whose      */
                     /* bound E_q(d) <= tol (B_{q+1}, B_{q+2}) accepts the cell     */
@@ -97,6 +105,14 @@ typedef struct {
     double box_lo[3]; /* periodic: lower corner of the cube; every position in   */
                     /* [box_lo, box_lo + box) (not checked: a particle outside    */
                     /* gives forces of no defined meaning, never a fault)         */
+    int background; /* 1: background subtraction (Sec. "Background Subtraction"):  */
+                    /* the field of the particles minus a uniform density M/L^3  */
+                    /* over the tree's root cube (the key frame), see           */
+                    /* hot_evaluate_forces; 0: off.  Plummer smoothing, open    */
+                    /* boundaries, a fixed order p <= 6 and no adjoint           */
+    int bg_up;      /* background subtraction: the surrounding cube of a group is */
+                    /* its cell's ancestor bg_up levels up (the root if fewer),   */
+                    /* 0..21                                                      */
 } hot_params;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
@@ -131,7 +147,13 @@ int hot_build_tree(hot_ctx *ctx, const double *pos, const double *mass, int64_t 
  * b_max = max |x - z|, B_{p+1}, B_{p+2} (B_n = sum m |x - z|^n), and the
  * interaction coefficient records.  Under per-interaction order selection
  * (p_min >= 0) also B_n for every n <= p+2 and the records of the orders p_min..p-1.
- * p in [0, 8], p >= p_min; asynchronous. */
+ * Under background subtraction also every cell's moments about its cube's centre to
+ * order p + 2, less those of the uniform cube of density rho = M / L^3 (the contrast),
+ * with Q_n = (sum_{|a|=n} n!/a! M_a^2)^(1/2) for n = p+1, p+2 and the contrast's
+ * order-p record, and the same for the empty octants of the inner cells (child cubes
+ * holding no particle: contrast -rho); this synchronises once (the number of empty
+ * octants sizes the records).
+ * p in [0, 8], p >= p_min; asynchronous otherwise. */
 int hot_compute_moments(hot_ctx *ctx, int p);
 
 /* Group-wise traversal (Sec. "Improving instruction-level parallelism": m
@@ -149,8 +171,18 @@ int hot_compute_moments(hot_ctx *ctx, int p);
  * opened.  Under periodic boundaries every group also traverses the images of the
  * tree within ws cubes (the tree moved by nL, |n|_inf <= ws; in the central one the
  * group's ancestors are opened as above, in the others every cell is tested), each
- * list entry tagged with its image.  tol > 0.  Synchronises the stream once (list
- * sizes); HOT_EINVAL under periodic boundaries with 2^24 cells or more. */
+ * list entry tagged with its image.
+ * Under background subtraction a group's surrounding cube S is its cell's ancestor
+ * bg_up levels up.  Cells inside S are tested as above; a cell outside S is tested by
+ * its contrast about the cube's centre c, d = |c - g| - Delta_max, b = the cube's
+ * half-diagonal: accepted iff d > b and
+ *   E(d) = G (1 - b/d)^-2 [(p+2) Q_{p+1} / d^{p+3} + (p+3) Q_{p+2} / d^{p+4}] <= tol
+ * (an estimate: the bound above needs a positive distribution); a rejected leaf goes
+ * to the particle-particle list and its cube to the analytic-cube list, a rejected inner
+ * cell is opened; every opened cell outside S (ancestors above S included) adds each
+ * empty octant, by its contrast expansion if accepted, else to the analytic-cube list.
+ * tol > 0.  Synchronises the stream once (list sizes); HOT_EINVAL under periodic
+ * boundaries with 2^24 cells or more. */
 int hot_traverse(hot_ctx *ctx, double tol);
 
 /* Interactions on the lists: M2P (expansion of the Plummer-softened kernel, or of
@@ -160,7 +192,14 @@ int hot_traverse(hot_ctx *ctx, double tol);
  * periodic boundaries the sources of an image entry are moved by its nL, no sink
  * meets itself outside the central cube, and the far images' local expansion of
  * order 8 (moments of all particles about the cube's centre, the lattice sums of
- * hot_lattice_sums, float32 in the mixed mode) is added.
+ * hot_lattice_sums, float32 in the mixed mode) is added.  Under background subtraction
+ * the result is the field of the particles less that of the uniform density rho over
+ * the root cube [lo, lo + L)^3 (the key frame), the background unsoftened:
+ *   a_i = (the softened sum above) - G rho int_root (x - x_i) / |x - x_i|^3 dV,
+ *   phi_i = (the softened sum above) + G rho int_root dV / |x - x_i|;
+ * each group's analytic cubes and its surrounding cube add the closed-form field of a
+ * uniform cube of density -rho at every sink (float32 on float64 corner offsets in the
+ * mixed mode).
  *   acc device, [N][3] float64, written in the caller's original order
  *   pot device, [N] float64 or NULL                                      */
 int hot_evaluate_forces(hot_ctx *ctx, double *acc, double *pot);
@@ -214,9 +253,24 @@ enum {
     HOT_DBG_P2P_CELLS = 21,   /* int32[n_p2p]                                */
     HOT_DBG_M2P_ORDERS = 22,  /* int32[n_m2p]: expansion order of each M2P entry */
     HOT_DBG_M2P_IMAGES = 23,  /* int32[n_m2p]: periodic image of each M2P entry  */
-    HOT_DBG_P2P_IMAGES = 24   /* int32[n_p2p]: periodic image of each P2P entry  */
+    HOT_DBG_P2P_IMAGES = 24,  /* int32[n_p2p]: periodic image of each P2P entry  */
+    /* background subtraction: M2P entries c < ncell are matter expansions, ncell + c the
+     * contrast expansion of cell c, 2 ncell + e that of empty octant e; cube entries c <
+     * ncell are cell c's cube, ncell + e empty octant e's */
+    HOT_DBG_BG_CUBE_OFFSETS = 25, /* int64[ngroup + 1]: the groups' analytic-cube lists */
+    HOT_DBG_BG_CUBES = 26,        /* int32[n_cube]                                     */
+    HOT_DBG_BG_GROUP_S = 27,      /* int32[ngroup]: the surrounding cube's cell          */
+    HOT_DBG_BG_EMPTY_PARENT = 28, /* int32[n_empty]: the cell an empty octant belongs to */
+    HOT_DBG_BG_EMPTY_OCTANT = 29  /* int32[n_empty]: its octant (0..7, x highest bit)    */
 };
 int hot_debug_get(hot_ctx *ctx, int what, void *host_dst, size_t bytes);
+
+/* Sizes of background subtraction after the latest stages: out[0] empty octants, [1]
+ * analytic-cube list entries, [2] analytic-cube evaluations (entries x sinks, plus each
+ * group's surrounding cube x its sinks), [3] contrast M2P interactions of cells, [4] of
+ * empty octants, [5] matter M2P interactions.  HOT_EINVAL when background subtraction is
+ * off. */
+int hot_bg_sizes(hot_ctx *ctx, int64_t out[6]);
 
 /* Hash-table lookup of n cell keys (host arrays): idx[i] = cell index of
  * keys[i] or -1 when no such cell exists.  Synchronises. */
@@ -226,11 +280,11 @@ int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
  * frame -- frame[0..2] = per-axis minimum of the positions, frame[3] = L, their
  * largest extent (1 when all coincide) -- and rejects non-finite positions and
  * non-positive masses.  The paper has no counterpart; this entry point exists for
- * callers that must not allocate device memory: code running inside a stream that
- * is being captured into a CUDA graph, hosts that pre-allocate all device memory
- * up front (embedded or real-time loops, pools owned by another framework) and
- * must never see cudaMalloc, or allocators that are not reentrant from a
- * callback.  It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * callers that must not allocate device memory: hosts that hand out all device
+ * memory up front (embedded or real-time loops, memory pools owned by another
+ * framework) and must never see cudaMalloc, or code running where the allocator is
+ * not reentrant (for instance from inside an allocator callback).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its
  * scratch (one partial record per 16384 particles, the frame record and a status
  * word) is a fixed device array inside the library (about 200 KB, held by every
  * GPU that loads the library until the process exits).
@@ -239,7 +293,8 @@ int hot_lookup(hot_ctx *ctx, const uint64_t *keys, int64_t n, int32_t *idx);
  *   N     1 .. 2^26; larger N returns HOT_EOVERFLOW (the scratch holds at most
  *         4096 partial records)
  *   cuda_stream  a cudaStream_t (NULL = legacy default stream); the call
- *         synchronises it to read the input check.
+ *         synchronises it and copies the input check to host memory before it
+ *         returns.
  * The first call on a device looks up the scratch array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the one scratch array and it keeps the last call's

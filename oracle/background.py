@@ -212,8 +212,14 @@ class BackgroundTree:
         lo = self.centre[c] - self.side[c] * 0.5 + s * off
         return lo + 0.5 * s, s
 
-    def force(self, tol, G=1.0, eps=0.0):
+    def force(self, tol, G=1.0, eps=0.0, record=False):
+        """With record=True, self.lists holds per group the set of its interactions:
+        ("m", c) matter expansion, ("c", c) contrast expansion, ("e", c, o) empty octant o
+        of cell c expanded, ("p", c) leaf c particle by particle, ("b", c) leaf c's cube,
+        ("be", c, o) empty octant o of c as a cube; and self.surround[g] the cell of S."""
         p, rho = self.p, self.rho
+        self.lists = [] if record else None
+        self.surround = np.zeros(len(self.gcell), dtype=np.int64)
         n = len(self.mass)
         acc = np.zeros((n, 3))
         pot = np.zeros(n)
@@ -231,6 +237,10 @@ class BackgroundTree:
             for _ in range(self.up):
                 if S > 0:
                     S = int(self.parent[S])
+            self.surround[g] = S
+            rec = set()
+            if record:
+                self.lists.append(rec)
 
             def cube_field(z, s):
                 fa, fp = box_field(xs, z - 0.5 * s, z + 0.5 * s, -rho, G)
@@ -270,7 +280,9 @@ class BackgroundTree:
                     if contrast_ok(z, s, self._omitted(-cube_moments(s, p + 2, rho))):
                         expand(-cube_moments(s, p, rho), z)
                         cnt["m2p_empty"] += len(sinks)
+                        rec.add(("e", int(c), o))
                     else:
+                        rec.add(("be", int(c), o))
                         fa, fp = cube_field(z, s)
                         a[:] += fa
                         ph[:] += fp
@@ -283,6 +295,7 @@ class BackgroundTree:
                 if c <= gc < self.cend[c]:  # the group's cell or an ancestor: open
                     if leaf:
                         p2p(c)
+                        rec.add(("p", int(c)))
                     else:
                         stack.extend(self.children[c])
                         if not inside:
@@ -294,8 +307,10 @@ class BackgroundTree:
                     if d > b and mac_bound(d, b, self.B1[c], self.B2[c], p, G) <= tol:
                         expand(self.mom[c], self.com[c])
                         cnt["m2p_matter"] += len(sinks)
+                        rec.add(("m", int(c)))
                     elif leaf:
                         p2p(c)
+                        rec.add(("p", int(c)))
                     else:
                         stack.extend(self.children[c])
                     continue
@@ -303,8 +318,11 @@ class BackgroundTree:
                 if contrast_ok(z, s, self.cQ[c]):
                     expand(self.cmom[c], z)
                     cnt["m2p_contrast"] += len(sinks)
+                    rec.add(("c", int(c)))
                 elif leaf:
                     p2p(c)
+                    rec.add(("p", int(c)))
+                    rec.add(("b", int(c)))
                     fa, fp = cube_field(z, s)
                     a[:] += fa
                     ph[:] += fp

@@ -28,8 +28,11 @@ every order p = 0..6:
   by derivative-carrying Horner chains.
 * the moment-translation (M2M) pair tables and multi-index tables.
 
-The flop count of each ``m2p_eval<P>`` (FMA = 2, the rsqrt as 1) is emitted as
-``M2P_FLOPS[P]``; that is the convention used for the interaction roofline.
+``M2P_FLOPS[P]`` is a fixed roofline convention: the operation count (FMA = 2, the
+rsqrt as 1) of the first, explicit-monomial form of this routine.  The shipped Horner
+form does the same mathematics in fewer operations; ``m2p_source_flops(P)`` counts the
+arithmetic operators of the shipped statements (FMA = 2, rsqrt = 1), so both figures
+can be reported side by side.
 
 Run: python gen_kernels.py  (rewrites generated.cuh next to this file).
 """
@@ -90,6 +93,32 @@ def s_terms(p):
 # form of this routine, p = 0..8).  The Horner form below does the same mathematics with
 # fewer instructions; the convention stays fixed so that rates stay comparable.
 M2P_FLOP_CONVENTION = [32, 40, 82, 164, 307, 534, 874, 1358, 2023]
+
+
+def _count_ops(stmt):
+    """Arithmetic operations of one generated statement: every binary +, -, * and every
+    compound assignment counts 1 (so a multiply-add counts 2), hot_rsqrt counts 1; unary
+    minus and the coefficient references do not count."""
+    import re
+    t = re.sub(r"@[^@]*@", "c", stmt)
+    n = t.count("hot_rsqrt(")
+    for op in ("+=", "-=", "*="):
+        n += t.count(op)
+        t = t.replace(op, " = ")
+    prev = ""
+    for ch in t:
+        if ch in "*+-":
+            if not (ch == "-" and prev in "(=,"):
+                n += 1
+        if not ch.isspace():
+            prev = ch
+    return n
+
+
+def m2p_source_flops(p):
+    """Operation count of the shipped m2p_eval<p> statements (the Horner form), FMA = 2."""
+    L, _ = _eval_stmts(p)
+    return sum(_count_ops(st) for st in L)
 
 
 class _Prog:
@@ -449,13 +478,18 @@ def layout(p):
 
 
 def gen_eval(p):
-    """Two specialisations: float (float4 loads) and double (double2 loads)."""
+    """Two specialisations: float (float4 loads) and double (double2 loads).  The routine
+    proper, m2p_eval_s, takes R already scaled by the record's inv_s (R/s, which a caller
+    holding x and the scaled centre offset forms with one fused multiply-add per axis,
+    exactly: the scale is a power of two); m2p_eval scales R and calls it."""
     L, fl = _eval_stmts(p)
+    assert L[0] == "rx *= is; ry *= is; rz *= is;"
+    L = L[1:]
     slot = layout(p)
     out = []
     for T, VEC, VW, suf in (("float", "float4", 4, "f32"), ("double", "double2", 2, "f64")):
         comp = "xyzw"
-        code = [f"__device__ __forceinline__ void m2p_eval_{p}_{suf}(const {T}* __restrict__ c, {T} rx, {T} ry, "
+        code = [f"__device__ __forceinline__ void m2p_eval_s_{p}_{suf}(const {T}* __restrict__ c, {T} rx, {T} ry, "
                 f"{T} rz, {T}& phi, {T}& ax, {T}& ay, {T}& az) {{",
                 f"  using T = {T};",
                 f"  const {VEC}* __restrict__ cv = reinterpret_cast<const {VEC}*>(c);"]
@@ -479,6 +513,11 @@ def gen_eval(p):
                 need(g)
                 parts[i] = f"v{g}.{comp[sl % VW]}"
             code.append("  " + "".join(parts))
+        code.append("}")
+        code.append(f"__device__ __forceinline__ void m2p_eval_{p}_{suf}(const {T}* __restrict__ c, {T} rx, {T} ry, "
+                    f"{T} rz, {T}& phi, {T}& ax, {T}& ay, {T}& az) {{")
+        code.append(f"  const {T} is = c[0];")
+        code.append(f"  m2p_eval_s_{p}_{suf}(c, rx * is, ry * is, rz * is, phi, ax, ay, az);")
         code.append("}")
         out.append("\n".join(code))
     return "\n".join(out), len(s_terms(p)), fl
@@ -581,6 +620,8 @@ def main(out_path):
     for w_ in (tw, cw, aw):
         w_.append("}")
         parts.append("\n".join(w_))
+    es = ["template <int P, typename T> __device__ __forceinline__ void m2p_eval_s("
+          "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {"]
     ev = ["template <int P, typename T> __device__ __forceinline__ void m2p_eval("
           "const T* __restrict__ c, T rx, T ry, T rz, T& phi, T& ax, T& ay, T& az) {"]
     rc = ["template <int P, typename T> __device__ __forceinline__ void m2p_record("
@@ -590,9 +631,13 @@ def main(out_path):
         kw = "if" if p == 0 else "else if"
         ev.append(f"  {kw} constexpr (P == {p}) {{ if constexpr (sizeof(T) == 4) m2p_eval_{p}_f32(c, rx, ry, rz, phi, ax, ay, az); "
                   f"else m2p_eval_{p}_f64(c, rx, ry, rz, phi, ax, ay, az); }}")
+        es.append(f"  {kw} constexpr (P == {p}) {{ if constexpr (sizeof(T) == 4) m2p_eval_s_{p}_f32(c, rx, ry, rz, phi, ax, ay, "
+                  f"az); else m2p_eval_s_{p}_f64(c, rx, ry, rz, phi, ax, ay, az); }}")
         rc.append(f"  {kw} constexpr (P == {p}) m2p_record_{p}<T>(M, z, inv_s, G, eps, rec);")
     ev.append("}")
+    es.append("}")
     rc.append("}")
+    parts.append("\n".join(es))
     parts.append("\n".join(ev))
     parts.append("\n".join(rc))
     src = "\n".join(parts) + "\n"

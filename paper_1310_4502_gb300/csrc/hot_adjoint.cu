@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(AW * 32) k_adj_l2l(const int32_t *__restrict__
 // loads sinks of the batch).  Per item and leaf particle the sums
 //   gx = sum_i [u_i/s^3 - 3 d (d.u_i)/s^5 + v_i d/s^3],  gm = sum_i [u_i.d/s^3 - v_i/s]
 // (d = x_j - x_i, s^2 = |d|^2 + eps^2; with K1 smoothing f u_i + (f2 (d.u_i) + v_i f) d and
-// (d.u_i) f - v_i psi, the pair functions of k1_pair) go to row roff[leaf] + k n_leaf + j of part (k:
+// (d.u_i) f - v_i psi, the pair functions of k1_pair or spline_pair) go to row roff[leaf] + k n_leaf + j of part (k:
 // the item's rank within its leaf); k_adj_p2p_combine adds the items of each leaf in
 // order: dL/dx_j += G m_j gx, dL/dm_j += G gm.
 constexpr int PS = 128;
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
     const int wi = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t nitem = *nitem_p;
-    K1Const<T> kc{};
-    if constexpr (SOFT == HOT_SOFT_K1) kc = k1_const(eps2);
+    SoftConst<T> kc{};
+    if constexpr (SOFT != HOT_SOFT_PLUMMER) kc = soft_const(eps2);
     for (;;) {
         unsigned I0 = 0;
         if (lane == 0) I0 = atomicAdd(work, 1u);
@@ -395,10 +395,10 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                         for (int q = 0; q < 2; ++q) {
                             if (!val[q]) continue;
                             const T dx = xj[q][0] - sx, dy = xj[q][1] - sy, dz = xj[q][2] - sz;
-                            if constexpr (SOFT == HOT_SOFT_K1) {
+                            if constexpr (SOFT != HOT_SOFT_PLUMMER) {
                                 const T r2 = dx * dx + dy * dy + dz * dz;
                                 T f, f2, psi;
-                                k1_pair(r2, kc, f, f2, psi);
+                                compact_pair<SOFT>(r2, kc, f, f2, psi);
                                 if constexpr (CK) {
                                     const bool ok = (r2 > T(0) || kc.e2 > T(0)) && (id != (int32_t)slot[q]);
                                     f = ok ? f : T(0);
@@ -751,8 +751,9 @@ int adjoint_pt(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_p
             HOT_CK(cudaMemsetAsync(pwork, 0, sizeof(unsigned), s));
             T *pp = (T *)c->adj_pp.p;
             HOT_COUNT_LAUNCH();
-            auto p2p_src = c->prm.softening == HOT_SOFT_K1 ? k_adj_p2p_src<T, HOT_SOFT_K1>
-                                                           : k_adj_p2p_src<T, HOT_SOFT_PLUMMER>;
+            auto p2p_src = c->prm.softening == HOT_SOFT_K1       ? k_adj_p2p_src<T, HOT_SOFT_K1>
+                           : c->prm.softening == HOT_SOFT_SPLINE ? k_adj_p2p_src<T, HOT_SOFT_SPLINE>
+                                                                 : k_adj_p2p_src<T, HOT_SOFT_PLUMMER>;
             p2p_src<<<c->nsm * 8, AW * 32, 0, s>>>(c->it_off.p + nc, c->it_cell.p, c->it_a.p, c->it_b.p,
                                                    c->tp_val.p, c->gcell.p, c->cbegin.p, c->ccount.p, c->cend.p,
                                                    c->ccom.p, c->spos.p, c->smass.p, c->prel.p, c->adj_xhl.p, w,

@@ -29,13 +29,19 @@ int check_params(const hot_params *p)
     if (!(p->tol > 0.0) || !(p->eps >= 0.0) || !(p->G == p->G)) return HOT_EINVAL;
     if (p->leaf_max < 1 || p->group_max < 1 || p->leaf_max > 4096 || p->group_max > (1 << 20)) return HOT_EINVAL;
     if (p->precision != HOT_FP32_MIXED && p->precision != HOT_FP64) return HOT_EINVAL;
-    if (p->softening != HOT_SOFT_PLUMMER && p->softening != HOT_SOFT_K1) return HOT_EINVAL;
+    if (p->softening != HOT_SOFT_PLUMMER && p->softening != HOT_SOFT_K1 && p->softening != HOT_SOFT_SPLINE)
+        return HOT_EINVAL;
     if (p->p_min < -1 || p->p_min > p->p) return HOT_EINVAL;
     if (!(p->box >= 0.0) || !std::isfinite(p->box) || (p->box > 0.0 && (p->ws < 1 || p->ws > HOT_WS_MAX)))
         return HOT_EINVAL;
     if (p->box > 0.0 && !(std::isfinite(p->box_lo[0]) && std::isfinite(p->box_lo[1]) && std::isfinite(p->box_lo[2])))
         return HOT_EINVAL;
     if (p->box > 0.0 && p->p_min >= 0) return HOT_EINVAL;  // one or the other
+    if (p->background != 0 && p->background != 1) return HOT_EINVAL;
+    if (p->background &&
+        (p->bg_up < 0 || p->bg_up > HOT_MAXLEVEL || p->softening != HOT_SOFT_PLUMMER || p->box > 0.0 ||
+         p->p_min >= 0 || p->p > HOT_BG_PMAX))
+        return HOT_EINVAL;
     return HOT_OK;
 }
 
@@ -115,7 +121,8 @@ int hot_set_params(hot_ctx *c, const hot_params *prm)
     bool rebuild = prm->leaf_max != c->prm.leaf_max || prm->group_max != c->prm.group_max;
     bool remoment = prm->p != c->prm.p || prm->eps != c->prm.eps || prm->G != c->prm.G ||
                     prm->precision != c->prm.precision || prm->softening != c->prm.softening ||
-                    prm->p_min != c->prm.p_min || prm->box != c->prm.box || prm->ws != c->prm.ws;
+                    prm->p_min != c->prm.p_min || prm->box != c->prm.box || prm->ws != c->prm.ws ||
+                    prm->background != c->prm.background;
     c->prm = *prm;
     if (rebuild) c->stage = 0;
     else if (remoment && c->stage > 1) c->stage = 1;
@@ -158,6 +165,7 @@ int hot_evaluate_forces(hot_ctx *c, double *acc, double *pot)
 int hot_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_pos, double *g_mass)
 {
     if (!c || !g_acc || !g_pos || !g_mass) return HOT_EINVAL;
+    if (c->prm.background) return HOT_EINVAL;  // its frozen-list passes carry no contrast or cube terms
     if (c->stage < 3) return HOT_ESTATE;
     return hot_impl_adjoint(c, g_acc, g_pot, g_pos, g_mass);
 }
@@ -170,6 +178,19 @@ int hot_stage_times(hot_ctx *c, float ms[6])
         ms[k] = 0.f;
         if (c->ev_used[k]) cudaEventElapsedTime(&ms[k], c->ev[2 * k], c->ev[2 * k + 1]);
     }
+    return HOT_OK;
+}
+
+int hot_bg_sizes(hot_ctx *c, int64_t out[6])
+{
+    if (!c || !out) return HOT_EINVAL;
+    if (!c->prm.background) return HOT_EINVAL;
+    out[0] = c->n_empty;
+    out[1] = c->n_box;
+    out[2] = c->n_box_eval;
+    out[3] = c->n_m2p_con;
+    out[4] = c->n_m2p_emp;
+    out[5] = c->n_m2p_int - c->n_m2p_con - c->n_m2p_emp;
     return HOT_OK;
 }
 
@@ -223,6 +244,14 @@ int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
         case HOT_DBG_M2P_ORDERS: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
         case HOT_DBG_M2P_IMAGES: src = c->l_m2p.p; need = c->n_m2p * sizeof(int32_t); min_stage = 3; break;
         case HOT_DBG_P2P_IMAGES: src = c->l_p2p.p; need = c->n_p2p * sizeof(int32_t); min_stage = 3; break;
+        case HOT_DBG_BG_CUBE_OFFSETS:
+            src = c->off_box.p; need = (ng + 1) * sizeof(int64_t); min_stage = c->prm.background ? 3 : 99; break;
+        case HOT_DBG_BG_CUBES: src = c->l_box.p; need = c->n_box * sizeof(int32_t); min_stage = c->prm.background ? 3 : 99; break;
+        case HOT_DBG_BG_GROUP_S: src = c->bg_gS.p; need = ng * sizeof(int32_t); min_stage = c->prm.background ? 3 : 99; break;
+        case HOT_DBG_BG_EMPTY_PARENT:
+            src = c->bg_eparent.p; need = c->n_empty * sizeof(int32_t); min_stage = c->prm.background ? 2 : 99; break;
+        case HOT_DBG_BG_EMPTY_OCTANT:
+            src = c->bg_eoct.p; need = c->n_empty * sizeof(int32_t); min_stage = c->prm.background ? 2 : 99; break;
         default: return HOT_EINVAL;
     }
     if (c->stage < min_stage) return HOT_ESTATE;
@@ -323,6 +352,10 @@ void hot_destroy(hot_ctx *c)
     cudaStream_t s = c->st;
     c->part.release(s); c->frame.release(s); c->key.release(s); c->key2.release(s); c->idx.release(s);
     c->idx2.release(s); c->hist.release(s); c->histoff.release(s); c->scan_tmp.release(s); c->spos.release(s);
+    c->rs_bhist.release(s); c->rs_goff.release(s); c->rs_ctr.release(s); c->rs_status.release(s);
+    c->bg_cen.release(s); c->bg_half.release(s); c->bg_q.release(s); c->bg_mom.release(s); c->bg_rho.release(s);
+    c->bg_ecnt.release(s); c->bg_eoff.release(s); c->bg_eparent.release(s); c->bg_eoct.release(s);
+    c->bg_tc.release(s); c->cnt_box.release(s); c->off_box.release(s); c->l_box.release(s); c->bg_gS.release(s);
     c->smass.release(s); c->lcp.release(s); c->leaflev.release(s); c->ncell_i.release(s); c->cell_off.release(s);
     c->ckey.release(s); c->clevel.release(s); c->cbegin.release(s); c->ccount.release(s); c->cparent.release(s);
     c->cend.release(s); c->child8.release(s); c->cnchild.release(s); c->level_cells.release(s);

@@ -109,22 +109,11 @@ __device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
     return c > 2097151ull ? 2097151ull : c;
 }
 
-__global__ void k_keys(const double *__restrict__ pos, int64_t N, const double *__restrict__ frame,
-                       uint64_t *__restrict__ key, uint32_t *__restrict__ idx)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double s = frame[4];
-    uint64_t cx = icoord(pos[3 * i + 0], frame[0], s);
-    uint64_t cy = icoord(pos[3 * i + 1], frame[1], s);
-    uint64_t cz = icoord(pos[3 * i + 2], frame[2], s);
-    key[i] = (1ull << 63) | (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
-    idx[i] = (uint32_t)i;
-}
-
 // ---------------------------------------------------------------------------
-// LSD radix sort of (key, index), 8-bit digits.  Stable: inside a tile the rank
-// of a key is (warp, round, lane) order, i.e. input order.
+// LSD radix sort of (key, value) pairs by their low bits, 8-bit digits, used to transpose
+// interaction lists (hot_sort_pairs): a histogram launch, a scan and a scatter launch per
+// pass.  Stable: inside a tile the rank of a key is (warp, round, lane) order, i.e. input
+// order.
 // ---------------------------------------------------------------------------
 constexpr int RS_W = 8;          // warps per block
 constexpr int RS_R = 16;         // rounds of 32 keys per warp
@@ -200,6 +189,190 @@ __global__ void __launch_bounds__(RS_W * 32) k_rs_scatter(
             kout[p] = kk[r];
             vout[p] = vv[r];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The particle keys' sort: eight LSD passes of 8 bits, one launch each.
+//   * k_keys_hist computes the keys and, in the same pass, the digit histograms of all
+//     eight passes (one per block, warp-aggregated with __match_any_sync);
+//   * k_rs_goff reduces the block histograms and scans them into each pass's global
+//     digit offsets;
+//   * k_rs_pass ranks a tile of OS_TILE keys by digit in shared memory (stable: warp w
+//     holds the tile's w-th run of OS_R * 32 consecutive keys, ranked round by round in
+//     lane order), publishes the tile's digit counts, and finds how many keys of each
+//     digit the earlier tiles hold by a decoupled look-back over their published counts
+//     (a tile publishes its own counts before it looks back, and tiles are numbered in
+//     the order their blocks start, so every wait ends); it then writes its keys in
+//     digit order, so that each digit's run leaves as contiguous stores.
+// A published word is epoch << 40 | flag << 38 | count: flag 1 = this tile's count, 2 =
+// the count of this tile and all before it; a word of another epoch is not yet written.
+// ---------------------------------------------------------------------------
+constexpr int OS_W = 8;                   // warps per block
+constexpr int OS_R = 16;                  // keys per lane
+constexpr int OS_TILE = OS_W * OS_R * 32;  // keys per tile
+constexpr int OS_SMEM = OS_W * 256 * 4 + OS_TILE * 8 + OS_TILE * 4 + 2 * 256 * 4;
+constexpr unsigned long long OS_FLAG_AGG = 1ull, OS_FLAG_INC = 2ull;
+constexpr long OS_POLL_LIMIT = 1l << 20;  // polls of one published word before giving up
+
+__device__ __forceinline__ unsigned long long os_pack(uint32_t epoch, unsigned long long flag, uint64_t cnt)
+{
+    return ((unsigned long long)epoch << 40) | (flag << 38) | cnt;
+}
+
+__global__ void __launch_bounds__(256) k_keys_hist(const double *__restrict__ pos, int64_t N,
+                                                   const double *__restrict__ frame, uint64_t *__restrict__ key,
+                                                   uint32_t *__restrict__ idx, uint32_t *__restrict__ bhist)
+{
+    __shared__ uint32_t h[8][256];
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) h[k >> 8][k & 255] = 0;
+    __syncthreads();
+    const double s = frame[4], lx = frame[0], ly = frame[1], lz = frame[2];
+    const unsigned lane = lane_id();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < N; w0 += nw * 32) {
+        const int64_t i = w0 + lane;
+        const bool valid = i < N;
+        uint64_t k = 0;
+        if (valid) {
+            const uint64_t cx = icoord(pos[3 * i + 0], lx, s);
+            const uint64_t cy = icoord(pos[3 * i + 1], ly, s);
+            const uint64_t cz = icoord(pos[3 * i + 2], lz, s);
+            k = (1ull << 63) | (spread3(cx) << 2) | (spread3(cy) << 1) | spread3(cz);
+            key[i] = k;
+            idx[i] = (uint32_t)i;
+        }
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const unsigned d = valid ? (unsigned)(k >> (8 * p)) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[p][d], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) bhist[(int64_t)blockIdx.x * 2048 + k] = h[k >> 8][k & 255];
+}
+
+// Block p: digit totals of pass p over the nb block histograms, scanned into goff[p][d].
+__global__ void __launch_bounds__(256) k_rs_goff(const uint32_t *__restrict__ bhist, int nb,
+                                                 uint32_t *__restrict__ goff)
+{
+    __shared__ uint32_t ws[8];
+    const int p = blockIdx.x, d = threadIdx.x;
+    uint32_t t = 0;
+    for (int b = 0; b < nb; ++b) t += bhist[(int64_t)b * 2048 + p * 256 + d];
+    const uint32_t inc = warp_incl_scan(t);
+    if (lane_id() == 31) ws[d >> 5] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < (d >> 5); ++w) base += ws[w];
+    goff[p * 256 + d] = base + inc - t;
+}
+
+__global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t N, int shift, const uint32_t *__restrict__ goff, uint32_t *tile_ctr,
+    unsigned long long *pub, uint32_t epoch, unsigned *status)
+{
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    uint64_t *sk = (uint64_t *)os_smem;                                 // [OS_TILE]
+    uint32_t *sv = (uint32_t *)(sk + OS_TILE);                          // [OS_TILE]
+    uint32_t(*wcnt)[256] = (uint32_t(*)[256])(sv + OS_TILE);            // [OS_W][256]
+    uint32_t *toff = (uint32_t *)(wcnt + OS_W);                         // [256] tile-local digit offsets
+    uint32_t *gbase = toff + 256;                                       // [256] global first slot
+    __shared__ uint32_t s_tile, ws[OS_W];
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int k = lane; k < 256; k += 32) wcnt[w][k] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * OS_TILE + (int64_t)w * (OS_R * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t kk[OS_R];
+    uint32_t vv[OS_R];
+    uint32_t rk[OS_R];
+#pragma unroll
+    for (int r = 0; r < OS_R; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < N;
+        const uint64_t k = valid ? kin[i] : 0ull;
+        const uint32_t v = valid ? vin[i] : 0u;
+        const unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned rank = __popc(peers & lt);
+        const uint32_t b = valid ? wcnt[w][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][d] = b + __popc(peers);
+        __syncwarp();
+        kk[r] = k;
+        vv[r] = v;
+        rk[r] = valid ? b + rank : 0xffffffffu;
+    }
+    __syncthreads();
+    // thread d: per-warp offsets of digit d within the tile, and the tile's count of d
+    const unsigned d = threadIdx.x;
+    uint32_t tot = 0;
+    for (int ww = 0; ww < OS_W; ++ww) {
+        const uint32_t c = wcnt[ww][d];
+        wcnt[ww][d] = tot;
+        tot += c;
+    }
+    unsigned long long *my = pub + tile * 256 + d;
+    if (tile == 0) {
+        atomicExch(my, os_pack(epoch, OS_FLAG_INC, tot));
+        gbase[d] = goff[d];
+    } else {
+        atomicExch(my, os_pack(epoch, OS_FLAG_AGG, tot));
+        uint64_t excl = 0;
+        int64_t t = tile - 1;
+        long polls = 0;
+        for (;;) {
+            const unsigned long long v = *((volatile unsigned long long *)(pub + t * 256 + d));
+            if ((uint32_t)(v >> 40) == epoch) {
+                excl += v & ((1ull << 38) - 1ull);
+                if (((v >> 38) & 3ull) == OS_FLAG_INC || t == 0) break;
+                --t;
+                continue;
+            }
+            if (++polls > OS_POLL_LIMIT) {
+                hot_flag(status, HOT_ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        atomicExch(my, os_pack(epoch, OS_FLAG_INC, excl + tot));
+        gbase[d] = goff[d] + (uint32_t)excl;
+    }
+    // tile-local exclusive scan of the digit counts
+    const uint32_t inc = warp_incl_scan(tot);
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int ww = 0; ww < w; ++ww) off += ws[ww];
+    toff[d] = off + inc - tot;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < OS_R; ++r) {
+        if (rk[r] == 0xffffffffu) continue;
+        const unsigned dd = (unsigned)(kk[r] >> shift) & 255u;
+        const uint32_t lp = toff[dd] + wcnt[w][dd] + rk[r];
+        sk[lp] = kk[r];
+        sv[lp] = vv[r];
+    }
+    __syncthreads();
+    const int64_t t0 = tile * OS_TILE;
+    const int n = (int)(N - t0 < OS_TILE ? N - t0 : OS_TILE);
+    for (int i = threadIdx.x; i < n; i += OS_W * 32) {
+        const uint64_t k = sk[i];
+        const unsigned dd = (unsigned)(k >> shift) & 255u;
+        const int64_t dst = (int64_t)gbase[dd] + (i - (int64_t)toff[dd]);
+        if (dst < 0 || dst >= N) {  // only after a look-back gave up: never store out of range
+            hot_flag(status, HOT_ST_INTERNAL);
+            continue;
+        }
+        kout[dst] = k;
+        vout[dst] = sv[i];
     }
 }
 
@@ -525,23 +698,34 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     k_bbox_part<<<nbb, BT, 0, s>>>(pos, mass, N, c->part.p, c->d_status);
     HOT_COUNT_LAUNCH();
     k_bbox_final<<<1, 32, 0, s>>>(c->part.p, nbb, c->frame.p);
+    // keys with the digit histograms of every pass, then the passes' global offsets
+    const int nkb = c->nsm * 4;
+    const int64_t ntiles = (N + OS_TILE - 1) / OS_TILE;
+    HOT_CK(c->rs_bhist.ensure(2048 * (size_t)nkb, s));
+    HOT_CK(c->rs_goff.ensure(2048, s));
+    HOT_CK(c->rs_ctr.ensure(8, s));
+    {
+        unsigned long long *old = c->rs_status.p;
+        HOT_CK(c->rs_status.ensure(256 * (size_t)ntiles, s));
+        if (c->rs_status.p != old || c->rs_epoch + 8 >= (1u << 24)) {
+            // fresh memory, or the epoch counter about to wrap: no word of any epoch
+            HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(unsigned long long) * c->rs_status.cap, s));
+            c->rs_epoch = 0;
+        }
+    }
+    HOT_CK(cudaMemsetAsync(c->rs_ctr.p, 0, 8 * sizeof(uint32_t), s));
     HOT_COUNT_LAUNCH();
-    k_keys<<<hot_blocks(N, BT), BT, 0, s>>>(pos, N, c->frame.p, c->key.p, c->idx.p);
-    // radix sort, 8 passes of 8 bits
-    int64_t ntiles = (N + RS_TILE - 1) / RS_TILE;
-    HOT_CK(c->hist.ensure(256 * (size_t)ntiles + 1, s));
-    HOT_CK(c->histoff.ensure(256 * (size_t)ntiles + 1, s));
-    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(N + 256 * ntiles + 64), s));
+    k_keys_hist<<<nkb, 256, 0, s>>>(pos, N, c->frame.p, c->key.p, c->idx.p, c->rs_bhist.p);
+    HOT_COUNT_LAUNCH();
+    k_rs_goff<<<8, 256, 0, s>>>(c->rs_bhist.p, nkb, c->rs_goff.p);
+    HOT_CK(cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, OS_SMEM));
     uint64_t *ka = c->key.p, *kb = c->key2.p;
     uint32_t *va = c->idx.p, *vb = c->idx2.p;
     for (int pass = 0; pass < 8; ++pass) {
-        int shift = 8 * pass;
         HOT_COUNT_LAUNCH();
-        k_rs_hist<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, N, shift, c->hist.p, ntiles);
-        int r = hot_scan_u32_to_u32(c->hist.p, c->histoff.p, 256 * ntiles, c->scan_tmp.p, s);
-        if (r) return r;
-        HOT_COUNT_LAUNCH();
-        k_rs_scatter<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, va, kb, vb, N, shift, c->histoff.p, ntiles);
+        k_rs_pass<<<(unsigned)ntiles, OS_W * 32, OS_SMEM, s>>>(ka, va, kb, vb, N, 8 * pass, c->rs_goff.p + 256 * pass,
+                                                               c->rs_ctr.p + pass, c->rs_status.p, ++c->rs_epoch,
+                                                               c->d_status);
         uint64_t *tk = ka;
         ka = kb;
         kb = tk;
@@ -549,6 +733,8 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
         va = vb;
         vb = tv;
     }
+    HOT_CK(cudaGetLastError());
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(N + 64), s));
     // 8 passes: sorted data is back in key/idx
     HOT_CK(c->spos.ensure(3 * (size_t)N, s));
     HOT_CK(c->smass.ensure(N, s));
@@ -723,10 +909,14 @@ extern "C" int hot_key_frame_noalloc(const double *pos, const double *mass, int6
     const int nb = (int)((N + NOALLOC_PER_BLOCK - 1) / NOALLOC_PER_BLOCK);
     // the status word keeps the previous call's value: clear it
     if (cudaMemsetAsync(status, 0, sizeof(unsigned), s) != cudaSuccess) return HOT_ECUDA;
+    // A rejected launch would leave the previous call's frame in the scratch array, so
+    // each launch is checked before that record is copied out.
     HOT_COUNT_LAUNCH();
     k_bbox_part<<<nb, BT, 0, s>>>(pos, mass, N, part, status);
+    if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     HOT_COUNT_LAUNCH();
     k_bbox_final<<<1, 32, 0, s>>>(part, nb, fr);
+    if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     if (cudaMemcpyAsync(frame, fr, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return HOT_ECUDA;
     unsigned bits = 0;

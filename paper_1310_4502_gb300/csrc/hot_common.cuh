@@ -33,6 +33,7 @@
 #define HOT_IMG_CELL_MASK ((1u << HOT_IMG_SHIFT) - 1u)
 #define HOT_WS_MAX 2  // (2 ws + 1)^3 images in the 8 bits above HOT_IMG_SHIFT
 #define HOT_PFAR 8    // order of the far images' local expansion
+#define HOT_BG_PMAX 6 // largest order under background subtraction (its moments go to p + 2)
 
 // Device memory the one-pass traversal may hold in per-group list slots (bytes).
 #define HOT_SLOT_BUDGET (16.0 * 1024 * 1024 * 1024)
@@ -113,6 +114,12 @@ struct hot_ctx {
     DBuf<uint32_t> idx, idx2;
     DBuf<uint32_t> hist, histoff;
     DBuf<uint64_t> scan_tmp;
+    // one-launch-per-pass radix sort of the keys: per-block digit histograms of all eight
+    // passes, the passes' global digit offsets, tile counters, and the tiles' published
+    // digit counts (epoch-tagged, so that no pass needs them cleared)
+    DBuf<uint32_t> rs_bhist, rs_goff, rs_ctr;
+    DBuf<unsigned long long> rs_status;
+    uint32_t rs_epoch = 0;
     DBuf<double> spos, smass;  // sorted copies [N][3], [N]
 
     // tree
@@ -156,6 +163,22 @@ struct hot_ctx {
     double per_D_L = 0.0;
     int per_D_ws = 0;
     DBuf<double> per_D, per_part, per_coef;
+
+    // background subtraction: the cubes are the cells [0, C) and the empty octants of the
+    // inner cells [C, C + E) (octants that hold no particle, absent from the tree); their
+    // centres and half sides, the contrast's Q_{p+1}, Q_{p+2}, the empty octants' parents
+    // and octant numbers, the cells' moments about their cube centres to order p + 2 (then
+    // their contrast), the mean density, and per tolerance each cube's acceptance record
+    int64_t n_empty = 0;
+    DBuf<double> bg_cen, bg_half, bg_q, bg_mom, bg_rho;
+    DBuf<uint32_t> bg_ecnt, bg_eoff;
+    DBuf<int32_t> bg_eparent, bg_eoct;
+    DBuf<TCell> bg_tc;
+    // per group: the analytic-cube list (cube indices) and the surrounding cube S
+    DBuf<uint32_t> cnt_box;
+    DBuf<int64_t> off_box;
+    DBuf<int32_t> l_box, bg_gS;
+    int64_t n_box = 0, n_box_eval = 0, n_m2p_con = 0, n_m2p_emp = 0;
 
     // lists
     double tol_lists = 0;
@@ -254,6 +277,7 @@ int hot_impl_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, doubl
                      double *g_mass);
 int hot_impl_adjoint_sink(hot_ctx *c, const void *wsink, double *gsink, cudaStream_t s);
 int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, int64_t n, int bits);
+int hot_impl_bg_box(hot_ctx *c, double *acc, double *pot);
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -330,14 +354,14 @@ __device__ __forceinline__ void hot_flag(unsigned *status, unsigned bit) { atomi
 //   f eps^3 = 1 + 3/2 t + 135/16 t^2,  f2 eps^5 = -(3 + 135/4 t),
 //   psi eps = 1 + t/2 + 3/8 t^2 + 45/32 t^3.
 template <class T>
-struct K1Const {
+struct SoftConst {
     T e2, ie2, ie, ie3, ie5;  // eps^2, 1/eps^2, 1/eps, 1/eps^3, 1/eps^5
 };
 
 template <class T>
-__device__ __forceinline__ K1Const<T> k1_const(T eps2)
+__device__ __forceinline__ SoftConst<T> soft_const(T eps2)
 {
-    K1Const<T> k;
+    SoftConst<T> k;
     k.e2 = eps2;
     k.ie2 = T(1) / eps2;
     k.ie = T(1) / sqrt(eps2);  // correctly rounded: a common factor of every inside pair
@@ -347,7 +371,7 @@ __device__ __forceinline__ K1Const<T> k1_const(T eps2)
 }
 
 template <class T>
-__device__ __forceinline__ void k1_pair(T r2, const K1Const<T> &k, T &f, T &f2, T &psi)
+__device__ __forceinline__ void k1_pair(T r2, const SoftConst<T> &k, T &f, T &f2, T &psi)
 {
     const bool in = r2 < k.e2;
     const T ri = hot_rsqrt(in ? k.e2 : r2);
@@ -359,6 +383,54 @@ __device__ __forceinline__ void k1_pair(T r2, const K1Const<T> &k, T &f, T &f2, 
     f = in ? fin : ri2 * ri;
     f2 = in ? f2in : T(-3) * ri2 * ri2 * ri;
     psi = in ? pin : ri;
+}
+
+// Cubic spline force smoothing of support eps (Sec. "Force Smoothing", the kernel of the
+// cited SPH code): the unit-mass density 8/(pi eps^3) w(x), x = r/eps, w = 1 - 6x^2 + 6x^3
+// for x < 1/2 and 2(1 - x)^3 for 1/2 <= x < 1, zero beyond.  Same pair functions as
+// k1_pair (a = G m f d, phi = -G m psi, f2 = 2 df/d(r^2)).  With M(x) the enclosed mass:
+//   x < 1/2:  f eps^3 = 32/3 - 192/5 x^2 + 32 x^3,  f2 eps^5 = -384/5 + 96 x,
+//             psi eps = 14/5 - 16/3 x^2 + 48/5 x^4 - 32/5 x^5;
+//   x >= 1/2, t = 1 - x (M = 1 - 16 t^4 + 128/5 t^5 - 32/3 t^6, from integrating the
+//   density 16/pi t^3 inwards from the edge, where M = 1):
+//             f = M / r^3,  f2 = 64 t^3 / (eps^3 r^2) - 3 M / r^5   (dM/dx = 64 x^2 t^3),
+//             psi = M / r + (16 t^4 - 64/5 t^5) / eps   (psi - M/r has derivative
+//             -dM/dx /(eps r) in r and vanishes at the edge);
+// Newtonian for r >= eps.  The outer branch is written in t so that its float32 terms do
+// not cancel near the edge, where the expanded powers of x sum terms of size 48 to 1.
+template <class T>
+__device__ __forceinline__ void spline_pair(T r2, const SoftConst<T> &k, T &f, T &f2, T &psi)
+{
+    const bool in = r2 < k.e2;
+    const T ri = hot_rsqrt(r2 > T(0) ? r2 : k.e2);  // r2 = 0 only reaches the inner branch
+    const T ri2 = ri * ri;
+    const T ri3 = ri2 * ri;
+    const T x = r2 * ri * k.ie;  // r / eps (0 at r = 0)
+    const T x2 = x * x;
+    const T gi = T(32.0 / 3.0) + x2 * (T(-192.0 / 5.0) + T(32) * x);
+    const T f2i = T(-384.0 / 5.0) + T(96) * x;
+    const T pi_ = T(14.0 / 5.0) + x2 * (T(-16.0 / 3.0) + x2 * (T(48.0 / 5.0) - T(32.0 / 5.0) * x));
+    const T t = T(1) - x;
+    const T t3 = t * t * t;
+    const T t4 = t3 * t;
+    const T mo = T(1) - t4 * (T(16) - t * (T(128.0 / 5.0) - T(32.0 / 3.0) * t));
+    const T fo = mo * ri3;
+    const T f2o = T(64) * t3 * ri2 * k.ie3 - T(3) * mo * ri3 * ri2;
+    const T po = mo * ri + t4 * (T(16) - T(64.0 / 5.0) * t) * k.ie;
+    const bool inner = x < T(0.5);
+    f = in ? (inner ? gi * k.ie3 : fo) : ri3;
+    f2 = in ? (inner ? f2i * k.ie5 : f2o) : T(-3) * ri2 * ri3;
+    psi = in ? (inner ? pi_ * k.ie : po) : ri;
+}
+
+// The pair functions of a kernel of compact support (K1 or the cubic spline).
+template <int SOFT, class T>
+__device__ __forceinline__ void compact_pair(T r2, const SoftConst<T> &k, T &f, T &f2, T &psi)
+{
+    if constexpr (SOFT == HOT_SOFT_SPLINE)
+        spline_pair(r2, k, f, f2, psi);
+    else
+        k1_pair(r2, k, f, f2, psi);
 }
 
 #endif  // __CUDACC__

@@ -11,6 +11,8 @@ int launch_interact(hot_ctx *c, cudaStream_t s, int cls, unsigned *work, double 
 {
     if (c->prm.softening == HOT_SOFT_K1)
         return launch_interact_s<P, T, NS, MODE, HOT_SOFT_K1>(c, s, cls, work, acc, pot, wsink, gsink);
+    if (c->prm.softening == HOT_SOFT_SPLINE)
+        return launch_interact_s<P, T, NS, MODE, HOT_SOFT_SPLINE>(c, s, cls, work, acc, pot, wsink, gsink);
     return launch_interact_s<P, T, NS, MODE, HOT_SOFT_PLUMMER>(c, s, cls, work, acc, pot, wsink, gsink);
 }
 
@@ -60,8 +62,11 @@ int hot_impl_forces(hot_ctx *c, double *acc, double *pot)
         case 8: r = forces_p<8>(c, acc, pot); break;
         default: return HOT_ESTATE;
     }
-    // periodic boundaries: the far images' local expansion, added to the tree's forces
+    // periodic boundaries: the far images' local expansion, added to the tree's forces;
+    // background subtraction: the analytic fields of the groups' cube lists and
+    // surrounding cubes
     if (!r) r = hot_impl_far_field(c, acc, pot);
+    if (!r && c->prm.background) r = hot_impl_bg_box(c, acc, pot);
     hot_toc(c, 4);
     return r;
 }

@@ -69,14 +69,15 @@ struct RecTab {
 
 // The order-q expansion, q <= Q chosen at run time (uniform over the warp except when a
 // slice's lanes split the list).
+// (R scaled by the record's inv_s, as m2p_eval_s takes it.)
 template <int Q, class T>
 __device__ __forceinline__ void m2p_eval_order(int q, const T *r, T rx, T ry, T rz, T &ph, T &ax, T &ay, T &az)
 {
     if constexpr (Q == 0) {
-        m2p_eval<0, T>(r, rx, ry, rz, ph, ax, ay, az);
+        m2p_eval_s<0, T>(r, rx, ry, rz, ph, ax, ay, az);
     } else {
         if (q == Q)
-            m2p_eval<Q, T>(r, rx, ry, rz, ph, ax, ay, az);
+            m2p_eval_s<Q, T>(r, rx, ry, rz, ph, ax, ay, az);
         else
             m2p_eval_order<Q - 1, T>(q, r, rx, ry, rz, ph, ax, ay, az);
     }
@@ -284,12 +285,23 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 oy += sy;
                 oz += sz;
             }
+            // forces: the offset scaled by the record's inv_s (a power of two), negated, with
+            // inv_s beside it, so that each evaluation forms (x - o) inv_s = fma(x, inv_s,
+            // -o inv_s) exactly; the adjoint's tangent routine takes the offset as it is
+            T is = T(1);
+            if constexpr (MODE == 0) {
+                is = sm.rec[b][lane][0];
+                ox = -ox * is;
+                oy = -oy * is;
+                oz = -oz * is;
+            }
             if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<float4 *>(&sm.off[b][lane][0]) = make_float4(ox, oy, oz, 0.f);
+                *reinterpret_cast<float4 *>(&sm.off[b][lane][0]) = make_float4(ox, oy, oz, is);
             } else {
                 sm.off[b][lane][0] = ox;
                 sm.off[b][lane][1] = oy;
                 sm.off[b][lane][2] = oz;
+                sm.off[b][lane][3] = is;
             }
         }
         __syncwarp();
@@ -299,14 +311,15 @@ __device__ __forceinline__ bool m2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             for (int s = 0; s < NS; ++s) ph[s] = ax[s] = ay[s] = az[s] = dx[s] = dy[s] = dz[s] = T(0);
             for (int k = sj; k < ne; k += nsplit) {
                 const T *r = &sm.rec[b][k][0];
-                const T ox = sm.off[b][k][0], oy = sm.off[b][k][1], oz = sm.off[b][k][2];
+                const T ox = sm.off[b][k][0], oy = sm.off[b][k][1], oz = sm.off[b][k][2], is = sm.off[b][k][3];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     if constexpr (VQ)
-                        m2p_eval_order<P, T>(sm.qo[b][k], r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, ph[s], ax[s],
-                                             ay[s], az[s]);
+                        m2p_eval_order<P, T>(sm.qo[b][k], r, fma(x[s][0], is, ox), fma(x[s][1], is, oy),
+                                             fma(x[s][2], is, oz), ph[s], ax[s], ay[s], az[s]);
                     else if constexpr (MODE == 0)
-                        m2p_eval<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, ph[s], ax[s], ay[s], az[s]);
+                        m2p_eval_s<P, T>(r, fma(x[s][0], is, ox), fma(x[s][1], is, oy), fma(x[s][2], is, oz), ph[s],
+                                         ax[s], ay[s], az[s]);
                     else
                         m2p_tangent<P, T>(r, x[s][0] - ox, x[s][1] - oy, x[s][2] - oz, wt[s][0], wt[s][1], wt[s][2],
                                           ph[s], ax[s], ay[s], az[s], dx[s], dy[s], dz[s]);
@@ -340,8 +353,8 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
     constexpr int RL = Cfg<P, T>::RL;
     const unsigned lane = lane_id();
     int fill = 0;
-    K1Const<T> kc{};
-    if constexpr (SOFT == HOT_SOFT_K1) kc = k1_const(eps2);
+    SoftConst<T> kc{};
+    if constexpr (SOFT != HOT_SOFT_PLUMMER) kc = soft_const(eps2);
     // A sink can meet itself, or a source at zero separation, only in a batch holding one
     // of the group's own leaves or when eps = 0; other batches take the loop without the
     // per-pair tests.
@@ -362,11 +375,11 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     const T dx = sx - x[s][0], dy = sy - x[s][1], dz = sz - x[s][2];
-                    if constexpr (SOFT == HOT_SOFT_K1) {
+                    if constexpr (SOFT != HOT_SOFT_PLUMMER) {
                         // K1: eps2 is the support squared, not added to the separation
                         const T r2 = dx * dx + dy * dy + dz * dz;
                         T f, f2, psi;
-                        k1_pair(r2, kc, f, f2, psi);
+                        compact_pair<SOFT>(r2, kc, f, f2, psi);
                         if constexpr (CK) {
                             const bool ok = (r2 > T(0) || kc.e2 > T(0)) && (id != self[s]);
                             f = ok ? f : T(0);
@@ -389,7 +402,8 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                             az[s] += cc * dz;
                         }
                     } else {
-                    const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+                    // from eps^2 up: three fused multiply-adds
+                    const T r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
                     T rinv;
                     if constexpr (CK) {
                         const bool ok = (r2 > T(0)) && (id != self[s]);

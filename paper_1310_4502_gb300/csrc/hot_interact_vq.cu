@@ -12,6 +12,8 @@ int forces_vq_t(hot_ctx *c, double *acc, double *pot)
     unsigned *work = (unsigned *)(c->sizes.p + 56);
     if (c->prm.softening == HOT_SOFT_K1)
         return launch_interact_s<P, T, 1, 0, HOT_SOFT_K1, true>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
+    if (c->prm.softening == HOT_SOFT_SPLINE)
+        return launch_interact_s<P, T, 1, 0, HOT_SOFT_SPLINE, true>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
     return launch_interact_s<P, T, 1, 0, HOT_SOFT_PLUMMER, true>(c, c->st, 0, work, acc, pot, nullptr, nullptr);
 }
 

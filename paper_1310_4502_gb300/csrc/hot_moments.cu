@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
 //   T1(i,j,k) = sum_{i' <= i} C(i,i') dx^{i-i'} M(i',j,k),  then likewise in j and in k,
 // at most p+1 terms per component and pass, each one fused multiply-add with the
 // factor C(e,e') d^{e-e'} taken from a per-child table (float64 throughout).
+// CUBE: the moments are about the cells' cube centres cen (background subtraction), which
+// are fixed, so nothing but the moments is written.
 // ---------------------------------------------------------------------------
 constexpr int M2M_W = 8;  // warps per block: one per child octant
 
@@ -137,7 +139,7 @@ __device__ __forceinline__ int mom_index(int i, int j, int k)
     return n * (n + 1) * (n + 2) / 6 + (n - i) * (n - i + 1) / 2 + (n - i - j);
 }
 
-template <int P>
+template <int P, bool CUBE = false>
 __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
     const int32_t *__restrict__ cells, int64_t ncells_lvl, const int32_t *__restrict__ child8,
     const int32_t *__restrict__ cnchild, double *__restrict__ cmass, double *__restrict__ ccom,
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
             const int32_t k = child8[8 * (int64_t)c + threadIdx.x];
             sch[threadIdx.x] = k;
             if (k >= 0) {
-                smc[threadIdx.x][0] = cmass[k];
+                smc[threadIdx.x][0] = CUBE ? 0.0 : cmass[k];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) smc[threadIdx.x][1 + d] = ccom[3 * (int64_t)k + d];
             }
@@ -193,7 +195,11 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
                 mz += mc * smc[q][3];
             }
         }
-        const double z[3] = {mx / m, my / m, mz / m};
+        double z[3] = {mx / m, my / m, mz / m};
+        if (CUBE) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) z[d] = ccom[3 * (int64_t)c + d];
+        }
         const int32_t k = sch[o];
         if (k >= 0) {
             for (int g = lane; g < 3 * NF; g += 32) {
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
                 if (sch[q] >= 0) t += sb[q][a];
             cmom[(int64_t)c * NC + a] = t;
         }
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !CUBE) {
             cmass[c] = m;
             ccom[3 * (int64_t)c + 0] = z[0];
             ccom[3 * (int64_t)c + 1] = z[1];
@@ -444,6 +450,256 @@ int records_of_order(hot_ctx *c, int q, int mom_stride, double eps_rec, T *dst)
     return HOT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Background subtraction (Sec. "Background Subtraction"): the expansion of a cell outside
+// a group's surrounding cube is that of its density contrast -- the particles' moments
+// about the cube's geometric centre minus those of the uniform density rho = M / L^3
+// filling the cube, both to order p -- and the empty octants of opened cells (cubes of
+// density -rho) are cells of their own.  Moments are taken to order p + 2 for the sizes
+// Q_n = (sum_{|a| = n} n!/a! M_a^2)^(1/2) of the contrast's first two omitted orders,
+// which its acceptance test uses.  All float64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t compact3(uint64_t v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v | (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v | (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v | (v >> 16)) & 0x1f00000000ffffull;
+    v = (v | (v >> 32)) & 0x1fffffull;
+    return v;
+}
+
+// Cube of every cell: side s = L / 2^level, centre lo + s (i + 1/2) per axis, i the cell's
+// integer coordinate at its level (the key's interleaved digits); and rho = M / L^3.
+__global__ void k_bg_geom(const uint64_t *__restrict__ ckey, const int32_t *__restrict__ clevel, int64_t ncell,
+                          const double *__restrict__ frame, const double *__restrict__ cmass, double *__restrict__ cen,
+                          double *__restrict__ half, double *__restrict__ rho)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int l = clevel[c];
+    const uint64_t k = l > 0 ? ckey[c] & ((1ull << (3 * l)) - 1ull) : 0ull;
+    const uint64_t ix = compact3(k >> 2), iy = compact3(k >> 1), iz = compact3(k);
+    const double L = frame[3];
+    const double s = L / (double)(1ull << l);
+    cen[3 * c + 0] = __dadd_rn(frame[0], __dmul_rn(s, (double)ix + 0.5));
+    cen[3 * c + 1] = __dadd_rn(frame[1], __dmul_rn(s, (double)iy + 0.5));
+    cen[3 * c + 2] = __dadd_rn(frame[2], __dmul_rn(s, (double)iz + 0.5));
+    half[c] = 0.5 * s;
+    if (c == 0) *rho = cmass[0] / (L * L * L);
+}
+
+// Moments of every leaf about its cube centre to order P2, one warp per leaf (lanes over
+// the components, the particles' powers staged 32 at a time).
+template <int P2>
+__global__ void __launch_bounds__(MW * 32) k_bg_p2m(const int32_t *__restrict__ cbegin,
+                                                    const int32_t *__restrict__ ccount,
+                                                    const int32_t *__restrict__ cnchild, int64_t ncell,
+                                                    const double *__restrict__ spos, const double *__restrict__ smass,
+                                                    const double *__restrict__ cen, double *__restrict__ mom)
+{
+    constexpr int NC = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
+    __shared__ double pw[MW][32][3][P2 + 1];
+    __shared__ double pm[MW][32];
+    __shared__ unsigned char mi[NC][3];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        mi[k][0] = hot_midx[k][0];
+        mi[k][1] = hot_midx[k][1];
+        mi[k][2] = hot_midx[k][2];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t c = (int64_t)blockIdx.x * MW + w; c < ncell; c += (int64_t)gridDim.x * MW) {
+        if (cnchild[c] != 0) continue;
+        const int64_t b = cbegin[c], n = ccount[c];
+        const double z[3] = {cen[3 * c + 0], cen[3 * c + 1], cen[3 * c + 2]};
+        double acc[(NC + 31) / 32];
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = 0.0;
+        for (int64_t s0 = b; s0 < b + n; s0 += 32) {
+            const int64_t s = s0 + lane;
+            const bool valid = s < b + n;
+            pm[w][lane] = valid ? smass[s] : 0.0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const double de = valid ? spos[3 * s + e] - z[e] : 0.0;
+                double v = 1.0;
+                for (int q = 0; q <= P2; ++q) {
+                    pw[w][lane][e][q] = v;
+                    v *= de;
+                }
+            }
+            __syncwarp();
+            const int cnt = (int)((b + n - s0) < 32 ? (b + n - s0) : 32);
+#pragma unroll
+            for (int q = 0; q < (NC + 31) / 32; ++q) {
+                const int a = lane + 32 * q;
+                if (a < NC) {
+                    const int ax = mi[a][0], ay = mi[a][1], az = mi[a][2];
+                    double t = 0.0;
+                    for (int j = 0; j < cnt; ++j) t += pm[w][j] * pw[w][j][0][ax] * pw[w][j][1][ay] * pw[w][j][2][az];
+                    acc[q] += t;
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < (NC + 31) / 32; ++q) {
+            const int a = lane + 32 * q;
+            if (a < NC) mom[c * NC + a] = acc[q];
+        }
+    }
+}
+
+// Empty octants of every inner cell (none for a leaf).
+__global__ void k_bg_ecount(const int32_t *__restrict__ cnchild, int64_t ncell, uint32_t *__restrict__ ecnt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) ecnt[c] = cnchild[c] > 0 ? (uint32_t)(8 - cnchild[c]) : 0u;
+}
+
+// Empty octant e = eoff[c] + k (the k-th missing child of c, ascending octants): its parent,
+// octant, and cube (side s = half the parent's, lower corner (centre_c - side_c / 2) + s off,
+// centre lower corner + s / 2), stored after the cells' cubes.
+__global__ void k_bg_efill(const int32_t *__restrict__ child8, const uint32_t *__restrict__ eoff, int64_t ncell,
+                           double *__restrict__ cen, double *__restrict__ half, int32_t *__restrict__ eparent,
+                           int32_t *__restrict__ eoct)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    uint32_t e = eoff[c];
+    if (eoff[c + 1] == e) return;
+    const double hc = half[c], s = hc;  // the octant's side is the parent's half side
+    for (int o = 0; o < 8; ++o) {
+        if (child8[8 * c + o] >= 0) continue;
+        const int off[3] = {(o >> 2) & 1, (o >> 1) & 1, o & 1};
+        const int64_t q = ncell + e;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double lo = __dadd_rn(__dsub_rn(cen[3 * c + d], hc), off[d] ? s : 0.0);
+            cen[3 * q + d] = __dadd_rn(lo, 0.5 * s);
+        }
+        half[q] = 0.5 * s;
+        eparent[e] = (int32_t)c;
+        eoct[e] = o;
+        ++e;
+    }
+}
+
+// Moment a of the uniform cube of density rho and half side h about its centre:
+// rho prod_d int_{-h}^{h} t^(a_d) dt (zero unless every a_d is even).
+__device__ __forceinline__ double cube_moment(int ax, int ay, int az, double h, double rho)
+{
+    auto one = [h](int k) {
+        if (k & 1) return 0.0;
+        double v = 2.0 * h;
+        for (int t = 0; t < k; ++t) v *= h;
+        return v / (double)(k + 1);
+    };
+    return rho * one(ax) * one(ay) * one(az);
+}
+
+// Contrast of every cube and its records: for a cell, its moments about the cube centre
+// minus the uniform cube's (in place, to order P + 2); for an empty octant, minus the
+// uniform cube's.  Q_{P+1}, Q_{P+2} to bg_q; the order-P record (scale: a power of two at
+// least the half-diagonal) to rec + (ncell + q) * reclen.
+template <int P, class T>
+__global__ void k_bg_records(int64_t ncell, int64_t ncube, const double *__restrict__ cen,
+                             const double *__restrict__ half, const double *__restrict__ rho_p,
+                             double *__restrict__ mom, double *__restrict__ bq, double G, double eps, int reclen,
+                             T *__restrict__ rec)
+{
+    constexpr int P2 = P + 2;
+    constexpr int NC2 = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
+    constexpr int NCP = (P + 1) * (P + 2) * (P + 3) / 6;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ncube) return;
+    const double rho = *rho_p, h = half[q];
+    double M[NCP];
+    double q1 = 0.0, q2 = 0.0;
+    double *m = q < ncell ? mom + q * NC2 : nullptr;
+    double fn[P2 + 1];
+    fn[0] = 1.0;
+    for (int t = 1; t <= P2; ++t) fn[t] = fn[t - 1] * (double)t;
+    for (int a = 0; a < NC2; ++a) {
+        const int ax = hot_midx[a][0], ay = hot_midx[a][1], az = hot_midx[a][2];
+        const double u = cube_moment(ax, ay, az, h, rho);
+        const double v = m ? m[a] - u : -u;
+        if (m) m[a] = v;
+        const int n = ax + ay + az;
+        if (a < NCP) M[a] = v;
+        if (n == P + 1) q1 += fn[n] / (fn[ax] * fn[ay] * fn[az]) * v * v;
+        if (n == P + 2) q2 += fn[n] / (fn[ax] * fn[ay] * fn[az]) * v * v;
+    }
+    bq[2 * q + 0] = sqrt(q1);
+    bq[2 * q + 1] = sqrt(q2);
+    const double b = 0.5 * sqrt(3.0) * (2.0 * h);
+    int e;
+    frexp(b, &e);
+    m2p_record<P, T>(M, cen + 3 * q, ldexp(1.0, -e), G, eps, rec + (ncell + q) * (int64_t)reclen);
+}
+
+// Background subtraction's moments, cube records and empty octants; the records go after
+// the cells' own in rec (which holds 2 ncell + n_empty records).
+template <int P, class T>
+int bg_records(hot_ctx *c, T *rec)
+{
+    constexpr int P2 = P + 2;
+    constexpr int NC2 = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
+    cudaStream_t s = c->st;
+    const int64_t nc = c->ncell, ncube = nc + c->n_empty;
+    HOT_CK(c->bg_mom.ensure((size_t)NC2 * nc, s));
+    HOT_CK(c->bg_q.ensure(2 * (size_t)ncube, s));
+    HOT_CK(c->bg_eparent.ensure(c->n_empty + 1, s));
+    HOT_CK(c->bg_eoct.ensure(c->n_empty + 1, s));
+    HOT_COUNT_LAUNCH();
+    k_bg_efill<<<hot_blocks(nc, 128), 128, 0, s>>>(c->child8.p, c->bg_eoff.p, nc, c->bg_cen.p, c->bg_half.p,
+                                                   c->bg_eparent.p, c->bg_eoct.p);
+    HOT_COUNT_LAUNCH();
+    k_bg_p2m<P2><<<c->nsm * 8, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, nc, c->spos.p, c->smass.p,
+                                                c->bg_cen.p, c->bg_mom.p);
+    for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
+        const int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
+        if (n <= 0) continue;
+        const int blocks = (int)(n < (int64_t)c->nsm * 8 ? n : (int64_t)c->nsm * 8);
+        HOT_COUNT_LAUNCH();
+        k_m2m_level<P2, true><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                            nullptr, c->bg_cen.p, c->bg_mom.p);
+    }
+    HOT_COUNT_LAUNCH();
+    k_bg_records<P, T><<<hot_blocks(ncube, 128), 128, 0, s>>>(nc, ncube, c->bg_cen.p, c->bg_half.p, c->bg_rho.p,
+                                                              c->bg_mom.p, c->bg_q.p, c->prm.G, c->prm.eps,
+                                                              HOT_REC_LEN[P], rec);
+    return HOT_OK;
+}
+
+// Number of empty octants (synchronises: it sizes the record array) and the cubes' geometry.
+int bg_prepare(hot_ctx *c)
+{
+    cudaStream_t s = c->st;
+    const int64_t nc = c->ncell;
+    HOT_CK(c->bg_ecnt.ensure(nc + 1, s));
+    HOT_CK(c->bg_eoff.ensure(nc + 1, s));
+    HOT_CK(c->bg_rho.ensure(1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(nc + 64), s));
+    HOT_COUNT_LAUNCH();
+    k_bg_ecount<<<hot_blocks(nc, 256), 256, 0, s>>>(c->cnchild.p, nc, c->bg_ecnt.p);
+    int r = hot_scan_u32_to_u32(c->bg_ecnt.p, c->bg_eoff.p, nc, c->scan_tmp.p, s);
+    if (r) return r;
+    uint32_t ne = 0;
+    HOT_CK(cudaMemcpyAsync(&ne, c->bg_eoff.p + nc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    HOT_CK(cudaStreamSynchronize(s));
+    c->n_empty = ne;
+    HOT_CK(c->bg_cen.ensure(3 * (size_t)(nc + ne), s));
+    HOT_CK(c->bg_half.ensure(nc + ne + 1, s));
+    HOT_COUNT_LAUNCH();
+    k_bg_geom<<<hot_blocks(nc, 128), 128, 0, s>>>(c->ckey.p, c->clevel.p, nc, c->frame.p, c->cmass.p, c->bg_cen.p,
+                                                  c->bg_half.p, c->bg_rho.p);
+    return HOT_OK;
+}
+
 template <int P>
 int moments_p(hot_ctx *c)
 {
@@ -475,9 +731,9 @@ int moments_p(hot_ctx *c)
         k_m2m_level<P><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
                                                      c->cmass.p, c->ccom.p, c->cmom.p);
     }
-    // the expansion's kernel: Plummer-softened, or Newtonian under K1 smoothing (whose
-    // kernel differs from 1/r only inside eps, which accepted cells keep clear of)
-    const double eps_rec = c->prm.softening == HOT_SOFT_K1 ? 0.0 : c->prm.eps;
+    // the expansion's kernel: Plummer-softened, or Newtonian under K1 or spline smoothing
+    // (whose kernels differ from 1/r only inside eps, which accepted cells keep clear of)
+    const double eps_rec = c->prm.softening != HOT_SOFT_PLUMMER ? 0.0 : c->prm.eps;
     // aggregates of inner cells
     const int64_t max_items = ncell + N * (c->maxlevel + 1) / CHUNK + 1;
     HOT_CK(c->item_off.ensure(ncell + 1, s));
@@ -498,19 +754,35 @@ int moments_p(hot_ctx *c)
     HOT_COUNT_LAUNCH();
     k_item_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
                                                           c->cbmax.p, c->cB1.p, c->cB2.p);
-    // records
+    // records (under background subtraction also those of the cells' contrasts and of the
+    // empty octants, after the cells' own)
     const int reclen = HOT_REC_LEN[P];
     c->reclen = reclen;
+    int64_t nrec = ncell;
+    if constexpr (P <= HOT_BG_PMAX) {
+        if (c->prm.background) {
+            r = bg_prepare(c);
+            if (r) return r;
+            nrec = 2 * ncell + c->n_empty;
+        }
+    }
     if (c->prm.precision == HOT_FP64) {
-        HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
+        HOT_CK(c->rec64.ensure((size_t)reclen * nrec, s));
         HOT_COUNT_LAUNCH();
         k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                     c->prm.G, eps_rec, reclen, NC, c->rec64.p);
     } else {
-        HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
+        HOT_CK(c->rec32.ensure((size_t)reclen * nrec, s));
         HOT_COUNT_LAUNCH();
         k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                    c->prm.G, eps_rec, reclen, NC, c->rec32.p);
+    }
+    if constexpr (P <= HOT_BG_PMAX) {
+        if (c->prm.background) {
+            r = c->prm.precision == HOT_FP64 ? bg_records<P, double>(c, c->rec64.p)
+                                             : bg_records<P, float>(c, c->rec32.p);
+            if (r) return r;
+        }
     }
     // per-interaction order selection: B_n of every cell and the records of orders p_min..p-1
     c->varq = c->prm.p_min >= 0 && c->prm.p_min < P;

@@ -5,10 +5,13 @@
 //
 // One warp per sink group.  The warp tests 32 cells of the current frontier at a time;
 // accepted cells go to the M2P list, rejected leaves to the P2P list, and the children
-// of rejected inner cells form the next frontier (kept in per-warp global scratch).  A
-// count pass, a scan and an identical fill pass produce CSR lists.  Every decision
-// depends only on the (cell, group) pair, so the lists equal those of a depth-first
-// traversal as sets; within a list the order is by level, then by parent, then octant.
+// of rejected inner cells form the next frontier (kept in per-warp global scratch).  One
+// pass writes each group's lists into per-group slots sized from the previous call's
+// largest counts, and a compaction copies them into CSR order; a group that does not fit
+// its slots makes that call fall back to a count pass, a scan and an identical fill
+// pass.  Every decision depends only on the (cell, group) pair, so the lists equal those
+// of a depth-first traversal as sets; within a list the order is by level, then by
+// parent, then octant.
 #include "hot_common.cuh"
 
 namespace {
@@ -361,6 +364,280 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Background subtraction (Sec. "Background Subtraction").  The acceptance estimate of a
+// contrast expansion about a cube's centre (half-diagonal b, Q_n the size of its order-n
+// multipole):
+//   E(d) = G / (1 - b/d)^2 [(p+2) Q_{p+1} / d^{p+3} + (p+3) Q_{p+2} / d^{p+4}],  d > b,
+// strictly decreasing on (b, inf), so it too is pre-solved per cube into a radius.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bg_bound(double d, double b, double Q1, double Q2, int p, double G)
+{
+    const double q = __dsub_rn(1.0, __ddiv_rn(b, d));
+    const double t1 = __ddiv_rn(__dmul_rn((double)(p + 2), Q1), pow(d, (double)(p + 3)));
+    const double t2 = __ddiv_rn(__dmul_rn((double)(p + 3), Q2), pow(d, (double)(p + 4)));
+    return __dmul_rn(__ddiv_rn(G, __dmul_rn(q, q)), __dadd_rn(t1, t2));
+}
+
+// The radius of E(d) = tol: a doubling bracket, then Newton steps in ln d with bisection
+// as the safeguard (as for the plain bound); b when E vanishes (a contrast with no omitted
+// multipole: accepted as soon as d > b).
+__device__ double bg_radius_solve(double b, double Q1, double Q2, int p, double G, double tol)
+{
+    if (!(Q1 > 0.0 || Q2 > 0.0)) return b;
+    double lo = b, hi = 2.0 * b;
+    int k = 0;
+    while (!(bg_bound(hi, b, Q1, Q2, p, G) <= tol) && k < 1100) {
+        lo = hi;
+        hi *= 2.0;
+        ++k;
+    }
+    if (k >= 1100) return INFINITY;
+    const double ltol = log(tol);
+    double d = hi;
+    for (int it = 0; it < 80; ++it) {
+        // ln E and its derivative in ln d
+        const double a1 = (p + 2) * Q1 * pow(d, -(double)(p + 3)), a2 = (p + 3) * Q2 * pow(d, -(double)(p + 4));
+        const double f = log(G) - 2.0 * log(1.0 - b / d) + log(a1 + a2) - ltol;
+        const double df = -2.0 * b / (d - b) - ((p + 3) * a1 + (p + 4) * a2) / (a1 + a2);
+        double dn = d * exp(-f / df);
+        if (fabs(dn - d) <= 1e-13 * d) {
+            d = dn;
+            break;
+        }
+        if (!(dn > lo && dn < hi)) dn = 0.5 * (lo + hi);
+        if (!(dn > lo && dn < hi)) break;
+        if (bg_bound(dn, b, Q1, Q2, p, G) <= tol)
+            hi = dn;
+        else
+            lo = dn;
+        d = dn;
+        if (hi - lo <= 1e-13 * hi) {
+            d = hi;
+            break;
+        }
+    }
+    return d;
+}
+
+__global__ void k_bg_radius(const double *__restrict__ cen, const double *__restrict__ half,
+                            const double *__restrict__ bq, int64_t ncube, int p, double G, double tol,
+                            TCell *__restrict__ tc)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ncube) return;
+    const double b = 0.5 * sqrt(3.0) * (2.0 * half[q]);
+    TCell t;
+    t.x = cen[3 * q + 0];
+    t.y = cen[3 * q + 1];
+    t.z = cen[3 * q + 2];
+    t.rc = bg_radius_solve(b, bq[2 * q], bq[2 * q + 1], p, G, tol);
+    tc[q] = t;
+}
+
+// Acceptance of a contrast expansion (cube q) for a group at (gx, gy, gz), Delta_max dmax:
+// d = |c - g| - dmax >= r_c, decided as stated within 1e-9 of the threshold.
+__device__ __forceinline__ bool bg_accept(const TCell &t, double half, const double *__restrict__ bq, int64_t q,
+                                          double gx, double gy, double gz, double dmax, int p, double G, double tol)
+{
+    if (!(t.rc < INFINITY)) return false;
+    const double dx = t.x - gx, dy = t.y - gy, dz = t.z - gz;
+    const double dist2 = dx * dx + dy * dy + dz * dz;
+    const double thr = dmax + t.rc;
+    const double thr2 = thr * thr;
+    if (dist2 > thr2 * (1.0 + 1e-9)) return true;
+    if (dist2 < thr2 * (1.0 - 1e-9)) return false;
+    const double ex = __dsub_rn(t.x, gx), ey = __dsub_rn(t.y, gy), ez = __dsub_rn(t.z, gz);
+    const double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+    const double d = __dsub_rn(dist, dmax);
+    const double b = 0.5 * sqrt(3.0) * (2.0 * half);
+    return d > b && bg_bound(d, b, bq[2 * q], bq[2 * q + 1], p, G) <= tol;
+}
+
+// The plain acceptance test of a cell's matter expansion (as in k_traverse, float64 only).
+__device__ __forceinline__ bool plain_accept(const TCell &t, double b, double B1, double B2, double gx, double gy,
+                                             double gz, double dmax, int p, double G, double tol)
+{
+    if (!(t.rc < INFINITY)) return false;
+    const double dx = t.x - gx, dy = t.y - gy, dz = t.z - gz;
+    const double dist2 = dx * dx + dy * dy + dz * dz;
+    const double thr = dmax + t.rc;
+    const double thr2 = thr * thr;
+    if (dist2 > thr2 * (1.0 + 1e-9)) return true;
+    if (dist2 < thr2 * (1.0 - 1e-9)) return false;
+    const double ex = __dsub_rn(t.x, gx), ey = __dsub_rn(t.y, gy), ez = __dsub_rn(t.z, gz);
+    const double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+    const double d = __dsub_rn(dist, dmax);
+    return d > b && mac_bound(d, b, B1, B2, p, G) <= tol;
+}
+
+// Group-wise traversal under background subtraction, one warp per group, breadth-first as
+// k_traverse.  S, the group's surrounding cube, is its cell's ancestor `up` levels up.
+//   * the group's cell and its ancestors are opened (a leaf among them goes to P2P);
+//   * a cell inside S: the plain method (matter expansion about the centre of mass, the
+//     plain test; else P2P for a leaf, else opened);
+//   * a cell outside S: its contrast expansion if accepted (M2P entry ncell + c); else a
+//     leaf goes to P2P and its cube's background to the cube list (entry c); else opened;
+//   * every opened cell outside S (ancestors above S included): each empty octant e is a
+//     contrast expansion if accepted (M2P entry 2 ncell + e), else an analytic cube (cube
+//     list entry ncell + e).
+// MODE 0 counts (and writes S, the totals and the cost keys), MODE 1 fills at the offsets.
+template <int MODE>
+__global__ void __launch_bounds__(TW * 32) k_traverse_bg(
+    int64_t ngroup, int64_t ncell, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
+    const double *__restrict__ gdmax, const int32_t *__restrict__ cparent, const TCell *__restrict__ tcell,
+    const TCell *__restrict__ tbg, const double *__restrict__ bhalf, const double *__restrict__ bq,
+    const uint32_t *__restrict__ eoff, const int32_t *__restrict__ cend, const int32_t *__restrict__ child8,
+    const int32_t *__restrict__ cnchild, const int32_t *__restrict__ ccount, const double *__restrict__ cbmax,
+    const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, int up,
+    int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
+    uint32_t *__restrict__ cnt_p2p, uint32_t *__restrict__ cnt_box, const int64_t *__restrict__ off_m2p,
+    const int64_t *__restrict__ off_p2p, const int64_t *__restrict__ off_box, int32_t *__restrict__ l_m2p,
+    int32_t *__restrict__ l_p2p, int32_t *__restrict__ l_box, int32_t *__restrict__ gS,
+    unsigned long long *__restrict__ stats, uint64_t *__restrict__ gkey, unsigned *__restrict__ status)
+{
+    constexpr bool FILL = MODE == 1;
+    const unsigned lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t *A = scratch + gw * 2 * (int64_t)cap;
+    int32_t *B = A + cap;
+    for (;;) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(work, 1u);
+        const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
+        if (g >= ngroup) break;
+        const int32_t gc = gcell[g];
+        const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+        const double dmax = gdmax[g];
+        int32_t S = gc;
+        for (int k = 0; k < up && S > 0; ++k) S = cparent[S];
+        const int32_t Send = cend[S];
+        const int64_t om = FILL ? off_m2p[g] : 0, op = FILL ? off_p2p[g] : 0, ob = FILL ? off_box[g] : 0;
+        uint32_t nm = 0, np = 0, nb = 0, ncon = 0, nemp = 0;
+        uint64_t parts = 0;
+        bool overflow = false;
+        if (lane == 0) A[0] = 0;
+        __syncwarp();
+        int na = 1;
+        while (na > 0 && !overflow) {
+            int nbf = 0;
+            for (int base = 0; base < na; base += 32) {
+                const int i = base + (int)lane;
+                const int32_t c = i < na ? A[i] : -1;
+                int32_t em = -1, eb = -1;  // this cell's M2P and cube entries
+                bool pp = false, open = false, empt = false;
+                if (c >= 0) {
+                    const bool leaf = cnchild[c] == 0;
+                    const bool anc = c <= gc && gc < cend[c];
+                    const bool inS = S <= c && c < Send;
+                    if (anc) {
+                        pp = leaf;
+                        open = !leaf;
+                        empt = !leaf && !inS;
+                    } else if (inS) {
+                        if (plain_accept(tcell[c], cbmax[c], cB1[c], cB2[c], gx, gy, gz, dmax, p, G, tol))
+                            em = c;
+                        else if (leaf)
+                            pp = true;
+                        else
+                            open = true;
+                    } else {
+                        if (bg_accept(tbg[c], bhalf[c], bq, c, gx, gy, gz, dmax, p, G, tol)) {
+                            em = (int32_t)(ncell + c);
+                        } else if (leaf) {
+                            pp = true;
+                            eb = c;
+                        } else {
+                            open = true;
+                            empt = true;
+                        }
+                    }
+                }
+                // empty octants of an opened cell outside S: accepted ones (bit set in am)
+                // or analytic cubes
+                unsigned am = 0, ab = 0;
+                uint32_t e0 = 0;
+                if (empt) {
+                    e0 = eoff[c];
+                    uint32_t e = e0;
+                    for (int o = 0; o < 8; ++o) {
+                        if (child8[8 * (int64_t)c + o] >= 0) continue;
+                        const int64_t qb = ncell + e;
+                        if (bg_accept(tbg[qb], bhalf[qb], bq, qb, gx, gy, gz, dmax, p, G, tol))
+                            am |= 1u << (e - e0);
+                        else
+                            ab |= 1u << (e - e0);
+                        ++e;
+                    }
+                }
+                const uint32_t lm = (em >= 0 ? 1u : 0u) + (uint32_t)__popc(am);
+                const uint32_t lp = pp ? 1u : 0u;
+                const uint32_t lb = (eb >= 0 ? 1u : 0u) + (uint32_t)__popc(ab);
+                const uint32_t im = warp_incl_scan(lm), ip = warp_incl_scan(lp), ib = warp_incl_scan(lb);
+                if (FILL) {
+                    int64_t km = om + nm + im - lm, kb = ob + nb + ib - lb;
+                    if (em >= 0) l_m2p[km++] = em;
+                    for (unsigned bm = am; bm; bm &= bm - 1u) l_m2p[km++] = (int32_t)(2 * ncell + e0 + __ffs(bm) - 1);
+                    if (pp) l_p2p[op + np + ip - lp] = c;
+                    if (eb >= 0) l_box[kb++] = eb;
+                    for (unsigned bb = ab; bb; bb &= bb - 1u) l_box[kb++] = (int32_t)(ncell + e0 + __ffs(bb) - 1);
+                } else if (pp) {
+                    parts += (uint64_t)ccount[c];
+                }
+                ncon += __popc(__ballot_sync(0xffffffffu, em >= ncell));
+                nemp += warp_sum((uint32_t)__popc(am));
+                nm += __shfl_sync(0xffffffffu, im, 31);
+                np += __shfl_sync(0xffffffffu, ip, 31);
+                nb += __shfl_sync(0xffffffffu, ib, 31);
+                const int nch = open ? cnchild[c] : 0;
+                const int incl = warp_incl_scan(nch);
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                if (nbf + tot > cap) {
+                    overflow = true;
+                    break;
+                }
+                if (open) {
+                    int k = nbf + incl - nch;
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const int32_t ch = child8[8 * (int64_t)c + o];
+                        if (ch >= 0) B[k++] = ch;
+                    }
+                }
+                nbf += tot;
+            }
+            __syncwarp();
+            int32_t *t = A;
+            A = B;
+            B = t;
+            na = nbf;
+        }
+        if (overflow) {
+            if (lane == 0) hot_flag(status, HOT_ST_FRONTIER);
+            nm = np = nb = ncon = nemp = 0;
+        }
+        if (!FILL) {
+            parts = warp_sum(parts);
+            if (lane == 0) {
+                cnt_m2p[g] = nm;
+                cnt_p2p[g] = np;
+                cnt_box[g] = nb;
+                gS[g] = S;
+                const uint64_t ns = (uint64_t)ccount[gc];
+                atomicAdd(&stats[0], (unsigned long long)(ns * nm));
+                atomicAdd(&stats[1], (unsigned long long)(ns * parts));
+                atomicAdd(&stats[2], (unsigned long long)(ns * (nb + 1)));
+                atomicAdd(&stats[3], (unsigned long long)(ns * ncon));
+                atomicAdd(&stats[4], (unsigned long long)(ns * nemp));
+                atomicAdd(&stats[5], (unsigned long long)parts);
+                const uint64_t cost = 10ull * nm + parts;
+                gkey[g] = 0xffffffffull - (cost < 0xffffffffull ? cost : 0xffffffffull);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_iota(uint32_t *__restrict__ v, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -403,11 +680,135 @@ __global__ void k_compact_lists(int64_t ngroup, int64_t capm, int64_t capp, cons
 
 }  // namespace
 
+namespace {
+
+// Work order of the interactions: groups by descending slice cost (stable, so ties keep
+// index order), each expanded into its 32-sink slices, so that no single large group is
+// one warp's work.
+int work_items(hot_ctx *c)
+{
+    cudaStream_t s = c->st;
+    const int64_t ng = c->ngroup;
+    HOT_COUNT_LAUNCH();
+    k_iota<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, ng);
+    int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 32);
+    if (rs) return rs;
+    HOT_CK(c->slice_cnt.ensure(ng + 1, s));
+    HOT_CK(c->slice_off.ensure(ng + 1, s));
+    HOT_CK(c->items.ensure(ng + c->N / 32 + 1, s));
+    HOT_COUNT_LAUNCH();
+    k_slice_count<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->gcell.p, c->ccount.p, ng, c->slice_cnt.p);
+    rs = hot_scan_u32_to_u32(c->slice_cnt.p, c->slice_off.p, ng, c->scan_tmp.p, s);
+    if (rs) return rs;
+    HOT_COUNT_LAUNCH();
+    k_slice_fill<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->slice_off.p, ng, c->items.p);
+    return HOT_OK;
+}
+
+// Lists under background subtraction: count, scan, fill (three lists per group), then the
+// work items as for the plain method.
+int traverse_bg(hot_ctx *c, double tol)
+{
+    cudaStream_t s = c->st;
+    const int64_t ng = c->ngroup, nc = c->ncell, ncube = nc + c->n_empty;
+    HOT_CK(c->cnt_m2p.ensure(ng + 1, s));
+    HOT_CK(c->cnt_p2p.ensure(ng + 1, s));
+    HOT_CK(c->cnt_box.ensure(ng + 1, s));
+    HOT_CK(c->off_m2p.ensure(ng + 1, s));
+    HOT_CK(c->off_p2p.ensure(ng + 1, s));
+    HOT_CK(c->off_box.ensure(ng + 1, s));
+    HOT_CK(c->bg_gS.ensure(ng + 1, s));
+    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ng + c->ncell + c->N + 64), s));
+    HOT_CK(c->tcell.ensure(nc, s));
+    HOT_CK(c->tcellf.ensure(nc, s));
+    HOT_CK(c->bg_tc.ensure(ncube, s));
+    HOT_CK(c->gkey.ensure(ng + 1, s));
+    HOT_CK(c->gkey2.ensure(ng + 1, s));
+    HOT_CK(c->gorder.ensure(ng + 1, s));
+    HOT_CK(c->gorder2.ensure(ng + 1, s));
+    const int blocks = c->nsm * 4;
+    const int64_t nwarps = (int64_t)blocks * TW;
+    unsigned *work = (unsigned *)(c->sizes.p + 50);
+    unsigned long long *stats = (unsigned long long *)(c->sizes.p + 52);  // 6 counters, 52..57
+    HOT_COUNT_LAUNCH();
+    k_mac_radius<<<hot_blocks(nc, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, nc, c->p_mom,
+                                                      c->prm.G, tol, 0.0, nullptr, c->q_lo, nullptr, c->tcell.p,
+                                                      c->tcellf.p);
+    HOT_COUNT_LAUNCH();
+    k_bg_radius<<<hot_blocks(ncube, 128), 128, 0, s>>>(c->bg_cen.p, c->bg_half.p, c->bg_q.p, ncube, c->p_mom,
+                                                       c->prm.G, tol, c->bg_tc.p);
+    int64_t host[9];
+    for (int attempt = 0;; ++attempt) {
+        HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
+        HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 8 * sizeof(int64_t), s));
+        HOT_COUNT_LAUNCH();
+        k_traverse_bg<0><<<blocks, TW * 32, 0, s>>>(
+            ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->bg_tc.p, c->bg_half.p, c->bg_q.p,
+            c->bg_eoff.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p, c->cbmax.p, c->cB1.p, c->cB2.p,
+            c->p_mom, c->prm.G, tol, c->prm.bg_up, c->trav_scratch.p, c->trav_cap, work, c->cnt_m2p.p,
+            c->cnt_p2p.p, c->cnt_box.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->bg_gS.p, stats,
+            c->gkey.p, c->d_status);
+        int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
+        if (r) return r;
+        r = hot_scan_u32_to_i64(c->cnt_p2p.p, c->off_p2p.p, ng, c->scan_tmp.p, s);
+        if (r) return r;
+        r = hot_scan_u32_to_i64(c->cnt_box.p, c->off_box.p, ng, c->scan_tmp.p, s);
+        if (r) return r;
+        HOT_CK(cudaMemcpyAsync(host + 0, c->off_m2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 1, c->off_p2p.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 2, c->off_box.p + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaMemcpyAsync(host + 3, stats, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        HOT_CK(cudaStreamSynchronize(s));
+        unsigned st = 0;
+        HOT_CK(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (st & HOT_ST_FRONTIER) {
+            HOT_CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s));
+            if (attempt >= 3) return HOT_EOVERFLOW;
+            c->trav_cap *= 4;
+            continue;
+        }
+        int e = hot_sync_status(c);
+        if (e) return e;
+        break;
+    }
+    c->n_m2p = host[0];
+    c->n_p2p = host[1];
+    c->n_box = host[2];
+    c->n_m2p_int = host[3];
+    c->n_pairs = host[4];
+    c->n_box_eval = host[5];
+    c->n_m2p_con = host[6];
+    c->n_m2p_emp = host[7];
+    c->n_p2p_src = host[8];
+    HOT_CK(c->l_m2p.ensure(c->n_m2p + 1, s));
+    HOT_CK(c->l_p2p.ensure(c->n_p2p + 1, s));
+    HOT_CK(c->l_box.ensure(c->n_box + 1, s));
+    HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
+    HOT_COUNT_LAUNCH();
+    k_traverse_bg<1><<<blocks, TW * 32, 0, s>>>(
+        ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->bg_tc.p, c->bg_half.p, c->bg_q.p,
+        c->bg_eoff.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom,
+        c->prm.G, tol, c->prm.bg_up, c->trav_scratch.p, c->trav_cap, work, nullptr, nullptr, nullptr, c->off_m2p.p,
+        c->off_p2p.p, c->off_box.p, c->l_m2p.p, c->l_p2p.p, c->l_box.p, nullptr, nullptr, nullptr, c->d_status);
+    return work_items(c);
+}
+
+}  // namespace
+
 int hot_impl_traverse(hot_ctx *c, double tol)
 {
     cudaStream_t s = c->st;
     const int64_t ng = c->ngroup;
     hot_tic(c, 3);
+    if (c->prm.background) {
+        const int r = traverse_bg(c, tol);
+        if (r) return r;
+        hot_toc(c, 3);
+        if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
+        c->tol_lists = tol;
+        c->stage = 3;
+        return HOT_OK;
+    }
     HOT_CK(c->cnt_m2p.ensure(ng + 1, s));
     HOT_CK(c->cnt_p2p.ensure(ng + 1, s));
     HOT_CK(c->off_m2p.ensure(ng + 1, s));
@@ -425,8 +826,9 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     HOT_CK(c->gkey2.ensure(ng + 1, s));
     HOT_CK(c->gorder.ensure(ng + 1, s));
     HOT_CK(c->gorder2.ensure(ng + 1, s));
-    // acceptance guard of K1 smoothing: no source of an accepted cell within eps of a sink
-    const double guard = c->prm.softening == HOT_SOFT_K1 ? c->prm.eps : 0.0;
+    // acceptance guard of the compact kernels (K1, spline): no source of an accepted cell
+    // within eps of a sink
+    const double guard = c->prm.softening != HOT_SOFT_PLUMMER ? c->prm.eps : 0.0;
     // per-interaction order selection: radii of every order, orders in the M2P entries
     const double *cBn = c->varq ? c->cBn.p : nullptr;
     // periodic boundaries: images of the tree, tagged in the entries
@@ -519,22 +921,8 @@ int hot_impl_traverse(hot_ctx *c, double tol)
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }
-    // work order of the interactions: groups by descending slice cost (stable, so ties keep
-    // index order), each expanded into its 32-sink slices, so that no single large group
-    // is one warp's work
-    HOT_COUNT_LAUNCH();
-    k_iota<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, ng);
-    int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 32);
+    int rs = work_items(c);
     if (rs) return rs;
-    HOT_CK(c->slice_cnt.ensure(ng + 1, s));
-    HOT_CK(c->slice_off.ensure(ng + 1, s));
-    HOT_CK(c->items.ensure(ng + c->N / 32 + 1, s));
-    HOT_COUNT_LAUNCH();
-    k_slice_count<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->gcell.p, c->ccount.p, ng, c->slice_cnt.p);
-    rs = hot_scan_u32_to_u32(c->slice_cnt.p, c->slice_off.p, ng, c->scan_tmp.p, s);
-    if (rs) return rs;
-    HOT_COUNT_LAUNCH();
-    k_slice_fill<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, c->slice_off.p, ng, c->items.p);
     hot_toc(c, 3);
     if (cudaGetLastError() != cudaSuccess) return HOT_ECUDA;
     c->tol_lists = tol;

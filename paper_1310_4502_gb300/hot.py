@@ -16,25 +16,26 @@ from . import build as _build
 HOT_OK, HOT_EINVAL, HOT_ESTATE, HOT_ENOMEM, HOT_EOVERFLOW, HOT_ECUDA, HOT_EINPUT, HOT_ETIMEOUT = (
     0, -1, -2, -3, -4, -5, -6, -7)
 HOT_FP32_MIXED, HOT_FP64 = 0, 1
-HOT_SOFT_PLUMMER, HOT_SOFT_K1 = 0, 1
+HOT_SOFT_PLUMMER, HOT_SOFT_K1, HOT_SOFT_SPLINE = 0, 1, 2
 HOT_DBGSET_FRONTIER_CAP, HOT_DBGSET_SLOT_CAP, HOT_DBGSET_WAIT_POLLS, HOT_DBGSET_WAIT_PROBE = 0, 1, 2, 3
 
 DBG = dict(FRAME=0, SORTED_KEYS=1, PERM=2, CELL_KEY=3, CELL_LEVEL=4, CELL_BEGIN=5, CELL_COUNT=6,
            CELL_PARENT=7, CELL_NCHILD=8, GROUP_CELL=9, GROUP_CENTRE=10, GROUP_DMAX=11, CELL_MASS=12,
            CELL_COM=13, MOMENTS=14, CELL_BMAX=15, CELL_B1=16, CELL_B2=17, M2P_OFFSETS=18, M2P_CELLS=19,
-           P2P_OFFSETS=20, P2P_CELLS=21, M2P_ORDERS=22, M2P_IMAGES=23, P2P_IMAGES=24)
+           P2P_OFFSETS=20, P2P_CELLS=21, M2P_ORDERS=22, M2P_IMAGES=23, P2P_IMAGES=24, BG_CUBE_OFFSETS=25,
+           BG_CUBES=26, BG_GROUP_S=27, BG_EMPTY_PARENT=28, BG_EMPTY_OCTANT=29)
 
 EXPORTS = ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
            "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
            "hot_lookup", "hot_fma_peak", "hot_strerror", "hot_destroy", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums")
+           "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums", "hot_bg_sizes")
 
 
 class hot_params(C.Structure):
     _fields_ = [("p", C.c_int), ("tol", C.c_double), ("eps", C.c_double), ("G", C.c_double),
                 ("leaf_max", C.c_int), ("group_max", C.c_int), ("precision", C.c_int),
                 ("softening", C.c_int), ("p_min", C.c_int), ("box", C.c_double), ("ws", C.c_int),
-                ("box_lo", C.c_double * 3)]
+                ("box_lo", C.c_double * 3), ("background", C.c_int), ("bg_up", C.c_int)]
 
 
 class HotError(RuntimeError):
@@ -82,10 +83,11 @@ def load():
     L.hot_synchronize.argtypes = [vp]
     L.hot_debug_set.argtypes = [vp, C.c_int, C.c_int64]
     L.hot_lattice_sums.argtypes = [C.c_double, C.c_int, C.c_int, vp]
+    L.hot_bg_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     for name in ("hot_create", "hot_set_params", "hot_build_tree", "hot_compute_moments", "hot_traverse",
                  "hot_evaluate_forces", "hot_adjoint", "hot_stage_times", "hot_sizes", "hot_debug_get",
                  "hot_lookup", "hot_fma_peak", "hot_key_frame_noalloc", "hot_axpy",
-           "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums"):
+                 "hot_memory_stats", "hot_synchronize", "hot_debug_set", "hot_lattice_sums", "hot_bg_sizes"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -114,12 +116,17 @@ def _need(t, shape_last=None):
 
 
 def make_params(p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
-                softening="plummer", p_min=None, box=0.0, ws=2, box_lo=(0.0, 0.0, 0.0)):
+                softening="plummer", p_min=None, box=0.0, ws=2, box_lo=(0.0, 0.0, 0.0), background=False,
+                bg_up=2):
     prec = HOT_FP64 if precision in ("fp64", "f64", HOT_FP64) else HOT_FP32_MIXED
-    soft = HOT_SOFT_K1 if softening in ("k1", HOT_SOFT_K1) else HOT_SOFT_PLUMMER
+    kinds = {"plummer": HOT_SOFT_PLUMMER, "k1": HOT_SOFT_K1, "spline": HOT_SOFT_SPLINE,
+             HOT_SOFT_PLUMMER: HOT_SOFT_PLUMMER, HOT_SOFT_K1: HOT_SOFT_K1, HOT_SOFT_SPLINE: HOT_SOFT_SPLINE}
+    if softening not in kinds:
+        raise ValueError(f"unknown softening {softening!r}: plummer, k1 or spline")
+    soft = kinds[softening]
     return hot_params(int(p), float(tol), float(eps), float(G), int(leaf_max), int(group_max), prec, soft,
                       -1 if p_min is None else int(p_min), float(box), int(ws),
-                      (C.c_double * 3)(*[float(v) for v in box_lo]))
+                      (C.c_double * 3)(*[float(v) for v in box_lo]), 1 if background else 0, int(bg_up))
 
 
 class Hot:
@@ -197,9 +204,17 @@ class Hot:
         return dict(zip(("N", "ncell", "ngroup", "nleaf", "maxlevel", "n_m2p", "n_p2p", "n_pairs", "n_m2p_int",
                          "launches"), list(out)))
 
+    def bg_sizes(self):
+        """Background subtraction's sizes (see hot_bg_sizes in include/hot.h)."""
+        out = (C.c_int64 * 6)()
+        _ck(load().hot_bg_sizes(self._h, out), "hot_bg_sizes")
+        return dict(zip(("n_empty", "n_cube_entries", "cube_evals", "m2p_contrast", "m2p_empty", "m2p_matter"),
+                        list(out)))
+
     def debug_get(self, what):
         s = self.sizes()
         N, nc, ng = s["N"], s["ncell"], s["ngroup"]
+        bg = self.bg_sizes() if self.params.background else {"n_empty": 0, "n_cube_entries": 0}
         ncomp = (self.params.p + 1) * (self.params.p + 2) * (self.params.p + 3) // 6
         spec = {
             "FRAME": (np.float64, (4,)), "SORTED_KEYS": (np.uint64, (N,)), "PERM": (np.int32, (N,)),
@@ -211,7 +226,9 @@ class Hot:
             "CELL_B2": (np.float64, (nc,)), "M2P_OFFSETS": (np.int64, (ng + 1,)), "M2P_CELLS": (np.int32, (s["n_m2p"],)),
             "P2P_OFFSETS": (np.int64, (ng + 1,)), "P2P_CELLS": (np.int32, (s["n_p2p"],)),
             "M2P_ORDERS": (np.int32, (s["n_m2p"],)), "M2P_IMAGES": (np.int32, (s["n_m2p"],)),
-            "P2P_IMAGES": (np.int32, (s["n_p2p"],)),
+            "P2P_IMAGES": (np.int32, (s["n_p2p"],)), "BG_CUBE_OFFSETS": (np.int64, (ng + 1,)),
+            "BG_CUBES": (np.int32, (bg["n_cube_entries"],)), "BG_GROUP_S": (np.int32, (ng,)),
+            "BG_EMPTY_PARENT": (np.int32, (bg["n_empty"],)), "BG_EMPTY_OCTANT": (np.int32, (bg["n_empty"],)),
         }[what]
         out = np.zeros(spec[1], dtype=spec[0])
         _ck(load().hot_debug_get(self._h, DBG[what], out.ctypes.data_as(C.c_void_p), out.nbytes),
@@ -274,6 +291,12 @@ def key_frame_noalloc(pos, mass, frame, stream=None):
     _need(pos)
     _need(mass)
     _need(frame)
+    if pos.dim() != 2 or pos.shape[1] != 3 or mass.dim() != 1 or pos.shape[0] != mass.shape[0]:
+        raise ValueError("key_frame_noalloc: pos must be [N,3] and mass [N] with the same N")
+    if frame.numel() < 4:
+        raise ValueError("key_frame_noalloc: frame needs at least 4 float64 elements")
+    if not (pos.device == mass.device == frame.device):
+        raise ValueError("key_frame_noalloc: pos, mass and frame must be on one device")
     st = stream or torch.cuda.current_stream()
     _ck(load().hot_key_frame_noalloc(_ptr(pos), _ptr(mass), int(mass.shape[0]), _ptr(frame),
                                      C.c_void_p(st.cuda_stream)), "hot_key_frame_noalloc")
@@ -282,12 +305,13 @@ def key_frame_noalloc(pos, mass, frame, stream=None):
 
 def tree_force(pos, mass, p=4, tol=1e-4, eps=0.0, G=1.0, leaf_max=64, group_max=128, precision="mixed",
                ctx: Hot | None = None, want_pot=True, softening="plummer", p_min=None, box=0.0, ws=2,
-               box_lo=(0.0, 0.0, 0.0)):
+               box_lo=(0.0, 0.0, 0.0), background=False, bg_up=2):
     """Tree-code acceleration (and potential) of float64 CUDA tensors pos [N,3], mass [N];
     box > 0: periodic cube [box_lo, box_lo + box) with the images within ws served by the tree."""
     import torch
     h = ctx or Hot(p=p, tol=tol, eps=eps, G=G, leaf_max=leaf_max, group_max=group_max, precision=precision,
-                   softening=softening, p_min=p_min, box=box, ws=ws, box_lo=box_lo)
+                   softening=softening, p_min=p_min, box=box, ws=ws, box_lo=box_lo, background=background,
+                   bg_up=bg_up)
     h.build_tree(pos, mass)
     h.compute_moments(p)
     h.traverse(tol)

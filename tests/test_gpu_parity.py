@@ -237,21 +237,23 @@ K1_CASES = {
 }
 
 
+@pytest.mark.parametrize("soft", ["k1", "spline"])
 @pytest.mark.parametrize("name", list(K1_CASES))
 @pytest.mark.parametrize("p", [4, 6])
-def test_k1_lists_and_forces(name, p):
-    """K1 compensating smoothing: the lists (with the d >= b_max + eps guard) and the forces
-    against the oracle's K1 tree, at the tolerances of the Plummer parity test."""
+def test_compact_lists_and_forces(name, p, soft):
+    """Kernels of compact support (K1 compensating smoothing, the cubic spline): the lists
+    (with the d >= b_max + eps guard) and the forces against the oracle's tree with the
+    same kernel, at the tolerances of the Plummer parity test."""
     pos, mass, eps = K1_CASES[name]()
     tol = 1e-4
     t = oracle.Tree(pos, mass)
-    t.softening("k1", eps)
+    t.softening(soft, eps)
     t.moments(p)
     t.traverse(tol)
     ra, rp = t.force(1.0, eps)
     cl = t.cells()
     for prec in ("fp64", "mixed"):
-        h, P, M = build(pos, mass, p=p, tol=tol, eps=eps, precision=prec, softening="k1")
+        h, P, M = build(pos, mass, p=p, tol=tol, eps=eps, precision=prec, softening=soft)
         h.compute_moments(p)
         h.traverse(tol)
         assert lists_match(h, t, cl) == 0
@@ -270,6 +272,38 @@ def test_k1_lists_and_forces(name, p):
             assert np.sqrt(np.mean(rel ** 2)) < 1e-5, np.sqrt(np.mean(rel ** 2))
             assert rel.max() < 1e-3, rel.max()
             assert prel.max() < 1e-4, prel.max()
+
+
+@pytest.mark.parametrize("soft", ["k1", "spline"])
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_compact_pair_functions(soft, prec, bound):
+    """The device pair functions against the oracle's at 400 separations from 0 to 1.5 eps
+    (both branches of the spline, the edge, the Newtonian range): a unit mass at the origin
+    and massless-in-effect probes (mass 1e-30) around it, one group, every interaction P2P,
+    so each probe's acceleration is f(r) d and its potential -psi(r) to within 1e-30."""
+    eps = 0.01
+    n = 400
+    rng = np.random.default_rng(17)
+    r = np.linspace(0.0, 1.5 * eps, n + 1)[1:]
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pos = np.concatenate([np.zeros((1, 3)), r[:, None] * d])
+    mass = np.concatenate([[1.0], np.full(n, 1e-30)])
+    h = hot.Hot(p=4, tol=1e-4, eps=eps, precision=prec, softening=soft, group_max=512, leaf_max=512)
+    P = torch.tensor(pos, device=dev())
+    M = torch.tensor(mass, device=dev())
+    acc = torch.empty_like(P)
+    pot = torch.empty_like(M)
+    h.force(P, M, acc, pot)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy()[1:]
+    ph = pot.cpu().numpy()[1:]
+    ref = np.array([oracle.soft_kernel(soft, eps, x) for x in r])
+    f_ref, psi_ref = ref[:, 0], ref[:, 2]
+    # a = f(r) (0 - x) = -f(r) r d
+    f_got = -np.sum(a * d, axis=1) / r
+    assert np.max(np.abs(f_got - f_ref) / f_ref) < bound
+    assert np.max(np.abs(-ph - psi_ref) / psi_ref) < bound
 
 
 def test_k1_differs_from_plummer_and_changing_it_recomputes():

@@ -1,10 +1,15 @@
-"""GPU parity at the benchmark's full sizes, on sampled outputs.
+"""GPU parity at the benchmark's full sizes.
 
-The CUDA path runs the whole workload in the launch configuration the benchmark times
-(default tree sizes, one context per precision); the oracle builds the same tree (its
-topology and groups are bit-identical, checked here on the group cells) but traverses
-and evaluates only a seeded sample of sink groups, whose sinks' forces it computes one
-group at a time.  Compared on those sinks: the FP64 path to 1e-11 relative, the mixed
+Bit-exact on every element: the key frame, the sorted keys, the sort permutation, every
+cell array (key, level, first slot, count, parent, child count) and the sink groups with
+their centres and extents, at 2^20 (clustered), 128^3 and 256^3 (lattices) -- the radix
+sort's multi-tile scans and the tree builder's long runs at the sizes the benchmark
+times.
+
+Forces on sampled outputs: the CUDA path runs the whole workload in the launch
+configuration the benchmark times (default tree sizes, one context per precision); the
+oracle builds the same tree but traverses and evaluates only a seeded sample of sink
+groups, whose sinks' forces it computes one group at a time.  Compared on those sinks: the FP64 path to 1e-11 relative, the mixed
 path to 1e-5 rms / 1e-3 max relative (acceleration) and 1e-4 max relative (potential),
 the tolerances of the small-size parity tests.
 
@@ -58,10 +63,46 @@ def sinks_of(t, gs):
     return np.concatenate(idx)
 
 
+@pytest.mark.parametrize("name", ["clustered20", "zeldovich128", "zeldovich256"])
+def test_full_size_tree_bit_exact(name):
+    w, t = workload(name)
+    dev = torch.device("cuda:0")
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed")
+    h.build_tree(P, M)
+    lo, L = t.frame()
+    fr = h.debug_get("FRAME")
+    assert np.array_equal(fr[:3], lo) and fr[3] == L
+    k, perm = t.keys()
+    assert np.array_equal(h.debug_get("PERM").astype(np.int64), perm)
+    assert np.array_equal(h.debug_get("SORTED_KEYS"), k[perm])
+    del k, perm
+    cl = t.cells()
+    assert h.sizes()["ncell"] == len(cl["key"])
+    assert np.array_equal(h.debug_get("CELL_KEY"), cl["key"])
+    assert np.array_equal(h.debug_get("CELL_LEVEL"), cl["level"])
+    assert np.array_equal(h.debug_get("CELL_BEGIN").astype(np.int64), cl["begin"])
+    assert np.array_equal(h.debug_get("CELL_COUNT").astype(np.int64), cl["count"])
+    assert np.array_equal(h.debug_get("CELL_PARENT"), cl["parent"])
+    assert np.array_equal(h.debug_get("CELL_NCHILD"), cl["nchild"])
+    g = t.groups()
+    assert np.array_equal(h.debug_get("GROUP_CELL"), g["cell"])
+    assert np.array_equal(h.debug_get("GROUP_CENTRE"), g["centre"])
+    assert np.array_equal(h.debug_get("GROUP_DMAX"), g["dmax"])
+    # every cell key is found by the hash table at its own index
+    keys = h.debug_get("CELL_KEY")
+    assert np.array_equal(h.lookup(keys), np.arange(len(keys), dtype=np.int32))
+    h.close()
+    del P, M
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("name,p,precisions,opts", [
     ("clustered20", 4, ("mixed", "fp64"), {}),
     ("clustered20", 6, ("mixed", "fp64"), {}),
     ("clustered20", 4, ("mixed", "fp64"), {"softening": "k1"}),
+    ("clustered20", 4, ("mixed", "fp64"), {"softening": "spline"}),
     ("clustered20", 8, ("mixed", "fp64"), {"p_min": 0}),
     ("zeldovich128", 6, ("mixed", "fp64"), {}),
     ("zeldovich256", 6, ("mixed",), {}),
