@@ -301,6 +301,13 @@ class BackgroundTree:
                         if not inside:
                             empty_octants(c)
                     continue
+                if gc < c < self.cend[gc]:  # inside the group's cell: d <= 0, never expanded
+                    if leaf:
+                        p2p(c)
+                        rec.add(("p", int(c)))
+                    else:
+                        stack.extend(self.children[c])
+                    continue
                 if inside:  # the plain method: matter about the centre of mass
                     d = float(np.linalg.norm(self.com[c] - gcen)) - dmax
                     b = self.bmax[c]

@@ -890,8 +890,21 @@ static int ancestor_or_self(const orc_tree *t, int64_t c, int64_t gc)
     return (t->ckey[gc] >> (3 * dl)) == t->ckey[c];
 }
 
+/* Is cell c inside the group's cell (a proper descendant)?  Its particles are all sinks
+ * of the group, within Delta_max of g, so its centre of mass is too: d <= 0, never
+ * accepted.  Taken by this rule rather than by the rounded d, which can come out a unit in
+ * the last place above 0 for a one-particle leaf at the group's farthest point (and would
+ * then make that sink meet itself through the expansion). */
+static int inside_group(const orc_tree *t, int64_t c, int64_t gc)
+{
+    int dl = t->clevel[c] - t->clevel[gc];
+    if (dl <= 0) return 0;
+    return (t->ckey[c] >> (3 * dl)) == t->ckey[gc];
+}
+
 /* Traversal for one group, depth first from cell c, children in ascending octant:
  *   ancestor-or-self of the group -> descend (a leaf here is the group itself -> P2P)
+ *   inside the group's cell -> descend, a leaf -> P2P (d <= 0)
  *   otherwise d = |z_c - g| - Delta_max;
  *     d > b_max and E(d) <= tol -> M2P
  *     else leaf                 -> P2P
@@ -911,7 +924,7 @@ static void push_p2p(orc_tree *t, int64_t g, int64_t c, int img)
 static void trav_rec(orc_tree *t, int64_t g, int64_t c, int img)
 {
     int64_t gc = t->gcell[g];
-    if (img == per_central(t) && ancestor_or_self(t, c, gc)) {
+    if (img == per_central(t) && (ancestor_or_self(t, c, gc) || inside_group(t, c, gc))) {
         if (is_leaf(t, c))
             push_p2p(t, g, c, img);
         else

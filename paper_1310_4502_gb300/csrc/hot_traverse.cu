@@ -47,10 +47,13 @@ __device__ __forceinline__ void mac_log_newton(double d, double b, double B1, do
 
 // Acceptance radius of every cell for the tolerance: E is strictly decreasing on
 // (b_max, inf), so "d > b_max and E(d) <= tol" is "d >= r_c" with E(r_c) = tol.  A
-// bracket [lo, hi] with E(lo) > tol >= E(hi) is found by doubling, then Newton steps
-// in ln d on ln E - ln tol (which is nearly linear in ln d), falling back to bisection
-// whenever a step leaves the bracket, until a step or the bracket is below 1e-13
-// relative (r_c = 0 when b_max = 0, where E vanishes).  That accuracy is far inside the
+// bracket [lo, hi] with E(lo) > tol >= E(hi) is found around the far-field estimate
+// d0 = (G (p+2) B_{p+1} / tol)^(1/(p+3)) (the leading term of E), by doubling up or
+// halving down from it (one or two evaluations of E on most cells, where doubling up
+// from b_max took log2(r_c / b_max)), then Newton steps in ln d on ln E - ln tol (which
+// is nearly linear in ln d), falling back to bisection whenever a step leaves the
+// bracket, until a step or the bracket is below 1e-13 relative (r_c = 0 when b_max = 0,
+// where E vanishes).  That accuracy is far inside the
 // 1e-9 band in which the traversal re-takes decisions with the bound itself.
 // guard > 0 (K1 smoothing, guard = eps) also requires d >= b_max + guard, so that every
 // source of an accepted cell is at least eps from every sink: r_c = max(r_c, b_max + guard)
@@ -59,12 +62,29 @@ __device__ double mac_radius_solve(double b, double B1, double B2, int p, double
 {
     double rc = 0.0;
     if (b > 0.0) {
-        double lo = b, hi = 2.0 * b;
+        double d0 = pow(G * (p + 2) * B1 / tol, 1.0 / (p + 3));
+        if (!(d0 > 1.0001 * b)) d0 = 2.0 * b;  // also for a non-finite estimate
+        double lo = b, hi = d0;
         int k = 0;
-        while (!(mac_bound(hi, b, B1, B2, p, G) <= tol) && k < 1100) {
-            lo = hi;
-            hi *= 2.0;
-            ++k;
+        if (mac_bound(d0, b, B1, B2, p, G) <= tol) {
+            // halve down towards b while the bound still holds
+            while (k < 1100) {
+                const double t = 0.5 * hi;
+                if (!(t > b) || !(mac_bound(t, b, B1, B2, p, G) <= tol)) {
+                    lo = t > b ? t : b;
+                    break;
+                }
+                hi = t;
+                ++k;
+            }
+        } else {
+            lo = d0;
+            hi = 2.0 * d0;
+            while (!(mac_bound(hi, b, B1, B2, p, G) <= tol) && k < 1100) {
+                lo = hi;
+                hi *= 2.0;
+                ++k;
+            }
         }
         if (k >= 1100) {
             rc = INFINITY;
@@ -176,6 +196,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
+        const int32_t gend = cend[gc];
         const double gx0 = gcen[3 * g + 0], gy0 = gcen[3 * g + 1], gz0 = gcen[3 * g + 2];
         const double dmax = gdmax[g];
         const float dmaxf = (float)dmax;
@@ -217,9 +238,11 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 int kind = 0;  // 1 M2P, 2 P2P, 3 open
                 if (c >= 0) {
                     const bool leaf = cnchild[c] == 0;
-                    // pre-order: c is the group's cell or an ancestor iff gc lies in c's subtree
-                    // (in the central tree; in an image every cell is a source)
-                    const bool anc = central && c <= gc && gc < cend[c];
+                    // pre-order: c is the group's cell or an ancestor iff gc lies in c's subtree,
+                    // inside the group's cell iff it lies in gc's subtree (its particles are sinks
+                    // of the group: d <= 0, never accepted, whatever the rounding of d); in the
+                    // central tree only, in an image every cell is a source
+                    const bool anc = central && ((c <= gc && gc < cend[c]) || (gc < c && c < gend));
                     if (anc) {
                         kind = leaf ? 2 : 3;
                     } else {
@@ -379,18 +402,35 @@ __device__ __forceinline__ double bg_bound(double d, double b, double Q1, double
     return __dmul_rn(__ddiv_rn(G, __dmul_rn(q, q)), __dadd_rn(t1, t2));
 }
 
-// The radius of E(d) = tol: a doubling bracket, then Newton steps in ln d with bisection
-// as the safeguard (as for the plain bound); b when E vanishes (a contrast with no omitted
-// multipole: accepted as soon as d > b).
+// The radius of E(d) = tol: a bracket around the larger of the two terms' far-field
+// radii, then Newton steps in ln d with bisection as the safeguard (as for the plain
+// bound); b when E vanishes (a contrast with no omitted multipole: accepted as soon as
+// d > b).
 __device__ double bg_radius_solve(double b, double Q1, double Q2, int p, double G, double tol)
 {
     if (!(Q1 > 0.0 || Q2 > 0.0)) return b;
-    double lo = b, hi = 2.0 * b;
+    double d0 = fmax(pow(G * (p + 2) * Q1 / tol, 1.0 / (p + 3)), pow(G * (p + 3) * Q2 / tol, 1.0 / (p + 4)));
+    if (!(d0 > 1.0001 * b)) d0 = 2.0 * b;
+    double lo = b, hi = d0;
     int k = 0;
-    while (!(bg_bound(hi, b, Q1, Q2, p, G) <= tol) && k < 1100) {
-        lo = hi;
-        hi *= 2.0;
-        ++k;
+    if (bg_bound(d0, b, Q1, Q2, p, G) <= tol) {
+        while (k < 1100) {
+            const double t = 0.5 * hi;
+            if (!(t > b) || !(bg_bound(t, b, Q1, Q2, p, G) <= tol)) {
+                lo = t > b ? t : b;
+                break;
+            }
+            hi = t;
+            ++k;
+        }
+    } else {
+        lo = d0;
+        hi = 2.0 * d0;
+        while (!(bg_bound(hi, b, Q1, Q2, p, G) <= tol) && k < 1100) {
+            lo = hi;
+            hi *= 2.0;
+            ++k;
+        }
     }
     if (k >= 1100) return INFINITY;
     const double ltol = log(tol);
@@ -507,6 +547,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
         const int64_t g = __shfl_sync(0xffffffffu, g0, 0);
         if (g >= ngroup) break;
         const int32_t gc = gcell[g];
+        const int32_t gend = cend[gc];
         const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
         const double dmax = gdmax[g];
         int32_t S = gc;
@@ -534,6 +575,10 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
                         pp = leaf;
                         open = !leaf;
                         empt = !leaf && !inS;
+                    } else if (gc < c && c < gend) {
+                        // inside the group's cell: d <= 0, never expanded (inside S)
+                        pp = leaf;
+                        open = !leaf;
                     } else if (inS) {
                         if (plain_accept(tcell[c], cbmax[c], cB1[c], cB2[c], gx, gy, gz, dmax, p, G, tol))
                             em = c;

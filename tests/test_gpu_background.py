@@ -51,8 +51,30 @@ def reference(name):
         bt = BG.BackgroundTree(x, m, p=P, leaf_max=lm, group_max=gm, up=up)
         a, ph, cnt = bt.force(TOL, 1.0, eps, record=True)
         full, fullp = oracle.direct(x, m, 1.0, eps)
-        _ref[name] = (x, m, lm, gm, up, eps, a, ph, cnt, bt.lists, bt.surround.copy(), full, fullp)
+        _ref[name] = (x, m, lm, gm, up, eps, a, ph, cnt, bt, full, fullp)
     return _ref[name]
+
+
+def borderline(bt, g, c):
+    """Whether the test of leaf c for group g lies at its threshold within rounding: d
+    within 1e-12 of b relative to the distances d was formed from (|z - g| and Delta_max),
+    or E within 1e-9 of tol, by the oracle's own numbers (the matter test inside the
+    surrounding cube, the contrast test outside it).  Such decisions may differ between
+    two correct evaluations (a norm rounded differently)."""
+    S = bt.surround[g]
+    gcen, dmax = bt.gcen[g], bt.gdmax[g]
+    if S <= c < bt.cend[S]:
+        dist = float(np.linalg.norm(bt.com[c] - gcen))
+        d = dist - dmax
+        b = bt.bmax[c]
+        E = oracle.mac_bound(d, b, bt.B1[c], bt.B2[c], P) if d > b else np.inf
+    else:
+        dist = float(np.linalg.norm(bt.centre[c] - gcen))
+        d = dist - dmax
+        b = 0.5 * np.sqrt(3.0) * bt.side[c]
+        E = (1.0 / (1.0 - b / d) ** 2 * ((P + 2) * bt.cQ[c][0] / d ** (P + 3) + (P + 3) * bt.cQ[c][1] / d ** (P + 4))
+             if d > b else np.inf)
+    return abs(d - b) <= 1e-12 * max(dist, dmax) or abs(E / TOL - 1.0) <= 1e-9
 
 
 def gpu_lists(h):
@@ -83,7 +105,8 @@ def gpu_lists(h):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_background_lists_counts_and_forces(name):
-    x, m, lm, gm, up, eps, ra, rp, cnt, rl, rS, full, fullp = reference(name)
+    x, m, lm, gm, up, eps, ra, rp, cnt, bt, full, fullp = reference(name)
+    rl, rS = bt.lists, bt.surround
     dev = torch.device("cuda:0")
     P_ = torch.tensor(x, device=dev)
     M_ = torch.tensor(m, device=dev)
@@ -98,11 +121,22 @@ def test_background_lists_counts_and_forces(name):
         assert np.array_equal(h.debug_get("BG_GROUP_S"), rS)
         gl = gpu_lists(h)
         assert len(gl) == len(rl)
-        bad = [g for g in range(len(gl)) if gl[g] != rl[g]]
-        assert not bad, (prec, len(bad), sorted(gl[bad[0]] ^ rl[bad[0]])[:10])
+        # differences only where a leaf's test sits at its threshold: the same leaf taken
+        # whole on one side and particle by particle on the other
+        flips = 0
+        for g in range(len(gl)):
+            d = gl[g] ^ rl[g]
+            if not d:
+                continue
+            leaves = {e[1] for e in d}
+            assert all(e[0] in ("m", "c", "p", "b") for e in d), (prec, g, sorted(d))
+            assert all(borderline(bt, g, c) for c in leaves), (prec, g, sorted(d))
+            flips += 1
+        assert flips <= 2, (prec, flips)
         bs = h.bg_sizes()
-        assert bs["m2p_contrast"] == cnt["m2p_contrast"] and bs["m2p_empty"] == cnt["m2p_empty"]
-        assert bs["m2p_matter"] == cnt["m2p_matter"] and bs["cube_evals"] == cnt["cube_fields"]
+        if flips == 0:
+            assert bs["m2p_contrast"] == cnt["m2p_contrast"] and bs["m2p_empty"] == cnt["m2p_empty"]
+            assert bs["m2p_matter"] == cnt["m2p_matter"] and bs["cube_evals"] == cnt["cube_fields"]
         a = acc.cpu().numpy()
         ph = pot.cpu().numpy()
         ea = np.linalg.norm(a - ra, axis=1) / scale_a
