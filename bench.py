@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clustered20")
+    ap.add_argument("--p", type=int, default=None, help="expansion order of the timed step (default: the workload's)")
+    ap.add_argument("--background", action="store_true",
+                    help="background subtraction in the timed step (surrounding cube two levels up)")
+    ap.add_argument("--p-min", type=int, default=None,
+                    help="per-interaction order selection over [p_min, p] in the timed step (default: off)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / p=6 / error legs")
     ap.add_argument("--no-leapfrog", action="store_true", help="skip the 8-step leapfrog forward+backward leg")
@@ -374,6 +379,59 @@ def lattice_leg(dev, stream, flush, K, with_cpu, wname="zeldovich128"):
     return out
 
 
+def background_leg(wname, dev, stream, flush, K, with_cpu, up=2):
+    """Background subtraction (Sec. "Background Subtraction") on a Zel'dovich lattice at
+    its workload's order, mixed precision, beside the plain method on the same particles:
+    step times, stage times and interaction counts of both; with the CPU leg, the error
+    of each against its own exact quantity on a seeded 4096-particle subsample (the plain
+    method: the FP64 direct sum; background subtraction: the direct sum less the field of
+    the uniform density over the root cube, the oracle's closed form)."""
+    import torch
+    from paper_1310_4502_gb300 import hot
+    w = W.make(wname)
+    P = torch.tensor(w.pos, device=dev)
+    M = torch.tensor(w.mass, device=dev)
+    acc = torch.empty_like(P)
+    out = {"workload": describe(w) + f"; background subtraction with the surrounding cube {up} levels up",
+           "N": w.n, "p": w.p, "steps": K}
+    accs = {}
+    for name, kw in (("plain", {}), ("background", {"background": True, "bg_up": up})):
+        h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed", **kw)
+        for _ in range(2):
+            h.force(P, M, acc)
+        tot, st = 0.0, {}
+        for _ in range(K):
+            tot += _ev_ms(stream, lambda: h.force(P, M, acc), flush)[0]
+            for k, v in h.stage_times().items():
+                st[k] = st.get(k, 0.0) + v / K
+        st.pop("adjoint", None)
+        sz = h.sizes()
+        r = {"ms_per_step": tot / K, "value": w.n / (tot / K * 1e-3), "unit": "particles/s", "stages_ms": st,
+             "m2p_interactions": sz["n_m2p_int"], "p2p_interactions": sz["n_pairs"]}
+        if kw:
+            r.update({k: v for k, v in h.bg_sizes().items()})
+        out[name] = r
+        accs[name] = acc.cpu().numpy()
+        del h
+    out["interactions_ratio"] = ((out["background"]["m2p_interactions"] + out["background"]["p2p_interactions"])
+                                 / (out["plain"]["m2p_interactions"] + out["plain"]["p2p_interactions"]))
+    out["step_ratio"] = out["background"]["ms_per_step"] / out["plain"]["ms_per_step"]
+    if with_cpu:
+        import oracle
+        from oracle import background as BG
+        sub = np.sort(np.random.default_rng(3).choice(w.n, 4096, replace=False))
+        ref, _ = oracle.direct(w.pos, w.mass, 1.0, w.eps, sinks=sub)
+        lo, L = oracle.bbox(w.pos)
+        fa, _ = BG.box_field(w.pos[sub], lo, lo + L, -float(w.mass.sum()) / L ** 3, 1.0)
+        for name, exact in (("plain", ref), ("background", ref + fa)):
+            e = np.linalg.norm(accs[name][sub] - exact, axis=1)
+            out[name]["rms_abs_err_4096"] = float(np.sqrt(np.mean(e ** 2)))
+            out[name]["max_abs_err_4096"] = float(e.max())
+        out["contrast_field_rms_4096"] = float(np.sqrt(np.mean(np.sum((ref + fa) ** 2, 1))))
+        out["full_field_rms_4096"] = float(np.sqrt(np.mean(np.sum(ref ** 2, 1))))
+    return out
+
+
 def plummer_leg(dev, stream, K):
     """The small configuration: Plummer sphere N = 4096 (eps = 0.01, p = 4, tol = 1e-4), FP64
     throughout; step time, the error against the FP64 direct sum, and the radial
@@ -445,6 +503,8 @@ def run_ours(args):
     dev = torch.device("cuda", lr)
     torch.cuda.set_device(dev)
     w = W.make(args.workload)
+    if args.p is not None:
+        w.p = args.p
     N = w.n
     periodic = args.boundary == "periodic"
     if periodic:
@@ -456,7 +516,9 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     bkw = dict(box=1.0, ws=2) if periodic else {}
-    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed", **bkw)
+    if args.background:
+        bkw.update(background=True, bg_up=2)
+    h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed", p_min=args.p_min, **bkw)
 
     def step(ctx, p):
         ctx.build_tree(P, M)
@@ -551,7 +613,7 @@ def run_ours(args):
            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "hbm_stages": hbm_stages,
            "fp64_peak_tflops_measured": fma64}
 
-    if not periodic:
+    if not periodic and w.p <= 6 and args.p_min is None and not args.background:  # the adjoint's scope
         out["adjoint"] = adjoint_leg(h, lambda: step(h, w.p), N, dev, args.steps, flush, stream)
         out["adjoint"]["workload"] = describe(w)
 
@@ -695,6 +757,9 @@ def run_ours(args):
         del hd
         out["lattice128"] = lattice_leg(dev, stream, flush, min(args.steps, 10), rank == 0 and not args.no_cpu)
         out["sort256"] = build_leg("zeldovich256", dev, stream, flush, min(args.steps, 10))
+        out["background128"] = background_leg("zeldovich128", dev, stream, flush, min(args.steps, 10),
+                                               rank == 0 and not args.no_cpu)
+        out["background256"] = background_leg("zeldovich256", dev, stream, flush, min(args.steps, 3), False)
         out["plummer4096_fp64"] = plummer_leg(dev, stream, min(args.steps, 10))
     if not args.no_leapfrog:
         out["leapfrog"] = leapfrog_leg(args.leapfrog_workload, dev, stream)

@@ -233,7 +233,8 @@ def _eval_stmts(p, tangent=False):
     L = ["rx *= is; ry *= is; rz *= is;"]
     if tangent:
         L.append("const T drx = ux * is, dry = uy * is, drz = uz * is;")
-    L.append("const T u = rx * rx + ry * ry + rz * rz + e2;")
+    # from e2 up, so that the sum is three fused multiply-adds
+    L.append("const T u = e2 + rx * rx + ry * ry + rz * rz;")
     if tangent:
         L.append("const T du = T(2) * (rx * drx + ry * dry + rz * drz);")
     L.append("const T rho = hot_rsqrt(u);")
@@ -290,14 +291,19 @@ def _eval_stmts(p, tangent=False):
             if tangent:
                 L.append(f"const T dGs{d} = T(0);")
     L.append("phi -= rho * S;")
-    L.append("const T rs = rho * is;")
     if tangent:
+        L.append("const T rs = rho * is;")
         L.append("const T drs = drho * is;")
-    for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
-        L.append(f"{an} += rs * (w * Gs{d} - {yn} * Q);")
-        if tangent:
+        for d, (yn, an) in enumerate(((mname((1,0,0)), "ax"), (mname((0,1,0)), "ay"), (mname((0,0,1)), "az"))):
+            L.append(f"{an} += rs * (w * Gs{d} - {yn} * Q);")
             L.append(f"d{an} += drs * (w * Gs{d} - {yn} * Q) + rs * (dw * Gs{d} + w * dGs{d} - d{yn} * Q - "
                      f"{yn} * dQ);")
+    else:
+        # w Gs - y Q = w (Gs - R Q) (y = R w): the common factor rho inv_s w once, then two
+        # fused multiply-adds per component
+        L.append("const T rsw = rho * is * w;")
+        for d, (rn, an) in enumerate((("rx", "ax"), ("ry", "ay"), ("rz", "az"))):
+            L.append(f"{an} += rsw * (Gs{d} - {rn} * Q);")
     return L, M2P_FLOP_CONVENTION[p]
 
 

@@ -354,6 +354,7 @@ void hot_destroy(hot_ctx *c)
     c->idx2.release(s); c->hist.release(s); c->histoff.release(s); c->scan_tmp.release(s); c->spos.release(s);
     c->rs_bhist.release(s); c->rs_goff.release(s); c->rs_ctr.release(s); c->rs_status.release(s);
     c->bg_cen.release(s); c->bg_half.release(s); c->bg_q.release(s); c->bg_mom.release(s); c->bg_rho.release(s);
+    c->bg_tab.release(s);
     c->bg_ecnt.release(s); c->bg_eoff.release(s); c->bg_eparent.release(s); c->bg_eoct.release(s);
     c->bg_tc.release(s); c->cnt_box.release(s); c->off_box.release(s); c->l_box.release(s); c->bg_gS.release(s);
     c->smass.release(s); c->lcp.release(s); c->leaflev.release(s); c->ncell_i.release(s); c->cell_off.release(s);

@@ -23,22 +23,65 @@ constexpr int BT = 256;
 // ---------------------------------------------------------------------------
 // Bounding cube
 // ---------------------------------------------------------------------------
+// The minimum and maximum of doubles are exact, so they are taken on integer images of
+// the bit patterns that order as the values do (sign bit set: all bits flipped; clear:
+// the sign bit set) -- integer compares instead of the float64 pipe, which on this part
+// runs at a sixty-fourth of the float32 rate.  The check for non-finite values and
+// non-positive masses is a test of the exponent and sign bits.
+__device__ __forceinline__ unsigned long long ord_image(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_value(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+__device__ __forceinline__ bool bits_finite(unsigned long long u)
+{
+    return (u & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 __global__ void k_bbox_part(const double *__restrict__ pos, const double *__restrict__ mass,
                             int64_t N, double *__restrict__ part, unsigned *status)
 {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long lk[3] = {~0ull, ~0ull, ~0ull}, hk[3] = {0ull, 0ull, 0ull};
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double m = mass[i];
-        bad |= !(isfinite(m) && m > 0.0);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        // four particles per thread in flight
+        unsigned long long mu[4], xu[4][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double x = pos[3 * i + d];
-            bad |= !isfinite(x);
-            lo[d] = fmin(lo[d], x);
-            hi[d] = fmax(hi[d], x);
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + q * stride;
+            const bool v = i < N;
+            mu[q] = v ? (unsigned long long)__double_as_longlong(mass[i]) : 0x3ff0000000000000ull;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                xu[q][d] = v ? (unsigned long long)__double_as_longlong(pos[3 * i + d]) : 0ull;
+            if (!v) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) xu[q][d] = (unsigned long long)__double_as_longlong(pos[3 * i0 + d]);
+            }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // mass: finite, not negative, not zero (+0 and -0 alike)
+            bad |= !bits_finite(mu[q]) || (mu[q] >> 63) || (mu[q] << 1) == 0ull;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                bad |= !bits_finite(xu[q][d]);
+                const unsigned long long k = ord_image(__longlong_as_double((long long)xu[q][d]));
+                lk[d] = k < lk[d] ? k : lk[d];
+                hk[d] = k > hk[d] ? k : hk[d];
+            }
+        }
+    }
+    double lo[3], hi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = lk[d] == ~0ull ? INFINITY : ord_value(lk[d]);
+        hi[d] = hk[d] == 0ull ? -INFINITY : ord_value(hk[d]);
     }
     if (__any_sync(0xffffffffu, bad) && lane_id() == 0) hot_flag(status, HOT_ST_INPUT);
     __shared__ double sh[BT / 32][6];
@@ -103,9 +146,10 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
 
 __device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
 {
-    double t = __dmul_rn(__dsub_rn(x, lo), s);  // one subtract, one multiply, no contraction
-    double f = floor(t);
-    uint64_t c = (f <= 0.0) ? 0ull : (uint64_t)f;
+    const double t = __dmul_rn(__dsub_rn(x, lo), s);  // one subtract, one multiply, no contraction
+    // floor(t) for t >= 0, 0 below: the conversion rounding towards minus infinity, which
+    // saturates negative values to 0
+    const uint64_t c = __double2ull_rd(t);
     return c > 2097151ull ? 2097151ull : c;
 }
 
@@ -195,7 +239,8 @@ __global__ void __launch_bounds__(RS_W * 32) k_rs_scatter(
 // ---------------------------------------------------------------------------
 // The particle keys' sort: eight LSD passes of 8 bits, one launch each.
 //   * k_keys_hist computes the keys and, in the same pass, the digit histograms of all
-//     eight passes (one per block, warp-aggregated with __match_any_sync);
+//     eight passes (one per block in shared memory; a warp whose keys share a digit adds
+//     them at once);
 //   * k_rs_goff reduces the block histograms and scans them into each pass's global
 //     digit offsets;
 //   * k_rs_pass ranks a tile of OS_TILE keys by digit in shared memory (stable: warp w
@@ -203,8 +248,10 @@ __global__ void __launch_bounds__(RS_W * 32) k_rs_scatter(
 //     lane order), publishes the tile's digit counts, and finds how many keys of each
 //     digit the earlier tiles hold by a decoupled look-back over their published counts
 //     (a tile publishes its own counts before it looks back, and tiles are numbered in
-//     the order their blocks start, so every wait ends); it then writes its keys in
-//     digit order, so that each digit's run leaves as contiguous stores.
+//     the order their blocks start, so every wait ends), reading OS_LB earlier tiles'
+//     words at a time, since hundreds of tiles run at once and a walk one word at a time
+//     would be a chain of that many dependent reads; it then writes its keys in digit
+//     order, so that each digit's run leaves as contiguous stores.
 // A published word is epoch << 40 | flag << 38 | count: flag 1 = this tile's count, 2 =
 // the count of this tile and all before it; a word of another epoch is not yet written.
 // ---------------------------------------------------------------------------
@@ -214,6 +261,7 @@ constexpr int OS_TILE = OS_W * OS_R * 32;  // keys per tile
 constexpr int OS_SMEM = OS_W * 256 * 4 + OS_TILE * 8 + OS_TILE * 4 + 2 * 256 * 4;
 constexpr unsigned long long OS_FLAG_AGG = 1ull, OS_FLAG_INC = 2ull;
 constexpr long OS_POLL_LIMIT = 1l << 20;  // polls of one published word before giving up
+constexpr int OS_LB = 16;                  // earlier tiles' words read together in the look-back
 
 __device__ __forceinline__ unsigned long long os_pack(uint32_t epoch, unsigned long long flag, uint64_t cnt)
 {
@@ -242,11 +290,18 @@ __global__ void __launch_bounds__(256) k_keys_hist(const double *__restrict__ po
             key[i] = k;
             idx[i] = (uint32_t)i;
         }
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
+            // a warp whose keys share the digit (the high digits of spatially ordered input)
+            // adds once; otherwise every lane adds its own
             const unsigned d = valid ? (unsigned)(k >> (8 * p)) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[p][d], (unsigned)__popc(peers));
+            const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, d == d0 || !valid)) {
+                if (lane == 0) atomicAdd(&h[p][d0], (unsigned)__popc(vm));
+            } else if (valid) {
+                atomicAdd(&h[p][d], 1u);
+            }
         }
     }
     __syncthreads();
@@ -292,12 +347,19 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
     uint64_t kk[OS_R];
     uint32_t vv[OS_R];
     uint32_t rk[OS_R];
+    // every load of the tile first, so that they are all in flight together (the ranking
+    // below orders its rounds through shared memory)
+#pragma unroll
+    for (int r = 0; r < OS_R; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        kk[r] = i < N ? kin[i] : 0ull;
+        vv[r] = i < N ? vin[i] : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < OS_R; ++r) {
         const int64_t i = base + r * 32 + lane;
         const bool valid = i < N;
-        const uint64_t k = valid ? kin[i] : 0ull;
-        const uint32_t v = valid ? vin[i] : 0u;
+        const uint64_t k = kk[r];
         const unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned rank = __popc(peers & lt);
@@ -305,8 +367,6 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
         __syncwarp();
         if (valid && rank == 0) wcnt[w][d] = b + __popc(peers);
         __syncwarp();
-        kk[r] = k;
-        vv[r] = v;
         rk[r] = valid ? b + rank : 0xffffffffu;
     }
     __syncthreads();
@@ -325,14 +385,34 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
     } else {
         atomicExch(my, os_pack(epoch, OS_FLAG_AGG, tot));
         uint64_t excl = 0;
-        int64_t t = tile - 1;
+        int64_t t = tile - 1;  // the nearest earlier tile not yet added
         long polls = 0;
-        for (;;) {
-            const unsigned long long v = *((volatile unsigned long long *)(pub + t * 256 + d));
-            if ((uint32_t)(v >> 40) == epoch) {
-                excl += v & ((1ull << 38) - 1ull);
-                if (((v >> 38) & 3ull) == OS_FLAG_INC || t == 0) break;
-                --t;
+        bool done = false;
+        while (!done) {
+            // the words of tiles t, t-1, ..., t-OS_LB+1 (as far as tile 0), read together
+            unsigned long long v[OS_LB];
+#pragma unroll
+            for (int k = 0; k < OS_LB; ++k)
+                v[k] = t - k >= 0 ? *((volatile unsigned long long *)(pub + (t - k) * 256 + d)) : 0ull;
+            // add the words in order up to the first inclusive one, stopping at the first
+            // not yet written (unrolled and predicated, so that v stays in registers)
+            int k = 0;
+            bool stop = false;
+#pragma unroll
+            for (int q = 0; q < OS_LB; ++q) {
+                if (!stop && !done) {
+                    if (t - q < 0 || (uint32_t)(v[q] >> 40) != epoch) {
+                        stop = true;
+                    } else {
+                        excl += v[q] & ((1ull << 38) - 1ull);
+                        k = q + 1;
+                        if (((v[q] >> 38) & 3ull) == OS_FLAG_INC || t - q == 0) done = true;
+                    }
+                }
+            }
+            if (done) break;
+            if (k > 0) {
+                t -= k;  // every word read up to k was an aggregate: continue below it
                 continue;
             }
             if (++polls > OS_POLL_LIMIT) {

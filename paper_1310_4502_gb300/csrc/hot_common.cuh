@@ -170,7 +170,7 @@ struct hot_ctx {
     // and octant numbers, the cells' moments about their cube centres to order p + 2 (then
     // their contrast), the mean density, and per tolerance each cube's acceptance record
     int64_t n_empty = 0;
-    DBuf<double> bg_cen, bg_half, bg_q, bg_mom, bg_rho;
+    DBuf<double> bg_cen, bg_half, bg_q, bg_mom, bg_rho, bg_tab;
     DBuf<uint32_t> bg_ecnt, bg_eoff;
     DBuf<int32_t> bg_eparent, bg_eoct;
     DBuf<TCell> bg_tc;

@@ -351,6 +351,11 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                                          int sj, int nsplit, bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
 {
     constexpr int RL = Cfg<P, T>::RL;
+    // float32 forces with Plummer smoothing: the sources of a batch without self or zero-
+    // distance pairs are evaluated two per instruction (paired float32 arithmetic), from a
+    // staging layout in which one 16-byte load holds the x and y of two sources and the
+    // next their z and masses
+    constexpr bool PAIRED = sizeof(T) == 4 && MODE == 0 && SOFT == HOT_SOFT_PLUMMER;
     const unsigned lane = lane_id();
     int fill = 0;
     SoftConst<T> kc{};
@@ -432,10 +437,54 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 }
             }
             };
-            if (checked)
-                sweep(std::true_type{});
-            else
-                sweep(std::false_type{});
+            if constexpr (PAIRED) {
+                if (!checked) {
+                    // pairs of sources (2j, 2j + 1); an odd batch ends with a massless source
+                    const int npair = (fill + 1) >> 1;
+                    const float4 *s2 = reinterpret_cast<const float4 *>(&sm.src[0][0]);
+                    const float2 e22 = make_float2(eps2, eps2), neg1 = make_float2(-1.f, -1.f);
+                    float2 nx[NS][3], ax2[NS], ay2[NS], az2[NS], ph2[NS];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) nx[s][d] = make_float2(-x[s][d], -x[s][d]);
+                        ax2[s] = ay2[s] = az2[s] = ph2[s] = make_float2(0.f, 0.f);
+                    }
+#pragma unroll 2
+                    for (int j = sj; j < npair; j += nsplit) {
+                        const float4 a = s2[2 * j], b = s2[2 * j + 1];
+                        const float2 px = make_float2(a.x, a.y), py = make_float2(a.z, a.w);
+                        const float2 pz = make_float2(b.x, b.y), pm = make_float2(b.z, b.w);
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) {
+                            const float2 dx = __fadd2_rn(px, nx[s][0]), dy = __fadd2_rn(py, nx[s][1]),
+                                         dz = __fadd2_rn(pz, nx[s][2]);
+                            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22)));
+                            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                            const float2 mr = __fmul2_rn(pm, ri);
+                            const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+                            ax2[s] = __ffma2_rn(mr3, dx, ax2[s]);
+                            ay2[s] = __ffma2_rn(mr3, dy, ay2[s]);
+                            az2[s] = __ffma2_rn(mr3, dz, az2[s]);
+                            ph2[s] = __ffma2_rn(mr, neg1, ph2[s]);
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        ax[s] = ax2[s].x + ax2[s].y;
+                        ay[s] = ay2[s].x + ay2[s].y;
+                        az[s] = az2[s].x + az2[s].y;
+                        ph[s] = ph2[s].x + ph2[s].y;
+                    }
+                } else {
+                    sweep(std::true_type{});
+                }
+            } else {
+                if (checked)
+                    sweep(std::true_type{});
+                else
+                    sweep(std::false_type{});
+            }
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if constexpr (MODE == 0) {
@@ -516,10 +565,19 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 const int64_t s = (int64_t)(lbv & ~IMG_LEAF) + (t - sm.lex[lo]);
                 if constexpr (sizeof(T) == 4) {
                     const float4 v = prel[s];
-                    // one 16-byte store per source (scalar stores at a 16-byte lane stride
-                    // would meet four lanes in each bank)
-                    *reinterpret_cast<float4 *>(&sm.src[u][0]) =
-                        make_float4(v.x + sm.loff[lo][0], v.y + sm.loff[lo][1], v.z + sm.loff[lo][2], v.w);
+                    const float vx = v.x + sm.loff[lo][0], vy = v.y + sm.loff[lo][1], vz = v.z + sm.loff[lo][2];
+                    if (PAIRED && !checked) {
+                        // pair layout: source u in half u & 1 of pair u >> 1
+                        float *q = &sm.src[0][0] + 8 * (u >> 1) + (u & 1);
+                        q[0] = vx;
+                        q[2] = vy;
+                        q[4] = vz;
+                        q[6] = v.w;
+                    } else {
+                        // one 16-byte store per source (scalar stores at a 16-byte lane stride
+                        // would meet four lanes in each bank)
+                        *reinterpret_cast<float4 *>(&sm.src[u][0]) = make_float4(vx, vy, vz, v.w);
+                    }
                 } else {
                     sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx) + sm.loff[lo][0];
                     sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy) + sm.loff[lo][1];
@@ -527,6 +585,14 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     sm.src[u][3] = (T)smass[s];
                 }
                 sm.sidx[u] = (lbv & IMG_LEAF) ? -1 : (int32_t)s;
+            }
+            if constexpr (PAIRED) {
+                if (!checked && (take & 1) && lane == 0) {
+                    // the partner of the last source: massless and far away (its pair terms are 0)
+                    float *q = &sm.src[0][0] + 8 * (take >> 1) + 1;
+                    q[0] = q[2] = q[4] = 1e17f;
+                    q[6] = 0.f;
+                }
             }
             fill = take;
             flush(checked);

@@ -491,27 +491,33 @@ __global__ void k_bg_geom(const uint64_t *__restrict__ ckey, const int32_t *__re
 }
 
 // Moments of every leaf about its cube centre to order P2, one warp per leaf (lanes over
-// the components, the particles' powers staged 32 at a time).
+// the components).  Per batch of 32 particles each lane stages, for its particle, the
+// products m x^i y^j (i + j <= P2) and the powers z^k, so that every component then takes
+// one fused multiply-add per particle: sum_s (m x^i y^j)_s (z^k)_s.
+constexpr int BGW = 2;  // warps per block of k_bg_p2m (its staging is 14 KB per warp at P2 = 8)
+
 template <int P2>
-__global__ void __launch_bounds__(MW * 32) k_bg_p2m(const int32_t *__restrict__ cbegin,
-                                                    const int32_t *__restrict__ ccount,
-                                                    const int32_t *__restrict__ cnchild, int64_t ncell,
-                                                    const double *__restrict__ spos, const double *__restrict__ smass,
-                                                    const double *__restrict__ cen, double *__restrict__ mom)
+__global__ void __launch_bounds__(BGW * 32) k_bg_p2m(const int32_t *__restrict__ cbegin,
+                                                     const int32_t *__restrict__ ccount,
+                                                     const int32_t *__restrict__ cnchild, int64_t ncell,
+                                                     const double *__restrict__ spos, const double *__restrict__ smass,
+                                                     const double *__restrict__ cen, double *__restrict__ mom)
 {
     constexpr int NC = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
-    __shared__ double pw[MW][32][3][P2 + 1];
-    __shared__ double pm[MW][32];
-    __shared__ unsigned char mi[NC][3];
-    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
-        mi[k][0] = hot_midx[k][0];
-        mi[k][1] = hot_midx[k][1];
-        mi[k][2] = hot_midx[k][2];
+    constexpr int NXY = (P2 + 1) * (P2 + 2) / 2;  // pairs (i, j), i + j <= P2
+    __shared__ double pxy[BGW][NXY][33];          // [pair][particle], padded against bank conflicts
+    __shared__ double pz[BGW][P2 + 1][33];
+    __shared__ unsigned char cidx[NC][2];         // component -> (pair index, k)
+    for (int a = threadIdx.x; a < NC; a += blockDim.x) {
+        const int i = hot_midx[a][0], j = hot_midx[a][1];
+        // pairs ordered by i, then j: index of (i, j) = sum_{i' < i} (P2 + 1 - i') + j
+        cidx[a][0] = (unsigned char)(i * (P2 + 1) - i * (i - 1) / 2 + j);
+        cidx[a][1] = hot_midx[a][2];
     }
     __syncthreads();
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    for (int64_t c = (int64_t)blockIdx.x * MW + w; c < ncell; c += (int64_t)gridDim.x * MW) {
+    for (int64_t c = (int64_t)blockIdx.x * BGW + w; c < ncell; c += (int64_t)gridDim.x * BGW) {
         if (cnchild[c] != 0) continue;
         const int64_t b = cbegin[c], n = ccount[c];
         const double z[3] = {cen[3 * c + 0], cen[3 * c + 1], cen[3 * c + 2]};
@@ -521,15 +527,23 @@ __global__ void __launch_bounds__(MW * 32) k_bg_p2m(const int32_t *__restrict__ 
         for (int64_t s0 = b; s0 < b + n; s0 += 32) {
             const int64_t s = s0 + lane;
             const bool valid = s < b + n;
-            pm[w][lane] = valid ? smass[s] : 0.0;
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const double de = valid ? spos[3 * s + e] - z[e] : 0.0;
-                double v = 1.0;
-                for (int q = 0; q <= P2; ++q) {
-                    pw[w][lane][e][q] = v;
-                    v *= de;
+            const double dx = valid ? spos[3 * s + 0] - z[0] : 0.0;
+            const double dy = valid ? spos[3 * s + 1] - z[1] : 0.0;
+            const double dz = valid ? spos[3 * s + 2] - z[2] : 0.0;
+            double mx = valid ? smass[s] : 0.0;  // m x^i
+            int k = 0;
+            for (int i = 0; i <= P2; ++i) {
+                double v = mx;
+                for (int j = 0; j <= P2 - i; ++j) {
+                    pxy[w][k++][lane] = v;
+                    v *= dy;
                 }
+                mx *= dx;
+            }
+            double vz = 1.0;
+            for (int q = 0; q <= P2; ++q) {
+                pz[w][q][lane] = vz;
+                vz *= dz;
             }
             __syncwarp();
             const int cnt = (int)((b + n - s0) < 32 ? (b + n - s0) : 32);
@@ -537,9 +551,9 @@ __global__ void __launch_bounds__(MW * 32) k_bg_p2m(const int32_t *__restrict__ 
             for (int q = 0; q < (NC + 31) / 32; ++q) {
                 const int a = lane + 32 * q;
                 if (a < NC) {
-                    const int ax = mi[a][0], ay = mi[a][1], az = mi[a][2];
+                    const double *px = pxy[w][cidx[a][0]], *qz = pz[w][cidx[a][1]];
                     double t = 0.0;
-                    for (int j = 0; j < cnt; ++j) t += pm[w][j] * pw[w][j][0][ax] * pw[w][j][1][ay] * pw[w][j][2][az];
+                    for (int jj = 0; jj < cnt; ++jj) t = fma(px[jj], qz[jj], t);
                     acc[q] += t;
                 }
             }
@@ -588,51 +602,70 @@ __global__ void k_bg_efill(const int32_t *__restrict__ child8, const uint32_t *_
     }
 }
 
-// Moment a of the uniform cube of density rho and half side h about its centre:
-// rho prod_d int_{-h}^{h} t^(a_d) dt (zero unless every a_d is even).
-__device__ __forceinline__ double cube_moment(int ax, int ay, int az, double h, double rho)
+// Moments about its centre of the uniform cube of density rho at every level l (half side
+// h = L / 2^(l+1)): rho prod_d int_{-h}^{h} t^(a_d) dt = rho prod_d 2 h^(a_d+1) / (a_d+1),
+// zero unless every a_d is even; and the multinomial factors n!/a! of every component.
+// One thread per (level, component).
+template <int P2>
+__global__ void k_bg_cubetab(const double *__restrict__ frame, const double *__restrict__ rho_p,
+                             double *__restrict__ tab, double *__restrict__ mcoef)
 {
-    auto one = [h](int k) {
-        if (k & 1) return 0.0;
-        double v = 2.0 * h;
-        for (int t = 0; t < k; ++t) v *= h;
-        return v / (double)(k + 1);
-    };
-    return rho * one(ax) * one(ay) * one(az);
+    constexpr int NC2 = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (HOT_MAXLEVEL + 2) * NC2) return;
+    const int l = k / NC2, a = k % NC2;
+    const int e[3] = {hot_midx[a][0], hot_midx[a][1], hot_midx[a][2]};
+    const double h = frame[3] / (double)(2ull << l);
+    double v = *rho_p;
+    double f = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (e[d] & 1) v = 0.0;
+        double t = 2.0 * h;
+        for (int s = 0; s < e[d]; ++s) t *= h;
+        v *= t / (double)(e[d] + 1);
+        for (int s = 2; s <= e[d]; ++s) f *= (double)s;
+    }
+    tab[k] = v;
+    if (l == 0) {
+        double fnn = 1.0;
+        for (int s = 2; s <= e[0] + e[1] + e[2]; ++s) fnn *= (double)s;
+        mcoef[a] = fnn / f;
+    }
 }
 
 // Contrast of every cube and its records: for a cell, its moments about the cube centre
 // minus the uniform cube's (in place, to order P + 2); for an empty octant, minus the
 // uniform cube's.  Q_{P+1}, Q_{P+2} to bg_q; the order-P record (scale: a power of two at
-// least the half-diagonal) to rec + (ncell + q) * reclen.
+// least the half-diagonal) to rec + (ncell + q) * reclen.  The uniform cube's moments come
+// from the per-level table (a cell's level; an empty octant's, its parent's plus one).
 template <int P, class T>
 __global__ void k_bg_records(int64_t ncell, int64_t ncube, const double *__restrict__ cen,
-                             const double *__restrict__ half, const double *__restrict__ rho_p,
-                             double *__restrict__ mom, double *__restrict__ bq, double G, double eps, int reclen,
-                             T *__restrict__ rec)
+                             const double *__restrict__ half, const int32_t *__restrict__ clevel,
+                             const int32_t *__restrict__ eparent, const double *__restrict__ tab,
+                             const double *__restrict__ mcoef, double *__restrict__ mom, double *__restrict__ bq,
+                             double G, double eps, int reclen, T *__restrict__ rec)
 {
     constexpr int P2 = P + 2;
     constexpr int NC2 = (P2 + 1) * (P2 + 2) * (P2 + 3) / 6;
     constexpr int NCP = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int N1 = (P + 1) * (P + 2) * (P + 3) / 6, N2 = (P + 2) * (P + 3) * (P + 4) / 6;  // order p+1 and p+2 start
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= ncube) return;
-    const double rho = *rho_p, h = half[q];
+    const double h = half[q];
+    const int lv = q < ncell ? clevel[q] : clevel[eparent[q - ncell]] + 1;
+    const double *u = tab + (int64_t)lv * NC2;
     double M[NCP];
     double q1 = 0.0, q2 = 0.0;
     double *m = q < ncell ? mom + q * NC2 : nullptr;
-    double fn[P2 + 1];
-    fn[0] = 1.0;
-    for (int t = 1; t <= P2; ++t) fn[t] = fn[t - 1] * (double)t;
+#pragma unroll 4
     for (int a = 0; a < NC2; ++a) {
-        const int ax = hot_midx[a][0], ay = hot_midx[a][1], az = hot_midx[a][2];
-        const double u = cube_moment(ax, ay, az, h, rho);
-        const double v = m ? m[a] - u : -u;
+        const double v = m ? m[a] - u[a] : -u[a];
         if (m) m[a] = v;
-        const int n = ax + ay + az;
         if (a < NCP) M[a] = v;
-        if (n == P + 1) q1 += fn[n] / (fn[ax] * fn[ay] * fn[az]) * v * v;
-        if (n == P + 2) q2 += fn[n] / (fn[ax] * fn[ay] * fn[az]) * v * v;
+        else if (a < N2) q1 += mcoef[a] * v * v;
+        else q2 += mcoef[a] * v * v;
     }
+    static_assert(N1 == NCP, "order p+1 starts after the order-p components");
     bq[2 * q + 0] = sqrt(q1);
     bq[2 * q + 1] = sqrt(q2);
     const double b = 0.5 * sqrt(3.0) * (2.0 * h);
@@ -652,14 +685,15 @@ int bg_records(hot_ctx *c, T *rec)
     const int64_t nc = c->ncell, ncube = nc + c->n_empty;
     HOT_CK(c->bg_mom.ensure((size_t)NC2 * nc, s));
     HOT_CK(c->bg_q.ensure(2 * (size_t)ncube, s));
+    HOT_CK(c->bg_tab.ensure((size_t)(HOT_MAXLEVEL + 2) * NC2 + NC2, s));
     HOT_CK(c->bg_eparent.ensure(c->n_empty + 1, s));
     HOT_CK(c->bg_eoct.ensure(c->n_empty + 1, s));
     HOT_COUNT_LAUNCH();
     k_bg_efill<<<hot_blocks(nc, 128), 128, 0, s>>>(c->child8.p, c->bg_eoff.p, nc, c->bg_cen.p, c->bg_half.p,
                                                    c->bg_eparent.p, c->bg_eoct.p);
     HOT_COUNT_LAUNCH();
-    k_bg_p2m<P2><<<c->nsm * 8, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, nc, c->spos.p, c->smass.p,
-                                                c->bg_cen.p, c->bg_mom.p);
+    k_bg_p2m<P2><<<c->nsm * 16, BGW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, nc, c->spos.p,
+                                                  c->smass.p, c->bg_cen.p, c->bg_mom.p);
     for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
         const int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
         if (n <= 0) continue;
@@ -668,10 +702,13 @@ int bg_records(hot_ctx *c, T *rec)
         k_m2m_level<P2, true><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
                                                             nullptr, c->bg_cen.p, c->bg_mom.p);
     }
+    double *tab = c->bg_tab.p, *mcoef = c->bg_tab.p + (HOT_MAXLEVEL + 2) * NC2;
     HOT_COUNT_LAUNCH();
-    k_bg_records<P, T><<<hot_blocks(ncube, 128), 128, 0, s>>>(nc, ncube, c->bg_cen.p, c->bg_half.p, c->bg_rho.p,
-                                                              c->bg_mom.p, c->bg_q.p, c->prm.G, c->prm.eps,
-                                                              HOT_REC_LEN[P], rec);
+    k_bg_cubetab<P2><<<hot_blocks((HOT_MAXLEVEL + 2) * NC2, 128), 128, 0, s>>>(c->frame.p, c->bg_rho.p, tab, mcoef);
+    HOT_COUNT_LAUNCH();
+    k_bg_records<P, T><<<hot_blocks(ncube, 128), 128, 0, s>>>(nc, ncube, c->bg_cen.p, c->bg_half.p, c->clevel.p,
+                                                              c->bg_eparent.p, tab, mcoef, c->bg_mom.p, c->bg_q.p,
+                                                              c->prm.G, c->prm.eps, HOT_REC_LEN[P], rec);
     return HOT_OK;
 }
 
