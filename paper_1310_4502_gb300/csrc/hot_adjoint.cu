@@ -379,10 +379,68 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                 }
             }
             T gx[2] = {0, 0}, gy[2] = {0, 0}, gz[2] = {0, 0}, gm[2] = {0, 0};
+            // float32 with Plummer smoothing: batches without self or zero-distance pairs take
+            // two sinks per instruction (paired float32 arithmetic) against each of the lane's
+            // sources, the sinks staged pair-interleaved (x0 x1 y0 y1 z0 z1 . . and
+            // ux0 ux1 uy0 uy1 uz0 uz1 v0 v1)
+            constexpr bool PAIRED = sizeof(T) == 4 && SOFT == HOT_SOFT_PLUMMER;
             // the self pair, or a zero separation, can only occur in a batch holding the group
             // whose cell contains this leaf, or when eps = 0: other batches skip the tests
             auto flush = [&](int fill, bool checked) {
                 __syncwarp();
+                if constexpr (PAIRED) {
+                    if (active && !checked) {
+                        const int npair = (fill + 1) >> 1;
+                        const float4 *s2 = reinterpret_cast<const float4 *>(&ss[wi][0][0]);
+                        const float4 *w4 = reinterpret_cast<const float4 *>(&sw[wi][0][0]);
+                        const float2 e22 = make_float2(eps2, eps2), neg1 = make_float2(-1.f, -1.f),
+                                     neg3 = make_float2(-3.f, -3.f);
+                        float2 xq[2][3], gx2[2], gy2[2], gz2[2], gm2[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) xq[q][d] = make_float2(xj[q][d], xj[q][d]);
+                            gx2[q] = gy2[q] = gz2[q] = gm2[q] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll 2
+                        for (int jp = sj; jp < npair; jp += nsplit) {
+                            const float4 a = s2[2 * jp], b = s2[2 * jp + 1], c = w4[2 * jp], d = w4[2 * jp + 1];
+                            const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w), sz = make_float2(b.x, b.y);
+                            const float2 ux = make_float2(c.x, c.y), uy = make_float2(c.z, c.w), uz = make_float2(d.x, d.y);
+                            const float2 vv = make_float2(d.z, d.w);
+                            const float2 nv = __fmul2_rn(vv, neg1);
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                if (!val[q]) continue;
+                                const float2 dx = __ffma2_rn(sx, neg1, xq[q][0]), dy = __ffma2_rn(sy, neg1, xq[q][1]),
+                                             dz = __ffma2_rn(sz, neg1, xq[q][2]);
+                                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22)));
+                                const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                                const float2 ri2 = __fmul2_rn(ri, ri);
+                                const float2 r3 = __fmul2_rn(ri2, ri);
+                                const float2 r5 = __fmul2_rn(r3, ri2);
+                                const float2 du = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
+                                // cd = v r^-3 - 3 r^-5 (d.u)
+                                const float2 cd = __ffma2_rn(vv, r3, __fmul2_rn(__fmul2_rn(r5, du), neg3));
+                                gx2[q] = __ffma2_rn(cd, dx, __ffma2_rn(r3, ux, gx2[q]));
+                                gy2[q] = __ffma2_rn(cd, dy, __ffma2_rn(r3, uy, gy2[q]));
+                                gz2[q] = __ffma2_rn(cd, dz, __ffma2_rn(r3, uz, gz2[q]));
+                                gm2[q] = __ffma2_rn(nv, ri, __ffma2_rn(du, r3, gm2[q]));
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            gx[q] += gx2[q].x + gx2[q].y;
+                            gy[q] += gy2[q].x + gy2[q].y;
+                            gz[q] += gz2[q].x + gz2[q].y;
+                            gm[q] += gm2[q].x + gm2[q].y;
+                        }
+                    }
+                    if (!checked) {
+                        __syncwarp();
+                        return;
+                    }
+                }
                 if (active) {
                     auto sweep = [&](auto ck) {
                         constexpr bool CK = decltype(ck)::value;
@@ -469,9 +527,23 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
                         }
                         const int64_t s = (int64_t)sgb[wi][lo] + (t - sex[wi][lo]);
                         if constexpr (sizeof(T) == 4) {
-                            ss[wi][u][0] = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
-                            ss[wi][u][1] = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
-                            ss[wi][u][2] = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
+                            const float px = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
+                            const float py = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
+                            const float pz = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
+                            if (PAIRED && !checked) {
+                                float *qs = &ss[wi][0][0] + 8 * (u >> 1) + (u & 1);
+                                float *qw = &sw[wi][0][0] + 8 * (u >> 1) + (u & 1);
+                                qs[0] = px;
+                                qs[2] = py;
+                                qs[4] = pz;
+#pragma unroll
+                                for (int d = 0; d < 4; ++d) qw[2 * d] = w[4 * s + d];
+                                sid[wi][u] = (int32_t)s;
+                                continue;
+                            }
+                            ss[wi][u][0] = px;
+                            ss[wi][u][1] = py;
+                            ss[wi][u][2] = pz;
                         } else {
                             ss[wi][u][0] = spos[3 * s + 0] - zx;
                             ss[wi][u][1] = spos[3 * s + 1] - zy;
@@ -480,6 +552,15 @@ __global__ void __launch_bounds__(AW * 32) k_adj_p2p_src(
 #pragma unroll
                         for (int d = 0; d < 4; ++d) sw[wi][u][d] = w[4 * s + d];
                         sid[wi][u] = (int32_t)s;
+                    }
+                    if constexpr (PAIRED) {
+                        if (!checked && (take & 1) && lane == 0) {
+                            // the partner of the last sink: far away, with zero weights (its terms are 0)
+                            float *qs = &ss[wi][0][0] + 8 * (take >> 1) + 1;
+                            float *qw = &sw[wi][0][0] + 8 * (take >> 1) + 1;
+                            qs[0] = qs[2] = qs[4] = 1e17f;
+                            qw[0] = qw[2] = qw[4] = qw[6] = 0.f;
+                        }
                     }
                     flush(take, checked);
                 }

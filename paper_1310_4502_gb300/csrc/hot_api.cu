@@ -351,12 +351,12 @@ void hot_destroy(hot_ctx *c)
     cudaStreamSynchronize(c->st);
     cudaStream_t s = c->st;
     c->part.release(s); c->frame.release(s); c->key.release(s); c->key2.release(s); c->idx.release(s);
-    c->idx2.release(s); c->hist.release(s); c->histoff.release(s); c->scan_tmp.release(s); c->spos.release(s);
+    c->idx2.release(s); c->scan_tmp.release(s); c->spos.release(s);
     c->rs_bhist.release(s); c->rs_goff.release(s); c->rs_ctr.release(s); c->rs_status.release(s);
     c->bg_cen.release(s); c->bg_half.release(s); c->bg_q.release(s); c->bg_mom.release(s); c->bg_rho.release(s);
     c->bg_tab.release(s);
     c->bg_ecnt.release(s); c->bg_eoff.release(s); c->bg_eparent.release(s); c->bg_eoct.release(s);
-    c->bg_tc.release(s); c->cnt_box.release(s); c->off_box.release(s); c->l_box.release(s); c->bg_gS.release(s);
+    c->bg_tc.release(s); c->bg_tcf.release(s); c->cnt_box.release(s); c->off_box.release(s); c->l_box.release(s); c->bg_gS.release(s);
     c->smass.release(s); c->lcp.release(s); c->leaflev.release(s); c->ncell_i.release(s); c->cell_off.release(s);
     c->ckey.release(s); c->clevel.release(s); c->cbegin.release(s); c->ccount.release(s); c->cparent.release(s);
     c->cend.release(s); c->child8.release(s); c->cnchild.release(s); c->level_cells.release(s);
@@ -371,6 +371,7 @@ void hot_destroy(hot_ctx *c)
     c->slice_cnt.release(s); c->slice_off.release(s); c->items.release(s);
     c->cBn.release(s); c->bn_cnt.release(s); c->bn_off.release(s); c->bn_cell.release(s); c->bn_part.release(s);
     c->rcq.release(s);
+    c->rcqf.release(s);
     c->per_D.release(s); c->per_part.release(s); c->per_coef.release(s);
     for (int q = 0; q < HOT_ORDERS; ++q) {
         c->rec32q[q].release(s);

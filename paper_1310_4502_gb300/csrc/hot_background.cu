@@ -19,6 +19,8 @@ __device__ __forceinline__ float hb_atan(float v) { return atanf(v); }
 __device__ __forceinline__ double hb_atan(double v) { return atan(v); }
 __device__ __forceinline__ float hb_sqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double hb_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float hb_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double hb_div(double a, double b) { return a / b; }
 
 #include "hot_box.cuh"
 

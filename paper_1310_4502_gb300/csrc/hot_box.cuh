@@ -14,8 +14,10 @@
 // within a few box sizes (farther boxes are expanded); the including file evaluates it in
 // float64.
 //
-// The including file supplies hb_log, hb_atan and hb_sqrt for T (the device's log, atan and
-// sqrt in CUDA code; std:: versions where the header is compiled for the host).
+// The including file supplies hb_log, hb_atan, hb_sqrt and hb_div for T (the device's log,
+// atan and sqrt in CUDA code, a division of at most a few units in the last place for
+// float32, whose terms then move by about 1e-7 of their size; std:: versions and exact
+// division where the header is compiled for the host).
 #pragma once
 
 // ln(a + r), r = |(a, b, c)|, bc2 = b^2 + c^2; 0 where a + r vanishes
@@ -23,14 +25,14 @@ template <class T>
 __device__ __forceinline__ T hb_log_plus_r(T a, T r, T bc2)
 {
     if (a >= T(0)) return a + r > T(0) ? hb_log(a + r) : T(0);
-    return bc2 > T(0) ? hb_log(bc2 / (r - a)) : T(0);
+    return bc2 > T(0) ? hb_log(hb_div(bc2, r - a)) : T(0);
 }
 
 // atan(v w / (u r)); 0 where u = 0 (its factor u or u^2 then vanishes)
 template <class T>
 __device__ __forceinline__ T hb_atan_term(T u, T v, T w, T r)
 {
-    return u != T(0) ? hb_atan(v * w / (u * r)) : T(0);
+    return u != T(0) ? hb_atan(hb_div(v * w, u * r)) : T(0);
 }
 
 // Adds to (ax, ay, az) the acceleration G rho int (x' - p) / |x' - p|^3 dV and to phi the
@@ -41,6 +43,7 @@ __device__ __forceinline__ void box_field(T px, T py, T pz, const T (&lo)[3], co
                                           T &az, T &phi)
 {
     T sx = T(0), sy = T(0), sz = T(0), sp = T(0);
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int cx = (k >> 2) & 1, cy = (k >> 1) & 1, cz = k & 1;
         const T sgn = ((3 - cx - cy - cz) & 1) ? T(-1) : T(1);  // (-1)^(number of lower limits)

@@ -154,89 +154,6 @@ __device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort of (key, value) pairs by their low bits, 8-bit digits, used to transpose
-// interaction lists (hot_sort_pairs): a histogram launch, a scan and a scatter launch per
-// pass.  Stable: inside a tile the rank of a key is (warp, round, lane) order, i.e. input
-// order.
-// ---------------------------------------------------------------------------
-constexpr int RS_W = 8;          // warps per block
-constexpr int RS_R = 16;         // rounds of 32 keys per warp
-constexpr int RS_TILE = RS_W * RS_R * 32;
-
-__global__ void __launch_bounds__(RS_W * 32) k_rs_hist(const uint64_t *__restrict__ key, int64_t N,
-                                                       int shift, uint32_t *__restrict__ hist,
-                                                       int64_t ntiles)
-{
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int k = threadIdx.x; k < RS_TILE; k += blockDim.x) {
-        int64_t i = base + k;
-        if (i < N) atomicAdd(&h[(unsigned)(key[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(RS_W * 32) k_rs_scatter(
-    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t N, int shift, const uint32_t *__restrict__ histoff,
-    int64_t ntiles)
-{
-    __shared__ uint32_t wcnt[RS_W][256];
-    __shared__ uint32_t goff[256];
-    const int w = threadIdx.x >> 5;
-    const unsigned lane = lane_id();
-    for (int k = lane; k < 256; k += 32) wcnt[w][k] = 0;
-    goff[threadIdx.x] = histoff[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-    __syncwarp();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (RS_R * 32);
-    const unsigned lt = (1u << lane) - 1u;
-    uint64_t kk[RS_R];
-    uint32_t vv[RS_R];
-    uint32_t rk[RS_R];
-#pragma unroll
-    for (int r = 0; r < RS_R; ++r) {
-        int64_t i = base + r * 32 + lane;
-        bool valid = i < N;
-        uint64_t k = valid ? kin[i] : 0ull;
-        uint32_t v = valid ? vin[i] : 0u;
-        unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned rank = __popc(peers & lt);
-        uint32_t b = valid ? wcnt[w][d] : 0u;
-        __syncwarp();
-        if (valid && rank == 0) wcnt[w][d] = b + __popc(peers);
-        __syncwarp();
-        kk[r] = k;
-        vv[r] = v;
-        rk[r] = b + rank;
-    }
-    __syncthreads();
-    {
-        unsigned d = threadIdx.x;
-        uint32_t run = 0;
-        for (int ww = 0; ww < RS_W; ++ww) {
-            uint32_t c = wcnt[ww][d];
-            wcnt[ww][d] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RS_R; ++r) {
-        int64_t i = base + r * 32 + lane;
-        if (i < N) {
-            unsigned d = (unsigned)(kk[r] >> shift) & 255u;
-            uint32_t p = goff[d] + wcnt[w][d] + rk[r];
-            kout[p] = kk[r];
-            vout[p] = vv[r];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // The particle keys' sort: eight LSD passes of 8 bits, one launch each.
 //   * k_keys_hist computes the keys and, in the same pass, the digit histograms of all
 //     eight passes (one per block in shared memory; a warp whose keys share a digit adds
@@ -295,6 +212,35 @@ __global__ void __launch_bounds__(256) k_keys_hist(const double *__restrict__ po
         for (int p = 0; p < 8; ++p) {
             // a warp whose keys share the digit (the high digits of spatially ordered input)
             // adds once; otherwise every lane adds its own
+            const unsigned d = valid ? (unsigned)(k >> (8 * p)) & 255u : 256u;
+            const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, d == d0 || !valid)) {
+                if (lane == 0) atomicAdd(&h[p][d0], (unsigned)__popc(vm));
+            } else if (valid) {
+                atomicAdd(&h[p][d], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) bhist[(int64_t)blockIdx.x * 2048 + k] = h[k >> 8][k & 255];
+}
+
+// The digit histograms of the first npass passes of existing keys (one per block, as in
+// k_keys_hist), for hot_sort_pairs.
+__global__ void __launch_bounds__(256) k_rs_hist_all(const uint64_t *__restrict__ key, int64_t n, int npass,
+                                                     uint32_t *__restrict__ bhist)
+{
+    __shared__ uint32_t h[8][256];
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) h[k >> 8][k & 255] = 0;
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n; w0 += nw * 32) {
+        const int64_t i = w0 + lane;
+        const bool valid = i < n;
+        const uint64_t k = valid ? key[i] : 0ull;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        for (int p = 0; p < npass; ++p) {
             const unsigned d = valid ? (unsigned)(k >> (8 * p)) & 255u : 256u;
             const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
             if (__all_sync(0xffffffffu, d == d0 || !valid)) {
@@ -1008,27 +954,41 @@ extern "C" int hot_key_frame_noalloc(const double *pos, const double *mass, int6
 
 // ---------------------------------------------------------------------------
 // Stable sort of (key, value) pairs by the low `bits` bits of the key (LSD passes of
-// 8 bits); used to transpose interaction lists.  The result is left in keys/vals.
+// 8 bits); used to transpose interaction lists and to order the groups by cost.  The
+// digit histograms of every pass in one launch, then one launch per pass (k_rs_pass).
+// The result is left in keys/vals.
 // ---------------------------------------------------------------------------
 int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, int64_t n, int bits)
 {
     cudaStream_t s = c->st;
     if (n <= 0) return HOT_OK;
-    const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    HOT_CK(c->hist.ensure(256 * (size_t)ntiles + 1, s));
-    HOT_CK(c->histoff.ensure(256 * (size_t)ntiles + 1, s));
-    HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(256 * ntiles + 64), s));
-    const int passes = (bits + 7) / 8;
+    const int passes = (bits + 7) / 8 < 8 ? (bits + 7) / 8 : 8;
+    const int nkb = c->nsm * 4;
+    const int64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+    HOT_CK(c->rs_bhist.ensure(2048 * (size_t)nkb, s));
+    HOT_CK(c->rs_goff.ensure(2048, s));
+    HOT_CK(c->rs_ctr.ensure(8, s));
+    {
+        unsigned long long *old = c->rs_status.p;
+        HOT_CK(c->rs_status.ensure(256 * (size_t)ntiles, s));
+        if (c->rs_status.p != old || c->rs_epoch + 8 >= (1u << 24)) {
+            HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(unsigned long long) * c->rs_status.cap, s));
+            c->rs_epoch = 0;
+        }
+    }
+    HOT_CK(cudaMemsetAsync(c->rs_ctr.p, 0, 8 * sizeof(uint32_t), s));
+    HOT_COUNT_LAUNCH();
+    k_rs_hist_all<<<nkb, 256, 0, s>>>(keys, n, passes, c->rs_bhist.p);
+    HOT_COUNT_LAUNCH();
+    k_rs_goff<<<passes, 256, 0, s>>>(c->rs_bhist.p, nkb, c->rs_goff.p);
+    HOT_CK(cudaFuncSetAttribute(k_rs_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, OS_SMEM));
     uint64_t *ka = keys, *kb = ktmp;
     uint32_t *va = vals, *vb = vtmp;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
         HOT_COUNT_LAUNCH();
-        k_rs_hist<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, n, shift, c->hist.p, ntiles);
-        int r = hot_scan_u32_to_u32(c->hist.p, c->histoff.p, 256 * ntiles, c->scan_tmp.p, s);
-        if (r) return r;
-        HOT_COUNT_LAUNCH();
-        k_rs_scatter<<<(unsigned)ntiles, RS_W * 32, 0, s>>>(ka, va, kb, vb, n, shift, c->histoff.p, ntiles);
+        k_rs_pass<<<(unsigned)ntiles, OS_W * 32, OS_SMEM, s>>>(ka, va, kb, vb, n, 8 * pass, c->rs_goff.p + 256 * pass,
+                                                               c->rs_ctr.p + pass, c->rs_status.p, ++c->rs_epoch,
+                                                               c->d_status);
         uint64_t *tk = ka;
         ka = kb;
         kb = tk;

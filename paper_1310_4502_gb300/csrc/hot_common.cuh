@@ -112,7 +112,6 @@ struct hot_ctx {
     DBuf<double> frame;    // lo[3], L, scale
     DBuf<uint64_t> key, key2;
     DBuf<uint32_t> idx, idx2;
-    DBuf<uint32_t> hist, histoff;
     DBuf<uint64_t> scan_tmp;
     // one-launch-per-pass radix sort of the keys: per-block digit histograms of all eight
     // passes, the passes' global digit offsets, tile counters, and the tiles' published
@@ -157,6 +156,7 @@ struct hot_ctx {
     DBuf<float> rec32q[HOT_ORDERS];    // records of the orders below p (order p: rec32 / rec64)
     DBuf<double> rec64q[HOT_ORDERS];
     DBuf<double> rcq;                  // [ncell][p - q_lo + 1]: acceptance radius of each order
+    DBuf<float> rcqf;                  // the same rounded to float32 (the traversal's pre-test)
     // periodic boundaries: lattice sums D^g psi_far(0) (host copy and device, for the side
     // per_D_L and ws per_D_ws), moment partials and L2P coefficients of the far images
     std::vector<double> per_Dh;
@@ -174,6 +174,7 @@ struct hot_ctx {
     DBuf<uint32_t> bg_ecnt, bg_eoff;
     DBuf<int32_t> bg_eparent, bg_eoct;
     DBuf<TCell> bg_tc;
+    DBuf<TCellF> bg_tcf;
     // per group: the analytic-cube list (cube indices) and the surrounding cube S
     DBuf<uint32_t> cnt_box;
     DBuf<int64_t> off_box;

@@ -351,11 +351,11 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                                          int sj, int nsplit, bool active, T eps2, T Gt, Acc<T> (&acc)[NS])
 {
     constexpr int RL = Cfg<P, T>::RL;
-    // float32 forces with Plummer smoothing: the sources of a batch without self or zero-
-    // distance pairs are evaluated two per instruction (paired float32 arithmetic), from a
-    // staging layout in which one 16-byte load holds the x and y of two sources and the
-    // next their z and masses
-    constexpr bool PAIRED = sizeof(T) == 4 && MODE == 0 && SOFT == HOT_SOFT_PLUMMER;
+    // float32 with Plummer smoothing (forces and the adjoint's tangent): the sources of a
+    // batch without self or zero-distance pairs are evaluated two per instruction (paired
+    // float32 arithmetic), from a staging layout in which one 16-byte load holds the x and y
+    // of two sources and the next their z and masses
+    constexpr bool PAIRED = sizeof(T) == 4 && SOFT == HOT_SOFT_PLUMMER;
     const unsigned lane = lane_id();
     int fill = 0;
     SoftConst<T> kc{};
@@ -443,13 +443,16 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                     const int npair = (fill + 1) >> 1;
                     const float4 *s2 = reinterpret_cast<const float4 *>(&sm.src[0][0]);
                     const float2 e22 = make_float2(eps2, eps2), neg1 = make_float2(-1.f, -1.f);
-                    float2 nx[NS][3], ax2[NS], ay2[NS], az2[NS], ph2[NS];
+                    float2 nx[NS][3], ax2[NS], ay2[NS], az2[NS], ph2[NS], w2[NS][4];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
 #pragma unroll
                         for (int d = 0; d < 3; ++d) nx[s][d] = make_float2(-x[s][d], -x[s][d]);
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) w2[s][d] = make_float2(wt[s][d], wt[s][d]);
                         ax2[s] = ay2[s] = az2[s] = ph2[s] = make_float2(0.f, 0.f);
                     }
+                    const float2 neg3 = make_float2(-3.f, -3.f);
 #pragma unroll 2
                     for (int j = sj; j < npair; j += nsplit) {
                         const float4 a = s2[2 * j], b = s2[2 * j + 1];
@@ -463,10 +466,22 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                             const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
                             const float2 mr = __fmul2_rn(pm, ri);
                             const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
-                            ax2[s] = __ffma2_rn(mr3, dx, ax2[s]);
-                            ay2[s] = __ffma2_rn(mr3, dy, ay2[s]);
-                            az2[s] = __ffma2_rn(mr3, dz, az2[s]);
-                            ph2[s] = __ffma2_rn(mr, neg1, ph2[s]);
+                            if constexpr (MODE == 0) {
+                                ax2[s] = __ffma2_rn(mr3, dx, ax2[s]);
+                                ay2[s] = __ffma2_rn(mr3, dy, ay2[s]);
+                                az2[s] = __ffma2_rn(mr3, dz, az2[s]);
+                                ph2[s] = __ffma2_rn(mr, neg1, ph2[s]);
+                            } else {
+                                // the tangent's pair term (see the scalar form below): ph sums
+                                // m/s^3, (a) sums (v m/s^3 - 3 m (d.u)/s^5) d
+                                const float2 du = __ffma2_rn(dz, w2[s][2], __ffma2_rn(dy, w2[s][1], __fmul2_rn(dx, w2[s][0])));
+                                const float2 k5 = __fmul2_rn(__fmul2_rn(mr3, __fmul2_rn(ri, ri)), du);
+                                const float2 cc = __ffma2_rn(k5, neg3, __fmul2_rn(mr3, w2[s][3]));
+                                ph2[s] = __fadd2_rn(ph2[s], mr3);
+                                ax2[s] = __ffma2_rn(cc, dx, ax2[s]);
+                                ay2[s] = __ffma2_rn(cc, dy, ay2[s]);
+                                az2[s] = __ffma2_rn(cc, dz, az2[s]);
+                            }
                         }
                     }
 #pragma unroll

@@ -123,7 +123,8 @@ __device__ double mac_radius_solve(double b, double B1, double B2, int p, double
 __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
                              const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
                              double G, double tol, double guard, const double *__restrict__ cBn, int q_lo,
-                             double *__restrict__ rcq, TCell *__restrict__ tc, TCellF *__restrict__ tcf)
+                             double *__restrict__ rcq, float *__restrict__ rcqf, TCell *__restrict__ tc,
+                             TCellF *__restrict__ tcf)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -136,6 +137,7 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
         for (int q = q_lo; q <= p; ++q) {
             const double r = mac_radius_solve(b, Bn[q + 1], Bn[q + 2], q, G, tol);
             rcq[(int64_t)nq * c + (q - q_lo)] = r;
+            rcqf[(int64_t)nq * c + (q - q_lo)] = (float)r;
             rc = fmin(rc, r);
         }
     } else {
@@ -177,7 +179,8 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
     const int32_t *__restrict__ child8, const int32_t *__restrict__ cnchild,
     const int32_t *__restrict__ ccount, const double *__restrict__ ccom, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, double guard,
-    const double *__restrict__ cBn, int q_lo, const double *__restrict__ rcq, double per_L, int per_ws,
+    const double *__restrict__ cBn, int q_lo, const double *__restrict__ rcq, const float *__restrict__ rcqf,
+    double per_L, int per_ws,
     int32_t *__restrict__ scratch, int cap, unsigned *__restrict__ work, uint32_t *__restrict__ cnt_m2p,
     uint32_t *__restrict__ cnt_p2p, const int64_t *__restrict__ off_m2p, const int64_t *__restrict__ off_p2p,
     int32_t *__restrict__ l_m2p, int32_t *__restrict__ l_p2p, unsigned long long *__restrict__ stats,
@@ -290,7 +293,27 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                         }
                         }
                         kind = acc ? 1 : (leaf ? 2 : 3);
+                        int qf = -1;  // the order when the float32 test decides it
                         if (cBn && acc) {
+                            // float32 first, on the squared distances as for the acceptance: the
+                            // lowest order whose radius the distance clearly reaches, every lower one
+                            // clearly not; a radius within 1e-5 leaves it to the float64 choice
+                            const int nq = p - q_lo + 1;
+                            for (int q = q_lo; q <= p; ++q) {
+                                const float rq = rcqf[(int64_t)nq * c + (q - q_lo)];
+                                if (!(rq < INFINITY)) continue;
+                                const float th = dmaxf + rq;
+                                const float t2 = th * th;
+                                if (d2f > t2 * 1.00001f) {
+                                    qf = q;
+                                    break;
+                                }
+                                if (!(d2f < t2 * 0.99999f)) break;
+                            }
+                        }
+                        if (qf >= 0) {
+                            ent = (int32_t)((uint32_t)c | ((uint32_t)qf << HOT_ORDER_SHIFT));
+                        } else if (cBn && acc) {
                             // the lowest order whose radius the distance reaches; within 1e-9 of a
                             // radius, that order's bound as stated (d rounded as the oracle does)
                             const TCell t = tcell[c];
@@ -397,8 +420,10 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
 __device__ __forceinline__ double bg_bound(double d, double b, double Q1, double Q2, int p, double G)
 {
     const double q = __dsub_rn(1.0, __ddiv_rn(b, d));
-    const double t1 = __ddiv_rn(__dmul_rn((double)(p + 2), Q1), pow(d, (double)(p + 3)));
-    const double t2 = __ddiv_rn(__dmul_rn((double)(p + 3), Q2), pow(d, (double)(p + 4)));
+    double dp = d;  // d^{p+3} by repeated multiplication
+    for (int i = 0; i < p + 2; ++i) dp = __dmul_rn(dp, d);
+    const double t1 = __ddiv_rn(__dmul_rn((double)(p + 2), Q1), dp);
+    const double t2 = __ddiv_rn(__dmul_rn((double)(p + 3), Q2), __dmul_rn(dp, d));
     return __dmul_rn(__ddiv_rn(G, __dmul_rn(q, q)), __dadd_rn(t1, t2));
 }
 
@@ -462,7 +487,7 @@ __device__ double bg_radius_solve(double b, double Q1, double Q2, int p, double 
 
 __global__ void k_bg_radius(const double *__restrict__ cen, const double *__restrict__ half,
                             const double *__restrict__ bq, int64_t ncube, int p, double G, double tol,
-                            TCell *__restrict__ tc)
+                            TCell *__restrict__ tc, TCellF *__restrict__ tcf)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= ncube) return;
@@ -473,6 +498,35 @@ __global__ void k_bg_radius(const double *__restrict__ cen, const double *__rest
     t.z = cen[3 * q + 2];
     t.rc = bg_radius_solve(b, bq[2 * q], bq[2 * q + 1], p, G, tol);
     tc[q] = t;
+    TCellF f;
+    f.hx = (float)t.x;
+    f.hy = (float)t.y;
+    f.hz = (float)t.z;
+    f.lx = (float)(t.x - (double)f.hx);
+    f.ly = (float)(t.y - (double)f.hy);
+    f.lz = (float)(t.z - (double)f.hz);
+    f.rc = (float)t.rc;
+    f.pad = 0.f;
+    tcf[q] = f;
+}
+
+// The float32 pre-test of a radius test on hi/lo offsets (relative error below 1e-6, as in
+// k_traverse): 1 accept, 0 reject, -1 within 1e-5 of the threshold (take the float64 test).
+struct GroupF {
+    float hx, hy, hz, lx, ly, lz, dmax;
+};
+__device__ __forceinline__ int pretest(const TCellF &f, const GroupF &g)
+{
+    const float ox = (f.hx - g.hx) + (f.lx - g.lx);
+    const float oy = (f.hy - g.hy) + (f.ly - g.ly);
+    const float oz = (f.hz - g.hz) + (f.lz - g.lz);
+    const float d2f = ox * ox + oy * oy + oz * oz;
+    const float thf = g.dmax + f.rc;
+    const float th2f = thf * thf;
+    if (!(f.rc < INFINITY)) return 0;
+    if (d2f > th2f * 1.00001f) return 1;
+    if (d2f < th2f * 0.99999f) return 0;
+    return -1;
 }
 
 // Acceptance of a contrast expansion (cube q) for a group at (gx, gy, gz), Delta_max dmax:
@@ -526,7 +580,8 @@ template <int MODE>
 __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
     int64_t ngroup, int64_t ncell, const int32_t *__restrict__ gcell, const double *__restrict__ gcen,
     const double *__restrict__ gdmax, const int32_t *__restrict__ cparent, const TCell *__restrict__ tcell,
-    const TCell *__restrict__ tbg, const double *__restrict__ bhalf, const double *__restrict__ bq,
+    const TCellF *__restrict__ tcf, const TCell *__restrict__ tbg, const TCellF *__restrict__ tbgf,
+    const double *__restrict__ bhalf, const double *__restrict__ bq,
     const uint32_t *__restrict__ eoff, const int32_t *__restrict__ cend, const int32_t *__restrict__ child8,
     const int32_t *__restrict__ cnchild, const int32_t *__restrict__ ccount, const double *__restrict__ cbmax,
     const double *__restrict__ cB1, const double *__restrict__ cB2, int p, double G, double tol, int up,
@@ -550,6 +605,22 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
         const int32_t gend = cend[gc];
         const double gx = gcen[3 * g + 0], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
         const double dmax = gdmax[g];
+        GroupF gf;
+        gf.hx = (float)gx;
+        gf.hy = (float)gy;
+        gf.hz = (float)gz;
+        gf.lx = (float)(gx - (double)gf.hx);
+        gf.ly = (float)(gy - (double)gf.hy);
+        gf.lz = (float)(gz - (double)gf.hz);
+        gf.dmax = (float)dmax;
+        auto plain_ok = [&](int32_t c) {
+            const int r = pretest(tcf[c], gf);
+            return r >= 0 ? r == 1 : plain_accept(tcell[c], cbmax[c], cB1[c], cB2[c], gx, gy, gz, dmax, p, G, tol);
+        };
+        auto bg_ok = [&](int64_t q) {
+            const int r = pretest(tbgf[q], gf);
+            return r >= 0 ? r == 1 : bg_accept(tbg[q], bhalf[q], bq, q, gx, gy, gz, dmax, p, G, tol);
+        };
         int32_t S = gc;
         for (int k = 0; k < up && S > 0; ++k) S = cparent[S];
         const int32_t Send = cend[S];
@@ -580,14 +651,14 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
                         pp = leaf;
                         open = !leaf;
                     } else if (inS) {
-                        if (plain_accept(tcell[c], cbmax[c], cB1[c], cB2[c], gx, gy, gz, dmax, p, G, tol))
+                        if (plain_ok(c))
                             em = c;
                         else if (leaf)
                             pp = true;
                         else
                             open = true;
                     } else {
-                        if (bg_accept(tbg[c], bhalf[c], bq, c, gx, gy, gz, dmax, p, G, tol)) {
+                        if (bg_ok(c)) {
                             em = (int32_t)(ncell + c);
                         } else if (leaf) {
                             pp = true;
@@ -608,7 +679,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
                     for (int o = 0; o < 8; ++o) {
                         if (child8[8 * (int64_t)c + o] >= 0) continue;
                         const int64_t qb = ncell + e;
-                        if (bg_accept(tbg[qb], bhalf[qb], bq, qb, gx, gy, gz, dmax, p, G, tol))
+                        if (bg_ok(qb))
                             am |= 1u << (e - e0);
                         else
                             ab |= 1u << (e - e0);
@@ -767,6 +838,7 @@ int traverse_bg(hot_ctx *c, double tol)
     HOT_CK(c->tcell.ensure(nc, s));
     HOT_CK(c->tcellf.ensure(nc, s));
     HOT_CK(c->bg_tc.ensure(ncube, s));
+    HOT_CK(c->bg_tcf.ensure(ncube, s));
     HOT_CK(c->gkey.ensure(ng + 1, s));
     HOT_CK(c->gkey2.ensure(ng + 1, s));
     HOT_CK(c->gorder.ensure(ng + 1, s));
@@ -777,18 +849,19 @@ int traverse_bg(hot_ctx *c, double tol)
     unsigned long long *stats = (unsigned long long *)(c->sizes.p + 52);  // 6 counters, 52..57
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(nc, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, nc, c->p_mom,
-                                                      c->prm.G, tol, 0.0, nullptr, c->q_lo, nullptr, c->tcell.p,
-                                                      c->tcellf.p);
+                                                      c->prm.G, tol, 0.0, nullptr, c->q_lo, nullptr, nullptr,
+                                                      c->tcell.p, c->tcellf.p);
     HOT_COUNT_LAUNCH();
     k_bg_radius<<<hot_blocks(ncube, 128), 128, 0, s>>>(c->bg_cen.p, c->bg_half.p, c->bg_q.p, ncube, c->p_mom,
-                                                       c->prm.G, tol, c->bg_tc.p);
+                                                       c->prm.G, tol, c->bg_tc.p, c->bg_tcf.p);
     int64_t host[9];
     for (int attempt = 0;; ++attempt) {
         HOT_CK(c->trav_scratch.ensure((size_t)nwarps * 2 * c->trav_cap, s));
         HOT_CK(cudaMemsetAsync(c->sizes.p + 50, 0, 8 * sizeof(int64_t), s));
         HOT_COUNT_LAUNCH();
         k_traverse_bg<0><<<blocks, TW * 32, 0, s>>>(
-            ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->bg_tc.p, c->bg_half.p, c->bg_q.p,
+            ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->tcellf.p, c->bg_tc.p, c->bg_tcf.p,
+            c->bg_half.p, c->bg_q.p,
             c->bg_eoff.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p, c->cbmax.p, c->cB1.p, c->cB2.p,
             c->p_mom, c->prm.G, tol, c->prm.bg_up, c->trav_scratch.p, c->trav_cap, work, c->cnt_m2p.p,
             c->cnt_p2p.p, c->cnt_box.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->bg_gS.p, stats,
@@ -831,7 +904,8 @@ int traverse_bg(hot_ctx *c, double tol)
     HOT_CK(cudaMemsetAsync(work, 0, sizeof(int64_t), s));
     HOT_COUNT_LAUNCH();
     k_traverse_bg<1><<<blocks, TW * 32, 0, s>>>(
-        ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->bg_tc.p, c->bg_half.p, c->bg_q.p,
+        ng, nc, c->gcell.p, c->gcen.p, c->gdmax.p, c->cparent.p, c->tcell.p, c->tcellf.p, c->bg_tc.p, c->bg_tcf.p,
+            c->bg_half.p, c->bg_q.p,
         c->bg_eoff.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom,
         c->prm.G, tol, c->prm.bg_up, c->trav_scratch.p, c->trav_cap, work, nullptr, nullptr, nullptr, c->off_m2p.p,
         c->off_p2p.p, c->off_box.p, c->l_m2p.p, c->l_p2p.p, c->l_box.p, nullptr, nullptr, nullptr, c->d_status);
@@ -882,11 +956,12 @@ int hot_impl_traverse(hot_ctx *c, double tol)
     if (c->varq) {
         if (c->ncell > (int64_t)HOT_CELL_MASK) return HOT_EINVAL;
         HOT_CK(c->rcq.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
+        HOT_CK(c->rcqf.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
     }
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
                                                             c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p,
-                                                            c->tcell.p, c->tcellf.p);
+                                                            c->rcqf.p, c->tcell.p, c->tcellf.p);
     // One pass into per-group slots when their capacities (the largest counts of the
     // previous traversal plus headroom) fit the budget; otherwise count, scan, fill.
     const int64_t capm = c->slot_capm, capp = c->slot_capp;
@@ -911,13 +986,13 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         if (slots)
             HOT_TRAV_LAUNCH(2,
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->rcqf.p, per_L, c->prm.ws, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, c->slot_m2p.p, c->slot_p2p.p, stats,
                 capm, capp, maxc, slot_over, c->gkey.p, c->d_status);
         else
             HOT_TRAV_LAUNCH(0,
                 ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p,
-                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p,
+                c->ccount.p, c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->rcqf.p, per_L, c->prm.ws, c->trav_scratch.p,
                 c->trav_cap, work, c->cnt_m2p.p, c->cnt_p2p.p, nullptr, nullptr, nullptr, nullptr, stats, 0, 0, maxc,
                 slot_over, c->gkey.p, c->d_status);
         int r = hot_scan_u32_to_i64(c->cnt_m2p.p, c->off_m2p.p, ng, c->scan_tmp.p, s);
@@ -962,7 +1037,7 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         HOT_COUNT_LAUNCH();
         HOT_TRAV_LAUNCH(1,
             ng, c->gcell.p, c->gcen.p, c->gdmax.p, c->tcell.p, c->tcellf.p, c->cend.p, c->child8.p, c->cnchild.p, c->ccount.p,
-            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, per_L, c->prm.ws, c->trav_scratch.p, c->trav_cap,
+            c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->p_mom, c->prm.G, tol, guard, cBn, c->q_lo, c->rcq.p, c->rcqf.p, per_L, c->prm.ws, c->trav_scratch.p, c->trav_cap,
             work, nullptr, nullptr, c->off_m2p.p, c->off_p2p.p, c->l_m2p.p, c->l_p2p.p, stats + 2, 0, 0, maxc,
             slot_over, nullptr, c->d_status);
     }

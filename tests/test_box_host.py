@@ -22,6 +22,7 @@ SHIM = r"""
 template <class T> inline T hb_log(T v) { return std::log(v); }
 template <class T> inline T hb_atan(T v) { return std::atan(v); }
 template <class T> inline T hb_sqrt(T v) { return std::sqrt(v); }
+template <class T> inline T hb_div(T a, T b) { return a / b; }
 #include "hot_box.cuh"
 extern "C" void field(int64_t n, const double *p, const double *lo, const double *hi, double Grho, double *acc,
                       double *pot)
