@@ -397,7 +397,7 @@ def background_leg(wname, dev, stream, flush, K, with_cpu, up=2):
     accs = {}
     for name, kw in (("plain", {}), ("background", {"background": True, "bg_up": up})):
         h = hot.Hot(p=w.p, tol=w.tol, eps=w.eps, precision="mixed", **kw)
-        for _ in range(2):
+        for _ in range(3):
             h.force(P, M, acc)
         tot, st = 0.0, {}
         for _ in range(K):
@@ -759,7 +759,7 @@ def run_ours(args):
         out["sort256"] = build_leg("zeldovich256", dev, stream, flush, min(args.steps, 10))
         out["background128"] = background_leg("zeldovich128", dev, stream, flush, min(args.steps, 10),
                                                rank == 0 and not args.no_cpu)
-        out["background256"] = background_leg("zeldovich256", dev, stream, flush, min(args.steps, 3), False)
+        out["background256"] = background_leg("zeldovich256", dev, stream, flush, min(args.steps, 5), False)
         out["plummer4096_fp64"] = plummer_leg(dev, stream, min(args.steps, 10))
     if not args.no_leapfrog:
         out["leapfrog"] = leapfrog_leg(args.leapfrog_workload, dev, stream)

@@ -166,24 +166,23 @@ __device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
 //     digit the earlier tiles hold by a decoupled look-back over their published counts
 //     (a tile publishes its own counts before it looks back, and tiles are numbered in
 //     the order their blocks start, so every wait ends), reading OS_LB earlier tiles'
-//     words at a time, since hundreds of tiles run at once and a walk one word at a time
-//     would be a chain of that many dependent reads; it then writes its keys in digit
-//     order, so that each digit's run leaves as contiguous stores.
-// A published word is epoch << 40 | flag << 38 | count: flag 1 = this tile's count, 2 =
-// the count of this tile and all before it; a word of another epoch is not yet written.
+//     words at a time: the tiles of a wave start together, so the last inclusive count
+//     a tile finds lies about a wave (hundreds of tiles) behind, and the walk's chain of
+//     dependent reads is that distance over OS_LB; it then writes its keys in digit order,
+//     so that each digit's run leaves as contiguous stores.
+// A published word is flag << 30 | count: flag 1 = this tile's count, 2 = the count of this
+// tile and all before it, 0 = not yet written (every pass has its own words, cleared once
+// per sort).
 // ---------------------------------------------------------------------------
 constexpr int OS_W = 8;                   // warps per block
 constexpr int OS_R = 16;                  // keys per lane
 constexpr int OS_TILE = OS_W * OS_R * 32;  // keys per tile
 constexpr int OS_SMEM = OS_W * 256 * 4 + OS_TILE * 8 + OS_TILE * 4 + 2 * 256 * 4;
-constexpr unsigned long long OS_FLAG_AGG = 1ull, OS_FLAG_INC = 2ull;
+constexpr uint32_t OS_FLAG_AGG = 1u, OS_FLAG_INC = 2u;
 constexpr long OS_POLL_LIMIT = 1l << 20;  // polls of one published word before giving up
-constexpr int OS_LB = 16;                  // earlier tiles' words read together in the look-back
+constexpr int OS_LB = 32;                  // earlier tiles' words read together in the look-back
 
-__device__ __forceinline__ unsigned long long os_pack(uint32_t epoch, unsigned long long flag, uint64_t cnt)
-{
-    return ((unsigned long long)epoch << 40) | (flag << 38) | cnt;
-}
+__device__ __forceinline__ uint32_t os_pack(uint32_t flag, uint32_t cnt) { return (flag << 30) | cnt; }
 
 __global__ void __launch_bounds__(256) k_keys_hist(const double *__restrict__ pos, int64_t N,
                                                    const double *__restrict__ frame, uint64_t *__restrict__ key,
@@ -273,7 +272,7 @@ __global__ void __launch_bounds__(256) k_rs_goff(const uint32_t *__restrict__ bh
 __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t N, int shift, const uint32_t *__restrict__ goff, uint32_t *tile_ctr,
-    unsigned long long *pub, uint32_t epoch, unsigned *status)
+    uint32_t *pub, unsigned *status)
 {
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t *sk = (uint64_t *)os_smem;                                 // [OS_TILE]
@@ -324,22 +323,21 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
         wcnt[ww][d] = tot;
         tot += c;
     }
-    unsigned long long *my = pub + tile * 256 + d;
+    uint32_t *my = pub + tile * 256 + d;
     if (tile == 0) {
-        atomicExch(my, os_pack(epoch, OS_FLAG_INC, tot));
+        atomicExch(my, os_pack(OS_FLAG_INC, tot));
         gbase[d] = goff[d];
     } else {
-        atomicExch(my, os_pack(epoch, OS_FLAG_AGG, tot));
+        atomicExch(my, os_pack(OS_FLAG_AGG, tot));
         uint64_t excl = 0;
         int64_t t = tile - 1;  // the nearest earlier tile not yet added
         long polls = 0;
         bool done = false;
         while (!done) {
             // the words of tiles t, t-1, ..., t-OS_LB+1 (as far as tile 0), read together
-            unsigned long long v[OS_LB];
+            uint32_t v[OS_LB];
 #pragma unroll
-            for (int k = 0; k < OS_LB; ++k)
-                v[k] = t - k >= 0 ? *((volatile unsigned long long *)(pub + (t - k) * 256 + d)) : 0ull;
+            for (int k = 0; k < OS_LB; ++k) v[k] = t - k >= 0 ? *((volatile uint32_t *)(pub + (t - k) * 256 + d)) : 0u;
             // add the words in order up to the first inclusive one, stopping at the first
             // not yet written (unrolled and predicated, so that v stays in registers)
             int k = 0;
@@ -347,12 +345,12 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
 #pragma unroll
             for (int q = 0; q < OS_LB; ++q) {
                 if (!stop && !done) {
-                    if (t - q < 0 || (uint32_t)(v[q] >> 40) != epoch) {
+                    if (t - q < 0 || (v[q] >> 30) == 0u) {
                         stop = true;
                     } else {
-                        excl += v[q] & ((1ull << 38) - 1ull);
+                        excl += v[q] & 0x3fffffffu;
                         k = q + 1;
-                        if (((v[q] >> 38) & 3ull) == OS_FLAG_INC || t - q == 0) done = true;
+                        if ((v[q] >> 30) == OS_FLAG_INC || t - q == 0) done = true;
                     }
                 }
             }
@@ -367,7 +365,7 @@ __global__ void __launch_bounds__(OS_W * 32) k_rs_pass(
             }
             __nanosleep(32);
         }
-        atomicExch(my, os_pack(epoch, OS_FLAG_INC, excl + tot));
+        atomicExch(my, os_pack(OS_FLAG_INC, (uint32_t)(excl + tot)));
         gbase[d] = goff[d] + (uint32_t)excl;
     }
     // tile-local exclusive scan of the digit counts
@@ -730,15 +728,9 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     HOT_CK(c->rs_bhist.ensure(2048 * (size_t)nkb, s));
     HOT_CK(c->rs_goff.ensure(2048, s));
     HOT_CK(c->rs_ctr.ensure(8, s));
-    {
-        unsigned long long *old = c->rs_status.p;
-        HOT_CK(c->rs_status.ensure(256 * (size_t)ntiles, s));
-        if (c->rs_status.p != old || c->rs_epoch + 8 >= (1u << 24)) {
-            // fresh memory, or the epoch counter about to wrap: no word of any epoch
-            HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(unsigned long long) * c->rs_status.cap, s));
-            c->rs_epoch = 0;
-        }
-    }
+    // every pass's published words, cleared once
+    HOT_CK(c->rs_status.ensure(8 * 256 * (size_t)ntiles, s));
+    HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(uint32_t) * 8 * 256 * (size_t)ntiles, s));
     HOT_CK(cudaMemsetAsync(c->rs_ctr.p, 0, 8 * sizeof(uint32_t), s));
     HOT_COUNT_LAUNCH();
     k_keys_hist<<<nkb, 256, 0, s>>>(pos, N, c->frame.p, c->key.p, c->idx.p, c->rs_bhist.p);
@@ -750,7 +742,7 @@ int hot_impl_build(hot_ctx *c, const double *pos, const double *mass, int64_t N)
     for (int pass = 0; pass < 8; ++pass) {
         HOT_COUNT_LAUNCH();
         k_rs_pass<<<(unsigned)ntiles, OS_W * 32, OS_SMEM, s>>>(ka, va, kb, vb, N, 8 * pass, c->rs_goff.p + 256 * pass,
-                                                               c->rs_ctr.p + pass, c->rs_status.p, ++c->rs_epoch,
+                                                               c->rs_ctr.p + pass, c->rs_status.p + (size_t)pass * 256 * ntiles,
                                                                c->d_status);
         uint64_t *tk = ka;
         ka = kb;
@@ -962,20 +954,15 @@ int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, u
 {
     cudaStream_t s = c->st;
     if (n <= 0) return HOT_OK;
+    if (n >= (int64_t)1 << 30) return HOT_EOVERFLOW;  // the published counts hold 30 bits
     const int passes = (bits + 7) / 8 < 8 ? (bits + 7) / 8 : 8;
     const int nkb = c->nsm * 4;
     const int64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
     HOT_CK(c->rs_bhist.ensure(2048 * (size_t)nkb, s));
     HOT_CK(c->rs_goff.ensure(2048, s));
     HOT_CK(c->rs_ctr.ensure(8, s));
-    {
-        unsigned long long *old = c->rs_status.p;
-        HOT_CK(c->rs_status.ensure(256 * (size_t)ntiles, s));
-        if (c->rs_status.p != old || c->rs_epoch + 8 >= (1u << 24)) {
-            HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(unsigned long long) * c->rs_status.cap, s));
-            c->rs_epoch = 0;
-        }
-    }
+    HOT_CK(c->rs_status.ensure((size_t)passes * 256 * (size_t)ntiles, s));
+    HOT_CK(cudaMemsetAsync(c->rs_status.p, 0, sizeof(uint32_t) * passes * 256 * (size_t)ntiles, s));
     HOT_CK(cudaMemsetAsync(c->rs_ctr.p, 0, 8 * sizeof(uint32_t), s));
     HOT_COUNT_LAUNCH();
     k_rs_hist_all<<<nkb, 256, 0, s>>>(keys, n, passes, c->rs_bhist.p);
@@ -987,7 +974,7 @@ int hot_sort_pairs(hot_ctx *c, uint64_t *keys, uint32_t *vals, uint64_t *ktmp, u
     for (int pass = 0; pass < passes; ++pass) {
         HOT_COUNT_LAUNCH();
         k_rs_pass<<<(unsigned)ntiles, OS_W * 32, OS_SMEM, s>>>(ka, va, kb, vb, n, 8 * pass, c->rs_goff.p + 256 * pass,
-                                                               c->rs_ctr.p + pass, c->rs_status.p, ++c->rs_epoch,
+                                                               c->rs_ctr.p + pass, c->rs_status.p + (size_t)pass * 256 * ntiles,
                                                                c->d_status);
         uint64_t *tk = ka;
         ka = kb;

@@ -115,10 +115,9 @@ struct hot_ctx {
     DBuf<uint64_t> scan_tmp;
     // one-launch-per-pass radix sort of the keys: per-block digit histograms of all eight
     // passes, the passes' global digit offsets, tile counters, and the tiles' published
-    // digit counts (epoch-tagged, so that no pass needs them cleared)
+    // digit counts (one array per pass, cleared once per sort)
     DBuf<uint32_t> rs_bhist, rs_goff, rs_ctr;
-    DBuf<unsigned long long> rs_status;
-    uint32_t rs_epoch = 0;
+    DBuf<uint32_t> rs_status;
     DBuf<double> spos, smass;  // sorted copies [N][3], [N]
 
     // tree
