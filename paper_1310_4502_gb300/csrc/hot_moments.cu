@@ -55,7 +55,15 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
         mx = warp_sum(mx);
         my = warp_sum(my);
         mz = warp_sum(mz);
-        const double z[3] = {mx / m, my / m, mz / m};
+        // the centre by one lane (float64 divisions are long sequences on this part)
+        double zl[3] = {0.0, 0.0, 0.0};
+        if (lane == 0) {
+            zl[0] = mx / m;
+            zl[1] = my / m;
+            zl[2] = mz / m;
+        }
+        const double z[3] = {__shfl_sync(0xffffffffu, zl[0], 0), __shfl_sync(0xffffffffu, zl[1], 0),
+                             __shfl_sync(0xffffffffu, zl[2], 0)};
         T acc[(NC + 31) / 32];
 #pragma unroll
         for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = T(0);
@@ -153,6 +161,7 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
     __shared__ unsigned char mi[NC][3];
     __shared__ int32_t sch[M2M_W];
     __shared__ double smc[M2M_W][4];  // child mass and centre
+    __shared__ double spz[4];         // parent mass and centre
     for (int k = threadIdx.x; k < NC; k += blockDim.x) {
         mi[k][0] = hot_midx[k][0];
         mi[k][1] = hot_midx[k][1];
@@ -183,23 +192,32 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
             }
         }
         __syncthreads();
-        // parent mass and centre of mass, children in octant order (every thread)
-        double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+        // parent mass and centre of mass, children in octant order (one thread: the float64
+        // divisions are long sequences on this part, and every thread needs only the result)
+        if (threadIdx.x == 0) {
+            double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
-        for (int q = 0; q < M2M_W; ++q) {
-            if (sch[q] >= 0) {
-                const double mc = smc[q][0];
-                m += mc;
-                mx += mc * smc[q][1];
-                my += mc * smc[q][2];
-                mz += mc * smc[q][3];
+            for (int q = 0; q < M2M_W; ++q) {
+                if (sch[q] >= 0) {
+                    const double mc = smc[q][0];
+                    m += mc;
+                    mx += mc * smc[q][1];
+                    my += mc * smc[q][2];
+                    mz += mc * smc[q][3];
+                }
+            }
+            spz[0] = m;
+            if (CUBE) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) spz[1 + d] = ccom[3 * (int64_t)c + d];
+            } else {
+                spz[1] = mx / m;
+                spz[2] = my / m;
+                spz[3] = mz / m;
             }
         }
-        double z[3] = {mx / m, my / m, mz / m};
-        if (CUBE) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) z[d] = ccom[3 * (int64_t)c + d];
-        }
+        __syncthreads();
+        const double z[3] = {spz[1], spz[2], spz[3]};
         const int32_t k = sch[o];
         if (k >= 0) {
             for (int g = lane; g < 3 * NF; g += 32) {
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
             cmom[(int64_t)c * NC + a] = t;
         }
         if (threadIdx.x == 0 && !CUBE) {
-            cmass[c] = m;
+            cmass[c] = spz[0];
             ccom[3 * (int64_t)c + 0] = z[0];
             ccom[3 * (int64_t)c + 1] = z[1];
             ccom[3 * (int64_t)c + 2] = z[2];
