@@ -287,12 +287,77 @@ def leapfrog_leg(wname, dev, stream, steps=8, dt=1e-3):
     launches = h.sizes()["launches"] - l0
     lib_peak = hot.memory_stats()[1]
     torch_peak = torch.cuda.max_memory_allocated(dev)
+    split = _backward_split(integ, h, gx, gv)
     return {"workload": describe(w) + f"; {steps} KDK steps dt={dt:g}, v0 = 0, tree rebuilt every step; "
             "L = wx.x_S + wv.v_S (w ~ N(0,1)^3, seeds 1, 2)",
             "N": N, "p": w.p, "steps": steps, "fwd_ms": t_fwd, "bwd_ms": t_bwd, "ratio": t_bwd / t_fwd,
+            "bwd_split_ms": split,
+            # the adjoints against the forward's force evaluations (both summed stage times)
+            "adjoint_ratio": split["adjoint"] / split["fwd_forces"] if split["fwd_forces"] > 0 else None,
             "fwd_particle_steps_per_s": N * steps / (t_fwd * 1e-3), "gpu_launches": launches,
             "peak_device_bytes": lib_peak + torch_peak, "peak_library_bytes": lib_peak,
             "peak_torch_bytes": torch_peak}
+
+
+def _backward_split(integ, h, gx, gv):
+    """A second, untimed backward with the library's per-stage CUDA-event times read after
+    every call: the tree rebuilds at the force points (keys + sort, build, moments,
+    traversal), the adjoints, and the rest (kicks, drifts and their adjoints).  Also the
+    forward's kick and drift time, so that the adjoint can be set against the forces."""
+    import time
+    acc = {"rebuild": 0.0, "adjoint": 0.0}
+    orig = {}
+
+    def wrap(name, keys, bucket):
+        f = getattr(h, name)
+        orig[name] = f
+
+        def g(*a, **k):
+            r = f(*a, **k)
+            t = h.stage_times()
+            acc[bucket] += sum(t[x] for x in keys)
+            return r
+        setattr(h, name, g)
+    wrap("build_tree", ("sort", "build"), "rebuild")
+    wrap("compute_moments", ("moments",), "rebuild")
+    wrap("traverse", ("traverse",), "rebuild")
+    wrap("adjoint", ("adjoint",), "adjoint")
+    try:
+        import torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        integ.backward(gx, gv)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3
+        # the forward's forces the same way: its stages against its total
+        fwd = {"forces": 0.0}
+        for name in ("build_tree", "compute_moments", "traverse"):
+            h.__dict__.pop(name, None)
+        ev = h.evaluate_forces
+        keys_all = ("sort", "build", "moments", "traverse", "interact")
+
+        def fwd_force(x, m, a, pot=None):
+            h.build_tree(x, m)
+            h.compute_moments(h.params.p)
+            h.traverse(h.params.tol)
+            ev(a, pot)
+            t = h.stage_times()
+            fwd["forces"] += sum(t[k] for k in keys_all)
+        h.force = fwd_force
+        x0, v0 = integ._ckpt[min(integ._ckpt)]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        integ.forward(x0, v0, integ._mass)
+        torch.cuda.synchronize()
+        fwall = (time.perf_counter() - t1) * 1e3
+    finally:
+        for name in list(orig) + ["force"]:
+            h.__dict__.pop(name, None)
+    return {"rebuild": acc["rebuild"], "adjoint": acc["adjoint"],
+            "other": max(wall - acc["rebuild"] - acc["adjoint"], 0.0),
+            "fwd_forces": fwd["forces"], "fwd_kicks_drifts": max(fwall - fwd["forces"], 0.0),
+            "note": "second pass, the stages' CUDA-event times summed over the calls (host waits between "
+                    "calls inflate 'other' and 'fwd_kicks_drifts')"}
 
 
 # Algorithmic bytes per particle of the keys and sort stage: bounding cube (read position

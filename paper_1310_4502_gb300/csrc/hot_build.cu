@@ -37,6 +37,8 @@ __device__ __forceinline__ double ord_value(unsigned long long k)
 {
     return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 __device__ __forceinline__ bool bits_finite(unsigned long long u)
 {
     return (u & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
@@ -829,30 +831,40 @@ __global__ void k_group_geom(const int32_t *__restrict__ gcell, const uint32_t *
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned lane = lane_id();
+    // min and max on the order-preserving integer images of the coordinates and on the bit
+    // patterns of the non-negative squared distances: exact, and off the float64 pipe
+    auto wmin = [](unsigned long long v) {
+        for (int o = 16; o > 0; o >>= 1) v = umin64(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    };
+    auto wmax = [](unsigned long long v) {
+        for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    };
     for (int64_t g = warp; g < ngroup; g += nw) {
         int32_t c = gcell[g];
         int64_t b = cbegin[c], n = ccount[c];
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
         for (int64_t s = b + lane; s < b + n; s += 32)
             for (int d = 0; d < 3; ++d) {
-                double x = spos[3 * s + d];
-                lo[d] = fmin(lo[d], x);
-                hi[d] = fmax(hi[d], x);
+                const unsigned long long x = ord_image(spos[3 * s + d]);
+                lo[d] = umin64(lo[d], x);
+                hi[d] = umax64(hi[d], x);
             }
         double cen[3];
-        for (int d = 0; d < 3; ++d) cen[d] = __dmul_rn(__dadd_rn(warp_min(lo[d]), warp_max(hi[d])), 0.5);
-        double r2m = 0.0;
+        for (int d = 0; d < 3; ++d) cen[d] = __dmul_rn(__dadd_rn(ord_value(wmin(lo[d])), ord_value(wmax(hi[d]))), 0.5);
+        unsigned long long r2m = 0ull;
         for (int64_t s = b + lane; s < b + n; s += 32) {
             double dx = __dsub_rn(spos[3 * s + 0], cen[0]);
             double dy = __dsub_rn(spos[3 * s + 1], cen[1]);
             double dz = __dsub_rn(spos[3 * s + 2], cen[2]);
             double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            r2m = fmax(r2m, r2);
+            r2m = umax64(r2m, (unsigned long long)__double_as_longlong(r2));
         }
-        r2m = warp_max(r2m);
+        const double r2max = __longlong_as_double((long long)wmax(r2m));
         if (lane == 0) {
             for (int d = 0; d < 3; ++d) gcen[3 * g + d] = cen[d];
-            gdmax[g] = __dsqrt_rn(r2m);
+            gdmax[g] = __dsqrt_rn(r2max);
         }
     }
 }
