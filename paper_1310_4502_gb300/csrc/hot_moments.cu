@@ -335,21 +335,29 @@ __global__ void __launch_bounds__(MW * 32) k_item_part(
     }
 }
 
+// One warp per inner cell: lane l takes items l, l + 32, ... (the root holds N / CHUNK
+// of them), then a butterfly over the lanes (a fixed order: reproducible).
 __global__ void k_item_combine(const uint32_t *__restrict__ off, const int32_t *__restrict__ cnchild,
                                int64_t ncell, const double *__restrict__ part, double *__restrict__ cbmax,
                                double *__restrict__ cB1, double *__restrict__ cB2)
 {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell || cnchild[c] == 0) return;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = lane_id();
+    if (c >= ncell || cnchild[c] == 0) return;  // uniform over the warp
     double bmax = 0.0, B1 = 0.0, B2 = 0.0;
-    for (uint32_t k = off[c]; k < off[c + 1]; ++k) {
+    for (uint32_t k = off[c] + lane; k < off[c + 1]; k += 32) {
         bmax = fmax(bmax, part[3 * (int64_t)k + 0]);
         B1 += part[3 * (int64_t)k + 1];
         B2 += part[3 * (int64_t)k + 2];
     }
-    cbmax[c] = bmax;
-    cB1[c] = B1;
-    cB2[c] = B2;
+    bmax = warp_max(bmax);
+    B1 = warp_sum(B1);
+    B2 = warp_sum(B2);
+    if (lane == 0) {
+        cbmax[c] = bmax;
+        cB1[c] = B1;
+        cB2[c] = B2;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -428,16 +436,19 @@ __global__ void __launch_bounds__(MW * 32) k_bn_part(
     }
 }
 
+// One warp per cell and order: lanes over the items, then a butterfly (a fixed order).
 __global__ void k_bn_combine(const uint32_t *__restrict__ off, int64_t ncell, int nb, const double *__restrict__ part,
                              double *__restrict__ cBn)
 {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    for (int q = 0; q < nb; ++q) {
-        double t = 0.0;
-        for (uint32_t k = off[c]; k < off[c + 1]; ++k) t += part[(int64_t)nb * k + q];
-        cBn[(int64_t)nb * c + q] = t;
-    }
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = lane_id();
+    if (i >= ncell * nb) return;  // uniform over the warp
+    const int64_t c = i / nb;
+    const int q = (int)(i - c * nb);
+    double t = 0.0;
+    for (uint32_t k = off[c] + lane; k < off[c + 1]; k += 32) t += part[(int64_t)nb * k + q];
+    t = warp_sum(t);
+    if (lane == 0) cBn[(int64_t)nb * c + q] = t;
 }
 
 // Records of order q from moments of stride mom_stride (the order-p moments).
@@ -807,7 +818,7 @@ int moments_p(hot_ctx *c)
                                                    c->cbegin.p, c->ccount.p, c->ccom.p, c->spos.p, c->smass.p,
                                                    c->item_part.p);
     HOT_COUNT_LAUNCH();
-    k_item_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
+    k_item_combine<<<hot_blocks(ncell * 32, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
                                                           c->cbmax.p, c->cB1.p, c->cB2.p);
     // records (under background subtraction also those of the cells' contrasts and of the
     // empty octants, after the cells' own)
@@ -859,7 +870,7 @@ int moments_p(hot_ctx *c)
         k_bn_part<P><<<c->nsm * 16, MW * 32, 0, s>>>(c->bn_cell.p, c->bn_off.p, c->bn_off.p + ncell, c->cbegin.p,
                                                      c->ccount.p, c->ccom.p, c->spos.p, c->smass.p, c->bn_part.p);
         HOT_COUNT_LAUNCH();
-        k_bn_combine<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->bn_off.p, ncell, NB, c->bn_part.p, c->cBn.p);
+        k_bn_combine<<<hot_blocks(ncell * NB * 32, 256), 256, 0, s>>>(c->bn_off.p, ncell, NB, c->bn_part.p, c->cBn.p);
         for (int q = c->q_lo; q < P; ++q) {
             if (c->prm.precision == HOT_FP64) {
                 HOT_CK(c->rec64q[q].ensure((size_t)HOT_REC_LEN[q] * ncell, s));

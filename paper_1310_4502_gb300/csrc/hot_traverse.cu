@@ -117,9 +117,27 @@ __device__ double mac_radius_solve(double b, double B1, double B2, int p, double
     return rc;
 }
 
+// Per-interaction order selection: the radius of order q of cell c, one thread per (cell,
+// order) pair (the solves are long float64 sequences: one thread per cell looping over
+// the orders left most of the GPU idle), into rcq[nq c + q - q_lo].
+__global__ void k_mac_radius_orders(const double *__restrict__ cbmax, int64_t ncell, int p, double G, double tol,
+                                    const double *__restrict__ cBn, int q_lo, double *__restrict__ rcq,
+                                    float *__restrict__ rcqf)
+{
+    const int nq = p - q_lo + 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell * nq) return;
+    const int64_t c = i / nq;
+    const int q = q_lo + (int)(i - c * nq);
+    const double *Bn = cBn + (int64_t)(p + 3) * c;
+    const double r = mac_radius_solve(cbmax[c], Bn[q + 1], Bn[q + 2], q, G, tol);
+    rcq[i] = r;
+    rcqf[i] = (float)r;
+}
+
 // With per-interaction order selection (cBn != nullptr: B_n of every cell, n = 0..p+2) the
-// radius of every order q_lo..p goes to rcq and a cell is accepted at the smallest one
-// (some order meets the tolerance).
+// radius of every order q_lo..p is in rcq (k_mac_radius_orders) and a cell is accepted at
+// the smallest one (some order meets the tolerance).
 __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__restrict__ cbmax,
                              const double *__restrict__ cB1, const double *__restrict__ cB2, int64_t ncell, int p,
                              double G, double tol, double guard, const double *__restrict__ cBn, int q_lo,
@@ -131,15 +149,9 @@ __global__ void k_mac_radius(const double *__restrict__ ccom, const double *__re
     const double b = cbmax[c];
     double rc;
     if (cBn) {
-        const double *Bn = cBn + (int64_t)(p + 3) * c;
         const int nq = p - q_lo + 1;
         rc = INFINITY;
-        for (int q = q_lo; q <= p; ++q) {
-            const double r = mac_radius_solve(b, Bn[q + 1], Bn[q + 2], q, G, tol);
-            rcq[(int64_t)nq * c + (q - q_lo)] = r;
-            rcqf[(int64_t)nq * c + (q - q_lo)] = (float)r;
-            rc = fmin(rc, r);
-        }
+        for (int q = q_lo; q <= p; ++q) rc = fmin(rc, rcq[(int64_t)nq * c + (q - q_lo)]);
     } else {
         rc = mac_radius_solve(b, cB1[c], cB2[c], p, G, tol);
     }
@@ -957,6 +969,12 @@ int hot_impl_traverse(hot_ctx *c, double tol)
         if (c->ncell > (int64_t)HOT_CELL_MASK) return HOT_EINVAL;
         HOT_CK(c->rcq.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
         HOT_CK(c->rcqf.ensure((size_t)(c->p_mom - c->q_lo + 1) * c->ncell, s));
+    }
+    if (cBn) {
+        const int64_t nrq = (int64_t)(c->p_mom - c->q_lo + 1) * c->ncell;
+        HOT_COUNT_LAUNCH();
+        k_mac_radius_orders<<<hot_blocks(nrq, 128), 128, 0, s>>>(c->cbmax.p, c->ncell, c->p_mom, c->prm.G, tol, cBn,
+                                                                 c->q_lo, c->rcq.p, c->rcqf.p);
     }
     HOT_COUNT_LAUNCH();
     k_mac_radius<<<hot_blocks(c->ncell, 128), 128, 0, s>>>(c->ccom.p, c->cbmax.p, c->cB1.p, c->cB2.p, c->ncell,
