@@ -72,6 +72,7 @@ __global__ void k_axpy(double *__restrict__ y, const double *__restrict__ x, dou
 
 int hot_sync_status(hot_ctx *c)
 {
+    if (hot_join_moments(c)) return HOT_ECUDA;
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
     unsigned bits = 0;
     if (cudaMemcpy(&bits, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return HOT_ECUDA;
@@ -105,7 +106,10 @@ int hot_create(hot_ctx **out, const hot_params *prm, void *cuda_stream)
     for (int k = 0; k < ST_TIMING_EVENTS; ++k) cudaEventCreate(&c->ev[k]);
     if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_mfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_mcomb, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_mjoin, cudaEventDisableTiming) != cudaSuccess) {
         hot_destroy(c);
         return HOT_ECUDA;
     }
@@ -133,6 +137,7 @@ int hot_set_params(hot_ctx *c, const hot_params *prm)
 int hot_build_tree(hot_ctx *c, const double *pos, const double *mass, int64_t N)
 {
     if (!c || !pos || !mass || N < 1 || N > (int64_t)INT32_MAX / 2) return HOT_EINVAL;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     c->stage = 0;
     return hot_impl_build(c, pos, mass, N);
 }
@@ -141,6 +146,7 @@ int hot_compute_moments(hot_ctx *c, int p)
 {
     if (!c || p < 0 || p > HOT_PMAX || c->prm.p_min > p) return HOT_EINVAL;
     if (c->stage < 1) return HOT_ESTATE;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     c->prm.p = p;
     c->stage = 1;
     return hot_impl_moments(c, p);
@@ -159,6 +165,7 @@ int hot_evaluate_forces(hot_ctx *c, double *acc, double *pot)
 {
     if (!c || !acc) return HOT_EINVAL;
     if (c->stage < 3) return HOT_ESTATE;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     return hot_impl_forces(c, acc, pot);
 }
 
@@ -167,12 +174,14 @@ int hot_adjoint(hot_ctx *c, const double *g_acc, const double *g_pot, double *g_
     if (!c || !g_acc || !g_pos || !g_mass) return HOT_EINVAL;
     if (c->prm.background) return HOT_EINVAL;  // its frozen-list passes carry no contrast or cube terms
     if (c->stage < 3) return HOT_ESTATE;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     return hot_impl_adjoint(c, g_acc, g_pot, g_pos, g_mass);
 }
 
 int hot_stage_times(hot_ctx *c, float ms[6])
 {
     if (!c || !ms) return HOT_EINVAL;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return HOT_ECUDA;
     for (int k = 0; k < 6; ++k) {
         ms[k] = 0.f;
@@ -212,6 +221,7 @@ int hot_sizes(hot_ctx *c, int64_t out[10])
 
 int hot_debug_get(hot_ctx *c, int what, void *dst, size_t bytes)
 {
+    if (c && hot_join_moments(c)) return HOT_ECUDA;
     if (!c || !dst) return HOT_EINVAL;
     const void *src = nullptr;
     size_t need = 0;
@@ -285,6 +295,7 @@ int hot_lookup(hot_ctx *c, const uint64_t *keys, int64_t n, int32_t *idx)
     if (!c || (n > 0 && (!keys || !idx)) || n < 0) return HOT_EINVAL;
     if (c->stage < 1) return HOT_ESTATE;
     if (n == 0) return HOT_OK;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     return hot_impl_lookup(c, keys, n, idx);
 }
 
@@ -292,6 +303,7 @@ int hot_axpy(hot_ctx *c, double *y, const double *x, double alpha, int64_t n)
 {
     if (!c || n < 0 || (n > 0 && (!y || !x))) return HOT_EINVAL;
     if (n == 0) return HOT_OK;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     HOT_COUNT_LAUNCH();
     k_axpy<<<hot_blocks(n, 256, c->nsm * 32), 256, 0, c->st>>>(y, x, alpha, n);
     return cudaGetLastError() == cudaSuccess ? HOT_OK : HOT_ECUDA;
@@ -300,6 +312,7 @@ int hot_axpy(hot_ctx *c, double *y, const double *x, double alpha, int64_t n)
 int hot_fma_peak(hot_ctx *c, int dbl, double *flops)
 {
     if (!c || !flops) return HOT_EINVAL;
+    if (hot_join_moments(c)) return HOT_ECUDA;
     void *buf = nullptr;
     if (cudaMalloc(&buf, 64) != cudaSuccess) return HOT_ENOMEM;
     const int threads = 256, blocks = c->nsm * 8;
@@ -348,6 +361,8 @@ const char *hot_strerror(int code)
 void hot_destroy(hot_ctx *c)
 {
     if (!c) return;
+    if (c->st2) cudaStreamSynchronize(c->st2);  // moment work may still be on it
+    c->mom_pending = false;
     cudaStreamSynchronize(c->st);
     cudaStream_t s = c->st;
     c->part.release(s); c->frame.release(s); c->key.release(s); c->key2.release(s); c->idx.release(s);
@@ -392,6 +407,9 @@ void hot_destroy(hot_ctx *c)
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_mfork) cudaEventDestroy(c->ev_mfork);
+    if (c->ev_mcomb) cudaEventDestroy(c->ev_mcomb);
+    if (c->ev_mjoin) cudaEventDestroy(c->ev_mjoin);
     delete c;
 }
 

@@ -103,6 +103,11 @@ struct hot_ctx {
     // and joined back into st by the two events
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the moment translations and the records run on st2 beside the acceptance aggregates
+    // and the traversal (forked after the centres of mass, the records after the
+    // aggregates); every later use joins them back into st (hot_join_moments)
+    cudaEvent_t ev_mfork = nullptr, ev_mcomb = nullptr, ev_mjoin = nullptr;
+    bool mom_pending = false;
     int dev = 0, nsm = 0;
     int stage = 0;  // 0 created, 1 tree, 2 moments, 3 lists
     int64_t N = 0;
@@ -249,6 +254,13 @@ static inline int hot_blocks(int64_t n, int threads, int cap = 1 << 30)
 
 // Stage timing: start/stop a CUDA-event pair on the context stream.
 static inline void hot_tic(hot_ctx *c, int stage) { cudaEventRecord(c->ev[2 * stage], c->st); }
+// st waits for the moment work left on st2 by the last hot_compute_moments.
+static inline int hot_join_moments(hot_ctx *c)
+{
+    if (!c->mom_pending) return 0;
+    c->mom_pending = false;
+    return cudaStreamWaitEvent(c->st, c->ev_mjoin, 0) == cudaSuccess ? 0 : HOT_ECUDA;
+}
 static inline void hot_toc(hot_ctx *c, int stage)
 {
     cudaEventRecord(c->ev[2 * stage + 1], c->st);

@@ -147,6 +147,36 @@ __device__ __forceinline__ int mom_index(int i, int j, int k)
     return n * (n + 1) * (n + 2) / 6 + (n - i) * (n - i + 1) / 2 + (n - i - j);
 }
 
+// Mass and centre of mass of the inner cells of one level from their children (octant
+// order), one thread per cell: the traversal's chain needs only these, so the moment
+// translations can run beside it.
+__global__ void k_com_level(const int32_t *__restrict__ cells, int64_t n, const int32_t *__restrict__ child8,
+                            const int32_t *__restrict__ cnchild, double *__restrict__ cmass, double *__restrict__ ccom)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t c = cells[q];
+    if (cnchild[c] == 0) return;
+    double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int32_t k = child8[8 * (int64_t)c + o];
+        if (k >= 0) {
+            const double mc = cmass[k];
+            m += mc;
+            mx += mc * ccom[3 * (int64_t)k + 0];
+            my += mc * ccom[3 * (int64_t)k + 1];
+            mz += mc * ccom[3 * (int64_t)k + 2];
+        }
+    }
+    cmass[c] = m;
+    ccom[3 * (int64_t)c + 0] = mx / m;
+    ccom[3 * (int64_t)c + 1] = my / m;
+    ccom[3 * (int64_t)c + 2] = mz / m;
+}
+
+// CUBE = false: the cells' mass and centre are those of k_com_level; CUBE = true (the
+// contrast expansions of background subtraction): about the given cube centres.
 template <int P, bool CUBE = false>
 __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
     const int32_t *__restrict__ cells, int64_t ncells_lvl, const int32_t *__restrict__ child8,
@@ -186,35 +216,16 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
             const int32_t k = child8[8 * (int64_t)c + threadIdx.x];
             sch[threadIdx.x] = k;
             if (k >= 0) {
-                smc[threadIdx.x][0] = CUBE ? 0.0 : cmass[k];
+                smc[threadIdx.x][0] = 0.0;  // (the child's mass: not needed here)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) smc[threadIdx.x][1 + d] = ccom[3 * (int64_t)k + d];
             }
         }
         __syncthreads();
-        // parent mass and centre of mass, children in octant order (one thread: the float64
-        // divisions are long sequences on this part, and every thread needs only the result)
+        // the expansion centre, shared by the block
         if (threadIdx.x == 0) {
-            double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
 #pragma unroll
-            for (int q = 0; q < M2M_W; ++q) {
-                if (sch[q] >= 0) {
-                    const double mc = smc[q][0];
-                    m += mc;
-                    mx += mc * smc[q][1];
-                    my += mc * smc[q][2];
-                    mz += mc * smc[q][3];
-                }
-            }
-            spz[0] = m;
-            if (CUBE) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) spz[1 + d] = ccom[3 * (int64_t)c + d];
-            } else {
-                spz[1] = mx / m;
-                spz[2] = my / m;
-                spz[3] = mz / m;
-            }
+            for (int d = 0; d < 3; ++d) spz[1 + d] = ccom[3 * (int64_t)c + d];
         }
         __syncthreads();
         const double z[3] = {spz[1], spz[2], spz[3]};
@@ -266,12 +277,6 @@ __global__ void __launch_bounds__(M2M_W * 32) k_m2m_level(
             for (int q = 0; q < M2M_W; ++q)
                 if (sch[q] >= 0) t += sb[q][a];
             cmom[(int64_t)c * NC + a] = t;
-        }
-        if (threadIdx.x == 0 && !CUBE) {
-            cmass[c] = spz[0];
-            ccom[3 * (int64_t)c + 0] = z[0];
-            ccom[3 * (int64_t)c + 1] = z[1];
-            ccom[3 * (int64_t)c + 2] = z[2];
         }
     }
 }
@@ -792,25 +797,49 @@ int moments_p(hot_ctx *c)
     for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
         int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
         if (n <= 0) continue;
-        const int blocks = (int)(n < (int64_t)c->nsm * 8 ? n : (int64_t)c->nsm * 8);
         HOT_COUNT_LAUNCH();
-        k_m2m_level<P><<<blocks, M2M_W * 32, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
-                                                     c->cmass.p, c->ccom.p, c->cmom.p);
+        k_com_level<<<hot_blocks(n, 128), 128, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                       c->cmass.p, c->ccom.p);
     }
-    // the expansion's kernel: Plummer-softened, or Newtonian under K1 or spline smoothing
-    // (whose kernels differ from 1/r only inside eps, which accepted cells keep clear of)
-    const double eps_rec = c->prm.softening != HOT_SOFT_PLUMMER ? 0.0 : c->prm.eps;
-    // aggregates of inner cells
+    // the moment translations, and later the records, on the second stream beside the
+    // aggregates (and the traversal that follows), except under background subtraction and
+    // order selection, whose later steps read the moments here
+    const bool fork = !c->prm.background && !(c->prm.p_min >= 0 && c->prm.p_min < P);
+    const int reclen = HOT_REC_LEN[P];
     const int64_t max_items = ncell + N * (c->maxlevel + 1) / CHUNK + 1;
     HOT_CK(c->item_off.ensure(ncell + 1, s));
     HOT_CK(c->item_cell.ensure(max_items, s));
     HOT_CK(c->item_part.ensure(3 * (size_t)max_items, s));
     HOT_CK(c->gflag.ensure(ncell + 1, s));
     HOT_CK(c->scan_tmp.ensure(hot_scan_tmp_elems(ncell + 64), s));
+    if (fork) {
+        if (c->prm.precision == HOT_FP64)
+            HOT_CK(c->rec64.ensure((size_t)reclen * ncell, s));
+        else
+            HOT_CK(c->rec32.ensure((size_t)reclen * ncell, s));
+        HOT_CK(cudaEventRecord(c->ev_mfork, s));
+        HOT_CK(cudaStreamWaitEvent(c->st2, c->ev_mfork, 0));
+    }
+    cudaStream_t ms = fork ? c->st2 : s;
+    for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
+        int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
+        if (n <= 0) continue;
+        const int blocks = (int)(n < (int64_t)c->nsm * 8 ? n : (int64_t)c->nsm * 8);
+        HOT_COUNT_LAUNCH();
+        k_m2m_level<P><<<blocks, M2M_W * 32, 0, ms>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                      c->cmass.p, c->ccom.p, c->cmom.p);
+    }
+    // the expansion's kernel: Plummer-softened, or Newtonian under K1 or spline smoothing
+    // (whose kernels differ from 1/r only inside eps, which accepted cells keep clear of)
+    const double eps_rec = c->prm.softening != HOT_SOFT_PLUMMER ? 0.0 : c->prm.eps;
+    // aggregates of inner cells
     HOT_COUNT_LAUNCH();
     k_item_count<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->ccount.p, c->cnchild.p, ncell, c->gflag.p);
     int r = hot_scan_u32_to_u32(c->gflag.p, c->item_off.p, ncell, c->scan_tmp.p, s);
-    if (r) return r;
+    if (r) {
+        if (fork && cudaEventRecord(c->ev_mjoin, ms) == cudaSuccess) c->mom_pending = true;
+        return r;
+    }
     HOT_COUNT_LAUNCH();
     k_item_cells<<<hot_blocks(ncell, 256), 256, 0, s>>>(c->item_off.p, ncell, c->item_cell.p);
     HOT_COUNT_LAUNCH();
@@ -821,9 +850,12 @@ int moments_p(hot_ctx *c)
     k_item_combine<<<hot_blocks(ncell * 32, 256), 256, 0, s>>>(c->item_off.p, c->cnchild.p, ncell, c->item_part.p,
                                                           c->cbmax.p, c->cB1.p, c->cB2.p);
     // records (under background subtraction also those of the cells' contrasts and of the
-    // empty octants, after the cells' own)
-    const int reclen = HOT_REC_LEN[P];
+    // empty octants, after the cells' own); they need the aggregates' b_max
     c->reclen = reclen;
+    if (fork) {
+        HOT_CK(cudaEventRecord(c->ev_mcomb, s));
+        HOT_CK(cudaStreamWaitEvent(ms, c->ev_mcomb, 0));
+    }
     int64_t nrec = ncell;
     if constexpr (P <= HOT_BG_PMAX) {
         if (c->prm.background) {
@@ -833,15 +865,19 @@ int moments_p(hot_ctx *c)
         }
     }
     if (c->prm.precision == HOT_FP64) {
-        HOT_CK(c->rec64.ensure((size_t)reclen * nrec, s));
+        if (!fork) HOT_CK(c->rec64.ensure((size_t)reclen * nrec, s));
         HOT_COUNT_LAUNCH();
-        k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+        k_records<P, double><<<hot_blocks(ncell, 128), 128, 0, ms>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                     c->prm.G, eps_rec, reclen, NC, c->rec64.p);
     } else {
-        HOT_CK(c->rec32.ensure((size_t)reclen * nrec, s));
+        if (!fork) HOT_CK(c->rec32.ensure((size_t)reclen * nrec, s));
         HOT_COUNT_LAUNCH();
-        k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, s>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
+        k_records<P, float><<<hot_blocks(ncell, 128), 128, 0, ms>>>(c->cmom.p, c->ccom.p, c->cbmax.p, c->clevel.p, ncell, c->frame.p,
                                                                    c->prm.G, eps_rec, reclen, NC, c->rec32.p);
+    }
+    if (fork) {
+        HOT_CK(cudaEventRecord(c->ev_mjoin, ms));
+        c->mom_pending = true;
     }
     if constexpr (P <= HOT_BG_PMAX) {
         if (c->prm.background) {
