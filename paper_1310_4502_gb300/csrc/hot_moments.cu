@@ -19,6 +19,42 @@ constexpr int CHUNK = 2048;  // particles per aggregate work item
 // the mixed mode, which only feeds float32 interaction records and the float64 M2M)
 // and are stored as float64.
 // ---------------------------------------------------------------------------
+// sqrt(x) to about 1e-13 relative, for the powers of the aggregates (b_max itself is the
+// correctly rounded square root of the largest x): the float32 reciprocal square root
+// refined by one Newton step in float64 (r0 = x y, r = r0 + (x - r0^2) y/2, error about
+// the square of y's), three float64 operations where the correctly rounded root takes
+// several times that; outside [1e-36, 1e36] the float64 root.
+__device__ __forceinline__ double near_sqrt(double x)
+{
+    if (!(x >= 1e-36 && x <= 1e36)) return sqrt(x);
+    const float y = rsqrtf((float)x);
+    const double r0 = x * (double)y;
+    return fma(fma(-r0, r0, x), 0.5 * (double)y, r0);
+}
+
+__device__ __forceinline__ unsigned long long dmax_bits(unsigned long long a, double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);  // x >= 0
+    return u > a ? u : a;
+}
+
+// r^(P+1) and r^(P+2) from r and r^2 = |d|^2 by powers of r^2 (three multiplications at
+// p = 4 where repeated multiplication by r took six: the float64 pipe is the bound here)
+template <int P>
+__device__ __forceinline__ void rpow_pair(double r, double r2, double &rp, double &rq)
+{
+    double h = 1.0;  // r2^floor((P+1)/2)
+#pragma unroll
+    for (int q = 0; q < (P + 1) / 2; ++q) h *= r2;
+    if constexpr ((P + 1) % 2 == 0) {
+        rp = h;
+        rq = h * r;
+    } else {
+        rp = h * r;
+        rq = h * r2;
+    }
+}
+
 template <int P, class T>
 __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
     const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
@@ -67,7 +103,8 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
         T acc[(NC + 31) / 32];
 #pragma unroll
         for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = T(0);
-        double bmax = 0.0, B1 = 0.0, B2 = 0.0;
+        double B1 = 0.0, B2 = 0.0;
+        unsigned long long r2max = 0ull;  // bit pattern of the largest |d|^2 (non-negative)
         for (int64_t s0 = b; s0 < b + n; s0 += 32) {
             int64_t s = s0 + lane;
             bool valid = s < b + n;
@@ -75,12 +112,12 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
             if (valid) {
                 ms = smass[s];
                 for (int e = 0; e < 3; ++e) d[e] = spos[3 * s + e] - z[e];
-                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                bmax = fmax(bmax, r);
-                double rp = 1.0;
-                for (int q = 0; q < P + 1; ++q) rp *= r;
+                const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                r2max = dmax_bits(r2max, r2);
+                double rp, rq;
+                rpow_pair<P>(near_sqrt(r2), r2, rp, rq);
                 B1 += ms * rp;
-                B2 += ms * rp * r;
+                B2 += ms * rq;
                 prel[s] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)ms);
             }
             pm[w][lane] = (T)ms;
@@ -107,7 +144,11 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
             }
             __syncwarp();
         }
-        bmax = warp_max(bmax);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, r2max, o);
+            r2max = t > r2max ? t : r2max;
+        }
+        const double bmax = sqrt(__longlong_as_double((long long)r2max));
         B1 = warp_sum(B1);
         B2 = warp_sum(B2);
 #pragma unroll
@@ -173,6 +214,39 @@ __global__ void k_com_level(const int32_t *__restrict__ cells, int64_t n, const 
     ccom[3 * (int64_t)c + 0] = mx / m;
     ccom[3 * (int64_t)c + 1] = my / m;
     ccom[3 * (int64_t)c + 2] = mz / m;
+}
+
+// The same for the levels l1-1 down to l0 in one block (levels of few cells: one launch
+// for several of them), a barrier between levels.
+__global__ void __launch_bounds__(1024) k_com_levels(const int32_t *__restrict__ cells, const int64_t *__restrict__ levoff,
+                                                     int l0, int l1, const int32_t *__restrict__ child8,
+                                                     const int32_t *__restrict__ cnchild, double *__restrict__ cmass,
+                                                     double *__restrict__ ccom)
+{
+    for (int l = l1 - 1; l >= l0; --l) {
+        const int64_t a = levoff[l], n = levoff[l + 1] - a;
+        for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+            const int32_t c = cells[a + q];
+            if (cnchild[c] == 0) continue;
+            double m = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int32_t k = child8[8 * (int64_t)c + o];
+                if (k >= 0) {
+                    const double mc = cmass[k];
+                    m += mc;
+                    mx += mc * ccom[3 * (int64_t)k + 0];
+                    my += mc * ccom[3 * (int64_t)k + 1];
+                    mz += mc * ccom[3 * (int64_t)k + 2];
+                }
+            }
+            cmass[c] = m;
+            ccom[3 * (int64_t)c + 0] = mx / m;
+            ccom[3 * (int64_t)c + 1] = my / m;
+            ccom[3 * (int64_t)c + 2] = mz / m;
+        }
+        __syncthreads();
+    }
 }
 
 // CUBE = false: the cells' mass and centre are those of k_com_level; CUBE = true (the
@@ -317,19 +391,23 @@ __global__ void __launch_bounds__(MW * 32) k_item_part(
         const int64_t e0 = cbegin[c] + (int64_t)ccount[c];
         const int64_t e = b + CHUNK < e0 ? b + CHUNK : e0;
         const double z0 = ccom[3 * (int64_t)c + 0], z1 = ccom[3 * (int64_t)c + 1], z2 = ccom[3 * (int64_t)c + 2];
-        double bmax = 0.0, B1 = 0.0, B2 = 0.0;
+        double B1 = 0.0, B2 = 0.0;
+        unsigned long long r2max = 0ull;  // bit pattern of the largest |d|^2 (non-negative)
         for (int64_t s = b + lane; s < e; s += 32) {
             double dx = spos[3 * s + 0] - z0, dy = spos[3 * s + 1] - z1, dz = spos[3 * s + 2] - z2;
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
-            bmax = fmax(bmax, r);
-            double rp = 1.0;
-#pragma unroll
-            for (int q = 0; q < P + 1; ++q) rp *= r;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            r2max = dmax_bits(r2max, r2);
+            double rp, rq;
+            rpow_pair<P>(near_sqrt(r2), r2, rp, rq);
             double ms = smass[s];
             B1 += ms * rp;
-            B2 += ms * rp * r;
+            B2 += ms * rq;
         }
-        bmax = warp_max(bmax);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, r2max, o);
+            r2max = t > r2max ? t : r2max;
+        }
+        const double bmax = sqrt(__longlong_as_double((long long)r2max));
         B1 = warp_sum(B1);
         B2 = warp_sum(B2);
         if (lane == 0) {
@@ -794,12 +872,28 @@ int moments_p(hot_ctx *c)
         k_p2m_leaf<P, float><<<grid, MW * 32, 0, s>>>(c->cbegin.p, c->ccount.p, c->cnchild.p, ncell, c->spos.p,
                                                       c->smass.p, c->cmass.p, c->ccom.p, c->cmom.p, c->cbmax.p,
                                                       c->cB1.p, c->cB2.p, c->prel.p);
-    for (int l = (int)c->maxlevel - 1; l >= 0; --l) {
-        int64_t a = c->level_off[l], n = c->level_off[l + 1] - a;
-        if (n <= 0) continue;
-        HOT_COUNT_LAUNCH();
-        k_com_level<<<hot_blocks(n, 128), 128, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
-                                                       c->cmass.p, c->ccom.p);
+    {
+        // runs of levels of at most COM_ONE cells in one single-block launch each, larger
+        // levels in a launch of their own
+        constexpr int64_t COM_ONE = 8192;
+        const int64_t *levoff = c->sizes.p + 24;  // the build's level offsets on the device
+        int hi = (int)c->maxlevel;               // the run is levels [l + 1, hi)
+        for (int l = (int)c->maxlevel - 1; l >= -1; --l) {
+            const int64_t n = l >= 0 ? c->level_off[l + 1] - c->level_off[l] : 0;
+            if (l >= 0 && n <= COM_ONE) continue;  // joins the run
+            if (hi > l + 1) {
+                HOT_COUNT_LAUNCH();
+                k_com_levels<<<1, 1024, 0, s>>>(c->level_cells.p, levoff, l + 1, hi, c->child8.p, c->cnchild.p,
+                                                c->cmass.p, c->ccom.p);
+            }
+            if (l >= 0) {
+                const int64_t a = c->level_off[l];
+                HOT_COUNT_LAUNCH();
+                k_com_level<<<hot_blocks(n, 128), 128, 0, s>>>(c->level_cells.p + a, n, c->child8.p, c->cnchild.p,
+                                                               c->cmass.p, c->ccom.p);
+            }
+            hi = l;
+        }
     }
     // the moment translations, and later the records, on the second stream beside the
     // aggregates (and the traversal that follows), except under background subtraction and

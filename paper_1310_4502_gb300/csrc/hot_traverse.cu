@@ -51,10 +51,11 @@ __device__ __forceinline__ void mac_log_newton(double d, double b, double B1, do
 // d0 = (G (p+2) B_{p+1} / tol)^(1/(p+3)) (the leading term of E), by doubling up or
 // halving down from it (one or two evaluations of E on most cells, where doubling up
 // from b_max took log2(r_c / b_max)), then Newton steps in ln d on ln E - ln tol (which
-// is nearly linear in ln d), falling back to bisection whenever a step leaves the
-// bracket, until a step or the bracket is below 1e-13 relative (r_c = 0 when b_max = 0,
-// where E vanishes).  That accuracy is far inside the
-// 1e-9 band in which the traversal re-takes decisions with the bound itself.
+// is nearly linear in ln d; the first ones in float32), falling back to bisection whenever
+// a step leaves the bracket, until a step or the bracket is below 1e-11 relative (r_c = 0
+// when b_max = 0, where E vanishes).  That accuracy moves (d_max + r_c)^2 by at most 2e-11
+// relative, far inside the 1e-9 band in which the traversal re-takes decisions with the
+// bound itself.
 // guard > 0 (K1 smoothing, guard = eps) also requires d >= b_max + guard, so that every
 // source of an accepted cell is at least eps from every sink: r_c = max(r_c, b_max + guard)
 // (guard = 0 leaves r_c, which is above b_max, unchanged).
@@ -91,11 +92,36 @@ __device__ double mac_radius_solve(double b, double B1, double B2, int p, double
         } else {
             const double ltol = log(tol);
             double d = hi;
+            // float32 Newton steps first, on the same function written with rho = B_{p+2} /
+            // B_{p+1} and C = ln G + ln B_{p+1} - ln tol (so that no float32 quantity
+            // under- or overflows): f = C - (p+3) ln d - 2 ln(1 - b/d) + ln((p+2) - (p+1)
+            // rho/d), inside the bracket, until a step is below 1e-6 relative; the float64
+            // steps below then take one or two iterations where they took about six from
+            // the bracket end
+            if (B1 > 0.0) {
+                const float Cf = (float)(log(G) + log(B1) - ltol);
+                const float bf = (float)b, rf = (float)(B2 / B1), lof = (float)lo, hif = (float)hi;
+                const float c1 = (float)(p + 1), c2 = (float)(p + 2), c3 = (float)(p + 3);
+                float x = (float)d;
+                for (int it = 0; it < 12; ++it) {
+                    const float q = 1.f - bf / x;
+                    const float u = c2 - c1 * rf / x;
+                    if (!(q > 0.f) || !(u > 0.f)) break;
+                    const float f = Cf - c3 * logf(x) - 2.f * logf(q) + logf(u);
+                    const float df = -2.f - 2.f * bf / (x - bf) - c1 * c2 * (x - rf) / (c2 * x - c1 * rf);
+                    const float xn = x * expf(-f / df);
+                    if (!(xn > lof && xn < hif)) break;  // left to the float64 steps
+                    const bool done = fabsf(xn - x) <= 1e-6f * x;
+                    x = xn;
+                    if (done) break;
+                }
+                if ((double)x > lo && (double)x < hi) d = (double)x;
+            }
             for (int it = 0; it < 60; ++it) {
                 double f, df;
                 mac_log_newton(d, b, B1, B2, p, G, ltol, f, df);
                 double dn = d * exp(-f / df);
-                if (fabs(dn - d) <= 1e-13 * d) {  // converged (possibly onto a bracket end)
+                if (fabs(dn - d) <= 1e-11 * d) {  // converged (possibly onto a bracket end)
                     d = dn;
                     break;
                 }
@@ -106,7 +132,7 @@ __device__ double mac_radius_solve(double b, double B1, double B2, int p, double
                 else
                     lo = dn;
                 d = dn;
-                if (hi - lo <= 1e-13 * hi) {
+                if (hi - lo <= 1e-11 * hi) {
                     d = hi;
                     break;
                 }
