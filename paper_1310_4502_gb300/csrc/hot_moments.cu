@@ -32,6 +32,39 @@ __device__ __forceinline__ double near_sqrt(double x)
     return fma(fma(-r0, r0, x), 0.5 * (double)y, r0);
 }
 
+// Warp sums of four (two) doubles in six (five) float64 additions per lane instead of
+// twenty (ten): the lanes specialise, each exchange halving the quantities a lane
+// carries, until each group of 8 (16) lanes reduces one; the totals are returned in every
+// lane.  (A float64 addition occupies the pipe for a whole warp instruction however many
+// lanes need it, at a sixty-fourth of the float32 rate.)
+__device__ __forceinline__ void warp_sum4(double &a, double &b, double &c, double &d)
+{
+    const unsigned lane = lane_id();
+    const bool h = lane & 16, q = lane & 8;
+    double k0 = h ? c : a, k1 = h ? d : b;
+    k0 += __shfl_xor_sync(0xffffffffu, h ? a : c, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h ? b : d, 16);
+    double v = q ? k1 : k0;
+    v += __shfl_xor_sync(0xffffffffu, q ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    a = __shfl_sync(0xffffffffu, v, 0);
+    b = __shfl_sync(0xffffffffu, v, 8);
+    c = __shfl_sync(0xffffffffu, v, 16);
+    d = __shfl_sync(0xffffffffu, v, 24);
+}
+__device__ __forceinline__ void warp_sum2(double &a, double &b)
+{
+    const unsigned lane = lane_id();
+    const bool h = lane & 16;
+    double v = h ? b : a;
+    v += __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    a = __shfl_sync(0xffffffffu, v, 0);
+    b = __shfl_sync(0xffffffffu, v, 16);
+}
+
 __device__ __forceinline__ unsigned long long dmax_bits(unsigned long long a, double x)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);  // x >= 0
@@ -87,19 +120,12 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
             my += ms * spos[3 * s + 1];
             mz += ms * spos[3 * s + 2];
         }
-        m = warp_sum(m);
-        mx = warp_sum(mx);
-        my = warp_sum(my);
-        mz = warp_sum(mz);
-        // the centre by one lane (float64 divisions are long sequences on this part)
-        double zl[3] = {0.0, 0.0, 0.0};
-        if (lane == 0) {
-            zl[0] = mx / m;
-            zl[1] = my / m;
-            zl[2] = mz / m;
-        }
-        const double z[3] = {__shfl_sync(0xffffffffu, zl[0], 0), __shfl_sync(0xffffffffu, zl[1], 0),
-                             __shfl_sync(0xffffffffu, zl[2], 0)};
+        warp_sum4(m, mx, my, mz);
+        // the centre's three components by lanes 0, 1, 2 in one division (a float64
+        // division is a long sequence of warp instructions on this part)
+        const double zq = (lane == 1 ? my : (lane == 2 ? mz : mx)) / m;
+        const double z[3] = {__shfl_sync(0xffffffffu, zq, 0), __shfl_sync(0xffffffffu, zq, 1),
+                             __shfl_sync(0xffffffffu, zq, 2)};
         T acc[(NC + 31) / 32];
 #pragma unroll
         for (int q = 0; q < (NC + 31) / 32; ++q) acc[q] = T(0);
@@ -149,8 +175,7 @@ __global__ void __launch_bounds__(MW * 32) k_p2m_leaf(
             r2max = t > r2max ? t : r2max;
         }
         const double bmax = sqrt(__longlong_as_double((long long)r2max));
-        B1 = warp_sum(B1);
-        B2 = warp_sum(B2);
+        warp_sum2(B1, B2);
 #pragma unroll
         for (int q = 0; q < (NC + 31) / 32; ++q) {
             int a = lane + 32 * q;
@@ -408,8 +433,7 @@ __global__ void __launch_bounds__(MW * 32) k_item_part(
             r2max = t > r2max ? t : r2max;
         }
         const double bmax = sqrt(__longlong_as_double((long long)r2max));
-        B1 = warp_sum(B1);
-        B2 = warp_sum(B2);
+        warp_sum2(B1, B2);
         if (lane == 0) {
             part[3 * it + 0] = bmax;
             part[3 * it + 1] = B1;
@@ -875,7 +899,7 @@ int moments_p(hot_ctx *c)
     {
         // runs of levels of at most COM_ONE cells in one single-block launch each, larger
         // levels in a launch of their own
-        constexpr int64_t COM_ONE = 8192;
+        constexpr int64_t COM_ONE = 1024;
         const int64_t *levoff = c->sizes.p + 24;  // the build's level offsets on the device
         int hi = (int)c->maxlevel;               // the run is levels [l + 1, hi)
         for (int l = (int)c->maxlevel - 1; l >= -1; --l) {
