@@ -18,6 +18,18 @@ namespace {
 
 constexpr int TW = 8;  // warps per block
 
+// Ascending 16-bit sort key of a descending cost: the cost's binary exponent and the 11
+// bits below its leading one (monotone, 1/2048 relative resolution: enough to order the
+// work largest first; the sort then needs two passes instead of four).
+__device__ __forceinline__ uint64_t cost_key16(uint64_t cost)
+{
+    if (cost == 0) return 0xffffull;
+    const uint64_t c = cost < 0xffffffffull ? cost : 0xffffffffull;
+    const int e = 63 - __clzll((long long)c);  // 0..31
+    const uint32_t m = e >= 11 ? (uint32_t)(c >> (e - 11)) & 0x7ffu : (uint32_t)(c << (11 - e)) & 0x7ffu;
+    return 0xffffull - (((uint64_t)e << 11) | m);
+}
+
 // Absolute acceleration error bound of one accepted cell at distance d (d > b):
 // E(d) = G/d^2 (1 - b/d)^-2 [(p+2) B_{p+1}/d^{p+1} - (p+1) B_{p+2}/d^{p+2}]
 __device__ __forceinline__ double mac_bound(double d, double b, double B1, double B2, int p, double G)
@@ -440,7 +452,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse(
                 // interaction cost of one 32-sink slice of the group (one M2P evaluation ~ 10
                 // P2P source visits), as an ascending sort key for largest-first processing
                 const uint64_t cost = 10ull * nm + p2p_parts;
-                gkey[g] = 0xffffffffull - (cost < 0xffffffffull ? cost : 0xffffffffull);
+                gkey[g] = cost_key16(cost);
                 if (SLOTS && ((int64_t)nm > capm || (int64_t)np > capp)) atomicOr(slot_over, 1u);
             }
         }
@@ -785,7 +797,7 @@ __global__ void __launch_bounds__(TW * 32) k_traverse_bg(
                 atomicAdd(&stats[4], (unsigned long long)(ns * nemp));
                 atomicAdd(&stats[5], (unsigned long long)parts);
                 const uint64_t cost = 10ull * nm + parts;
-                gkey[g] = 0xffffffffull - (cost < 0xffffffffull ? cost : 0xffffffffull);
+                gkey[g] = cost_key16(cost);
             }
         }
         __syncwarp();
@@ -845,7 +857,7 @@ int work_items(hot_ctx *c)
     const int64_t ng = c->ngroup;
     HOT_COUNT_LAUNCH();
     k_iota<<<hot_blocks(ng, 256), 256, 0, s>>>(c->gorder.p, ng);
-    int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 32);
+    int rs = hot_sort_pairs(c, c->gkey.p, c->gorder.p, c->gkey2.p, c->gorder2.p, ng, 16);
     if (rs) return rs;
     HOT_CK(c->slice_cnt.ensure(ng + 1, s));
     HOT_CK(c->slice_off.ensure(ng + 1, s));
