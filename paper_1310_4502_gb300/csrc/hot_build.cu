@@ -164,10 +164,15 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
 __device__ __forceinline__ uint64_t icoord(double x, double lo, double s)
 {
     const double t = __dmul_rn(__dsub_rn(x, lo), s);  // one subtract, one multiply, no contraction
-    // floor(t) for t >= 0, 0 below: the conversion rounding towards minus infinity, which
-    // saturates negative values to 0
-    const uint64_t c = __double2ull_rd(t);
-    return c > 2097151ull ? 2097151ull : c;
+    // floor(t) for 0 <= t < 2^21 from the bit pattern (the integer part of the significand
+    // shifted by the exponent), 0 below, 2^21 - 1 above: exact, and on the integer pipe
+    // where a rounding conversion would take the float64 one
+    const uint64_t u = (uint64_t)__double_as_longlong(t);
+    if ((int64_t)u <= 0) return 0ull;  // t <= 0 (the sign bit set, or +0)
+    const int e = (int)((u >> 52) & 0x7ffull) - 1023;
+    if (e < 0) return 0ull;
+    if (e >= 21) return 2097151ull;  // also inf and NaN
+    return ((u & 0xfffffffffffffull) | 0x10000000000000ull) >> (52 - e);
 }
 
 // ---------------------------------------------------------------------------
