@@ -34,7 +34,13 @@
  *
  * Synchronisation: hot_build_tree and hot_traverse synchronise the stream once
  * (they need sizes on the host to allocate); the other calls are asynchronous
- * on the stream unless stated.
+ * on the stream unless stated.  The context also owns a second stream: the
+ * adjoint's sink pass and, after hot_compute_moments (without background
+ * subtraction or order selection), the moment translations and the interaction
+ * records run on it beside the work on the caller's stream; every later call
+ * except hot_traverse first makes the caller's stream wait for that work, so
+ * that a synchronisation of the caller's stream after any call other than
+ * hot_compute_moments covers it (hot_synchronize always does).
  */
 #ifndef HOT_H
 #define HOT_H
