@@ -40,7 +40,7 @@
  * records run on it beside the work on the caller's stream; every later call
  * except hot_traverse first makes the caller's stream wait for that work, so
  * that a synchronisation of the caller's stream after any call other than
- * hot_compute_moments covers it (hot_synchronize always does).
+ * hot_compute_moments and hot_traverse covers it (hot_synchronize always does).
  */
 #ifndef HOT_H
 #define HOT_H
