@@ -508,63 +508,69 @@ __global__ void __launch_bounds__(AW * 32, 5) k_adj_p2p_src(
                     gn = ccount[gc];
                     own = L >= gc && L < cend[gc];
                 }
-                const bool checked = __any_sync(0xffffffffu, own) || !(eps2 > T(0));
-                const int incl = warp_incl_scan(gn);
-                const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                sex[wi][lane + 1] = incl;
-                if (lane == 0) sex[wi][0] = 0;
-                sgb[wi][lane] = gb;
-                __syncwarp();
-                for (int t0 = 0; t0 < tot; t0 += PS) {
-                    const int take = tot - t0 < PS ? tot - t0 : PS;
-                    for (int u = lane; u < take; u += 32) {
-                        const int t = t0 + u;
-                        int lo = 0, hi = ne;  // entry with sex[lo] <= t < sex[lo + 1]
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (sex[wi][mid] <= t)
-                                lo = mid;
-                            else
-                                hi = mid;
-                        }
-                        const int64_t s = (int64_t)sgb[wi][lo] + (t - sex[wi][lo]);
-                        if constexpr (sizeof(T) == 4) {
-                            const float px = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
-                            const float py = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
-                            const float pz = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
-                            if (PAIRED && !checked) {
-                                float *qs = &ss[wi][0][0] + 8 * (u >> 1) + (u & 1);
-                                float *qw = &sw[wi][0][0] + 8 * (u >> 1) + (u & 1);
-                                qs[0] = px;
-                                qs[2] = py;
-                                qs[4] = pz;
-#pragma unroll
-                                for (int d = 0; d < 4; ++d) qw[2 * d] = w[4 * s + d];
-                                sid[wi][u] = (int32_t)s;
-                                continue;
+                // a chunk holding a group that contains L is staged in two passes: the other
+                // groups' sinks first, without the per-pair tests, then that group's with them
+                const bool anyown = __any_sync(0xffffffffu, own);
+                for (int pass = anyown ? 0 : 1; pass < 2; ++pass) {
+                    const bool mine = !anyown || (own == (pass == 1));
+                    const bool checked = (anyown && pass == 1) || !(eps2 > T(0));
+                    const int incl = warp_incl_scan(mine ? gn : 0);
+                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                    sex[wi][lane + 1] = incl;
+                    if (lane == 0) sex[wi][0] = 0;
+                    sgb[wi][lane] = gb;
+                    __syncwarp();
+                    for (int t0 = 0; t0 < tot; t0 += PS) {
+                        const int take = tot - t0 < PS ? tot - t0 : PS;
+                        for (int u = lane; u < take; u += 32) {
+                            const int t = t0 + u;
+                            int lo = 0, hi = ne;  // entry with sex[lo] <= t < sex[lo + 1]
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (sex[wi][mid] <= t)
+                                    lo = mid;
+                                else
+                                    hi = mid;
                             }
-                            ss[wi][u][0] = px;
-                            ss[wi][u][1] = py;
-                            ss[wi][u][2] = pz;
-                        } else {
-                            ss[wi][u][0] = spos[3 * s + 0] - zx;
-                            ss[wi][u][1] = spos[3 * s + 1] - zy;
-                            ss[wi][u][2] = spos[3 * s + 2] - zz;
-                        }
+                            const int64_t s = (int64_t)sgb[wi][lo] + (t - sex[wi][lo]);
+                            if constexpr (sizeof(T) == 4) {
+                                const float px = (xhl[8 * s + 0] - zhi[0]) + (xhl[8 * s + 4] - zlo[0]);
+                                const float py = (xhl[8 * s + 1] - zhi[1]) + (xhl[8 * s + 5] - zlo[1]);
+                                const float pz = (xhl[8 * s + 2] - zhi[2]) + (xhl[8 * s + 6] - zlo[2]);
+                                if (PAIRED && !checked) {
+                                    float *qs = &ss[wi][0][0] + 8 * (u >> 1) + (u & 1);
+                                    float *qw = &sw[wi][0][0] + 8 * (u >> 1) + (u & 1);
+                                    qs[0] = px;
+                                    qs[2] = py;
+                                    qs[4] = pz;
 #pragma unroll
-                        for (int d = 0; d < 4; ++d) sw[wi][u][d] = w[4 * s + d];
-                        sid[wi][u] = (int32_t)s;
-                    }
-                    if constexpr (PAIRED) {
-                        if (!checked && (take & 1) && lane == 0) {
-                            // the partner of the last sink: far away, with zero weights (its terms are 0)
-                            float *qs = &ss[wi][0][0] + 8 * (take >> 1) + 1;
-                            float *qw = &sw[wi][0][0] + 8 * (take >> 1) + 1;
-                            qs[0] = qs[2] = qs[4] = 1e17f;
-                            qw[0] = qw[2] = qw[4] = qw[6] = 0.f;
+                                    for (int d = 0; d < 4; ++d) qw[2 * d] = w[4 * s + d];
+                                    sid[wi][u] = (int32_t)s;
+                                    continue;
+                                }
+                                ss[wi][u][0] = px;
+                                ss[wi][u][1] = py;
+                                ss[wi][u][2] = pz;
+                            } else {
+                                ss[wi][u][0] = spos[3 * s + 0] - zx;
+                                ss[wi][u][1] = spos[3 * s + 1] - zy;
+                                ss[wi][u][2] = spos[3 * s + 2] - zz;
+                            }
+#pragma unroll
+                            for (int d = 0; d < 4; ++d) sw[wi][u][d] = w[4 * s + d];
+                            sid[wi][u] = (int32_t)s;
                         }
+                        if constexpr (PAIRED) {
+                            if (!checked && (take & 1) && lane == 0) {
+                                // the partner of the last sink: far away, with zero weights (its terms are 0)
+                                float *qs = &ss[wi][0][0] + 8 * (take >> 1) + 1;
+                                float *qw = &sw[wi][0][0] + 8 * (take >> 1) + 1;
+                                qs[0] = qs[2] = qs[4] = 1e17f;
+                                qw[0] = qw[2] = qw[4] = qw[6] = 0.f;
+                            }
+                        }
+                        flush(take, checked);
                     }
-                    flush(take, checked);
                 }
             }
             if (two) {

@@ -554,63 +554,69 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                 oz = sz;
             }
         }
-        const bool checked = __any_sync(0xffffffffu, own) || !(eps2 > T(0));
-        const int incl = warp_incl_scan(lc);
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        sm.lex[lane + 1] = incl;
-        if (lane == 0) sm.lex[0] = 0;
-        sm.lbeg[lane] = lb;
-        sm.loff[lane][0] = ox;
-        sm.loff[lane][1] = oy;
-        sm.loff[lane][2] = oz;
-        __syncwarp();
-        for (int t0 = 0; t0 < tot; t0 += SRC) {
-            const int take = tot - t0 < SRC ? tot - t0 : SRC;
-            for (int u = lane; u < take; u += 32) {
-                const int t = t0 + u;
-                int lo = 0, hi = ne;  // leaf j with lex[j] <= t < lex[j + 1]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sm.lex[mid] <= t)
-                        lo = mid;
-                    else
-                        hi = mid;
-                }
-                const int32_t lbv = sm.lbeg[lo];
-                const int64_t s = (int64_t)(lbv & ~IMG_LEAF) + (t - sm.lex[lo]);
-                if constexpr (sizeof(T) == 4) {
-                    const float4 v = prel[s];
-                    const float vx = v.x + sm.loff[lo][0], vy = v.y + sm.loff[lo][1], vz = v.z + sm.loff[lo][2];
-                    if (PAIRED && !checked) {
-                        // pair layout: source u in half u & 1 of pair u >> 1
-                        float *q = &sm.src[0][0] + 8 * (u >> 1) + (u & 1);
-                        q[0] = vx;
-                        q[2] = vy;
-                        q[4] = vz;
-                        q[6] = v.w;
-                    } else {
-                        // one 16-byte store per source (scalar stores at a 16-byte lane stride
-                        // would meet four lanes in each bank)
-                        *reinterpret_cast<float4 *>(&sm.src[u][0]) = make_float4(vx, vy, vz, v.w);
+        // A chunk holding some of the group's own leaves is staged in two passes: its other
+        // leaves first, without the per-pair tests, then its own leaves with them.
+        const bool anyown = __any_sync(0xffffffffu, own);
+        for (int pass = anyown ? 0 : 1; pass < 2; ++pass) {
+            const bool mine = !anyown || (own == (pass == 1));
+            const bool checked = (anyown && pass == 1) || !(eps2 > T(0));
+            const int incl = warp_incl_scan(mine ? lc : 0);
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            sm.lex[lane + 1] = incl;
+            if (lane == 0) sm.lex[0] = 0;
+            sm.lbeg[lane] = lb;
+            sm.loff[lane][0] = ox;
+            sm.loff[lane][1] = oy;
+            sm.loff[lane][2] = oz;
+            __syncwarp();
+            for (int t0 = 0; t0 < tot; t0 += SRC) {
+                const int take = tot - t0 < SRC ? tot - t0 : SRC;
+                for (int u = lane; u < take; u += 32) {
+                    const int t = t0 + u;
+                    int lo = 0, hi = ne;  // leaf j with lex[j] <= t < lex[j + 1]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sm.lex[mid] <= t)
+                            lo = mid;
+                        else
+                            hi = mid;
                     }
-                } else {
-                    sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx) + sm.loff[lo][0];
-                    sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy) + sm.loff[lo][1];
-                    sm.src[u][2] = (T)(spos[3 * s + 2] - G.gz) + sm.loff[lo][2];
-                    sm.src[u][3] = (T)smass[s];
+                    const int32_t lbv = sm.lbeg[lo];
+                    const int64_t s = (int64_t)(lbv & ~IMG_LEAF) + (t - sm.lex[lo]);
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 v = prel[s];
+                        const float vx = v.x + sm.loff[lo][0], vy = v.y + sm.loff[lo][1], vz = v.z + sm.loff[lo][2];
+                        if (PAIRED && !checked) {
+                            // pair layout: source u in half u & 1 of pair u >> 1
+                            float *q = &sm.src[0][0] + 8 * (u >> 1) + (u & 1);
+                            q[0] = vx;
+                            q[2] = vy;
+                            q[4] = vz;
+                            q[6] = v.w;
+                        } else {
+                            // one 16-byte store per source (scalar stores at a 16-byte lane stride
+                            // would meet four lanes in each bank)
+                            *reinterpret_cast<float4 *>(&sm.src[u][0]) = make_float4(vx, vy, vz, v.w);
+                        }
+                    } else {
+                        sm.src[u][0] = (T)(spos[3 * s + 0] - G.gx) + sm.loff[lo][0];
+                        sm.src[u][1] = (T)(spos[3 * s + 1] - G.gy) + sm.loff[lo][1];
+                        sm.src[u][2] = (T)(spos[3 * s + 2] - G.gz) + sm.loff[lo][2];
+                        sm.src[u][3] = (T)smass[s];
+                    }
+                    sm.sidx[u] = (lbv & IMG_LEAF) ? -1 : (int32_t)s;
                 }
-                sm.sidx[u] = (lbv & IMG_LEAF) ? -1 : (int32_t)s;
-            }
-            if constexpr (PAIRED) {
-                if (!checked && (take & 1) && lane == 0) {
-                    // the partner of the last source: massless and far away (its pair terms are 0)
-                    float *q = &sm.src[0][0] + 8 * (take >> 1) + 1;
-                    q[0] = q[2] = q[4] = 1e17f;
-                    q[6] = 0.f;
+                if constexpr (PAIRED) {
+                    if (!checked && (take & 1) && lane == 0) {
+                        // the partner of the last source: massless and far away (its pair terms are 0)
+                        float *q = &sm.src[0][0] + 8 * (take >> 1) + 1;
+                        q[0] = q[2] = q[4] = 1e17f;
+                        q[6] = 0.f;
+                    }
                 }
+                fill = take;
+                flush(checked);
             }
-            fill = take;
-            flush(checked);
         }
     }
 }
