@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(AW * 32, 5) k_adj_p2p_src(
                                 const float2 dx = __ffma2_rn(sx, neg1, xq[q][0]), dy = __ffma2_rn(sy, neg1, xq[q][1]),
                                              dz = __ffma2_rn(sz, neg1, xq[q][2]);
                                 const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22)));
-                                const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                                const float2 ri = make_float2(hot_rsqrt(r2.x), hot_rsqrt(r2.y));
                                 const float2 ri2 = __fmul2_rn(ri, ri);
                                 const float2 r3 = __fmul2_rn(ri2, ri);
                                 const float2 r5 = __fmul2_rn(r3, ri2);

@@ -296,7 +296,17 @@ int hot_impl_bg_box(hot_ctx *c, double *acc, double *pot);
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 
-__device__ __forceinline__ float hot_rsqrt(float u) { return rsqrtf(u); }
+// 1/sqrt(u) in float32: the approximate reciprocal square root with subnormal inputs flushed
+// to zero (rsqrt.approx.ftz.f32), one special-function instruction.  Every float32 caller
+// passes |R|^2 + eps^2 of an accepted cell or a source pair (normal numbers, or 0 where the
+// result is masked); a subnormal argument gives +inf here, where the plain approximation
+// gives a value that overflows the same expressions.
+__device__ __forceinline__ float hot_rsqrt(float u)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(u));
+    return r;
+}
 __device__ __forceinline__ double hot_rsqrt(double u) { return rsqrt(u); }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -463,7 +463,7 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
                             const float2 dx = __fadd2_rn(px, nx[s][0]), dy = __fadd2_rn(py, nx[s][1]),
                                          dz = __fadd2_rn(pz, nx[s][2]);
                             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e22)));
-                            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                            const float2 ri = make_float2(hot_rsqrt(r2.x), hot_rsqrt(r2.y));
                             const float2 mr = __fmul2_rn(pm, ri);
                             const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
                             if constexpr (MODE == 0) {
