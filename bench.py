@@ -635,7 +635,7 @@ def run_ours(args):
     fma32 = h.fma_peak(False) / 1e12
     fma64 = h.fma_peak(True) / 1e12
     roof = {"kernel": f"k_interact<p={w.p},float>", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None if periodic else traffic_for(w.p),
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None if periodic else traffic_for(w.p, h.params),
             "peak_note": (f"FP32 non-tensor: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max clock); "
                           f"FMA microbenchmark measured {fma32:.1f} TFLOP/s"),
             "flop_convention": (f"M2P {FLOPS_M2P[w.p]} flop per interaction (the explicit-monomial form of the "
@@ -647,7 +647,7 @@ def run_ours(args):
             "interactions_per_s": (sz["n_m2p_int"] + sz["n_pairs"]) / t_int,
             "m2p_interactions_per_s": sz["n_m2p_int"] / t_int, "p2p_pairs_per_s": sz["n_pairs"] / t_int}
     roof["frac_source_form"] = roof["achieved_source_form"] / peak
-    ex = None if periodic else executed_for(w.p)
+    ex = None if periodic else executed_for(w.p, h.params)
     if ex is not None:
         # FP32 operations the captured launch executed (ncu thread-instruction counters:
         # FFMA 2, FADD 1, FMUL 1, the paired forms twice that), over the live launch time
@@ -860,25 +860,26 @@ def _flops_source_table():
 FLOPS_M2P_SRC = _flops_source_table()
 
 # ncu thread-instruction counts of one interaction-kernel launch on the headline workload,
-# with the hash of the kernel sources they were taken on (reported only while unchanged).
+# keyed by order, leaf and group sizes and the hash of the kernel sources they were taken
+# on (reported only while all four are unchanged).
 # One-pass capture of "python bench.py --steps 1 --warmup 1 --no-cpu --no-extras
 # --no-leapfrog" (clustered 2^20, p = 4), the timed step's force launch (10.75 ms under ncu).
-EXECUTED = {(4, "917a1f71b064e37d"): {
+EXECUTED = {(4, 64, 128, "917a1f71b064e37d"): {
     "ffma": 143868950010, "fadd": 5998156861, "fmul": 12836251388,
     "ffma2": 13811025053, "fadd2": 5919010737, "fmul2": 5919010737, "mufu": 199434968,
     "source": "ncu sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2}_pred_on.sum, "
               "sm__inst_executed_pipe_xu.sum; profiles/k_interact_clustered20_p4.md"}}
 
 
-def executed_for(p):
-    return EXECUTED.get((p, _kernel_hash()))
+def executed_for(p, prm):
+    return EXECUTED.get((p, prm.leaf_max, prm.group_max, _kernel_hash()))
 
 # ncu-measured DRAM traffic of the interaction kernel, per launch, on the workload above,
-# with the source hash it was taken on; reported only while the kernel is unchanged.
-# (p, hash): dram__bytes_read.sum + dram__bytes_write.sum of the timed step's force
+# with the tree sizes and source hash it was taken on; reported only while they are unchanged.
+# (p, leaf_max, group_max, hash): dram__bytes_read.sum + dram__bytes_write.sum of the timed step's force
 # launch, one-pass capture of "python bench.py --steps 1 --warmup 1 --no-cpu --no-extras
 # --no-leapfrog" (clustered 2^20, p = 4): 293.69 MB read + 52.45 MB written.
-TRAFFIC = {(4, "917a1f71b064e37d"): 346.14e6}
+TRAFFIC = {(4, 64, 128, "917a1f71b064e37d"): 346.14e6}
 
 
 def _kernel_hash():
@@ -889,8 +890,8 @@ def _kernel_hash():
     return hsh.hexdigest()[:16]
 
 
-def traffic_for(p):
-    t = TRAFFIC.get((p, _kernel_hash()))
+def traffic_for(p, prm):
+    t = TRAFFIC.get((p, prm.leaf_max, prm.group_max, _kernel_hash()))
     return t
 
 
