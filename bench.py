@@ -863,10 +863,10 @@ FLOPS_M2P_SRC = _flops_source_table()
 # keyed by order, leaf and group sizes and the hash of the kernel sources they were taken
 # on (reported only while all four are unchanged).
 # One-pass capture of "python bench.py --steps 1 --warmup 1 --no-cpu --no-extras
-# --no-leapfrog" (clustered 2^20, p = 4), the timed step's force launch (10.75 ms under ncu).
-EXECUTED = {(4, 64, 128, "917a1f71b064e37d"): {
-    "ffma": 143868950010, "fadd": 5998156861, "fmul": 12836251388,
-    "ffma2": 13811025053, "fadd2": 5919010737, "fmul2": 5919010737, "mufu": 199434968,
+# --no-leapfrog" (clustered 2^20, p = 4), the timed step's force launch (10.66 ms under ncu).
+EXECUTED = {(4, 64, 128, "7cbd088b06ae525a"): {
+    "ffma": 143868950010, "fadd": 3004987677, "fmul": 12836251388,
+    "ffma2": 13811025053, "fadd2": 7415595329, "fmul2": 5919010737, "mufu": 199434968,
     "source": "ncu sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2}_pred_on.sum, "
               "sm__inst_executed_pipe_xu.sum; profiles/k_interact_clustered20_p4.md"}}
 
@@ -878,8 +878,8 @@ def executed_for(p, prm):
 # with the tree sizes and source hash it was taken on; reported only while they are unchanged.
 # (p, leaf_max, group_max, hash): dram__bytes_read.sum + dram__bytes_write.sum of the timed step's force
 # launch, one-pass capture of "python bench.py --steps 1 --warmup 1 --no-cpu --no-extras
-# --no-leapfrog" (clustered 2^20, p = 4): 293.69 MB read + 52.45 MB written.
-TRAFFIC = {(4, 64, 128, "917a1f71b064e37d"): 346.14e6}
+# --no-leapfrog" (clustered 2^20, p = 4): 293.78 MB read + 52.71 MB written.
+TRAFFIC = {(4, 64, 128, "7cbd088b06ae525a"): 346.48e6}
 
 
 def _kernel_hash():

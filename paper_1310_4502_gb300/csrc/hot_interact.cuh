@@ -162,6 +162,34 @@ struct Acc {
     __device__ __forceinline__ double get(int d) const { return (double)s[d] - (double)c[d]; }
 };
 
+// float32: the running sums and their compensations in pairs, (a_x, a_y) and (a_z, phi), so
+// that each step of the compensated sum is one paired instruction for two components; the
+// same round-to-nearest operations as kahan_add, a difference x - y taken as x + (-y)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+template <>
+struct Acc<float> {
+    float2 s01, s23, c01, c23;
+    __device__ __forceinline__ void zero() { s01 = s23 = c01 = c23 = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ static void kahan2(float2 &s, float2 &c, float2 v)
+    {
+        const float2 y = __fadd2_rn(v, neg2(c));
+        const float2 t = __fadd2_rn(s, y);
+        c = __fadd2_rn(__fadd2_rn(t, neg2(s)), neg2(y));
+        s = t;
+    }
+    __device__ __forceinline__ void add(float ax, float ay, float az, float ph)
+    {
+        kahan2(s01, c01, make_float2(ax, ay));
+        kahan2(s23, c23, make_float2(az, ph));
+    }
+    __device__ __forceinline__ double get(int d) const
+    {
+        const float sv = d == 0 ? s01.x : d == 1 ? s01.y : d == 2 ? s23.x : s23.y;
+        const float cv = d == 0 ? c01.x : d == 1 ? c01.y : d == 2 ? c23.x : c23.y;
+        return (double)sv - (double)cv;
+    }
+};
+
 template <class T>
 struct Group {
     int64_t gb;      // first sorted slot of the group's sinks
@@ -569,11 +597,13 @@ __device__ __forceinline__ void p2p_list(Smem<P, T> &sm, const Group<T> &G, cons
             sm.loff[lane][1] = oy;
             sm.loff[lane][2] = oz;
             __syncwarp();
+            // a lane's sources t only grow, so each search starts from the leaf of its last one
+            int lo = 0;
             for (int t0 = 0; t0 < tot; t0 += SRC) {
                 const int take = tot - t0 < SRC ? tot - t0 : SRC;
                 for (int u = lane; u < take; u += 32) {
                     const int t = t0 + u;
-                    int lo = 0, hi = ne;  // leaf j with lex[j] <= t < lex[j + 1]
+                    int hi = ne;  // leaf j with lex[j] <= t < lex[j + 1]
                     while (hi - lo > 1) {
                         const int mid = (lo + hi) >> 1;
                         if (sm.lex[mid] <= t)
